@@ -1,0 +1,326 @@
+"""CPU oracle for CAPS (arXiv 2308.15014) -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``caps_oracle.c`` (plain C,
+compiled by ``oracle/build.py``) with numpy marshalling and adds the recall
+metric of the paper's appendix ("Metric").  It shares nothing with the CUDA
+library and never calls it.
+
+Function map (paper passage -> function):
+  Def. 1 query filter ............... filter_dense, filter_sparse
+  distances (fp32 fixed order, fp64) dist32, dist64
+  Alg. 1 first level (k-means) ...... kmeans, assign, centroid_update
+  Alg. 1 second level (AFT) ......... aft
+  contiguous sub-partition layout ... layout
+  Alg. 2 top-m probe ................ probe
+  Alg. 2 sub-partition selection .... select
+  Alg. 2 full query ................. search
+  Def. 2 / appendix ground truth .... bruteforce
+  appendix RecallK@K ................ recall
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+from .build import build_oracle
+
+L2, IP = 0, 1
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ct.CDLL(build_oracle())
+        P = ct.c_void_p
+        i64, i32 = ct.c_int64, ct.c_int
+        _lib.orc_filter_dense.argtypes = [P, P, i32]
+        _lib.orc_filter_sparse.argtypes = [P, i64, P, i64]
+        _lib.orc_dist32.argtypes = [P, P, i32, i32]
+        _lib.orc_dist32.restype = ct.c_float
+        _lib.orc_dist64.argtypes = [P, P, i32, i32]
+        _lib.orc_dist64.restype = ct.c_double
+        _lib.orc_assign.argtypes = [P, i64, i32, P, i32, i32, P]
+        _lib.orc_centroid_update.argtypes = [P, i64, i32, P, i32, i32, P]
+        _lib.orc_kmeans.argtypes = [P, i64, i32, i32, i32, P, i32, P, P]
+        _lib.orc_aft.argtypes = [P, i64, i32, i32, i32, P, P, P, P, ct.c_int32, P, P]
+        _lib.orc_layout.argtypes = [P, P, i64, i32, i32, P, P]
+        _lib.orc_probe.argtypes = [P, i64, i32, P, i32, i32, i32, P]
+        _lib.orc_select.argtypes = [P, i32, i32, P, ct.c_int32, P, i64, i32, P, P, P, P]
+        _lib.orc_search.argtypes = [P, i64, i32, i32, P, P, P, P, ct.c_int32, P, i32, i32,
+                                    P, i32, P, P, P, i64, P, P, P, i32, i32, P, P, P, P]
+        _lib.orc_bruteforce.argtypes = [P, i64, i32, i32, P, P, P, P, ct.c_int32, P, i64,
+                                        P, P, P, i32, i32, i32, P, P, P, P]
+        _lib.orc_set_threads.argtypes = [i32]
+        _lib.orc_set_threads.restype = i32
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def _c(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def set_threads(n: int = 0) -> int:
+    """Set the OpenMP thread count (0 keeps it); returns the count in use."""
+    return lib().orc_set_threads(int(n))
+
+
+@dataclasses.dataclass
+class Attrs:
+    """Data attributes: dense ``A [N,L]`` + ``vocab [L]``, or sparse CSR."""
+    A: Optional[np.ndarray] = None
+    vocab: Optional[np.ndarray] = None
+    sp_off: Optional[np.ndarray] = None
+    sp_lab: Optional[np.ndarray] = None
+    sp_vocab: int = 0
+
+    def __post_init__(self):
+        self.A = _c(self.A, np.int32)
+        self.vocab = _c(self.vocab, np.int32)
+        self.sp_off = _c(self.sp_off, np.int64)
+        self.sp_lab = _c(self.sp_lab, np.int32)
+
+    @property
+    def L(self) -> int:
+        return 0 if self.A is None else int(self.A.shape[1])
+
+    def args(self):
+        return (self.L, _p(self.A), _p(self.vocab), _p(self.sp_off), _p(self.sp_lab),
+                int(self.sp_vocab))
+
+    @staticmethod
+    def of(w) -> "Attrs":
+        if w.A is not None:
+            return Attrs(A=w.A, vocab=w.vocab)
+        return Attrs(sp_off=w.sp_off, sp_lab=w.sp_lab, sp_vocab=w.sp_vocab)
+
+
+@dataclasses.dataclass
+class Cons:
+    """Query constraints: dense ``Qb [nq,L]`` (-1 = unconstrained) or sparse CSR."""
+    Qb: Optional[np.ndarray] = None
+    q_off: Optional[np.ndarray] = None
+    q_lab: Optional[np.ndarray] = None
+
+    def __post_init__(self):
+        self.Qb = _c(self.Qb, np.int32)
+        self.q_off = _c(self.q_off, np.int64)
+        self.q_lab = _c(self.q_lab, np.int32)
+
+    def args(self):
+        return (_p(self.Qb), _p(self.q_off), _p(self.q_lab))
+
+    @staticmethod
+    def of(w) -> "Cons":
+        if w.Qb is not None:
+            return Cons(Qb=w.Qb)
+        return Cons(q_off=w.q_off, q_lab=w.q_lab)
+
+    def subset(self, idx) -> "Cons":
+        idx = np.asarray(idx)
+        if self.Qb is not None:
+            return Cons(Qb=self.Qb[idx])
+        rows = [self.q_lab[self.q_off[i]:self.q_off[i + 1]] for i in idx]
+        off = np.zeros(len(rows) + 1, dtype=np.int64)
+        off[1:] = np.cumsum([len(r) for r in rows])
+        lab = np.concatenate(rows) if rows else np.zeros(0, np.int32)
+        return Cons(q_off=off, q_lab=lab)
+
+
+# ---- Def. 1 ---------------------------------------------------------------
+
+def filter_dense(a, b) -> bool:
+    a = _c(a, np.int32)
+    b = _c(b, np.int32)
+    return bool(lib().orc_filter_dense(_p(a), _p(b), len(a)))
+
+
+def filter_sparse(a, b) -> bool:
+    a = _c(a, np.int32)
+    b = _c(b, np.int32)
+    return bool(lib().orc_filter_sparse(_p(a), len(a), _p(b), len(b)))
+
+
+# ---- distances ------------------------------------------------------------
+
+def dist32(x, q, metric=L2) -> float:
+    x = _c(x, np.float32)
+    q = _c(q, np.float32)
+    return float(lib().orc_dist32(_p(x), _p(q), len(x), metric))
+
+
+def dist64(x, q, metric=L2) -> float:
+    x = _c(x, np.float32)
+    q = _c(q, np.float32)
+    return float(lib().orc_dist64(_p(x), _p(q), len(x), metric))
+
+
+# ---- Alg. 1 ---------------------------------------------------------------
+
+def assign(X, C, metric=L2) -> np.ndarray:
+    X = _c(X, np.float32)
+    C = _c(C, np.float32)
+    out = np.empty(X.shape[0], dtype=np.int32)
+    lib().orc_assign(_p(X), X.shape[0], X.shape[1], _p(C), C.shape[0], metric, _p(out))
+    return out
+
+
+def centroid_update(X, bin, C, metric=L2) -> np.ndarray:
+    X = _c(X, np.float32)
+    bin = _c(bin, np.int32)
+    C = np.array(C, dtype=np.float32, copy=True, order="C")
+    lib().orc_centroid_update(_p(X), X.shape[0], X.shape[1], _p(bin), C.shape[0],
+                              metric, _p(C))
+    return C
+
+
+def kmeans(X, B, iters, init_idx, metric=L2):
+    X = _c(X, np.float32)
+    init_idx = _c(init_idx, np.int64)
+    C = np.empty((B, X.shape[1]), dtype=np.float32)
+    bin = np.empty(X.shape[0], dtype=np.int32)
+    lib().orc_kmeans(_p(X), X.shape[0], X.shape[1], B, iters, _p(init_idx), metric,
+                     _p(C), _p(bin))
+    return C, bin
+
+
+def aft(bin, B, h, attrs: Attrs):
+    bin = _c(bin, np.int32)
+    N = len(bin)
+    tags = np.empty((B, h), dtype=np.int32)
+    key = np.zeros(N, dtype=np.uint8)
+    lib().orc_aft(_p(bin), N, B, h, *attrs.args(), _p(tags), _p(key))
+    return tags, key
+
+
+def layout(bin, key, B, h):
+    bin = _c(bin, np.int32)
+    key = _c(key, np.uint8)
+    N = len(bin)
+    perm = np.empty(N, dtype=np.int32)
+    offsets = np.empty(B * (h + 1) + 1, dtype=np.int32)
+    lib().orc_layout(_p(bin), _p(key), N, B, h, _p(perm), _p(offsets))
+    return perm, offsets
+
+
+# ---- Alg. 2 ---------------------------------------------------------------
+
+def probe(Q, C, m, metric=L2) -> np.ndarray:
+    Q = _c(Q, np.float32)
+    C = _c(C, np.float32)
+    out = np.empty((Q.shape[0], m), dtype=np.int32)
+    lib().orc_probe(_p(Q), Q.shape[0], Q.shape[1], _p(C), C.shape[0], metric, m, _p(out))
+    return out
+
+
+def select(tags, h, attrs: Attrs, probe_bins, cons: Cons) -> np.ndarray:
+    tags = _c(tags, np.int32)
+    probe_bins = _c(probe_bins, np.int32)
+    nq, m = probe_bins.shape
+    out = np.empty((nq, m), dtype=np.uint64)
+    lib().orc_select(_p(tags), h, attrs.L, _p(attrs.vocab), int(attrs.sp_vocab),
+                     _p(probe_bins), nq, m, *cons.args(), _p(out))
+    return out
+
+
+@dataclasses.dataclass
+class Index:
+    """Oracle-built CAPS index (Alg. 1)."""
+    C: np.ndarray
+    bin: np.ndarray
+    tags: np.ndarray
+    key: np.ndarray
+    perm: np.ndarray
+    offsets: np.ndarray
+    B: int
+    h: int
+    metric: int
+
+
+def build(X, attrs: Attrs, B, h, iters, init_idx, metric=L2, C=None) -> Index:
+    """Alg. 1: k-means first level (or given centroids), AFT, layout."""
+    if C is None:
+        C, bin = kmeans(X, B, iters, init_idx, metric)
+    else:
+        C = _c(C, np.float32)
+        bin = assign(X, C, metric)
+    tags, key = aft(bin, B, h, attrs)
+    perm, offsets = layout(bin, key, B, h)
+    return Index(C=C, bin=bin, tags=tags, key=key, perm=perm, offsets=offsets, B=B, h=h,
+                 metric=metric)
+
+
+def search(X, attrs: Attrs, index: Index, Q, cons: Cons, k, m):
+    """Alg. 2 for every query: returns ids [nq,k] (original ids, -1 pad),
+    fp32 distances [nq,k], rows attribute-tested and rows matched per query."""
+    X = _c(X, np.float32)
+    Q = _c(Q, np.float32)
+    nq = Q.shape[0]
+    ids = np.empty((nq, k), dtype=np.int64)
+    dist = np.empty((nq, k), dtype=np.float32)
+    n_scan = np.empty(nq, dtype=np.int64)
+    n_match = np.empty(nq, dtype=np.int64)
+    C = _c(index.C, np.float32)
+    tags = _c(index.tags, np.int32)
+    perm = _c(index.perm, np.int32)
+    offsets = _c(index.offsets, np.int32)
+    lib().orc_search(_p(X), X.shape[0], X.shape[1], *attrs.args(), _p(C), index.B,
+                     index.metric, _p(tags), index.h, _p(perm), _p(offsets), _p(Q), nq,
+                     *cons.args(), k, m, _p(ids), _p(dist), _p(n_scan), _p(n_match))
+    return ids, dist, n_scan, n_match
+
+
+def bruteforce(X, attrs: Attrs, Q, cons: Cons, k, metric=L2, order64=True):
+    """Exact filtered kNN (Def. 2, appendix "Groundtruth")."""
+    X = _c(X, np.float32)
+    Q = _c(Q, np.float32)
+    nq = Q.shape[0]
+    ids = np.empty((nq, k), dtype=np.int64)
+    d32 = np.empty((nq, k), dtype=np.float32)
+    d64 = np.empty((nq, k), dtype=np.float64)
+    cnt = np.empty(nq, dtype=np.int64)
+    lib().orc_bruteforce(_p(X), X.shape[0], X.shape[1], *attrs.args(), _p(Q), nq,
+                         *cons.args(), k, metric, int(bool(order64)), _p(ids), _p(d32),
+                         _p(d64), _p(cnt))
+    return ids, d32, d64, cnt
+
+
+# ---- appendix "Metric": RecallK@K -------------------------------------------
+
+def recall(ids, gt_ids, gt_d64, gt_count, k, X=None, Q=None, metric=L2):
+    """RecallK@K = |index top-K  intersect  true top-K| / K, with two readings:
+
+    strict: id-set intersection, divided by min(K, |D_C|);
+    tie-aware (needs X, Q): a returned id is a hit when its exact distance is
+    no worse than the true K-th distance (ids tied at the boundary count).
+    Returns (strict_mean, tie_mean, per-query strict, per-query tie).
+    """
+    ids = np.asarray(ids)
+    nq = ids.shape[0]
+    strict = np.ones(nq)
+    tie = np.ones(nq)
+    for q in range(nq):
+        denom = int(min(k, gt_count[q]))
+        if denom == 0:
+            continue
+        truth = set(int(v) for v in gt_ids[q, :denom])
+        got = [int(v) for v in ids[q, :k] if v >= 0]
+        strict[q] = len(truth.intersection(got)) / denom
+        if X is not None:
+            kth = gt_d64[q, denom - 1]
+            hits = 0
+            for v in got:
+                dv = dist64(X[v], Q[q], metric)
+                if (dv <= kth) if metric == L2 else (dv >= kth):
+                    hits += 1
+            tie[q] = min(hits, denom) / denom
+    return float(strict.mean()), float(tie.mean()), strict, tie
