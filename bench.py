@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the CAPS filtered-search hot path on one GB300.
+
+Workload: 1,000,000 x 128 byte-valued vectors (fp32), 3 attribute fields
+(vocab 20/50/100, Zipf 1.0), B = 1024 k-means partitions (20 Lloyd
+iterations), AFT height 15, 10,000 queries with 1-3 AND constraints
+(selectivity 0.1%-30%), k = 10, squared L2.  A step is one batched query of
+all 10,000 queries (Alg. 2: filter packing, centroid scores, top-m, block
+selection, fused scan + top-k) with queries resident in HBM; the index build
+(Alg. 1) runs once before and is reported as build time.  m is the smallest
+probe count in {8,12,16,24,32,48,64} whose tie-aware recall@10 (against the
+CPU oracle's exact filtered kNN on a seeded sample of queries) is >= 0.9.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+(the plain C restatement of the method) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filtered QPS at recall@10>=0.9 (plain FP32 k-means path)"
+UNIT = "queries/s"
+M_SWEEP = (8, 12, 16, 24, 32, 48, 64)
+RECALL_SAMPLE = 500
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["caps", "reference"], default="caps")
+    ap.add_argument("--config", choices=["sift1m", "small"], default="sift1m")
+    ap.add_argument("--m", type=int, default=0, help="fixed probe count (0 = sweep)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_workload(name):
+    from workloads import config_sift1m_like, config_small
+    return config_sift1m_like() if name == "sift1m" else config_small()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def scan_traffic_bytes(w, perm, offsets, probe, sel, words_pad):
+    """Algorithmic bytes of the scan for one batch.
+
+    union: attribute words of every row some query selects, plus the vector
+    of every row that passes some query's filter (each byte once: the HBM
+    floor of the whole batch).  per_query: the same sums taken query by query
+    (the paper's query-time term sum |p| (L + d*match), in bytes)."""
+    N, d, h = w.N, w.d, w.h
+    nb = h + 1
+    Ar = w.A[perm]
+    q_list, s_list = [], []
+    for j in range(nb):
+        qq, ii = np.nonzero((sel >> np.uint64(j)) & np.uint64(1))
+        q_list.append(qq)
+        s_list.append(probe[qq, ii].astype(np.int64) * nb + j)
+    qs = np.concatenate(q_list)
+    ss = np.concatenate(s_list)
+    order = np.argsort(ss, kind="stable")
+    qs, ss = qs[order], ss[order]
+    bounds = np.flatnonzero(np.diff(ss)) + 1
+    touched = np.zeros(N, bool)
+    passed = np.zeros(N, bool)
+    pq_scan = pq_pass = 0
+    for grp_q, s in zip(np.split(qs, bounds), ss[np.concatenate([[0], bounds])] if len(ss) else []):
+        r0, r1 = int(offsets[s]), int(offsets[s + 1])
+        if r1 <= r0:
+            continue
+        touched[r0:r1] = True
+        b = w.Qb[grp_q]
+        ok = np.all((b[:, None, :] < 0) | (Ar[None, r0:r1, :] == b[:, None, :]), axis=2)
+        passed[r0:r1] |= ok.any(0)
+        pq_scan += (r1 - r0) * len(grp_q)
+        pq_pass += int(ok.sum())
+    attr_b = 4 * words_pad
+    union = int(touched.sum()) * attr_b + int(passed.sum()) * d * 4
+    per_query = pq_scan * attr_b + pq_pass * d * 4
+    return union, per_query, pq_scan, pq_pass
+
+
+def traffic_from_profile():
+    """dram bytes per scan launch from the committed ncu summary, if it was
+    taken on the current scan kernel source."""
+    p = os.path.join(ROOT, "profiles", "scan_topk_traffic.json")
+    src = os.path.join(ROOT, "paper_2308_15014_gb300", "csrc", "search_kernels.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return j.get("dram_bytes_per_launch") if j.get("src_sha") == sha else None
+
+
+def oracle_baseline(w, m, k, budget_s=15.0):
+    """CPU oracle (plain C, all host cores) on a bounded sample of queries."""
+    import oracle as O
+    cores = O.set_threads(0)
+    at = O.Attrs.of(w)
+    t0 = time.perf_counter()
+    # k-means at this size is beyond a CPU budget of seconds: the oracle's
+    # index uses the same seed points as centroids (0 Lloyd iterations)
+    idx = O.build(w.X, at, w.B, w.h, 0, w.init_idx, w.metric)
+    build_s = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    order = rng.permutation(w.nq)
+    n, done, spent = 256, 0, 0.0
+    while done < w.nq and spent < budget_s:
+        sub = order[done:done + n]
+        t0 = time.perf_counter()
+        O.search(w.X, at, idx, w.Q[sub], O.Cons(Qb=w.Qb[sub]), k, m)
+        spent += time.perf_counter() - t0
+        done += len(sub)
+        n *= 2
+    return {"value": done / spent, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {w.nq} queries at m={m}, k={k}; oracle index built from the "
+                      f"same seed centroids without Lloyd iterations ({build_s:.1f} s, untimed)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from oracle.build import build_oracle
+    build_oracle()
+    w = load_workload(args.config)
+    m = args.m or 16
+    at = O.Attrs.of(w)
+    idx = O.build(w.X, at, w.B, w.h, 0, w.init_idx, w.metric)
+    cores = O.set_threads(0)
+    rng = np.random.default_rng(11)
+    per_step = min(w.nq, 2000)
+    for _ in range(args.warmup):
+        sub = rng.choice(w.nq, per_step, replace=False)
+        O.search(w.X, at, idx, w.Q[sub], O.Cons(Qb=w.Qb[sub]), w.k, m)
+    times = []
+    for _ in range(args.steps):
+        sub = rng.choice(w.nq, per_step, replace=False)
+        t0 = time.perf_counter()
+        O.search(w.X, at, idx, w.Q[sub], O.Cons(Qb=w.Qb[sub]), w.k, m)
+        times.append(time.perf_counter() - t0)
+    v = per_step * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "d": w.d, "B": w.B, "h": w.h, "m": m,
+                       "k": w.k, "queries_per_step": per_step},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} random queries per step; oracle index from "
+                                       "the seed centroids (0 Lloyd iterations)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_caps(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2308_15014_gb300 import build as capsbuild
+    capsbuild.build()
+    import paper_2308_15014_gb300 as caps
+    import oracle as O
+    from oracle.build import build_oracle
+    build_oracle()
+
+    w = load_workload(args.config)
+    X = torch.from_numpy(w.X).cuda()
+    A = torch.from_numpy(w.A).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, metric=w.metric,
+                          init_idx=w.init_idx)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Qd = torch.from_numpy(w.Q).cuda()
+    Qbd = torch.from_numpy(w.Qb).cuda()
+    out_ids = torch.empty((w.nq, w.k), dtype=torch.int64, device="cuda")
+    out_dist = torch.empty((w.nq, w.k), dtype=torch.float32, device="cuda")
+
+    # recall on a seeded sample of queries against the oracle's exact kNN
+    rng = np.random.default_rng(5)
+    samp = np.sort(rng.choice(w.nq, min(RECALL_SAMPLE, w.nq), replace=False))
+    O.set_threads(0)
+    gt, _, g64, cnt = O.bruteforce(w.X, O.Attrs.of(w), w.Q[samp], O.Cons(Qb=w.Qb[samp]), w.k)
+
+    def search(m):
+        ix.search(Qd, Qbd, w.k, m, out_ids=out_ids, out_dist=out_dist)
+
+    def recall_at(m):
+        search(m)
+        ids = out_ids.cpu().numpy()[samp]
+        return O.recall(ids, gt, g64, cnt, w.k, X=w.X, Q=w.Q[samp])
+
+    sweep = []
+    chosen = args.m
+    for m in ((args.m,) if args.m else M_SWEEP):
+        strict, tie, _, _ = recall_at(m)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        search(m)
+        ev0.record()
+        for _ in range(3):
+            search(m)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / 3
+        sweep.append({"m": m, "recall_tie": round(tie, 4), "recall_strict": round(strict, 4),
+                      "qps": round(w.nq / (ms / 1e3), 1)})
+        if not chosen and tie >= 0.9:
+            chosen = m
+    if not chosen:
+        chosen = M_SWEEP[-1]
+    m = chosen
+    rec = next(s for s in sweep if s["m"] == m)
+
+    # ---- timed region: K batches, L2 flushed between them -------------------
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        search(m)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record()
+            search(m)
+            e1.record()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.nq / (ms / 1e3)
+
+    # ---- per-stage device times (events on the launching stream) -----------
+    caps.set_timing(True)
+    stage = {}
+    reps = 5
+    for _ in range(reps):
+        flush.zero_()
+        search(m)
+        st = caps.stage_times()
+        for kk, vv in st.items():
+            stage[kk] = stage.get(kk, 0.0) + vv / reps
+    caps.set_timing(False)
+    launches_per_step = int(round(stage.pop("launches")))
+
+    # ---- algorithmic bytes of the scan (the dominant kernel) ---------------
+    perm = ix.export(caps.ARR_PERM)
+    offsets = ix.export(caps.ARR_OFFSETS)
+    probe = ix.probe(w.Q, m)
+    sel = ix.select(probe, w.Qb)
+    union, per_query, rows_scanned, rows_passed = scan_traffic_bytes(
+        w, perm, offsets, probe, sel, ix.info.attr_words)
+    hbm, hbm_src = peaks()
+    scan_s = stage["scan_ms"] / 1e3
+    achieved = union / scan_s / 1e9
+
+    # ---- end to end: host buffers through the same C-ABI call --------------
+    Qh, Qbh = np.ascontiguousarray(w.Q), np.ascontiguousarray(w.Qb)
+    ids_h = np.empty((w.nq, w.k), np.int64)
+    dist_h = np.empty((w.nq, w.k), np.float32)
+    for _ in range(args.warmup):
+        ix.search(Qh, Qbh, w.k, m, out_ids=ids_h, out_dist=dist_h)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix.search(Qh, Qbh, w.k, m, out_ids=ids_h, out_dist=dist_h)  # returns after D2H
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_v = world * w.nq / float(np.mean(e2e_t))
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_baseline(w, m, w.k)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "d": w.d, "L": int(w.A.shape[1]),
+                   "B": w.B, "h": w.h, "kmeans_iters": w.iters, "m": m, "k": w.k,
+                   "queries_per_step": w.nq, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "recall_at_10": {"tie_aware": rec["recall_tie"], "strict": rec["recall_strict"],
+                         "sample_queries": int(len(samp))},
+        "sweep": sweep,
+        "build_s": round(build_s, 3),
+        "stage_ms": {k_: round(v_, 4) for k_, v_ in stage.items()},
+        "roofline": {"kernel": "k_scan_topk", "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": hbm, "peak_source": hbm_src, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": traffic_from_profile(),
+                     "algorithmic_bytes_union": union, "algorithmic_bytes_per_query_sum": per_query,
+                     "rows_attr_tested": rows_scanned, "rows_distance": rows_passed},
+        "e2e": {"value": round(e2e_v, 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(Qh.nbytes + Qbh.nbytes),
+                "d2h_bytes_per_step": int(ids_h.nbytes + dist_h.nbytes)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    ix.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_caps(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

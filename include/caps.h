@@ -1,0 +1,238 @@
+/*
+ * caps.h -- C ABI of the GB300 (sm_103a) CAPS filtered-search library.
+ *
+ * CAPS = Constrained Approximate Partitioned Search (arXiv 2308.15014).
+ * The data model is the paper's Def. 1-2: a dataset of N pairs (x_i, a_i),
+ * x_i in R^d, a_i an attribute vector; a query (q, b) asks for the k nearest
+ * x_i among the points whose attributes satisfy the AND-filter C(a_i, b).
+ * The index is the paper's two-level partition (Alg. 1): a first-level
+ * partition function f(.) (k-means here, Sec. 5.2) and, inside each of the B
+ * partitions, an attribute-frequency tree (AFT) of height h that splits the
+ * partition into h+1 disjoint sub-partitions laid out contiguously.  A query
+ * (Alg. 2) probes the m best partitions, selects the sub-partitions that can
+ * hold valid points, filters them and keeps the k best distances.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Pointers.  Every array argument may point to host memory or to device
+ * memory of the current CUDA device (the library tells them apart with
+ * cudaPointerGetAttributes).  Host inputs are copied to the device inside the
+ * call; when an output is in host memory the call synchronises `stream` and
+ * the output is complete on return.  With device inputs and outputs the call
+ * only enqueues work on `stream` and returns.
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Ownership.  The caller owns every array it passes; the library never keeps
+ * a caller pointer past the call.  A caps_index owns all of its device
+ * memory and releases it in caps_free.
+ * Errors.  Every int-returning call returns CAPS_OK (0) or one of the codes
+ * below and never aborts; caps_last_error() returns a message for the last
+ * failure on the calling thread.
+ * Layouts.  Row-major, 0-based.  float = IEEE fp32.
+ * Concurrency.  A caps_index keeps per-index search workspace: searches on
+ * one index must not overlap (serialise them on one stream); distinct
+ * indexes are independent.
+ */
+#ifndef CAPS_H_
+#define CAPS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CAPS_OK 0
+#define CAPS_EINVAL 1   /* bad argument (shape, range, unsupported option) */
+#define CAPS_ENOMEM 2   /* device or host allocation failed */
+#define CAPS_ECUDA 3    /* a CUDA runtime call or kernel launch failed */
+#define CAPS_ETIMEOUT 4 /* a bounded device-side wait expired */
+
+typedef struct caps_index caps_index;
+
+typedef enum { CAPS_L2 = 0, CAPS_IP = 1 } caps_metric;
+typedef enum { CAPS_PART_KMEANS = 0, CAPS_PART_MLP = 1 } caps_partitioner;
+typedef enum { CAPS_FP32 = 0, CAPS_BF16 = 1, CAPS_FP8E4M3 = 2 } caps_precision;
+
+/*
+ * Attribute vectors (Def. 1, "attribute model") -- exactly one of the two
+ * forms is used:
+ *   dense:  L > 0, dense = [N*L] int32, dense[i*L+f] in [0, vocab[f]);
+ *           vocab = [L] int32 (values per field).  For a query constraint
+ *           array the same layout holds with -1 meaning "field f is
+ *           unconstrained" (variable constraints, Sec. 6.1).
+ *   sparse: L = 0, dense = NULL; point i carries the label set
+ *           sp_labels[sp_offsets[i] .. sp_offsets[i+1]) (int32 in
+ *           [0, sp_vocab), sorted ascending, no repeats), sp_offsets = [N+1]
+ *           int64.  For a query the set lists the REQUIRED labels; the
+ *           filter holds when every required label is present.
+ */
+typedef struct {
+  int32_t L;
+  const int32_t* dense;
+  const int32_t* vocab;
+  const int64_t* sp_offsets;
+  const int32_t* sp_labels;
+  int32_t sp_vocab;
+} caps_attrs;
+
+/*
+ * Build parameters (Alg. 1 inputs).
+ *   B            first-level partitions (k-means clusters), 1 <= B <= N.
+ *   h            AFT height, 0 <= h <= 63: each partition is split into h+1
+ *                sub-partitions (Alg. 1; Sec. 6.1 ablation on h+1).
+ *   kmeans_iters Lloyd iterations (Sec. 5.2), >= 0.
+ *   seed         used only when init_idx is NULL: the B seed points are then
+ *                drawn without replacement by Floyd's method driven by
+ *                SplitMix64(seed).
+ *   metric       CAPS_L2 (squared Euclidean, smaller is better) or CAPS_IP
+ *                (inner product, larger is better; k-means then normalises
+ *                each centroid to unit length).
+ *   part         CAPS_PART_KMEANS.
+ *   prec         CAPS_FP32.
+ *   rerank_factor, mlp_hidden, mlp_epochs: reserved, pass 0.
+ *   init_idx     optional [B] int64: k-means seed point ids (distinct).
+ *   centroids    optional [B*d] fp32: fixed first-level centroids; k-means is
+ *                skipped and f(x) = best centroid (Alg. 1 first loop).
+ */
+typedef struct {
+  int32_t B, h, kmeans_iters;
+  uint64_t seed;
+  caps_metric metric;
+  caps_partitioner part;
+  caps_precision prec;
+  int32_t rerank_factor;
+  int32_t mlp_hidden, mlp_epochs;
+  const int64_t* init_idx;
+  const float* centroids;
+} caps_build_params;
+
+/*
+ * caps_build -- Alg. 1 (CAPS index construction) on the GPU.
+ * X = [N*d] fp32 vectors, attrs = the points' attributes.  Steps: k-means
+ * first level (fp64 centroid sums in id order), assignment f(x_i), per
+ * partition the greedy attribute-frequency peel (most frequent code among the
+ * points not yet peeled, ties to the lowest code; a dense code is
+ * sum(vocab[0..f-1]) + value), then a stable sort by (partition, block, id)
+ * into contiguous sub-partitions.  Inputs may be freed on return.
+ * Returns CAPS_EINVAL for N < 1, d < 1, B outside [1, N], h outside [0, 63],
+ * bad attribute values, a dense packing wider than 128 bits, or sparse
+ * attributes (not yet supported by this build).
+ */
+int caps_build(const caps_build_params* params, const float* X, int64_t N,
+               int32_t d, const caps_attrs* attrs, void* stream,
+               caps_index** out);
+
+/*
+ * caps_search_batch -- Alg. 2 (CAPS query) for nq queries.
+ * Q = [nq*d] fp32; constraints = the queries' attribute constraints in the
+ * form the index was built with (dense: [nq*L], -1 = unconstrained).
+ * For each query: the m partitions with the best centroid score are probed
+ * (ties to the lower partition); in each, the sub-partitions that can hold a
+ * valid point are selected (Alg. 2; every block up to the first block whose
+ * tag the query carries, skipping blocks whose tag contradicts the query, and
+ * the remainder block only when no tag matches); every row of those blocks
+ * is filtered with Def. 1 and its distance computed in fp32 (coordinates in
+ * order, one fused multiply-add each); the k best are kept.
+ * out_ids = [nq*k] int64 original point ids, best first, ties to the lower
+ * id, -1 where fewer than k valid points were found; out_dist = [nq*k] fp32
+ * (squared L2 or inner product), +inf (L2) / -inf (IP) on padded slots.
+ * 1 <= k <= 128, 1 <= m <= B.  nq = 0 is a no-op.
+ */
+int caps_search_batch(const caps_index* index, const float* Q, int64_t nq,
+                      const caps_attrs* constraints, int32_t k, int32_t m,
+                      int64_t* out_ids, float* out_dist, void* stream);
+
+/* caps_free -- release an index and all its device memory (NULL is a no-op).
+ * Synchronises the device first so no enqueued work still uses it. */
+void caps_free(caps_index* index);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* caps_last_error(void);
+
+/* ---- introspection and single steps (used to check each step alone) ---- */
+
+typedef struct {
+  int64_t N;
+  int32_t d, B, h, L, metric;
+  int64_t n_codes;       /* dense: sum(vocab); sparse: sp_vocab */
+  int32_t attr_words;    /* packed 32-bit attribute words per row */
+  int64_t device_bytes;  /* device memory held by the index */
+} caps_index_info;
+
+int caps_get_info(const caps_index* index, caps_index_info* out);
+
+/*
+ * caps_export -- copy one index array to `dst` (host or device), `bytes`
+ * must equal the array size.  Arrays (the paper's objects in brackets):
+ *   CAPS_ARR_CENTROIDS [B*d] fp32    first-level centroids (Sec. 5.2)
+ *   CAPS_ARR_BIN       [N] int32     f(x_i), by original id (Alg. 1 loop 1)
+ *   CAPS_ARR_TAGS      [B*h] int32   A(p_j) codes, -1 = empty (Alg. 1)
+ *   CAPS_ARR_KEY       [N] uint8     sub-partition j in 1..h+1 of point i
+ *   CAPS_ARR_PERM      [N] int32     row r of the layout holds point perm[r]
+ *   CAPS_ARR_OFFSETS   [B*(h+1)+1] int32  rows of block (b, j) are
+ *                      [offsets[b*(h+1)+j-1], offsets[b*(h+1)+j])
+ */
+enum {
+  CAPS_ARR_CENTROIDS = 0,
+  CAPS_ARR_BIN = 1,
+  CAPS_ARR_TAGS = 2,
+  CAPS_ARR_KEY = 3,
+  CAPS_ARR_PERM = 4,
+  CAPS_ARR_OFFSETS = 5
+};
+int caps_export(const caps_index* index, int32_t which, void* dst,
+                size_t bytes, void* stream);
+
+/*
+ * caps_assign -- Alg. 1 first loop, f(x) = best centroid: out_bin[i] = the
+ * centroid with the smallest fp32 squared distance (CAPS_L2) or largest
+ * inner product (CAPS_IP) to X[i], coordinates accumulated in order with one
+ * fused multiply-add each, ties to the lower centroid.  X = [N*d],
+ * C = [B*d], out_bin = [N] int32.
+ */
+int caps_assign(const float* X, int64_t N, int32_t d, const float* C,
+                int32_t B, int32_t metric, int32_t* out_bin, void* stream);
+
+/*
+ * caps_probe -- Alg. 2 "select top m partitions": out_probe = [nq*m] int32,
+ * partitions of each query best first (same score and tie rule as
+ * caps_assign).
+ */
+int caps_probe(const caps_index* index, const float* Q, int64_t nq, int32_t m,
+               int32_t* out_probe, void* stream);
+
+/*
+ * caps_select -- Alg. 2 sub-partition selection for given probes:
+ * probe = [nq*m] int32 partition ids, out_sel = [nq*m] uint64, bit j-1 set
+ * when block j (1..h+1) of that partition is scanned.
+ */
+int caps_select(const caps_index* index, const int32_t* probe, int64_t nq,
+                int32_t m, const caps_attrs* constraints, uint64_t* out_sel,
+                void* stream);
+
+/* ---- stage timing (measurement aid, off by default) ---------------------- */
+
+/* Per-stage device time of the last caps_search_batch call made on this
+ * thread while timing was on, in milliseconds, summed over query chunks.
+ * The stages are the kernels of Alg. 2: query filter packing, centroid
+ * scores, top-m partition choice, sub-partition selection, and the fused
+ * attribute match + distance + top-k scan. */
+typedef struct {
+  float prep_ms, scores_ms, topm_ms, select_ms, scan_ms;
+  int32_t launches; /* kernels launched by that call */
+} caps_stage_times;
+
+/* enable = 1: record CUDA events between the stages of every following
+ * caps_search_batch on this thread (adds event records, no syncs).
+ * enable = 0: stop. */
+int caps_set_timing(int32_t enable);
+
+/* Wait for the last timed search and read its stage times (CAPS_EINVAL if
+ * no search was timed on this thread). */
+int caps_get_stage_times(caps_stage_times* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAPS_H_ */

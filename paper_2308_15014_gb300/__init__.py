@@ -1,0 +1,267 @@
+"""Python binding of the CAPS GB300 library (include/caps.h).
+
+Argument marshalling only: every step of index construction (Alg. 1) and of
+the batched query (Alg. 2) runs in the CUDA kernels of libcaps_gb300.so.
+There is no CPU fallback: importing works anywhere, but the first call fails
+loudly if the compiled library is missing or no GPU is present.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; CPU/numpy arrays
+are host memory and go through the library's own host<->device staging.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcaps_gb300.so")
+
+CAPS_OK, CAPS_EINVAL, CAPS_ENOMEM, CAPS_ECUDA, CAPS_ETIMEOUT = 0, 1, 2, 3, 4
+L2, IP = 0, 1
+ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS = range(6)
+
+# Every symbol declared in include/caps.h.
+EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "caps_get_info",
+           "caps_export", "caps_assign", "caps_probe", "caps_select", "caps_set_timing",
+           "caps_get_stage_times")
+
+
+class CapsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"CAPS error {code}: {msg}")
+        self.code = code
+
+
+class caps_attrs(ct.Structure):
+    _fields_ = [("L", ct.c_int32), ("dense", ct.c_void_p), ("vocab", ct.c_void_p),
+                ("sp_offsets", ct.c_void_p), ("sp_labels", ct.c_void_p), ("sp_vocab", ct.c_int32)]
+
+
+class caps_build_params(ct.Structure):
+    _fields_ = [("B", ct.c_int32), ("h", ct.c_int32), ("kmeans_iters", ct.c_int32),
+                ("seed", ct.c_uint64), ("metric", ct.c_int), ("part", ct.c_int),
+                ("prec", ct.c_int), ("rerank_factor", ct.c_int32), ("mlp_hidden", ct.c_int32),
+                ("mlp_epochs", ct.c_int32), ("init_idx", ct.c_void_p), ("centroids", ct.c_void_p)]
+
+
+class caps_stage_times(ct.Structure):
+    _fields_ = [("prep_ms", ct.c_float), ("scores_ms", ct.c_float), ("topm_ms", ct.c_float),
+                ("select_ms", ct.c_float), ("scan_ms", ct.c_float), ("launches", ct.c_int32)]
+
+
+class caps_index_info(ct.Structure):
+    _fields_ = [("N", ct.c_int64), ("d", ct.c_int32), ("B", ct.c_int32), ("h", ct.c_int32),
+                ("L", ct.c_int32), ("metric", ct.c_int32), ("n_codes", ct.c_int64),
+                ("attr_words", ct.c_int32), ("device_bytes", ct.c_int64)]
+
+
+_lib = None
+
+
+def lib(path: Optional[str] = None):
+    """Load libcaps_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"CAPS CUDA library not built: {p} is missing "
+                          "(run paper_2308_15014_gb300/build.py); there is no CPU fallback")
+    L = ct.CDLL(p)
+    P, i64, i32 = ct.c_void_p, ct.c_int64, ct.c_int32
+    L.caps_build.argtypes = [ct.POINTER(caps_build_params), P, i64, i32, ct.POINTER(caps_attrs),
+                             P, ct.POINTER(P)]
+    L.caps_search_batch.argtypes = [P, P, i64, ct.POINTER(caps_attrs), i32, i32, P, P, P]
+    L.caps_free.argtypes = [P]
+    L.caps_free.restype = None
+    L.caps_last_error.restype = ct.c_char_p
+    L.caps_get_info.argtypes = [P, ct.POINTER(caps_index_info)]
+    L.caps_export.argtypes = [P, i32, P, ct.c_size_t, P]
+    L.caps_assign.argtypes = [P, i64, i32, P, i32, i32, P, P]
+    L.caps_probe.argtypes = [P, P, i64, i32, P, P]
+    L.caps_select.argtypes = [P, P, i64, i32, ct.POINTER(caps_attrs), P, P]
+    L.caps_set_timing.argtypes = [i32]
+    L.caps_get_stage_times.argtypes = [ct.POINTER(caps_stage_times)]
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != CAPS_OK:
+        raise CapsError(rc, lib().caps_last_error().decode())
+
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # pragma: no cover
+        return None
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    t = _torch()
+    if t is not None and isinstance(a, t.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    t = _torch()
+    if t is not None and t.cuda.is_available():
+        return t.cuda.current_stream().cuda_stream
+    return 0
+
+
+def _np_or_keep(a, dtype):
+    t = _torch()
+    if t is not None and isinstance(a, t.Tensor):
+        want = {np.float32: t.float32, np.int32: t.int32, np.int64: t.int64}[dtype]
+        if a.dtype != want:
+            raise TypeError(f"expected {want}, got {a.dtype}")
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _dense_attrs(A, vocab=None):
+    A = _np_or_keep(A, np.int32)
+    at = caps_attrs()
+    at.L = int(A.shape[1])
+    at.dense = _ptr(A)
+    keep = [A]
+    if vocab is not None:
+        v = np.ascontiguousarray(vocab, dtype=np.int32)
+        at.vocab = _ptr(v)
+        keep.append(v)
+    return at, keep
+
+
+def assign(X, C, metric=L2, out=None, stream=None):
+    """f(x) = best centroid for every row of X (caps_assign)."""
+    X = _np_or_keep(X, np.float32)
+    C = _np_or_keep(C, np.float32)
+    N, d = X.shape
+    if out is None:
+        out = np.empty(N, dtype=np.int32)
+    _check(lib().caps_assign(_ptr(X), N, d, _ptr(C), C.shape[0], metric, _ptr(out),
+                             _stream(stream)))
+    return out
+
+
+def set_timing(enable: bool):
+    """Record per-stage CUDA events in later searches on this thread."""
+    _check(lib().caps_set_timing(1 if enable else 0))
+
+
+def stage_times() -> dict:
+    """Stage times (ms) of the last timed search on this thread."""
+    t = caps_stage_times()
+    _check(lib().caps_get_stage_times(ct.byref(t)))
+    return {f: getattr(t, f) for f, _ in caps_stage_times._fields_}
+
+
+class Index:
+    """A CAPS index living in GPU memory (caps_build / caps_free)."""
+
+    def __init__(self, handle, keep=None):
+        self._h = handle
+        info = caps_index_info()
+        _check(lib().caps_get_info(self._h, ct.byref(info)))
+        self.info = info
+
+    @classmethod
+    def build(cls, X, A, vocab, B, h=15, iters=20, metric=L2, init_idx=None, centroids=None,
+              seed=0, stream=None) -> "Index":
+        X = _np_or_keep(X, np.float32)
+        N, d = X.shape
+        at, keep = _dense_attrs(A, vocab)
+        p = caps_build_params()
+        p.B, p.h, p.kmeans_iters, p.seed, p.metric = B, h, iters, seed, metric
+        p.part, p.prec = 0, 0
+        if init_idx is not None:
+            init_idx = _np_or_keep(init_idx, np.int64)
+            p.init_idx = _ptr(init_idx)
+        if centroids is not None:
+            centroids = _np_or_keep(centroids, np.float32)
+            p.centroids = _ptr(centroids)
+        h_out = ct.c_void_p()
+        _check(lib().caps_build(ct.byref(p), _ptr(X), N, d, ct.byref(at), _stream(stream),
+                                ct.byref(h_out)))
+        return cls(h_out)
+
+    def close(self):
+        if self._h:
+            lib().caps_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self, which: int) -> np.ndarray:
+        i = self.info
+        shapes = {ARR_CENTROIDS: ((i.B, i.d), np.float32), ARR_BIN: ((i.N,), np.int32),
+                  ARR_TAGS: ((i.B, i.h), np.int32), ARR_KEY: ((i.N,), np.uint8),
+                  ARR_PERM: ((i.N,), np.int32),
+                  ARR_OFFSETS: ((i.B * (i.h + 1) + 1,), np.int32)}
+        shape, dt = shapes[which]
+        out = np.empty(shape, dtype=dt)
+        _check(lib().caps_export(self._h, which, _ptr(out) if out.size else 1, out.nbytes,
+                                 _stream(None)))
+        return out
+
+    def probe(self, Q, m, out=None, stream=None):
+        Q = _np_or_keep(Q, np.float32)
+        nq = Q.shape[0]
+        if out is None:
+            out = np.empty((nq, m), dtype=np.int32)
+        _check(lib().caps_probe(self._h, _ptr(Q), nq, m, _ptr(out), _stream(stream)))
+        return out
+
+    def select(self, probe, Qb, out=None, stream=None):
+        probe = _np_or_keep(probe, np.int32)
+        nq, m = probe.shape
+        at, keep = _dense_attrs(Qb)
+        if out is None:
+            out = np.empty((nq, m), dtype=np.uint64)
+        _check(lib().caps_select(self._h, _ptr(probe), nq, m, ct.byref(at), _ptr(out),
+                                 _stream(stream)))
+        return out
+
+    def search(self, Q, Qb, k, m, out_ids=None, out_dist=None, stream=None):
+        """Alg. 2 for a batch; returns (ids [nq,k] int64, dist [nq,k] fp32).
+        Outputs land where the inputs live unless given explicitly."""
+        Q = _np_or_keep(Q, np.float32)
+        nq = Q.shape[0]
+        at, keep = _dense_attrs(Qb)
+        t = _torch()
+        if out_ids is None:
+            if t is not None and isinstance(Q, t.Tensor) and Q.is_cuda:
+                out_ids = t.empty((nq, k), dtype=t.int64, device=Q.device)
+                out_dist = t.empty((nq, k), dtype=t.float32, device=Q.device)
+            else:
+                out_ids = np.empty((nq, k), dtype=np.int64)
+                out_dist = np.empty((nq, k), dtype=np.float32)
+        _check(lib().caps_search_batch(self._h, _ptr(Q), nq, ct.byref(at), k, m, _ptr(out_ids),
+                                       _ptr(out_dist), _stream(stream)))
+        return out_ids, out_dist

@@ -1,0 +1,626 @@
+// C ABI of the CAPS GB300 library: argument checks, host/device staging and
+// the order of the kernels for index construction (Alg. 1) and batched query
+// (Alg. 2).  All arithmetic of the method runs in the kernels.
+#include <cstring>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "caps_internal.cuh"
+
+namespace caps {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return CAPS_ECUDA;
+}
+
+namespace {
+
+// Is p a pointer the current device can dereference (device or managed)?
+int is_device_ptr(const void* p, bool* dev) {
+  *dev = false;
+  if (!p) return CAPS_OK;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return CAPS_OK;  // unknown to CUDA: plain host memory
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    int cur = 0;
+    CAPS_CUDA(cudaGetDevice(&cur));
+    if (at.type == cudaMemoryTypeDevice && at.device != cur)
+      return fail(CAPS_EINVAL, "device pointer belongs to another GPU");
+    *dev = true;
+  }
+  return CAPS_OK;
+}
+
+// Device view of an input array: the pointer itself, or a stream-ordered copy.
+template <class T>
+int stage_in(const T* src, size_t count, Scratch& scr, cudaStream_t s, const T** out) {
+  *out = nullptr;
+  if (count == 0) return CAPS_OK;
+  if (!src) return fail(CAPS_EINVAL, "null input array");
+  bool dev = false;
+  if (int rc = is_device_ptr(src, &dev)) return rc;
+  if (dev) {
+    *out = src;
+    return CAPS_OK;
+  }
+  T* d = nullptr;
+  if (int rc = scr.get(&d, count)) return rc;
+  CAPS_CUDA(cudaMemcpyAsync(d, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  *out = d;
+  return CAPS_OK;
+}
+
+// Host copy of a small input array (for validation and metadata).
+template <class T>
+int to_host(const T* src, size_t count, std::vector<T>* out, cudaStream_t s) {
+  out->assign(count, T());
+  if (count == 0) return CAPS_OK;
+  if (!src) return fail(CAPS_EINVAL, "null input array");
+  bool dev = false;
+  if (int rc = is_device_ptr(src, &dev)) return rc;
+  if (!dev) {
+    std::memcpy(out->data(), src, count * sizeof(T));
+    return CAPS_OK;
+  }
+  CAPS_CUDA(cudaMemcpyAsync(out->data(), src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
+// Output array: the caller's device pointer, or scratch copied back later.
+template <class T>
+struct Out {
+  T* user = nullptr;
+  T* dev = nullptr;
+  size_t count = 0;
+  bool host = false;
+  int init(T* u, size_t n, Scratch& scr) {
+    user = u;
+    count = n;
+    if (n == 0) return CAPS_OK;
+    if (!u) return fail(CAPS_EINVAL, "null output array");
+    bool d = false;
+    if (int rc = is_device_ptr(u, &d)) return rc;
+    host = !d;
+    if (d) {
+      dev = u;
+      return CAPS_OK;
+    }
+    return scr.get(&dev, n);
+  }
+  int finish(cudaStream_t s) {
+    if (host && count)
+      CAPS_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    return CAPS_OK;
+  }
+};
+
+void keep_pool_warm() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done = true;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) driving Floyd's sampling of B
+// distinct seed ids out of N.
+uint64_t splitmix64(uint64_t* st) {
+  uint64_t z = (*st += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+std::vector<int64_t> floyd_sample(int64_t N, int64_t B, uint64_t seed) {
+  std::vector<int64_t> out;
+  std::unordered_set<int64_t> seen;
+  uint64_t st = seed;
+  for (int64_t j = N - B; j < N; j++) {
+    const int64_t t = (int64_t)(splitmix64(&st) % (uint64_t)(j + 1));
+    const int64_t v = seen.count(t) ? j : t;
+    seen.insert(v);
+    out.push_back(v);
+  }
+  return out;
+}
+
+int make_meta(const caps_attrs* at, cudaStream_t s, DenseMeta* meta) {
+  if (!at) return fail(CAPS_EINVAL, "attributes are required");
+  if (at->dense == nullptr || at->L <= 0)
+    return fail(CAPS_EINVAL, "sparse label attributes are not supported by this build");
+  if (at->L > kMaxFields) return fail(CAPS_EINVAL, "more than 16 attribute fields");
+  std::vector<int32_t> vocab;
+  if (int rc = to_host(at->vocab, (size_t)at->L, &vocab, s)) return rc;
+  DenseMeta m;
+  m.L = at->L;
+  int64_t off = 0;
+  int word = 0, used = 0;
+  for (int f = 0; f < m.L; f++) {
+    if (vocab[f] < 1) return fail(CAPS_EINVAL, "vocab entries must be >= 1");
+    m.vocab[f] = vocab[f];
+    m.code_off[f] = (int)off;
+    off += vocab[f];
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)vocab[f]) bits++;
+    if (used + bits > 32) {
+      word++;
+      used = 0;
+    }
+    m.word[f] = word;
+    m.shift[f] = used;
+    m.bits[f] = bits;
+    used += bits;
+  }
+  if (off > (int64_t)1 << 24) return fail(CAPS_EINVAL, "too many attribute codes (sum of vocab)");
+  m.words = word + 1;
+  if (m.words > 4) return fail(CAPS_EINVAL, "packed attributes exceed 128 bits");
+  m.words_pad = m.words == 1 ? 1 : (m.words == 2 ? 2 : 4);
+  m.n_codes = off;
+  *meta = m;
+  return CAPS_OK;
+}
+
+}  // namespace
+}  // namespace caps
+
+using namespace caps;
+
+struct caps_index {
+  int64_t N = 0;
+  int d = 0, B = 0, h = 0, metric = 0;
+  DenseMeta meta;
+  float* C = nullptr;
+  int32_t* bin = nullptr;
+  uint8_t* key = nullptr;
+  int32_t* tags = nullptr;
+  int32_t* perm = nullptr;
+  int32_t* offsets = nullptr;
+  uint8_t* pos = nullptr;
+  uint8_t* code_field = nullptr;
+  float* Xp = nullptr;
+  uint32_t* Ap = nullptr;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+
+  template <class T>
+  int alloc(T** p, size_t count) {
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CAPS_ENOMEM, "cudaMalloc failed for an index array");
+    }
+    allocs.push_back(q);
+    bytes += (int64_t)(count * sizeof(T));
+    *p = (T*)q;
+    return CAPS_OK;
+  }
+  ~caps_index() {
+    for (void* q : allocs) cudaFree(q);
+  }
+};
+
+extern "C" const char* caps_last_error(void) { return g_err.c_str(); }
+
+static int build_impl(const caps_build_params* p, const float* X, int64_t N, int32_t d,
+                      const caps_attrs* attrs, cudaStream_t s, caps_index* ix) {
+  if (!p || !X || !attrs) return fail(CAPS_EINVAL, "null argument");
+  if (N < 1 || N >= (int64_t)INT32_MAX) return fail(CAPS_EINVAL, "N must be in [1, 2^31-1)");
+  if (d < 1) return fail(CAPS_EINVAL, "d must be >= 1");
+  if (p->B < 1 || p->B > N) return fail(CAPS_EINVAL, "B must be in [1, N]");
+  if (p->h < 0 || p->h > kMaxH) return fail(CAPS_EINVAL, "h must be in [0, 63]");
+  if ((int64_t)p->B * (p->h + 1) >= (int64_t)INT32_MAX) return fail(CAPS_EINVAL, "B*(h+1) too large");
+  if (p->kmeans_iters < 0) return fail(CAPS_EINVAL, "kmeans_iters must be >= 0");
+  if (p->metric != CAPS_L2 && p->metric != CAPS_IP) return fail(CAPS_EINVAL, "unknown metric");
+  if (p->part != CAPS_PART_KMEANS) return fail(CAPS_EINVAL, "only the k-means partitioner is built");
+  if (p->prec != CAPS_FP32) return fail(CAPS_EINVAL, "only fp32 precision is built");
+  keep_pool_warm();
+  DenseMeta meta;
+  if (int rc = make_meta(attrs, s, &meta)) return rc;
+  const int B = p->B, h = p->h, L = meta.L;
+  ix->N = N;
+  ix->d = d;
+  ix->B = B;
+  ix->h = h;
+  ix->metric = p->metric;
+  ix->meta = meta;
+
+  Scratch scr(s);
+  const float* dX = nullptr;
+  const int32_t* dA = nullptr;
+  if (int rc = stage_in(X, (size_t)N * d, scr, s, &dX)) return rc;
+  if (int rc = stage_in(attrs->dense, (size_t)N * L, scr, s, &dA)) return rc;
+  int32_t* bad = nullptr;
+  if (int rc = scr.get(&bad, 1)) return rc;
+  CAPS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
+  if (int rc = launch_check_dense(dA, N, meta, bad, s)) return rc;
+  int32_t bad_h = 0;
+  CAPS_CUDA(cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  if (bad_h) return fail(CAPS_EINVAL, "attribute value outside [0, vocab[f])");
+
+  const int64_t nseg = (int64_t)B * (h + 1);
+  if (int rc = ix->alloc(&ix->C, (size_t)B * d)) return rc;
+  if (int rc = ix->alloc(&ix->bin, (size_t)N)) return rc;
+  if (int rc = ix->alloc(&ix->key, (size_t)N)) return rc;
+  if (int rc = ix->alloc(&ix->tags, (size_t)B * h)) return rc;
+  if (int rc = ix->alloc(&ix->perm, (size_t)N)) return rc;
+  if (int rc = ix->alloc(&ix->offsets, (size_t)nseg + 1)) return rc;
+  if (int rc = ix->alloc(&ix->pos, (size_t)B * meta.n_codes)) return rc;
+  if (int rc = ix->alloc(&ix->code_field, (size_t)meta.n_codes)) return rc;
+  if (int rc = ix->alloc(&ix->Xp, (size_t)N * d)) return rc;
+  if (int rc = ix->alloc(&ix->Ap, (size_t)N * meta.words_pad)) return rc;
+  if (int rc = launch_code_field(meta, ix->code_field, s)) return rc;
+
+  int32_t *perm_bin = nullptr, *bin_off = nullptr;
+  if (int rc = scr.get(&perm_bin, (size_t)N)) return rc;
+  if (int rc = scr.get(&bin_off, (size_t)B + 1)) return rc;
+
+  // ---- first level: fixed centroids or k-means (Sec. 5.2) ----
+  if (p->centroids) {
+    const float* dC = nullptr;
+    if (int rc = stage_in(p->centroids, (size_t)B * d, scr, s, &dC)) return rc;
+    CAPS_CUDA(cudaMemcpyAsync(ix->C, dC, sizeof(float) * B * d, cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::vector<int64_t> init;
+    if (p->init_idx) {
+      if (int rc = to_host(p->init_idx, (size_t)B, &init, s)) return rc;
+      std::unordered_set<int64_t> seen;
+      for (int64_t v : init) {
+        if (v < 0 || v >= N) return fail(CAPS_EINVAL, "init_idx entry outside [0, N)");
+        if (!seen.insert(v).second) return fail(CAPS_EINVAL, "init_idx entries must be distinct");
+      }
+    } else {
+      init = floyd_sample(N, B, p->seed);
+    }
+    int64_t* dinit = nullptr;
+    if (int rc = scr.get(&dinit, (size_t)B)) return rc;
+    CAPS_CUDA(cudaMemcpyAsync(dinit, init.data(), sizeof(int64_t) * B, cudaMemcpyHostToDevice, s));
+    if (int rc = launch_gather_rows(dX, dinit, B, d, ix->C, s)) return rc;
+    CAPS_CUDA(cudaStreamSynchronize(s));  // `init` leaves scope
+    for (int it = 0; it < p->kmeans_iters; it++) {
+      Scratch it_scr(s);  // per-iteration temporaries, released in stream order
+      if (int rc = launch_assign(dX, N, d, ix->C, B, p->metric, ix->bin, s)) return rc;
+      if (int rc = stable_sort_by_key(ix->bin, N, B, perm_bin, bin_off, it_scr, s)) return rc;
+      if (int rc = launch_centroid_update(dX, d, perm_bin, bin_off, B, p->metric, ix->C, it_scr, s))
+        return rc;
+    }
+  }
+  // ---- f(x_i) for every point (Alg. 1, first loop) ----
+  if (int rc = launch_assign(dX, N, d, ix->C, B, p->metric, ix->bin, s)) return rc;
+  if (int rc = stable_sort_by_key(ix->bin, N, B, perm_bin, bin_off, scr, s)) return rc;
+  // ---- attribute frequency tree per partition (Alg. 1, second loop) ----
+  CAPS_CUDA(cudaMemsetAsync(ix->key, 0, (size_t)N, s));
+  if (int rc = launch_aft(perm_bin, bin_off, B, h, dA, meta, ix->code_field, ix->tags, ix->key, s))
+    return rc;
+  // ---- contiguous sub-partitions: stable order by (partition, block, id) ----
+  int32_t* seg = nullptr;
+  if (int rc = scr.get(&seg, (size_t)N)) return rc;
+  if (int rc = launch_segment_keys(ix->bin, ix->key, N, h, seg, s)) return rc;
+  if (int rc = stable_sort_by_key(seg, N, nseg, ix->perm, ix->offsets, scr, s)) return rc;
+  if (int rc = launch_layout(dX, dA, ix->perm, N, d, meta, ix->Xp, ix->Ap, s)) return rc;
+  CAPS_CUDA(cudaMemsetAsync(ix->pos, 0, (size_t)B * meta.n_codes, s));
+  if (int rc = launch_pos_table(ix->tags, B, h, meta.n_codes, ix->pos, s)) return rc;
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
+extern "C" int caps_build(const caps_build_params* params, const float* X, int64_t N, int32_t d,
+                          const caps_attrs* attrs, void* stream, caps_index** out) {
+  if (!out) return fail(CAPS_EINVAL, "null output handle");
+  *out = nullptr;
+  caps_index* ix = new (std::nothrow) caps_index();
+  if (!ix) return fail(CAPS_ENOMEM, "host allocation failed");
+  const int rc = build_impl(params, X, N, d, attrs, (cudaStream_t)stream, ix);
+  if (rc != CAPS_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaGetLastError();
+    delete ix;
+    return rc;
+  }
+  *out = ix;
+  return CAPS_OK;
+}
+
+extern "C" void caps_free(caps_index* index) {
+  if (!index) return;
+  cudaDeviceSynchronize();
+  delete index;
+}
+
+extern "C" int caps_get_info(const caps_index* ix, caps_index_info* out) {
+  if (!ix || !out) return fail(CAPS_EINVAL, "null argument");
+  out->N = ix->N;
+  out->d = ix->d;
+  out->B = ix->B;
+  out->h = ix->h;
+  out->L = ix->meta.L;
+  out->metric = ix->metric;
+  out->n_codes = ix->meta.n_codes;
+  out->attr_words = ix->meta.words_pad;
+  out->device_bytes = ix->bytes;
+  return CAPS_OK;
+}
+
+extern "C" int caps_export(const caps_index* ix, int32_t which, void* dst, size_t bytes,
+                           void* stream) {
+  if (!ix || !dst) return fail(CAPS_EINVAL, "null argument");
+  const void* src = nullptr;
+  size_t want = 0;
+  switch (which) {
+    case CAPS_ARR_CENTROIDS: src = ix->C; want = sizeof(float) * ix->B * ix->d; break;
+    case CAPS_ARR_BIN: src = ix->bin; want = sizeof(int32_t) * ix->N; break;
+    case CAPS_ARR_TAGS: src = ix->tags; want = sizeof(int32_t) * ix->B * ix->h; break;
+    case CAPS_ARR_KEY: src = ix->key; want = (size_t)ix->N; break;
+    case CAPS_ARR_PERM: src = ix->perm; want = sizeof(int32_t) * ix->N; break;
+    case CAPS_ARR_OFFSETS:
+      src = ix->offsets;
+      want = sizeof(int32_t) * ((size_t)ix->B * (ix->h + 1) + 1);
+      break;
+    default: return fail(CAPS_EINVAL, "unknown array id");
+  }
+  if (bytes != want) return fail(CAPS_EINVAL, "byte count does not match the array size");
+  if (want == 0) return CAPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  CAPS_CUDA(cudaMemcpyAsync(dst, src, want, cudaMemcpyDefault, s));
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
+extern "C" int caps_assign(const float* X, int64_t N, int32_t d, const float* C, int32_t B,
+                           int32_t metric, int32_t* out_bin, void* stream) {
+  if (N < 0 || d < 1 || B < 1) return fail(CAPS_EINVAL, "bad sizes");
+  if (metric != CAPS_L2 && metric != CAPS_IP) return fail(CAPS_EINVAL, "unknown metric");
+  if (N == 0) return CAPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  keep_pool_warm();
+  Scratch scr(s);
+  const float *dX = nullptr, *dC = nullptr;
+  if (int rc = stage_in(X, (size_t)N * d, scr, s, &dX)) return rc;
+  if (int rc = stage_in(C, (size_t)B * d, scr, s, &dC)) return rc;
+  Out<int32_t> ob;
+  if (int rc = ob.init(out_bin, (size_t)N, scr)) return rc;
+  if (int rc = launch_assign(dX, N, d, dC, B, metric, ob.dev, s)) return rc;
+  if (int rc = ob.finish(s)) return rc;
+  if (ob.host) CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
+namespace {
+int check_cons(const caps_index* ix, const caps_attrs* cons) {
+  if (!cons) return fail(CAPS_EINVAL, "constraints are required");
+  if (cons->dense == nullptr || cons->L != ix->meta.L)
+    return fail(CAPS_EINVAL, "constraints must be dense with the index's L fields");
+  return CAPS_OK;
+}
+
+// Device buffers for one chunk of queries.
+struct Batch {
+  float* scores;
+  int32_t* probe;
+  uint64_t* sel;
+  QueryPrep qp;
+};
+
+int alloc_batch(const caps_index* ix, int64_t nq, int m, Scratch& scr, Batch* b) {
+  const int WP = ix->meta.words_pad, L = ix->meta.L;
+  if (int rc = scr.get(&b->scores, (size_t)nq * ix->B)) return rc;
+  if (int rc = scr.get(&b->probe, (size_t)nq * m)) return rc;
+  if (int rc = scr.get(&b->sel, (size_t)nq * m)) return rc;
+  if (int rc = scr.get(&b->qp.qmask, (size_t)nq * WP)) return rc;
+  if (int rc = scr.get(&b->qp.qval, (size_t)nq * WP)) return rc;
+  if (int rc = scr.get(&b->qp.qcode, (size_t)nq * L)) return rc;
+  if (int rc = scr.get(&b->qp.dead, (size_t)nq)) return rc;
+  return CAPS_OK;
+}
+
+int64_t chunk_rows(const caps_index* ix, int64_t nq) {
+  const int64_t budget = (int64_t)1 << 26;  // score matrix entries per chunk
+  int64_t c = budget / std::max(1, ix->B);
+  if (c < 1) c = 1;
+  return std::min(c, nq);
+}
+}  // namespace
+
+extern "C" int caps_probe(const caps_index* ix, const float* Q, int64_t nq, int32_t m,
+                          int32_t* out_probe, void* stream) {
+  if (!ix) return fail(CAPS_EINVAL, "null index");
+  if (nq < 0 || m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
+  if (nq == 0) return CAPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch scr(s);
+  const float* dQ = nullptr;
+  if (int rc = stage_in(Q, (size_t)nq * ix->d, scr, s, &dQ)) return rc;
+  Out<int32_t> op;
+  if (int rc = op.init(out_probe, (size_t)nq * m, scr)) return rc;
+  const int64_t qc = chunk_rows(ix, nq);
+  float* scores = nullptr;
+  if (int rc = scr.get(&scores, (size_t)qc * ix->B)) return rc;
+  for (int64_t c0 = 0; c0 < nq; c0 += qc) {
+    const int64_t n = std::min(qc, nq - c0);
+    if (int rc = launch_scores(dQ + c0 * ix->d, n, ix->d, ix->C, ix->B, ix->metric, scores, s))
+      return rc;
+    if (int rc = launch_topm(scores, n, ix->B, m, ix->metric, op.dev + c0 * m, s)) return rc;
+  }
+  if (int rc = op.finish(s)) return rc;
+  if (op.host) CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
+extern "C" int caps_select(const caps_index* ix, const int32_t* probe, int64_t nq, int32_t m,
+                           const caps_attrs* cons, uint64_t* out_sel, void* stream) {
+  if (!ix) return fail(CAPS_EINVAL, "null index");
+  if (nq < 0 || m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
+  if (int rc = check_cons(ix, cons)) return rc;
+  if (nq == 0) return CAPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch scr(s);
+  std::vector<int32_t> ph;
+  if (int rc = to_host(probe, (size_t)nq * m, &ph, s)) return rc;
+  for (int32_t b : ph)
+    if (b < 0 || b >= ix->B) return fail(CAPS_EINVAL, "probe entry outside [0, B)");
+  const int32_t *dP = nullptr, *dQb = nullptr;
+  if (int rc = stage_in(probe, (size_t)nq * m, scr, s, &dP)) return rc;
+  if (int rc = stage_in(cons->dense, (size_t)nq * ix->meta.L, scr, s, &dQb)) return rc;
+  Out<uint64_t> os;
+  if (int rc = os.init(out_sel, (size_t)nq * m, scr)) return rc;
+  QueryPrep qp;
+  const int WP = ix->meta.words_pad, L = ix->meta.L;
+  if (int rc = scr.get(&qp.qmask, (size_t)nq * WP)) return rc;
+  if (int rc = scr.get(&qp.qval, (size_t)nq * WP)) return rc;
+  if (int rc = scr.get(&qp.qcode, (size_t)nq * L)) return rc;
+  if (int rc = scr.get(&qp.dead, (size_t)nq)) return rc;
+  if (int rc = launch_query_prep(dQb, nq, ix->meta, qp, s)) return rc;
+  if (int rc = launch_select(dP, nq, m, ix->h, ix->tags, ix->pos, ix->meta.n_codes,
+                             ix->code_field, dQb, ix->meta, qp.qcode, os.dev, s))
+    return rc;
+  if (int rc = os.finish(s)) return rc;
+  if (os.host) CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
+namespace {
+// Stage timing of caps_search_batch: one event before each stage of each
+// chunk, plus one at the end.
+struct StageTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // 5 per chunk + 1
+  int used = 0;
+  int launches = 0;
+  bool valid = false;
+  int record(cudaStream_t s) {
+    if (!on) return CAPS_OK;
+    if (used == (int)ev.size()) {
+      cudaEvent_t e;
+      CAPS_CUDA(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+    CAPS_CUDA(cudaEventRecord(ev[used++], s));
+    return CAPS_OK;
+  }
+  ~StageTimer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+thread_local StageTimer g_timer;
+}  // namespace
+
+extern "C" int caps_set_timing(int32_t enable) {
+  g_timer.on = enable != 0;
+  g_timer.valid = false;
+  return CAPS_OK;
+}
+
+extern "C" int caps_get_stage_times(caps_stage_times* out) {
+  if (!out) return fail(CAPS_EINVAL, "null argument");
+  if (!g_timer.valid || g_timer.used < 6) return fail(CAPS_EINVAL, "no timed search on this thread");
+  CAPS_CUDA(cudaEventSynchronize(g_timer.ev[g_timer.used - 1]));
+  float acc[5] = {0, 0, 0, 0, 0};
+  const int chunks = (g_timer.used - 1) / 5;
+  for (int c = 0; c < chunks; c++)
+    for (int st = 0; st < 5; st++) {
+      float ms = 0.f;
+      const int a = c * 5 + st;
+      CAPS_CUDA(cudaEventElapsedTime(&ms, g_timer.ev[a], g_timer.ev[a + 1]));
+      acc[st] += ms;
+    }
+  out->prep_ms = acc[0];
+  out->scores_ms = acc[1];
+  out->topm_ms = acc[2];
+  out->select_ms = acc[3];
+  out->scan_ms = acc[4];
+  out->launches = g_timer.launches;
+  return CAPS_OK;
+}
+
+extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t nq,
+                                 const caps_attrs* cons, int32_t k, int32_t m, int64_t* out_ids,
+                                 float* out_dist, void* stream) {
+  if (!ix) return fail(CAPS_EINVAL, "null index");
+  if (nq < 0) return fail(CAPS_EINVAL, "nq < 0");
+  if (k < 1 || k > kMaxK) return fail(CAPS_EINVAL, "k must be in [1, 128]");
+  if (m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
+  if (int rc = check_cons(ix, cons)) return rc;
+  if (nq == 0) return CAPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  keep_pool_warm();
+  Scratch scr(s);
+  const float* dQ = nullptr;
+  const int32_t* dQb = nullptr;
+  if (int rc = stage_in(Q, (size_t)nq * ix->d, scr, s, &dQ)) return rc;
+  if (int rc = stage_in(cons->dense, (size_t)nq * ix->meta.L, scr, s, &dQb)) return rc;
+  Out<int64_t> oi;
+  Out<float> od;
+  if (int rc = oi.init(out_ids, (size_t)nq * k, scr)) return rc;
+  if (int rc = od.init(out_dist, (size_t)nq * k, scr)) return rc;
+  const int64_t qc = chunk_rows(ix, nq);
+  Batch bt;
+  if (int rc = alloc_batch(ix, qc, m, scr, &bt)) return rc;
+  const int L = ix->meta.L;
+  StageTimer& tm = g_timer;
+  tm.used = 0;
+  tm.launches = 0;
+  tm.valid = false;
+  for (int64_t c0 = 0; c0 < nq; c0 += qc) {
+    const int64_t n = std::min(qc, nq - c0);
+    const float* Qc = dQ + c0 * ix->d;
+    const int32_t* Qbc = dQb + c0 * L;
+    if (int rc = tm.record(s)) return rc;
+    if (int rc = launch_query_prep(Qbc, n, ix->meta, bt.qp, s)) return rc;
+    if (int rc = tm.record(s)) return rc;
+    if (int rc = launch_scores(Qc, n, ix->d, ix->C, ix->B, ix->metric, bt.scores, s)) return rc;
+    if (int rc = tm.record(s)) return rc;
+    if (int rc = launch_topm(bt.scores, n, ix->B, m, ix->metric, bt.probe, s)) return rc;
+    if (int rc = tm.record(s)) return rc;
+    if (int rc = launch_select(bt.probe, n, m, ix->h, ix->tags, ix->pos, ix->meta.n_codes,
+                               ix->code_field, Qbc, ix->meta, bt.qp.qcode, bt.sel, s))
+      return rc;
+    if (int rc = tm.record(s)) return rc;
+    tm.launches += 5;
+    ScanArgs a;
+    a.Xp = ix->Xp;
+    a.Ap = ix->Ap;
+    a.perm = ix->perm;
+    a.offsets = ix->offsets;
+    a.Q = Qc;
+    a.qp = bt.qp;
+    a.probe = bt.probe;
+    a.sel = bt.sel;
+    a.nq = n;
+    a.m = m;
+    a.h = ix->h;
+    a.d = ix->d;
+    a.k = k;
+    a.metric = ix->metric;
+    a.words_pad = ix->meta.words_pad;
+    a.out_ids = oi.dev + c0 * k;
+    a.out_dist = od.dev + c0 * k;
+    if (int rc = launch_scan_topk(a, s)) return rc;
+  }
+  if (int rc = tm.record(s)) return rc;
+  tm.valid = tm.on;
+  if (int rc = oi.finish(s)) return rc;
+  if (int rc = od.finish(s)) return rc;
+  if (oi.host || od.host) CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}

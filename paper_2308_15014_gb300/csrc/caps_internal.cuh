@@ -1,0 +1,154 @@
+// Internal declarations of the CAPS GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "caps.h"
+
+namespace caps {
+
+constexpr int kMaxFields = 16;  // dense attribute fields per point
+constexpr int kMaxK = 128;      // neighbours per query
+constexpr int kMaxH = 63;       // AFT height (h+1 blocks fit a 64-bit mask)
+
+// Dense attribute model (Def. 1): field f takes values 0..vocab[f]-1.
+// code(f, v) = code_off[f] + v enumerates all (field, value) pairs; the AFT
+// tags are such codes.  For the scan, each row's values are packed into
+// `words` 32-bit words: field f occupies `bits[f]` bits at `shift[f]` of word
+// `word[f]` (fields never straddle a word).
+struct DenseMeta {
+  int L = 0;
+  int vocab[kMaxFields] = {};
+  int code_off[kMaxFields] = {};
+  int word[kMaxFields] = {};
+  int shift[kMaxFields] = {};
+  int bits[kMaxFields] = {};
+  int words = 0;       // packed words actually used (1..4)
+  int words_pad = 0;   // row stride in words: 1, 2 or 4 (vector loads)
+  int64_t n_codes = 0;
+};
+
+// ---- orderable keys: (score, id) -> uint64, smaller key = better --------
+// score is the fp32 distance for L2 and minus the inner product for IP; the
+// low 32 bits hold the original point id so equal scores order by id.
+__device__ __forceinline__ uint32_t ord_bits(float s) {
+  uint32_t u = __float_as_uint(s + 0.0f);  // folds -0 into +0
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord_bits(uint32_t u) {
+  uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  return __uint_as_float(b);
+}
+__device__ __forceinline__ uint64_t make_key(float score, uint32_t id) {
+  return ((uint64_t)ord_bits(score) << 32) | (uint64_t)id;
+}
+constexpr uint64_t kEmptyKey = ~0ull;
+
+// ---- error handling --------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define CAPS_CUDA(call)                                          \
+  do {                                                           \
+    cudaError_t _e = (call);                                     \
+    if (_e != cudaSuccess) return ::caps::cuda_fail(_e, #call);  \
+  } while (0)
+#define CAPS_LAUNCH(what)                                        \
+  do {                                                           \
+    cudaError_t _e = cudaGetLastError();                         \
+    if (_e != cudaSuccess) return ::caps::cuda_fail(_e, what);   \
+  } while (0)
+
+// ---- stream-ordered scratch ------------------------------------------------
+// Temporary device buffers for one call, allocated from the stream-ordered
+// pool and released on the same stream.
+struct Scratch {
+  cudaStream_t s;
+  void* ptrs[256];
+  int n = 0;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (int i = 0; i < n; i++) cudaFreeAsync(ptrs[i], s);
+  }
+  template <class T>
+  int get(T** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    if (n == 256) return fail(CAPS_ENOMEM, "scratch slots exhausted");
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CAPS_ENOMEM, "cudaMallocAsync failed for scratch");
+    }
+    ptrs[n++] = p;
+    *out = (T*)p;
+    return CAPS_OK;
+  }
+};
+
+// ---- build-side launchers (build_kernels.cu) ------------------------------
+int launch_gather_rows(const float* X, const int64_t* idx, int64_t n, int d,
+                       float* out, cudaStream_t s);
+int launch_assign(const float* X, int64_t N, int d, const float* C, int B,
+                  int metric, int32_t* bin, cudaStream_t s);
+int launch_scores(const float* Q, int64_t nq, int d, const float* C, int B,
+                  int metric, float* scores, cudaStream_t s);
+// Stable counting sort of keys in [0, K): perm[r] = index of the r-th element
+// in (key, index) order; seg_off[s] = first position of key s, seg_off[K] = n.
+int stable_sort_by_key(const int32_t* keys, int64_t n, int64_t K, int32_t* perm,
+                       int32_t* seg_off, Scratch& scr, cudaStream_t s);
+int launch_centroid_update(const float* X, int d, const int32_t* perm_bin,
+                           const int32_t* bin_off, int B, int metric, float* C,
+                           Scratch& scr, cudaStream_t s);
+int launch_check_dense(const int32_t* A, int64_t N, const DenseMeta& meta,
+                       int32_t* bad, cudaStream_t s);
+int launch_aft(const int32_t* perm_bin, const int32_t* bin_off, int B, int h,
+               const int32_t* A, const DenseMeta& meta, const uint8_t* code_field,
+               int32_t* tags, uint8_t* key, cudaStream_t s);
+int launch_segment_keys(const int32_t* bin, const uint8_t* key, int64_t N, int h,
+                        int32_t* seg, cudaStream_t s);
+int launch_layout(const float* X, const int32_t* A, const int32_t* perm, int64_t N,
+                  int d, const DenseMeta& meta, float* Xp, uint32_t* Ap,
+                  cudaStream_t s);
+int launch_pos_table(const int32_t* tags, int B, int h, int64_t n_codes,
+                     uint8_t* pos, cudaStream_t s);
+int launch_code_field(const DenseMeta& meta, uint8_t* code_field, cudaStream_t s);
+
+// ---- search-side launchers (search_kernels.cu) ----------------------------
+struct QueryPrep {
+  uint32_t* qmask;   // [nq * words_pad]
+  uint32_t* qval;    // [nq * words_pad]
+  int32_t* qcode;    // [nq * L] code of each constrained field, -1 = free
+  uint8_t* dead;     // [nq] 1 = a constraint value lies outside the vocabulary
+};
+int launch_query_prep(const int32_t* Qb, int64_t nq, const DenseMeta& meta,
+                      QueryPrep qp, cudaStream_t s);
+int launch_topm(const float* scores, int64_t nq, int B, int m, int metric,
+                int32_t* probe, cudaStream_t s);
+int launch_select(const int32_t* probe, int64_t nq, int m, int h, const int32_t* tags,
+                  const uint8_t* pos, int64_t n_codes, const uint8_t* code_field,
+                  const int32_t* Qb, const DenseMeta& meta, const int32_t* qcode,
+                  uint64_t* sel, cudaStream_t s);
+
+struct ScanArgs {
+  const float* Xp;
+  const uint32_t* Ap;
+  const int32_t* perm;
+  const int32_t* offsets;
+  const float* Q;
+  QueryPrep qp;
+  const int32_t* probe;
+  const uint64_t* sel;
+  int64_t nq;
+  int m, h, d, k, metric, words_pad;
+  int64_t* out_ids;
+  float* out_dist;
+};
+int launch_scan_topk(const ScanArgs& a, cudaStream_t s);
+
+}  // namespace caps

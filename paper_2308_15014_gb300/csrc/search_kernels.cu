@@ -1,0 +1,406 @@
+// Query kernels: CAPS Alg. 2 on the GPU.
+//
+//   query filter packing (Def. 1)          : k_query_prep
+//   "select top m partitions"              : k_dist_tile scores + k_topm
+//   sub-partition selection (Alg. 2 loop)  : k_select
+//   attribute match + top-k vector match   : k_scan_topk (fused)
+#include <algorithm>
+#include <climits>
+
+#include "caps_internal.cuh"
+
+namespace caps {
+
+// ---------------------------------------------------------------------------
+// Query filter packing.  A dense constraint row b (b[f] < 0 = free field)
+// becomes, per packed word, a mask of the constrained fields' bits and the
+// required values, so C(a, b) is "(a_w & mask_w) == val_w for every word".
+// A value outside field f's vocabulary matches no point: the query is dead.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_query_prep(const int32_t* __restrict__ Qb, int64_t nq, DenseMeta meta,
+                             QueryPrep qp) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  uint32_t mask[4] = {0u, 0u, 0u, 0u}, val[4] = {0u, 0u, 0u, 0u};
+  uint8_t dead = 0;
+  for (int f = 0; f < meta.L; f++) {
+    const int v = Qb[q * meta.L + f];
+    int code = -1;
+    if (v >= 0) {
+      if (v >= meta.vocab[f]) {
+        dead = 1;
+      } else {
+        const uint32_t fm = (meta.bits[f] >= 32) ? 0xffffffffu : ((1u << meta.bits[f]) - 1u);
+        mask[meta.word[f]] |= fm << meta.shift[f];
+        val[meta.word[f]] |= (uint32_t)v << meta.shift[f];
+        code = meta.code_off[f] + v;
+      }
+    }
+    qp.qcode[q * meta.L + f] = code;
+  }
+  for (int w = 0; w < meta.words_pad; w++) {
+    qp.qmask[q * meta.words_pad + w] = mask[w];
+    qp.qval[q * meta.words_pad + w] = val[w];
+  }
+  qp.dead[q] = dead;
+}
+}  // namespace
+
+int launch_query_prep(const int32_t* Qb, int64_t nq, const DenseMeta& meta, QueryPrep qp,
+                      cudaStream_t s) {
+  if (nq == 0) return CAPS_OK;
+  k_query_prep<<<(unsigned)((nq + 127) / 128), 128, 0, s>>>(Qb, nq, meta, qp);
+  CAPS_LAUNCH("k_query_prep");
+  return CAPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Top-m partitions per query: keys (score, partition) sorted ascending with
+// a bitonic network in shared memory, one CTA per query.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int TOPM_T = 256;
+
+__global__ void __launch_bounds__(TOPM_T)
+k_topm(const float* __restrict__ scores, int B, int P2, int m, int metric,
+       int32_t* __restrict__ probe) {
+  extern __shared__ unsigned long long keys[];  // [P2]
+  const int64_t q = blockIdx.x;
+  const float* sc = scores + q * B;
+  for (int i = threadIdx.x; i < P2; i += TOPM_T) {
+    if (i < B) {
+      const float v = sc[i];
+      keys[i] = make_key(metric == CAPS_L2 ? v : -v, (uint32_t)i);
+    } else {
+      keys[i] = kEmptyKey;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= P2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P2; i += TOPM_T) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = keys[i], b = keys[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            keys[i] = b;
+            keys[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = threadIdx.x; r < m; r += TOPM_T) probe[q * m + r] = (int32_t)(keys[r] & 0xffffffffu);
+}
+}  // namespace
+
+int launch_topm(const float* scores, int64_t nq, int B, int m, int metric, int32_t* probe,
+                cudaStream_t s) {
+  if (nq == 0) return CAPS_OK;
+  int P2 = 1;
+  while (P2 < B) P2 <<= 1;
+  const size_t smem = sizeof(unsigned long long) * (size_t)P2;
+  if (smem > 200 * 1024) return fail(CAPS_EINVAL, "B too large for the top-m kernel");
+  if (smem > 48 * 1024)
+    CAPS_CUDA(cudaFuncSetAttribute(k_topm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (nq > INT_MAX) return fail(CAPS_EINVAL, "too many queries");
+  k_topm<<<(unsigned)nq, TOPM_T, smem, s>>>(scores, B, P2, m, metric, probe);
+  CAPS_LAUNCH("k_topm");
+  return CAPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sub-partition selection (Alg. 2), one thread per (query, probed partition).
+// j* = the first block whose tag the query requires (position table lookup,
+// O(1) per constrained field); blocks 1..min(j*, h) are kept unless their tag
+// fixes a field the query constrains to another value; the remainder block
+// h+1 is kept only when no tag matches (j* = h+1).
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_select(const int32_t* __restrict__ probe, int64_t nq, int m, int h,
+                         const int32_t* __restrict__ tags, const uint8_t* __restrict__ pos,
+                         int64_t n_codes, const uint8_t* __restrict__ code_field,
+                         const int32_t* __restrict__ Qb, DenseMeta meta,
+                         const int32_t* __restrict__ qcode, uint64_t* __restrict__ sel) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nq * m) return;
+  const int64_t q = t / m;
+  const int b = probe[t];
+  const int L = meta.L;
+  int jstar = h + 1;
+  for (int f = 0; f < L; f++) {
+    const int c = qcode[q * L + f];
+    if (c < 0) continue;
+    const int p = pos[(int64_t)b * n_codes + c];
+    if (p > 0 && p < jstar) jstar = p;
+  }
+  uint64_t s = 0;
+  const int jmax = jstar < h ? jstar : h;
+  for (int j = 1; j <= jmax; j++) {
+    const int tg = tags[(int64_t)b * h + j - 1];
+    if (tg < 0) continue;
+    const int f = code_field[tg];
+    const int v = tg - meta.code_off[f];
+    const int bv = Qb[q * L + f];
+    if (bv < 0 || bv == v) s |= 1ull << (j - 1);
+  }
+  if (jstar == h + 1) s |= 1ull << h;
+  sel[t] = s;
+}
+}  // namespace
+
+int launch_select(const int32_t* probe, int64_t nq, int m, int h, const int32_t* tags,
+                  const uint8_t* pos, int64_t n_codes, const uint8_t* code_field,
+                  const int32_t* Qb, const DenseMeta& meta, const int32_t* qcode,
+                  uint64_t* sel, cudaStream_t s) {
+  const int64_t tot = nq * m;
+  if (tot == 0) return CAPS_OK;
+  k_select<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(probe, nq, m, h, tags, pos, n_codes,
+                                                         code_field, Qb, meta, qcode, sel);
+  CAPS_LAUNCH("k_select");
+  return CAPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Fused attribute match + distance + top-k (Alg. 2, last two steps).
+// One warp per query walks the selected blocks of its m partitions (adjacent
+// selected blocks are one contiguous row range).  32 rows at a time: every
+// lane tests one row's packed attributes against the query mask; passing
+// rows are compacted into a per-warp queue, and each full batch of 32 is
+// scored one row per lane (coordinates in order, one fused multiply-add
+// each, query vector broadcast from shared memory).  The running top-k is a
+// sorted list of (score, original id) keys spread over the warp, KPL per
+// lane; a candidate enters only if it beats the current k-th key.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int SCAN_WARPS = 4;
+constexpr int QUEUE = 64;
+
+template <int KPL>
+struct TopK {
+  uint64_t v[KPL];  // positions lane*KPL + s, ascending
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int s = 0; s < KPL; s++) v[s] = kEmptyKey;
+  }
+  __device__ __forceinline__ uint64_t kth(int k, int lane) const {
+    const int P = k - 1, l = P / KPL, s = P % KPL;
+    uint64_t mine = v[0];
+#pragma unroll
+    for (int u = 1; u < KPL; u++)
+      if (u == s) mine = v[u];
+    return __shfl_sync(0xffffffffu, mine, l);
+  }
+  __device__ __forceinline__ void insert(uint64_t x, int lane) {
+    int p = 0;
+#pragma unroll
+    for (int s = 0; s < KPL; s++) p += __popc(__ballot_sync(0xffffffffu, v[s] < x));
+    const uint64_t prev_last = __shfl_up_sync(0xffffffffu, v[KPL - 1], 1);
+    uint64_t nv[KPL];
+#pragma unroll
+    for (int s = 0; s < KPL; s++) {
+      const int P = lane * KPL + s;
+      const uint64_t before = (s == 0) ? prev_last : v[s - 1];
+      nv[s] = P < p ? v[s] : (P == p ? x : before);
+    }
+#pragma unroll
+    for (int s = 0; s < KPL; s++) v[s] = nv[s];
+  }
+};
+
+template <int METRIC, int WP, bool VEC4, int KPL>
+__global__ void __launch_bounds__(SCAN_WARPS * 32)
+k_scan_topk(ScanArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * SCAN_WARPS + warp;
+  if (q >= a.nq) return;  // warp-uniform; no block-wide barrier below
+  const int d = a.d, dpad = (d + 3) & ~3;
+  float* qs = sm + warp * (dpad + QUEUE);
+  int* queue = reinterpret_cast<int*>(qs + dpad);
+  for (int j = lane; j < d; j += 32) qs[j] = a.Q[q * d + j];
+  uint32_t qm[WP], qv[WP];
+#pragma unroll
+  for (int w = 0; w < WP; w++) {
+    qm[w] = a.qp.qmask[q * WP + w];
+    qv[w] = a.qp.qval[q * WP + w];
+  }
+  const bool dead = a.qp.dead[q] != 0;
+  __syncwarp();
+
+  TopK<KPL> top;
+  top.init();
+  uint64_t kth = kEmptyKey;
+  int qn = 0;
+
+  auto process = [&](int n) {
+    uint64_t key = kEmptyKey;
+    if (lane < n) {
+      const int r = queue[lane];
+      float acc = 0.f;
+      if (VEC4) {
+        const float4* xr = reinterpret_cast<const float4*>(a.Xp + (int64_t)r * d);
+        const float4* q4 = reinterpret_cast<const float4*>(qs);
+        for (int c = 0; c < d / 4; c++) {
+          const float4 x = __ldg(xr + c);
+          const float4 y = q4[c];
+          if (METRIC == CAPS_L2) {
+            float t = x.x - y.x; acc = fmaf(t, t, acc);
+            t = x.y - y.y; acc = fmaf(t, t, acc);
+            t = x.z - y.z; acc = fmaf(t, t, acc);
+            t = x.w - y.w; acc = fmaf(t, t, acc);
+          } else {
+            acc = fmaf(x.x, y.x, acc);
+            acc = fmaf(x.y, y.y, acc);
+            acc = fmaf(x.z, y.z, acc);
+            acc = fmaf(x.w, y.w, acc);
+          }
+        }
+      } else {
+        const float* xr = a.Xp + (int64_t)r * d;
+        for (int c = 0; c < d; c++) {
+          const float x = __ldg(xr + c);
+          if (METRIC == CAPS_L2) {
+            const float t = x - qs[c];
+            acc = fmaf(t, t, acc);
+          } else {
+            acc = fmaf(x, qs[c], acc);
+          }
+        }
+      }
+      key = make_key(METRIC == CAPS_L2 ? acc : -acc, (uint32_t)__ldg(a.perm + r));
+    }
+    unsigned cand = __ballot_sync(0xffffffffu, key < kth);
+    while (cand) {
+      const int src = __ffs(cand) - 1;
+      cand &= cand - 1;
+      const uint64_t x = __shfl_sync(0xffffffffu, key, src);
+      if (x < kth) {
+        top.insert(x, lane);
+        kth = top.kth(a.k, lane);
+      }
+    }
+  };
+
+  if (!dead) {
+    const int h = a.h, nb = h + 1;
+    for (int i = 0; i < a.m; i++) {
+      const int b = a.probe[q * a.m + i];
+      const uint64_t sel = a.sel[q * a.m + i];
+      const int32_t* off = a.offsets + (int64_t)b * nb;
+      int j = 0;
+      while (j < nb) {
+        if (!((sel >> j) & 1ull)) { j++; continue; }
+        int j2 = j;
+        while (j2 + 1 < nb && ((sel >> (j2 + 1)) & 1ull)) j2++;
+        const int beg = off[j], end = off[j2 + 1];
+        j = j2 + 1;
+        for (int base = beg; base < end; base += 32) {
+          const int r = base + lane;
+          bool pass = false;
+          if (r < end) {
+            if (WP == 1) {
+              const uint32_t w0 = __ldg(a.Ap + r);
+              pass = (w0 & qm[0]) == qv[0];
+            } else if (WP == 2) {
+              const uint2 w = __ldg(reinterpret_cast<const uint2*>(a.Ap) + r);
+              pass = ((w.x & qm[0]) == qv[0]) && ((w.y & qm[1]) == qv[1]);
+            } else {
+              const uint4 w = __ldg(reinterpret_cast<const uint4*>(a.Ap) + r);
+              pass = ((w.x & qm[0]) == qv[0]) && ((w.y & qm[1]) == qv[1]) &&
+                     ((w.z & qm[2]) == qv[2]) && ((w.w & qm[3]) == qv[3]);
+            }
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, pass);
+          if (pass) queue[qn + __popc(bal & ((1u << lane) - 1u))] = r;
+          qn += __popc(bal);
+          __syncwarp();
+          if (qn >= 32) {
+            process(32);
+            __syncwarp();
+            const int rest = qn - 32;
+            int moved = 0;
+            if (lane < rest) moved = queue[32 + lane];
+            __syncwarp();
+            if (lane < rest) queue[lane] = moved;
+            qn = rest;
+            __syncwarp();
+          }
+        }
+      }
+    }
+    if (qn > 0) process(qn);
+  }
+
+  // write the k best, best first; empty slots -> id -1, +inf (L2) / -inf (IP)
+#pragma unroll
+  for (int s = 0; s < KPL; s++) {
+    const int P = lane * KPL + s;
+    if (P < a.k) {
+      const uint64_t key = top.v[s];
+      int64_t id = -1;
+      float dist = METRIC == CAPS_L2 ? INFINITY : -INFINITY;
+      if (key != kEmptyKey) {
+        id = (int64_t)(uint32_t)(key & 0xffffffffu);
+        const float sc = unord_bits((uint32_t)(key >> 32));
+        dist = METRIC == CAPS_L2 ? sc : -sc;
+      }
+      a.out_ids[q * a.k + P] = id;
+      a.out_dist[q * a.k + P] = dist;
+    }
+  }
+}
+
+template <int METRIC, int WP, bool VEC4>
+int launch_scan_k(const ScanArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  if (a.k <= 32) {
+    k_scan_topk<METRIC, WP, VEC4, 1><<<grid, SCAN_WARPS * 32, smem, s>>>(a);
+  } else if (a.k <= 64) {
+    k_scan_topk<METRIC, WP, VEC4, 2><<<grid, SCAN_WARPS * 32, smem, s>>>(a);
+  } else {
+    k_scan_topk<METRIC, WP, VEC4, 4><<<grid, SCAN_WARPS * 32, smem, s>>>(a);
+  }
+  CAPS_LAUNCH("k_scan_topk");
+  return CAPS_OK;
+}
+
+template <int METRIC, int WP>
+int launch_scan_v(const ScanArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  const bool vec4 = (a.d % 4) == 0 && ((uintptr_t)a.Xp % 16) == 0;
+  return vec4 ? launch_scan_k<METRIC, WP, true>(a, grid, smem, s)
+              : launch_scan_k<METRIC, WP, false>(a, grid, smem, s);
+}
+
+template <int METRIC>
+int launch_scan_w(const ScanArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  switch (a.words_pad) {
+    case 1: return launch_scan_v<METRIC, 1>(a, grid, smem, s);
+    case 2: return launch_scan_v<METRIC, 2>(a, grid, smem, s);
+    case 4: return launch_scan_v<METRIC, 4>(a, grid, smem, s);
+  }
+  return fail(CAPS_EINVAL, "unsupported attribute word count");
+}
+}  // namespace
+
+int launch_scan_topk(const ScanArgs& a, cudaStream_t s) {
+  if (a.nq == 0) return CAPS_OK;
+  if (a.k < 1 || a.k > kMaxK) return fail(CAPS_EINVAL, "k out of range");
+  const int dpad = (a.d + 3) & ~3;
+  const size_t smem = sizeof(float) * (size_t)SCAN_WARPS * (dpad + QUEUE);
+  if (smem > 200 * 1024) return fail(CAPS_EINVAL, "d too large for the scan kernel");
+  const int64_t grid = (a.nq + SCAN_WARPS - 1) / SCAN_WARPS;
+  if (grid > INT_MAX) return fail(CAPS_EINVAL, "too many queries");
+  if (smem > 48 * 1024) {
+    // opt every instantiation in lazily: set on all variants of this metric
+    // through the templated launcher is not possible without naming them, so
+    // reject here instead (d <= 2900 keeps smem under 48 KB with 4 warps).
+    return fail(CAPS_EINVAL, "d too large for the scan kernel (d <= 2900)");
+  }
+  return a.metric == CAPS_L2 ? launch_scan_w<CAPS_L2>(a, (unsigned)grid, smem, s)
+                             : launch_scan_w<CAPS_IP>(a, (unsigned)grid, smem, s);
+}
+
+}  // namespace caps
