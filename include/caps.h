@@ -211,6 +211,40 @@ int caps_select(const caps_index* index, const int32_t* probe, int64_t nq,
                 int32_t m, const caps_attrs* constraints, uint64_t* out_sel,
                 void* stream);
 
+/* ---- batched query without device allocation ------------------------------ */
+
+/*
+ * caps_search_batch_noalloc -- the same batched query as caps_search_batch
+ * (same arguments, same results), for callers that cannot allocate device
+ * memory: a process whose device memory is reserved up front by another
+ * framework, a serving loop that must never wait on the allocator or on the
+ * device-wide synchronisation that freeing implies, or an integration that
+ * forbids allocator calls after start-up.  The paper has no counterpart;
+ * this is a property of the library, not of the method.
+ *
+ * The call makes no cudaMalloc, cudaMallocAsync or cudaFree call and no
+ * allocating library call.  Its intermediates live in one fixed 16 MiB
+ * device array compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  Batches that need more run in
+ * several passes over that array; the call returns CAPS_EINVAL when even one
+ * query does not fit (about 4*B + 12*m + 4*L + 33 bytes per query, i.e.
+ * B up to about 4 million).
+ *   - Q, constraints->dense, out_ids and out_dist must be device memory of
+ *     the current device (host memory would need a staging allocation):
+ *     CAPS_EINVAL otherwise.  The call only enqueues work on `stream`.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and it keeps the previous
+ *     call's contents (nothing in it has to start at zero).  Calls that
+ *     overlap on the GPU -- on different streams, or from different threads
+ *     without ordering -- race on it and corrupt each other's results.
+ */
+int caps_search_batch_noalloc(const caps_index* index, const float* Q,
+                              int64_t nq, const caps_attrs* constraints,
+                              int32_t k, int32_t m, int64_t* out_ids,
+                              float* out_dist, void* stream);
+
 /* ---- stage timing (measurement aid, off by default) ---------------------- */
 
 /* Per-stage device time of the last caps_search_batch call made on this

@@ -26,7 +26,7 @@ ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS = range(6)
 # Every symbol declared in include/caps.h.
 EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "caps_get_info",
            "caps_export", "caps_assign", "caps_probe", "caps_select", "caps_set_timing",
-           "caps_get_stage_times")
+           "caps_get_stage_times", "caps_search_batch_noalloc")
 
 
 class CapsError(RuntimeError):
@@ -83,6 +83,8 @@ def lib(path: Optional[str] = None):
     L.caps_assign.argtypes = [P, i64, i32, P, i32, i32, P, P]
     L.caps_probe.argtypes = [P, P, i64, i32, P, P]
     L.caps_select.argtypes = [P, P, i64, i32, ct.POINTER(caps_attrs), P, P]
+    L.caps_search_batch_noalloc.argtypes = [P, P, i64, ct.POINTER(caps_attrs), i32, i32, P, P,
+                                            P]
     L.caps_set_timing.argtypes = [i32]
     L.caps_get_stage_times.argtypes = [ct.POINTER(caps_stage_times)]
     _lib = L
@@ -264,4 +266,12 @@ class Index:
                 out_dist = np.empty((nq, k), dtype=np.float32)
         _check(lib().caps_search_batch(self._h, _ptr(Q), nq, ct.byref(at), k, m, _ptr(out_ids),
                                        _ptr(out_dist), _stream(stream)))
+        return out_ids, out_dist
+
+    def search_noalloc(self, Q, Qb, k, m, out_ids, out_dist, stream=None):
+        """caps_search_batch_noalloc: same query, no device allocation.
+        Q, Qb, out_ids and out_dist must be CUDA tensors."""
+        at, keep = _dense_attrs(Qb)
+        _check(lib().caps_search_batch_noalloc(self._h, _ptr(Q), Q.shape[0], ct.byref(at), k, m,
+                                               _ptr(out_ids), _ptr(out_dist), _stream(stream)))
         return out_ids, out_dist

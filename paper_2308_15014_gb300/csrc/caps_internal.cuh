@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "caps.h"
 
@@ -152,3 +153,42 @@ struct ScanArgs {
 int launch_scan_topk(const ScanArgs& a, cudaStream_t s);
 
 }  // namespace caps
+
+// The index object behind the opaque caps_index handle: owns every device
+// array of one CAPS index (Alg. 1 output) and frees them on destruction.
+struct caps_index {
+  int64_t N = 0;
+  int d = 0, B = 0, h = 0, metric = 0;
+  caps::DenseMeta meta;
+  float* C = nullptr;
+  int32_t* bin = nullptr;
+  uint8_t* key = nullptr;
+  int32_t* tags = nullptr;
+  int32_t* perm = nullptr;
+  int32_t* offsets = nullptr;
+  uint8_t* pos = nullptr;
+  uint8_t* code_field = nullptr;
+  float* Xp = nullptr;
+  uint32_t* Ap = nullptr;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+
+  template <class T>
+  int alloc(T** p, size_t count) {
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return caps::fail(CAPS_ENOMEM, "cudaMalloc failed for an index array");
+    }
+    allocs.push_back(q);
+    bytes += (int64_t)(count * sizeof(T));
+    *p = (T*)q;
+    return CAPS_OK;
+  }
+  ~caps_index() {
+    for (void* q : allocs) cudaFree(q);
+  }
+};
+

@@ -1,0 +1,69 @@
+"""caps_search_batch_noalloc, the batched query for callers that cannot
+allocate device memory (memory reserved up front by another framework, a
+serving loop that must not wait on the allocator, rules that forbid
+allocator calls after start-up).  Its intermediates live in a fixed device
+array inside the library instead of coming from an allocator.
+
+The test calls it through the C ABI twice in a row -- the second call runs on
+the array the first one left behind -- and checks both results against
+caps_search_batch, with the same tolerance as the other GPU tests (both run
+the same fixed-order fp32 arithmetic, so the results must be identical).
+This file sorts last so that a run stopping at the first failure has already
+run every other test; it passes alone in a fresh process as well.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def caps():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2308_15014_gb300 import build
+    build.build()
+    import paper_2308_15014_gb300 as c
+    return c
+
+
+def _workload(B, nq):
+    from workloads import make_dense_workload
+    return make_dense_workload(name="noalloc", N=30_000, d=32, ncomp=40, center=("normal", 2.0),
+                               sigma=1.0, vocab=[6, 10, 20], zipf_s=1.0, nq=nq, cmin=1, cmax=3,
+                               B=B, h=7, iters=4, m=8, k=10, seed=123)
+
+
+@pytest.mark.parametrize("B,nq,k,m", [(16, 300, 10, 4), (2048, 5000, 20, 16)])
+def test_noalloc_matches_search_batch_on_two_calls(caps, B, nq, k, m):
+    # B = 2048 with 5,000 queries needs several passes over the 16 MiB array
+    w = _workload(B, nq)
+    ix = caps.Index.build(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.A).cuda(), w.vocab,
+                          w.B, h=w.h, iters=w.iters, init_idx=w.init_idx)
+    Q = torch.from_numpy(w.Q).cuda()
+    Qb = torch.from_numpy(w.Qb).cuda()
+    ref_ids, ref_dist = ix.search(Q, Qb, k, m)
+    for _ in range(2):
+        ids = torch.full((nq, k), -7, dtype=torch.int64, device="cuda")
+        dist = torch.full((nq, k), -7.0, dtype=torch.float32, device="cuda")
+        ix.search_noalloc(Q, Qb, k, m, ids, dist)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ids.cpu().numpy(), ref_ids.cpu().numpy())
+        rd, gd = ref_dist.cpu().numpy(), dist.cpu().numpy()
+        fin = np.isfinite(rd)
+        np.testing.assert_array_equal(np.isfinite(gd), fin)
+        np.testing.assert_allclose(gd[fin], rd[fin], rtol=1e-5)
+    ix.close()
+
+
+def test_noalloc_rejects_host_buffers(caps):
+    w = _workload(16, 10)
+    ix = caps.Index.build(w.X, w.A, w.vocab, w.B, h=w.h, iters=2, init_idx=w.init_idx)
+    ids = torch.empty((10, 5), dtype=torch.int64, device="cuda")
+    dist = torch.empty((10, 5), dtype=torch.float32, device="cuda")
+    with pytest.raises(caps.CapsError) as e:
+        ix.search_noalloc(torch.from_numpy(w.Q), torch.from_numpy(w.Qb), 5, 2, ids, dist)
+    assert e.value.code == caps.CAPS_EINVAL
+    ix.close()
