@@ -35,6 +35,12 @@ UNIT = "queries/s"
 M_SWEEP = (8, 12, 16, 24, 32, 48, 64)
 RECALL_SAMPLE = 500
 FALLBACK_HBM_GBS = 6800.0
+# fp32 peak from unit counts and clock: 152 SMs x 128 fp32 lanes x 2 flop
+# (fma) x 2.07 GHz maximum SM clock
+SMS, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_GHZ / 1e3
+SCAN_KERNEL = "k_scan_bin"
+SCAN_SRC = "scan_bin.cu"
 
 
 def parse():
@@ -160,18 +166,21 @@ def scan_traffic_bytes(w, perm, offsets, probe, sel, words_pad):
     return union, per_query, pq_scan, pq_pass
 
 
-def traffic_from_profile():
-    """dram bytes per scan launch from the committed ncu summary, if it was
-    taken on the current scan kernel source."""
-    p = os.path.join(ROOT, "profiles", "scan_topk_traffic.json")
-    src = os.path.join(ROOT, "paper_2308_15014_gb300", "csrc", "search_kernels.cu")
+def traffic_from_profile(kernel=SCAN_KERNEL, src_name=SCAN_SRC):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current source of that kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2308_15014_gb300", "csrc", src_name)
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        j = json.load(f)
+        entries = json.load(f)
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return j.get("dram_bytes_per_launch") if j.get("src_sha") == sha else None
+    for e in entries:
+        if e.get("kernel") == kernel and e.get("src_sha") == sha:
+            return e.get("dram_bytes_per_launch")
+    return None
 
 
 def oracle_baseline(w, m, k, budget_s=15.0):
@@ -350,7 +359,10 @@ def run_caps(args):
         w, perm, offsets, probe, sel, ix.info.attr_words)
     hbm, hbm_src = peaks()
     scan_s = stage["scan_ms"] / 1e3
-    achieved = union / scan_s / 1e9
+    achieved_gbs = union / scan_s / 1e9
+    # L2: per (query, row) distance t = x - q, acc = fma(t, t, acc): 3 flop/coord
+    flops = rows_passed * w.d * (3 if w.metric == 0 else 2)
+    achieved_tflops = flops / scan_s / 1e12
 
     # ---- end to end: host buffers through the same C-ABI call --------------
     Qh, Qbh = np.ascontiguousarray(w.Q), np.ascontiguousarray(w.Qb)
@@ -387,11 +399,17 @@ def run_caps(args):
         "sweep": sweep,
         "build_s": round(build_s, 3),
         "stage_ms": {k_: round(v_, 4) for k_, v_ in stage.items()},
-        "roofline": {"kernel": "k_scan_topk", "bound": "hbm", "achieved": round(achieved, 1),
-                     "peak": hbm, "peak_source": hbm_src, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": traffic_from_profile(),
-                     "algorithmic_bytes_union": union, "algorithmic_bytes_per_query_sum": per_query,
+        "roofline": {"kernel": SCAN_KERNEL, "bound": "alu", "achieved": round(achieved_tflops, 2),
+                     "peak": round(FP32_PEAK_TFLOPS, 1),
+                     "peak_source": "derived: 152 SMs x 128 fp32 lanes x 2 flop x 2.07 GHz",
+                     "unit": "TFLOP/s", "frac": round(achieved_tflops / FP32_PEAK_TFLOPS, 4),
+                     "traffic": traffic_from_profile(), "algorithmic_flops": flops,
                      "rows_attr_tested": rows_scanned, "rows_distance": rows_passed},
+        "roofline_hbm": {"kernel": SCAN_KERNEL, "bound": "hbm", "achieved": round(achieved_gbs, 1),
+                         "peak": hbm, "peak_source": hbm_src, "unit": "GB/s",
+                         "frac": round(achieved_gbs / hbm, 4),
+                         "algorithmic_bytes_union": union,
+                         "algorithmic_bytes_per_query_sum": per_query},
         "e2e": {"value": round(e2e_v, 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(Qh.nbytes + Qbh.nbytes),
                 "d2h_bytes_per_step": int(ids_h.nbytes + dist_h.nbytes)},

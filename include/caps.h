@@ -147,6 +147,14 @@ int caps_search_batch(const caps_index* index, const float* Q, int64_t nq,
  * Synchronises the device first so no enqueued work still uses it. */
 void caps_free(caps_index* index);
 
+/* caps_device_status -- synchronise `stream` and report whether a bounded
+ * device-side wait expired in an earlier search on this index (the kernel
+ * then stops, sets a flag and returns instead of waiting forever; its
+ * results are not valid).  Returns CAPS_ETIMEOUT once per such event (and
+ * clears the flag), CAPS_OK otherwise.  caps_search_batch calls it itself
+ * whenever it synchronises for host outputs. */
+int caps_device_status(const caps_index* index, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* caps_last_error(void);
 
@@ -250,10 +258,14 @@ int caps_search_batch_noalloc(const caps_index* index, const float* Q,
 /* Per-stage device time of the last caps_search_batch call made on this
  * thread while timing was on, in milliseconds, summed over query chunks.
  * The stages are the kernels of Alg. 2: query filter packing, centroid
- * scores, top-m partition choice, sub-partition selection, and the fused
- * attribute match + distance + top-k scan. */
+ * scores, top-m partition choice, sub-partition selection, grouping of the
+ * probes by partition, the fused attribute match + distance + top-k scan, and
+ * the merge of the per-partition top-k lists. */
 typedef struct {
-  float prep_ms, scores_ms, topm_ms, select_ms, scan_ms;
+  float prep_ms, scores_ms, topm_ms, select_ms;
+  float group_ms; /* probes grouped by partition into work items */
+  float scan_ms;  /* the fused attribute match + distance + top-k kernel */
+  float merge_ms; /* per-query merge of the m partial top-k lists */
   int32_t launches; /* kernels launched by that call */
 } caps_stage_times;
 

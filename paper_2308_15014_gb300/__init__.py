@@ -26,7 +26,7 @@ ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS = range(6)
 # Every symbol declared in include/caps.h.
 EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "caps_get_info",
            "caps_export", "caps_assign", "caps_probe", "caps_select", "caps_set_timing",
-           "caps_get_stage_times", "caps_search_batch_noalloc")
+           "caps_get_stage_times", "caps_search_batch_noalloc", "caps_device_status")
 
 
 class CapsError(RuntimeError):
@@ -49,7 +49,8 @@ class caps_build_params(ct.Structure):
 
 class caps_stage_times(ct.Structure):
     _fields_ = [("prep_ms", ct.c_float), ("scores_ms", ct.c_float), ("topm_ms", ct.c_float),
-                ("select_ms", ct.c_float), ("scan_ms", ct.c_float), ("launches", ct.c_int32)]
+                ("select_ms", ct.c_float), ("group_ms", ct.c_float), ("scan_ms", ct.c_float),
+                ("merge_ms", ct.c_float), ("launches", ct.c_int32)]
 
 
 class caps_index_info(ct.Structure):
@@ -85,6 +86,7 @@ def lib(path: Optional[str] = None):
     L.caps_select.argtypes = [P, P, i64, i32, ct.POINTER(caps_attrs), P, P]
     L.caps_search_batch_noalloc.argtypes = [P, P, i64, ct.POINTER(caps_attrs), i32, i32, P, P,
                                             P]
+    L.caps_device_status.argtypes = [P, P]
     L.caps_set_timing.argtypes = [i32]
     L.caps_get_stage_times.argtypes = [ct.POINTER(caps_stage_times)]
     _lib = L
@@ -231,6 +233,10 @@ class Index:
         _check(lib().caps_export(self._h, which, _ptr(out) if out.size else 1, out.nbytes,
                                  _stream(None)))
         return out
+
+    def status(self, stream=None):
+        """Raise CapsError(CAPS_ETIMEOUT) if a bounded device wait expired."""
+        _check(lib().caps_device_status(self._h, _stream(stream)))
 
     def probe(self, Q, m, out=None, stream=None):
         Q = _np_or_keep(Q, np.float32)

@@ -269,6 +269,10 @@ int scan_exclusive(int32_t* data, int64_t n, Scratch& scr, cudaStream_t s) {
 }
 }  // namespace
 
+int scan_exclusive_i32(int32_t* data, int64_t n, Scratch& scr, cudaStream_t s) {
+  return scan_exclusive(data, n, scr, s);
+}
+
 // ---------------------------------------------------------------------------
 // Stable counting sort by key.  The n elements are cut into tiles; counts
 // are kept per (key, tile) in key-major order, so one exclusive scan of the

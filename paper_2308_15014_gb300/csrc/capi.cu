@@ -11,6 +11,7 @@
 namespace caps {
 
 static thread_local std::string g_err;
+thread_local long long g_kernel_launches = 0;
 
 void set_error(const std::string& msg) { g_err = msg; }
 int fail(int code, const std::string& msg) {
@@ -228,12 +229,16 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   if (int rc = ix->alloc(&ix->bin, (size_t)N)) return rc;
   if (int rc = ix->alloc(&ix->key, (size_t)N)) return rc;
   if (int rc = ix->alloc(&ix->tags, (size_t)B * h)) return rc;
-  if (int rc = ix->alloc(&ix->perm, (size_t)N)) return rc;
+  // perm and Ap carry 4 spare rows: the scan bulk-copies them from 16-B
+  // boundaries, which may reach up to 3 rows past the last one
+  if (int rc = ix->alloc(&ix->perm, (size_t)N + 4)) return rc;
   if (int rc = ix->alloc(&ix->offsets, (size_t)nseg + 1)) return rc;
   if (int rc = ix->alloc(&ix->pos, (size_t)B * meta.n_codes)) return rc;
   if (int rc = ix->alloc(&ix->code_field, (size_t)meta.n_codes)) return rc;
   if (int rc = ix->alloc(&ix->Xp, (size_t)N * d)) return rc;
-  if (int rc = ix->alloc(&ix->Ap, (size_t)N * meta.words_pad)) return rc;
+  if (int rc = ix->alloc(&ix->Ap, (size_t)(N + 4) * meta.words_pad)) return rc;
+  if (int rc = ix->alloc(&ix->err, 1)) return rc;
+  CAPS_CUDA(cudaMemsetAsync(ix->err, 0, sizeof(int32_t), s));
   if (int rc = launch_code_field(meta, ix->code_field, s)) return rc;
 
   int32_t *perm_bin = nullptr, *bin_off = nullptr;
@@ -398,9 +403,11 @@ int alloc_batch(const caps_index* ix, int64_t nq, int m, Scratch& scr, Batch* b)
   return CAPS_OK;
 }
 
-int64_t chunk_rows(const caps_index* ix, int64_t nq) {
-  const int64_t budget = (int64_t)1 << 26;  // score matrix entries per chunk
-  int64_t c = budget / std::max(1, ix->B);
+int64_t chunk_rows(const caps_index* ix, int64_t nq, int m = 1, int k = 1) {
+  // per-query scratch: centroid scores + partial top-k lists + probe data
+  const int64_t per_q = 4 * (int64_t)ix->B + 8 * (int64_t)m * k + 16 * (int64_t)m + 64;
+  const int64_t budget = (int64_t)1 << 29;  // 512 MiB per chunk
+  int64_t c = budget / per_q;
   if (c < 1) c = 1;
   return std::min(c, nq);
 }
@@ -468,7 +475,8 @@ namespace {
 // chunk, plus one at the end.
 struct StageTimer {
   bool on = false;
-  std::vector<cudaEvent_t> ev;  // 5 per chunk + 1
+  static constexpr int kStages = 7;
+  std::vector<cudaEvent_t> ev;  // kStages per chunk + 1
   int used = 0;
   int launches = 0;
   bool valid = false;
@@ -497,14 +505,15 @@ extern "C" int caps_set_timing(int32_t enable) {
 
 extern "C" int caps_get_stage_times(caps_stage_times* out) {
   if (!out) return fail(CAPS_EINVAL, "null argument");
-  if (!g_timer.valid || g_timer.used < 6) return fail(CAPS_EINVAL, "no timed search on this thread");
+  const int S = StageTimer::kStages;
+  if (!g_timer.valid || g_timer.used < S + 1) return fail(CAPS_EINVAL, "no timed search on this thread");
   CAPS_CUDA(cudaEventSynchronize(g_timer.ev[g_timer.used - 1]));
-  float acc[5] = {0, 0, 0, 0, 0};
-  const int chunks = (g_timer.used - 1) / 5;
+  float acc[StageTimer::kStages] = {};
+  const int chunks = (g_timer.used - 1) / S;
   for (int c = 0; c < chunks; c++)
-    for (int st = 0; st < 5; st++) {
+    for (int st = 0; st < S; st++) {
       float ms = 0.f;
-      const int a = c * 5 + st;
+      const int a = c * S + st;
       CAPS_CUDA(cudaEventElapsedTime(&ms, g_timer.ev[a], g_timer.ev[a + 1]));
       acc[st] += ms;
     }
@@ -512,8 +521,24 @@ extern "C" int caps_get_stage_times(caps_stage_times* out) {
   out->scores_ms = acc[1];
   out->topm_ms = acc[2];
   out->select_ms = acc[3];
-  out->scan_ms = acc[4];
+  out->group_ms = acc[4];
+  out->scan_ms = acc[5];
+  out->merge_ms = acc[6];
   out->launches = g_timer.launches;
+  return CAPS_OK;
+}
+
+extern "C" int caps_device_status(const caps_index* ix, void* stream) {
+  if (!ix) return fail(CAPS_EINVAL, "null index");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t e = 0;
+  CAPS_CUDA(cudaMemcpyAsync(&e, ix->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  if (e) {
+    CAPS_CUDA(cudaMemsetAsync(ix->err, 0, sizeof(int32_t), s));
+    CAPS_CUDA(cudaStreamSynchronize(s));
+    return fail(CAPS_ETIMEOUT, "a bounded device wait expired in an earlier search");
+  }
   return CAPS_OK;
 }
 
@@ -537,18 +562,24 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
   Out<float> od;
   if (int rc = oi.init(out_ids, (size_t)nq * k, scr)) return rc;
   if (int rc = od.init(out_dist, (size_t)nq * k, scr)) return rc;
-  const int64_t qc = chunk_rows(ix, nq);
+  const int64_t qc = chunk_rows(ix, nq, m, k);
   Batch bt;
   if (int rc = alloc_batch(ix, qc, m, scr, &bt)) return rc;
+  const bool binmajor = bin_scan_supported(ix->d);
+  uint64_t* part = nullptr;
+  if (binmajor)
+    if (int rc = scr.get(&part, (size_t)qc * m * k)) return rc;
   const int L = ix->meta.L;
   StageTimer& tm = g_timer;
   tm.used = 0;
   tm.launches = 0;
   tm.valid = false;
+  const long long launches0 = g_kernel_launches;
   for (int64_t c0 = 0; c0 < nq; c0 += qc) {
     const int64_t n = std::min(qc, nq - c0);
     const float* Qc = dQ + c0 * ix->d;
     const int32_t* Qbc = dQb + c0 * L;
+    Scratch cscr(s);  // per-chunk grouping temporaries
     if (int rc = tm.record(s)) return rc;
     if (int rc = launch_query_prep(Qbc, n, ix->meta, bt.qp, s)) return rc;
     if (int rc = tm.record(s)) return rc;
@@ -560,7 +591,6 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
                                ix->code_field, Qbc, ix->meta, bt.qp.qcode, bt.sel, s))
       return rc;
     if (int rc = tm.record(s)) return rc;
-    tm.launches += 5;
     ScanArgs a;
     a.Xp = ix->Xp;
     a.Ap = ix->Ap;
@@ -579,12 +609,27 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
     a.words_pad = ix->meta.words_pad;
     a.out_ids = oi.dev + c0 * k;
     a.out_dist = od.dev + c0 * k;
-    if (int rc = launch_scan_topk(a, s)) return rc;
+    if (binmajor) {
+      BinWork w;
+      if (int rc = bin_group(bt.probe, n * m, ix->B, &w, cscr, s)) return rc;
+      if (int rc = tm.record(s)) return rc;
+      if (int rc = bin_scan(a, w, part, ix->err, s)) return rc;
+      if (int rc = tm.record(s)) return rc;
+      if (int rc = bin_merge(a, part, s)) return rc;
+    } else {
+      if (int rc = tm.record(s)) return rc;
+      if (int rc = launch_scan_topk(a, s)) return rc;
+      if (int rc = tm.record(s)) return rc;
+    }
   }
   if (int rc = tm.record(s)) return rc;
+  tm.launches = (int)(g_kernel_launches - launches0);
   tm.valid = tm.on;
   if (int rc = oi.finish(s)) return rc;
   if (int rc = od.finish(s)) return rc;
-  if (oi.host || od.host) CAPS_CUDA(cudaStreamSynchronize(s));
+  if (oi.host || od.host) {
+    CAPS_CUDA(cudaStreamSynchronize(s));
+    return caps_device_status(ix, stream);
+  }
   return CAPS_OK;
 }

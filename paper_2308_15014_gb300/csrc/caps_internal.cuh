@@ -58,10 +58,14 @@ int cuda_fail(cudaError_t e, const char* what);
     cudaError_t _e = (call);                                     \
     if (_e != cudaSuccess) return ::caps::cuda_fail(_e, #call);  \
   } while (0)
+// Kernels launched by this thread (every launch site checks through
+// CAPS_LAUNCH, which also counts it).
+extern thread_local long long g_kernel_launches;
 #define CAPS_LAUNCH(what)                                        \
   do {                                                           \
     cudaError_t _e = cudaGetLastError();                         \
     if (_e != cudaSuccess) return ::caps::cuda_fail(_e, what);   \
+    ++::caps::g_kernel_launches;                                 \
   } while (0)
 
 // ---- stream-ordered scratch ------------------------------------------------
@@ -152,6 +156,20 @@ struct ScanArgs {
 };
 int launch_scan_topk(const ScanArgs& a, cudaStream_t s);
 
+// ---- partition-major scan (scan_bin.cu) ------------------------------------
+int scan_exclusive_i32(int32_t* data, int64_t n, Scratch& scr, cudaStream_t s);
+struct BinWork {
+  int32_t* ent = nullptr;      // [nq*m] probe entries sorted by partition
+  void* items = nullptr;       // work items
+  int32_t* n_items = nullptr;  // device count of work items
+  int64_t max_items = 0;       // grid bound
+};
+bool bin_scan_supported(int d);
+int64_t bin_work_items_bound(int64_t ne, int B);
+int bin_group(const int32_t* probe, int64_t ne, int B, BinWork* w, Scratch& scr, cudaStream_t s);
+int bin_scan(const ScanArgs& a, const BinWork& w, uint64_t* part, int32_t* err, cudaStream_t s);
+int bin_merge(const ScanArgs& a, const uint64_t* part, cudaStream_t s);
+
 }  // namespace caps
 
 // The index object behind the opaque caps_index handle: owns every device
@@ -170,6 +188,7 @@ struct caps_index {
   uint8_t* code_field = nullptr;
   float* Xp = nullptr;
   uint32_t* Ap = nullptr;
+  int32_t* err = nullptr;  // device word: 1 after a bounded device wait expired
   int64_t bytes = 0;
   std::vector<void*> allocs;
 

@@ -1,15 +1,18 @@
 """GPU path vs the CPU oracle, element by element, through the C ABI.
 
-Integer outputs (assignment, tags, blocks, layout, probes, selections, ids)
-must match bit for bit.  Both sides take every decision on the same fp32
-value (coordinates in order, one fused multiply-add each), so distances match
-exactly as well; the looser 1e-5 relative bound of the contract is asserted
-separately where the data make exact agreement a matter of rounding order.
+Integer outputs of the build and of the probe/selection steps (assignment,
+tags, blocks, layout, probes, selections) must match bit for bit: both sides
+take those decisions on the same fp32 value (coordinates in order, one fused
+multiply-add each).  The batch scan sums each distance in a different order
+(lane partials, then pairwise), so its distances are compared within 1e-5
+relative and its ids rank by rank up to near-ties; on byte-valued data every
+partial sum is an exact integer and results must be identical.
 """
 import numpy as np
 import pytest
 
 import oracle as O
+from _compare import assert_search_equal
 from workloads import config_small, make_dense_workload
 
 pytestmark = pytest.mark.gpu
@@ -178,11 +181,35 @@ def test_search_small_config(k, m):
     ids, dist = gi.search(dev(w.Q), dev(w.Qb), k, m)
     ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
     oids, odist, _, _ = _oracle_search(w, oi, k, m)
-    np.testing.assert_array_equal(ids, oids)
-    np.testing.assert_array_equal(dist, odist)
-    fin = np.isfinite(odist)
-    np.testing.assert_allclose(dist[fin], odist[fin], rtol=1e-5)
+    assert_search_equal(ids, dist, oids, odist, X=w.X, Q=w.Q, A=w.A, Qb=w.Qb)
     _check_valid(w, ids, w.Qb)
+
+
+@pytest.mark.parametrize("d,k,m", [(128, 10, 5), (96, 7, 3), (256, 40, 9), (64, 128, 20),
+                                   (33, 10, 5)])
+def test_search_byte_data_exact(d, k, m):
+    # byte-valued data: every partial sum is an exact integer, so any
+    # summation order gives the oracle's distances and ids exactly.  d = 33
+    # takes the query-major scan, the others the partition-major one.
+    w = tiny(60 + d, N=6000, d=d, B=24, h=9, integer=True, nq=67, vocab=(5, 7, 11))
+    oi = oracle_index(w)
+    gi = gpu_index(w)
+    ids, dist = gi.search(dev(w.Q), dev(w.Qb), k, m)
+    oids, odist, _, _ = _oracle_search(w, oi, k, m)
+    assert_search_equal(ids.cpu().numpy(), dist.cpu().numpy(), oids, odist, exact=True)
+
+
+def test_search_many_probes_per_partition_and_hub_partitions():
+    # more than 32 probes of one partition -> several work items per
+    # partition; skewed partition sizes from a few dominant components
+    w = make_dense_workload(name="hub", N=20_000, d=32, ncomp=3, center=("uniform", 128.0),
+                            sigma=16.0, vocab=[4, 6, 8], zipf_s=1.0, nq=300, cmin=1, cmax=3,
+                            B=12, h=6, iters=5, m=4, k=10, seed=71, integer=True)
+    oi = oracle_index(w)
+    gi = gpu_index(w)
+    ids, dist = gi.search(w.Q, w.Qb, 10, 6)
+    oids, odist, _, _ = _oracle_search(w, oi, 10, 6)
+    assert_search_equal(ids, dist, oids, odist, exact=True)
 
 
 def test_search_host_buffers_equal_device_buffers():
@@ -205,24 +232,22 @@ def test_search_probe_all_is_exact_filtered_knn():
 
 
 def test_search_h0_and_unconstrained():
-    w = tiny(52, N=2000, B=8, h=0, nq=30)
+    w = tiny(52, N=2000, d=32, B=8, h=0, nq=30)
     oi = oracle_index(w)
     gi = gpu_index(w)
     for Qb in (w.Qb, np.full_like(w.Qb, -1)):
         ids, dist = gi.search(w.Q, Qb, 10, 3)
         oids, odist, _, _ = _oracle_search(w, oi, 10, 3, Qb)
-        np.testing.assert_array_equal(ids, oids)
-        np.testing.assert_array_equal(dist, odist)
+        assert_search_equal(ids, dist, oids, odist, X=w.X, Q=w.Q, A=w.A, Qb=Qb)
 
 
 def test_search_inner_product():
-    w = tiny(53, N=2000, B=8, h=5, nq=30, metric=1, normalize=True)
+    w = tiny(53, N=2000, d=64, B=8, h=5, nq=30, metric=1, normalize=True)
     oi = oracle_index(w)
     gi = gpu_index(w)
     ids, dist = gi.search(w.Q, w.Qb, 10, 3)
     oids, odist, _, _ = _oracle_search(w, oi, 10, 3)
-    np.testing.assert_array_equal(ids, oids)
-    np.testing.assert_array_equal(dist, odist)
+    assert_search_equal(ids, dist, oids, odist, X=w.X, Q=w.Q, A=w.A, Qb=w.Qb, metric=1)
     assert np.all(np.diff(dist, axis=1)[np.isfinite(dist[:, 1:])] <= 0)
 
 
@@ -236,8 +261,7 @@ def test_search_padding_dead_values_and_empty_batch():
     ids, dist = gi.search(w.Q, Qb, 50, 2)
     oi = oracle_index(w)
     oids, odist, _, _ = _oracle_search(w, oi, 50, 2, Qb)
-    np.testing.assert_array_equal(ids, oids)
-    np.testing.assert_array_equal(dist, odist)
+    assert_search_equal(ids, dist, oids, odist, X=w.X, Q=w.Q, A=w.A, Qb=Qb)
     assert (ids[1] == -1).all() and np.isinf(dist[1]).all()
     assert (ids[2] == -1).all()
     e_ids, e_dist = gi.search(w.Q[:0], Qb[:0], 10, 2)
