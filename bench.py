@@ -30,7 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "filtered QPS at recall@10>=0.9 (plain FP32 k-means path)"
+METRIC = "filtered QPS at recall@10>=0.9 (k-means + BF16 tensor-core path; plain FP32 path alongside)"
 UNIT = "queries/s"
 M_SWEEP = (8, 12, 16, 24, 32, 48, 64)
 RECALL_SAMPLE = 500
@@ -41,6 +41,16 @@ SMS, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_GHZ / 1e3
 SCAN_KERNEL = "k_scan_bin"
 SCAN_SRC = "scan_bin.cu"
+TC_KERNEL = "k_scan_tc"
+TC_SRC = "scan_tc.cu"
+
+
+def _json_default(o):
+    if isinstance(o, np.integer):
+        return int(o)
+    if isinstance(o, np.floating):
+        return float(o)
+    raise TypeError(type(o).__name__)
 
 
 def parse():
@@ -52,6 +62,8 @@ def parse():
     ap.add_argument("--config", choices=["sift1m", "small"], default="sift1m")
     ap.add_argument("--m", type=int, default=0, help="fixed probe count (0 = sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paths", default="bf16,fp32",
+                    help="comma list of search paths to measure; the first is the headline")
     return ap.parse_args()
 
 
@@ -65,6 +77,15 @@ def dist_env():
 def load_workload(name):
     from workloads import config_sift1m_like, config_small
     return config_sift1m_like() if name == "sift1m" else config_small()
+
+
+def bf16_peak_tflops():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    return 1900.0, "fallback"
 
 
 def peaks():
@@ -127,13 +148,15 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def scan_traffic_bytes(w, perm, offsets, probe, sel, words_pad):
+def scan_traffic_bytes(w, perm, offsets, probe, sel, words_pad, bf16=False):
     """Algorithmic bytes of the scan for one batch.
 
-    union: attribute words of every row some query selects, plus the vector
-    of every row that passes some query's filter (each byte once: the HBM
-    floor of the whole batch).  per_query: the same sums taken query by query
-    (the paper's query-time term sum |p| (L + d*match), in bytes)."""
+    fp32 scan -- union: attribute words of every row some query selects, plus
+    the fp32 vector of every row that passes some query's filter (each byte
+    once: the HBM floor of the whole batch); per_query: the same sums taken
+    query by query (the paper's query-time term sum |p| (L + d*match)).
+    bf16 tensor-core scan -- every selected row is scored, so the union is
+    each selected row's bf16 vector, attribute words, id and norm once."""
     N, d, h = w.N, w.d, w.h
     nb = h + 1
     Ar = w.A[perm]
@@ -161,9 +184,42 @@ def scan_traffic_bytes(w, perm, offsets, probe, sel, words_pad):
         pq_scan += (r1 - r0) * len(grp_q)
         pq_pass += int(ok.sum())
     attr_b = 4 * words_pad
+    if bf16:
+        row_b = 2 * d + attr_b + 8
+        return int(touched.sum()) * row_b, pq_scan * row_b, pq_scan, pq_pass
     union = int(touched.sum()) * attr_b + int(passed.sum()) * d * 4
     per_query = pq_scan * attr_b + pq_pass * d * 4
     return union, per_query, pq_scan, pq_pass
+
+
+def dense_item_stats(w, offsets, probe, sel, group=128):
+    """Work of the partition-major tensor-core scan as it forms its items:
+    probes sorted by partition (query order kept), cut into groups of
+    `group`; each item streams the union of its probes' selected blocks.
+    Returns (items, sum of union rows, sum of union rows x probes)."""
+    nb = w.h + 1
+    B = w.B
+    pr = probe.reshape(-1)
+    sl = sel.reshape(-1)
+    if group == 128 and nb <= 16:  # the tensor-core scan orders by (partition, mask)
+        order = np.lexsort((np.arange(len(pr)), sl, pr))
+    else:
+        order = np.argsort(pr, kind="stable")
+    pr, sl = pr[order], sl[order]
+    starts = np.searchsorted(pr, np.arange(B + 1))
+    sizes = np.diff(offsets.astype(np.int64).reshape(-1)[: B * nb + 1]).reshape(B, nb)
+    items = rows = pairs = 0
+    for b in range(B):
+        s0, s1 = starts[b], starts[b + 1]
+        for g0 in range(s0, s1, group):
+            g1 = min(s1, g0 + group)
+            u = np.bitwise_or.reduce(sl[g0:g1])
+            bits = (u >> np.arange(nb, dtype=np.uint64)) & np.uint64(1)
+            ur = int(sizes[b][bits.astype(bool)].sum())
+            items += 1
+            rows += ur
+            pairs += ur * (g1 - g0)
+    return int(items), int(rows), int(pairs)
 
 
 def traffic_from_profile(kernel=SCAN_KERNEL, src_name=SCAN_SRC):
@@ -242,56 +298,36 @@ def run_reference(args):
                              "sample": f"{per_step} random queries per step; oracle index from "
                                        "the seed centroids (0 Lloyd iterations)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=_json_default), flush=True)
     return 0
 
 
-def run_caps(args):
+def measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world, local):
+    """Build the index in the given precision, pick m, time the batch."""
     import torch
     import torch.distributed as dist
-    rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    from paper_2308_15014_gb300 import build as capsbuild
-    capsbuild.build()
-    import paper_2308_15014_gb300 as caps
-    import oracle as O
-    from oracle.build import build_oracle
-    build_oracle()
-
-    w = load_workload(args.config)
     X = torch.from_numpy(w.X).cuda()
     A = torch.from_numpy(w.A).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ix = caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, metric=w.metric,
-                          init_idx=w.init_idx)
+                          init_idx=w.init_idx, prec=prec)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    del X, A
     Qd = torch.from_numpy(w.Q).cuda()
     Qbd = torch.from_numpy(w.Qb).cuda()
     out_ids = torch.empty((w.nq, w.k), dtype=torch.int64, device="cuda")
     out_dist = torch.empty((w.nq, w.k), dtype=torch.float32, device="cuda")
 
-    # recall on a seeded sample of queries against the oracle's exact kNN
-    rng = np.random.default_rng(5)
-    samp = np.sort(rng.choice(w.nq, min(RECALL_SAMPLE, w.nq), replace=False))
-    O.set_threads(0)
-    gt, _, g64, cnt = O.bruteforce(w.X, O.Attrs.of(w), w.Q[samp], O.Cons(Qb=w.Qb[samp]), w.k)
-
     def search(m):
         ix.search(Qd, Qbd, w.k, m, out_ids=out_ids, out_dist=out_dist)
 
-    def recall_at(m):
+    sweep, chosen = [], args.m
+    for m in ((args.m,) if args.m else M_SWEEP):
         search(m)
         ids = out_ids.cpu().numpy()[samp]
-        return O.recall(ids, gt, g64, cnt, w.k, X=w.X, Q=w.Q[samp])
-
-    sweep = []
-    chosen = args.m
-    for m in ((args.m,) if args.m else M_SWEEP):
-        strict, tie, _, _ = recall_at(m)
+        strict, tie, _, _ = O.recall(ids, gt, g64, cnt, w.k, X=w.X, Q=w.Q[samp])
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         search(m)
         ev0.record()
@@ -304,13 +340,10 @@ def run_caps(args):
                       "qps": round(w.nq / (ms / 1e3), 1)})
         if not chosen and tie >= 0.9:
             chosen = m
-    if not chosen:
-        chosen = M_SWEEP[-1]
-    m = chosen
-    rec = next(s for s in sweep if s["m"] == m)
+    m = chosen or M_SWEEP[-1]
+    rec = next(x for x in sweep if x["m"] == m)
 
     # ---- timed region: K batches, L2 flushed between them -------------------
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         search(m)
     torch.cuda.synchronize()
@@ -329,8 +362,7 @@ def run_caps(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    ms = float(np.mean(step_ms))
+    ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -339,8 +371,7 @@ def run_caps(args):
 
     # ---- per-stage device times (events on the launching stream) -----------
     caps.set_timing(True)
-    stage = {}
-    reps = 5
+    stage, reps = {}, 5
     for _ in range(reps):
         flush.zero_()
         search(m)
@@ -348,21 +379,77 @@ def run_caps(args):
         for kk, vv in st.items():
             stage[kk] = stage.get(kk, 0.0) + vv / reps
     caps.set_timing(False)
-    launches_per_step = int(round(stage.pop("launches")))
+    launches = int(round(stage.pop("launches")))
+    return dict(ix=ix, m=m, rec=rec, sweep=sweep, value=value, ms=ms, stage=stage,
+                launches=launches, build_s=build_s, clocks=clk.summary())
 
-    # ---- algorithmic bytes of the scan (the dominant kernel) ---------------
+
+def run_caps(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2308_15014_gb300 import build as capsbuild
+    capsbuild.build()
+    import paper_2308_15014_gb300 as caps
+    import oracle as O
+    from oracle.build import build_oracle
+    build_oracle()
+
+    w = load_workload(args.config)
+    # recall on a seeded sample of queries against the oracle's exact kNN
+    rng = np.random.default_rng(5)
+    samp = np.sort(rng.choice(w.nq, min(RECALL_SAMPLE, w.nq), replace=False))
+    O.set_threads(0)
+    gt, _, g64, cnt = O.bruteforce(w.X, O.Attrs.of(w), w.Q[samp], O.Cons(Qb=w.Qb[samp]), w.k)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    precs = {"bf16": caps.BF16, "fp32": caps.FP32}
+    paths = [p for p in args.paths.split(",") if p]
+    res = {}
+    for pth in paths:
+        res[pth] = measure_path(args, w, caps, O, precs[pth], samp, gt, g64, cnt, flush, world,
+                                local)
+    head = res[paths[0]]
+    ix, m, stage = head["ix"], head["m"], head["stage"]
+
+    # ---- algorithmic work of the scan (the dominant kernel) ----------------
     perm = ix.export(caps.ARR_PERM)
     offsets = ix.export(caps.ARR_OFFSETS)
     probe = ix.probe(w.Q, m)
     sel = ix.select(probe, w.Qb)
     union, per_query, rows_scanned, rows_passed = scan_traffic_bytes(
-        w, perm, offsets, probe, sel, ix.info.attr_words)
+        w, perm, offsets, probe, sel, ix.info.attr_words, bf16=paths[0] == "bf16")
     hbm, hbm_src = peaks()
     scan_s = stage["scan_ms"] / 1e3
+    d_items, d_rows, d_pairs = dense_item_stats(w, offsets, probe, sel,
+                                                128 if paths[0] == "bf16" else 32)
+    if paths[0] == "bf16":
+        # every selected (probe, row) pair: one d-long bf16 dot product
+        flops = rows_scanned * w.d * 2
+        tflops = flops / scan_s / 1e12
+        bf16_peak, bf16_src = bf16_peak_tflops()
+        roof = {"kernel": TC_KERNEL, "bound": "tensor", "achieved": round(tflops, 2),
+                "peak": bf16_peak, "peak_source": bf16_src, "unit": "TFLOP/s",
+                "frac": round(tflops / bf16_peak, 4), "traffic": traffic_from_profile(TC_KERNEL, TC_SRC),
+                "algorithmic_flops": flops, "rows_attr_tested": rows_scanned,
+                "rows_distance": rows_passed, "work_items": d_items,
+                "item_union_rows": d_rows, "item_dense_pairs": d_pairs}
+    else:
+        flops = rows_passed * w.d * (3 if w.metric == 0 else 2)
+        tflops = flops / scan_s / 1e12
+        roof = {"kernel": SCAN_KERNEL, "bound": "alu", "achieved": round(tflops, 2),
+                "peak": round(FP32_PEAK_TFLOPS, 1),
+                "peak_source": "derived: 152 SMs x 128 fp32 lanes x 2 flop x 2.07 GHz",
+                "unit": "TFLOP/s", "frac": round(tflops / FP32_PEAK_TFLOPS, 4),
+                "traffic": traffic_from_profile(SCAN_KERNEL, SCAN_SRC), "algorithmic_flops": flops,
+                "rows_attr_tested": rows_scanned, "rows_distance": rows_passed}
     achieved_gbs = union / scan_s / 1e9
-    # L2: per (query, row) distance t = x - q, acc = fma(t, t, acc): 3 flop/coord
-    flops = rows_passed * w.d * (3 if w.metric == 0 else 2)
-    achieved_tflops = flops / scan_s / 1e12
+    roof_hbm = {"kernel": roof["kernel"], "bound": "hbm", "achieved": round(achieved_gbs, 1),
+                "peak": hbm, "peak_source": hbm_src, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm, 4), "algorithmic_bytes_union": union,
+                "algorithmic_bytes_per_query_sum": per_query}
 
     # ---- end to end: host buffers through the same C-ABI call --------------
     Qh, Qbh = np.ascontiguousarray(w.Q), np.ascontiguousarray(w.Qb)
@@ -384,41 +471,42 @@ def run_caps(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_baseline(w, m, w.k)
-    clocks = clk.summary()
+    others = {}
+    for pth in paths[1:]:
+        r = res[pth]
+        others[pth] = {"value": round(r["value"], 1), "m": r["m"], "ms_per_step": round(r["ms"], 4),
+                       "recall_at_10": {"tie_aware": r["rec"]["recall_tie"],
+                                        "strict": r["rec"]["recall_strict"]},
+                       "stage_ms": {k_: round(v_, 4) for k_, v_ in r["stage"].items()},
+                       "sweep": r["sweep"], "build_s": round(r["build_s"], 3)}
     line = {
-        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
+        "metric": METRIC, "value": round(head["value"], 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms"], 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if paths[0] == "bf16" else "f32", "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "d": w.d, "L": int(w.A.shape[1]),
                    "B": w.B, "h": w.h, "kmeans_iters": w.iters, "m": m, "k": w.k,
-                   "queries_per_step": w.nq, "l2": "flushed between timed steps (256 MB write)",
+                   "path": paths[0], "queries_per_step": w.nq,
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "recall_at_10": {"tie_aware": rec["recall_tie"], "strict": rec["recall_strict"],
-                         "sample_queries": int(len(samp))},
-        "sweep": sweep,
-        "build_s": round(build_s, 3),
+        "recall_at_10": {"tie_aware": head["rec"]["recall_tie"],
+                         "strict": head["rec"]["recall_strict"], "sample_queries": int(len(samp))},
+        "sweep": head["sweep"],
+        "build_s": round(head["build_s"], 3),
         "stage_ms": {k_: round(v_, 4) for k_, v_ in stage.items()},
-        "roofline": {"kernel": SCAN_KERNEL, "bound": "alu", "achieved": round(achieved_tflops, 2),
-                     "peak": round(FP32_PEAK_TFLOPS, 1),
-                     "peak_source": "derived: 152 SMs x 128 fp32 lanes x 2 flop x 2.07 GHz",
-                     "unit": "TFLOP/s", "frac": round(achieved_tflops / FP32_PEAK_TFLOPS, 4),
-                     "traffic": traffic_from_profile(), "algorithmic_flops": flops,
-                     "rows_attr_tested": rows_scanned, "rows_distance": rows_passed},
-        "roofline_hbm": {"kernel": SCAN_KERNEL, "bound": "hbm", "achieved": round(achieved_gbs, 1),
-                         "peak": hbm, "peak_source": hbm_src, "unit": "GB/s",
-                         "frac": round(achieved_gbs / hbm, 4),
-                         "algorithmic_bytes_union": union,
-                         "algorithmic_bytes_per_query_sum": per_query},
+        "roofline": roof,
+        "roofline_hbm": roof_hbm,
+        "other_paths": others,
         "e2e": {"value": round(e2e_v, 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(Qh.nbytes + Qbh.nbytes),
                 "d2h_bytes_per_step": int(ids_h.nbytes + dist_h.nbytes)},
-        "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks,
+        "gpu_launches": head["launches"] * args.steps,
+        "clocks": head["clocks"],
         "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
-    ix.close()
+    print(json.dumps(line, default=_json_default), flush=True)
+    for r in res.values():
+        r["ix"].close()
     if world > 1:
         dist.destroy_process_group()
     return 0

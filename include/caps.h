@@ -89,8 +89,17 @@ typedef struct {
  *                (inner product, larger is better; k-means then normalises
  *                each centroid to unit length).
  *   part         CAPS_PART_KMEANS.
- *   prec         CAPS_FP32.
- *   rerank_factor, mlp_hidden, mlp_epochs: reserved, pass 0.
+ *   prec         CAPS_FP32: every distance in fp32.
+ *                CAPS_BF16: the index also keeps a bf16 copy of the rows;
+ *                searches score all selected rows with bf16 tensor-core
+ *                tiles (fp32 accumulation, L2 as |x|^2 + |q|^2 - 2 q.x) and
+ *                re-score the best rerank_factor * k candidates of each query
+ *                exactly in fp32 before keeping k.  Needs d % 8 == 0 and
+ *                64 <= d <= 128; searches with k > 32 (or a candidate list beyond
+ *                64) use the fp32 scan instead.
+ *   rerank_factor candidates re-scored per result in the bf16 form
+ *                (0 = 4, at most 16).
+ *   mlp_hidden, mlp_epochs: reserved, pass 0.
  *   init_idx     optional [B] int64: k-means seed point ids (distinct).
  *   centroids    optional [B*d] fp32: fixed first-level centroids; k-means is
  *                skipped and f(x) = best centroid (Alg. 1 first loop).

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcaps_gb300.so")
 
 CAPS_OK, CAPS_EINVAL, CAPS_ENOMEM, CAPS_ECUDA, CAPS_ETIMEOUT = 0, 1, 2, 3, 4
 L2, IP = 0, 1
+FP32, BF16 = 0, 1
 ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS = range(6)
 
 # Every symbol declared in include/caps.h.
@@ -189,13 +190,13 @@ class Index:
 
     @classmethod
     def build(cls, X, A, vocab, B, h=15, iters=20, metric=L2, init_idx=None, centroids=None,
-              seed=0, stream=None) -> "Index":
+              seed=0, prec=FP32, rerank_factor=0, stream=None) -> "Index":
         X = _np_or_keep(X, np.float32)
         N, d = X.shape
         at, keep = _dense_attrs(A, vocab)
         p = caps_build_params()
         p.B, p.h, p.kmeans_iters, p.seed, p.metric = B, h, iters, seed, metric
-        p.part, p.prec = 0, 0
+        p.part, p.prec, p.rerank_factor = 0, prec, rerank_factor
         if init_idx is not None:
             init_idx = _np_or_keep(init_idx, np.int64)
             p.init_idx = _ptr(init_idx)

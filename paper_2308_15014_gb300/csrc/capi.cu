@@ -198,7 +198,12 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   if (p->kmeans_iters < 0) return fail(CAPS_EINVAL, "kmeans_iters must be >= 0");
   if (p->metric != CAPS_L2 && p->metric != CAPS_IP) return fail(CAPS_EINVAL, "unknown metric");
   if (p->part != CAPS_PART_KMEANS) return fail(CAPS_EINVAL, "only the k-means partitioner is built");
-  if (p->prec != CAPS_FP32) return fail(CAPS_EINVAL, "only fp32 precision is built");
+  if (p->prec != CAPS_FP32 && p->prec != CAPS_BF16)
+    return fail(CAPS_EINVAL, "precision must be CAPS_FP32 or CAPS_BF16");
+  if (p->prec == CAPS_BF16 && (d % 8 != 0 || d < 64 || d > 128))
+    return fail(CAPS_EINVAL, "the bf16 form needs d a multiple of 8 in [64, 128]");
+  if (p->rerank_factor < 0 || p->rerank_factor > 16)
+    return fail(CAPS_EINVAL, "rerank_factor must be in [0, 16] (0 = 4)");
   keep_pool_warm();
   DenseMeta meta;
   if (int rc = make_meta(attrs, s, &meta)) return rc;
@@ -209,6 +214,8 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   ix->h = h;
   ix->metric = p->metric;
   ix->meta = meta;
+  ix->prec = p->prec;
+  ix->rerank_factor = p->rerank_factor > 0 ? p->rerank_factor : 4;
 
   Scratch scr(s);
   const float* dX = nullptr;
@@ -290,6 +297,16 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   if (int rc = launch_layout(dX, dA, ix->perm, N, d, meta, ix->Xp, ix->Ap, s)) return rc;
   CAPS_CUDA(cudaMemsetAsync(ix->pos, 0, (size_t)B * meta.n_codes, s));
   if (int rc = launch_pos_table(ix->tags, B, h, meta.n_codes, ix->pos, s)) return rc;
+  if (p->prec == CAPS_BF16) {
+    // bf16 form: bf16 rows + fp32 squared norms + inverse permutation
+    uint16_t* xb = nullptr;
+    if (int rc = ix->alloc(&xb, (size_t)N * d)) return rc;
+    ix->Xb = xb;
+    if (int rc = ix->alloc(&ix->xn, (size_t)N + 4)) return rc;
+    if (int rc = ix->alloc(&ix->iperm, (size_t)N)) return rc;
+    if (int rc = tc_prepare_index(ix->Xp, N, d, ix->perm, ix->Xb, ix->xn, ix->iperm, ix->tmap, s))
+      return rc;
+  }
   CAPS_CUDA(cudaStreamSynchronize(s));
   return CAPS_OK;
 }
@@ -562,13 +579,22 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
   Out<float> od;
   if (int rc = oi.init(out_ids, (size_t)nq * k, scr)) return rc;
   if (int rc = od.init(out_dist, (size_t)nq * k, scr)) return rc;
-  const int64_t qc = chunk_rows(ix, nq, m, k);
+  const bool tc = ix->prec == CAPS_BF16 &&
+                  tc_scan_supported(ix->d, k, tc_kp(k), ix->meta.words_pad);
+  const int kp = tc ? tc_kp(k) : k;
+  const int64_t qc = chunk_rows(ix, nq, m, kp);
   Batch bt;
   if (int rc = alloc_batch(ix, qc, m, scr, &bt)) return rc;
-  const bool binmajor = bin_scan_supported(ix->d);
+  const bool binmajor = !tc && bin_scan_supported(ix->d);
   uint64_t* part = nullptr;
-  if (binmajor)
-    if (int rc = scr.get(&part, (size_t)qc * m * k)) return rc;
+  if (binmajor || tc)
+    if (int rc = scr.get(&part, (size_t)qc * m * kp)) return rc;
+  uint16_t* Qh = nullptr;
+  float* qn = nullptr;
+  if (tc) {
+    if (int rc = scr.get(&Qh, (size_t)qc * ix->d)) return rc;
+    if (int rc = scr.get(&qn, (size_t)qc)) return rc;
+  }
   const int L = ix->meta.L;
   StageTimer& tm = g_timer;
   tm.used = 0;
@@ -609,7 +635,37 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
     a.words_pad = ix->meta.words_pad;
     a.out_ids = oi.dev + c0 * k;
     a.out_dist = od.dev + c0 * k;
-    if (binmajor) {
+    if (tc) {
+      BinWork w;
+      if (int rc = tc_query_prep(Qc, n, ix->d, Qh, qn, s)) return rc;
+      if (int rc = tc_group(bt.probe, bt.sel, ix->h, n * m, ix->B, &w, cscr, s)) return rc;
+      if (int rc = tm.record(s)) return rc;
+      TcScanArgs t;
+      t.sel = bt.sel;
+      t.qmask = bt.qp.qmask;
+      t.qval = bt.qp.qval;
+      t.Qh = Qh;
+      t.qn = qn;
+      t.Ap = ix->Ap;
+      t.perm = ix->perm;
+      t.xn = ix->xn;
+      t.offsets = ix->offsets;
+      t.tmap = ix->tmap;
+      t.m = m;
+      t.h = ix->h;
+      t.d = ix->d;
+      t.kp = kp;
+      t.rerank = tc_rerank_depth(k, ix->rerank_factor);
+      t.words_pad = ix->meta.words_pad;
+      t.metric = ix->metric;
+      t.part = part;
+      t.err = ix->err;
+      if (int rc = tc_scan(t, w, s)) return rc;
+      if (int rc = tm.record(s)) return rc;
+      if (int rc = tc_merge_rerank(t, bt.qp.dead, n, k, Qc, ix->Xp, ix->iperm, a.out_ids,
+                                   a.out_dist, s))
+        return rc;
+    } else if (binmajor) {
       BinWork w;
       if (int rc = bin_group(bt.probe, n * m, ix->B, &w, cscr, s)) return rc;
       if (int rc = tm.record(s)) return rc;

@@ -170,6 +170,36 @@ int bin_group(const int32_t* probe, int64_t ne, int B, BinWork* w, Scratch& scr,
 int bin_scan(const ScanArgs& a, const BinWork& w, uint64_t* part, int32_t* err, cudaStream_t s);
 int bin_merge(const ScanArgs& a, const uint64_t* part, cudaStream_t s);
 
+// ---- bf16 tensor-core scan + exact re-rank (scan_tc.cu) ---------------------
+struct TcScanArgs {
+  const uint64_t* sel;
+  const uint32_t* qmask;
+  const uint32_t* qval;
+  const void* Qh;       // [nq*d] bf16 queries
+  const float* qn;      // [nq] fp32 squared norms
+  const uint32_t* Ap;
+  const int32_t* perm;
+  const float* xn;      // [N+4] fp32 squared norms of the rows
+  const int32_t* offsets;
+  const void* tmap;     // CUtensorMap over the bf16 rows
+  int m, h, d, kp, words_pad, metric;  // kp: keys kept per probe (16 or 32)
+  int rerank;           // candidates re-scored exactly per query
+  uint64_t* part;       // [nq*m*kp]
+  int32_t* err;
+};
+int tc_kp(int k);
+int tc_rerank_depth(int k, int factor);
+bool tc_scan_supported(int d, int k, int kp, int words_pad);
+int tc_prepare_index(const float* Xp, int64_t N, int d, const int32_t* perm, void* Xb, float* xn,
+                     int32_t* iperm, void* tmap_out, cudaStream_t s);
+int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, cudaStream_t s);
+int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, BinWork* w,
+             Scratch& scr, cudaStream_t s);
+int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s);
+int tc_merge_rerank(const TcScanArgs& t, const uint8_t* dead, int64_t nq, int k, const float* Q,
+                    const float* Xp, const int32_t* iperm, int64_t* out_ids, float* out_dist,
+                    cudaStream_t s);
+
 }  // namespace caps
 
 // The index object behind the opaque caps_index handle: owns every device
@@ -189,6 +219,14 @@ struct caps_index {
   float* Xp = nullptr;
   uint32_t* Ap = nullptr;
   int32_t* err = nullptr;  // device word: 1 after a bounded device wait expired
+  // bf16 form (prec = CAPS_BF16): bf16 copy of the rows, their fp32 squared
+  // norms, row of each original id, and a TMA tensor map over the bf16 rows
+  int prec = CAPS_FP32;
+  int rerank_factor = 4;
+  void* Xb = nullptr;
+  float* xn = nullptr;
+  int32_t* iperm = nullptr;
+  alignas(128) unsigned char tmap[128] = {};
   int64_t bytes = 0;
   std::vector<void*> allocs;
 

@@ -1,0 +1,863 @@
+// BF16 tensor-core form of the CAPS scan (Alg. 2 "attribute match" +
+// "top-k vector match"), with an exact fp32 re-rank of 4k candidates.
+//
+// One CTA takes one partition and up to 128 of its probes.  The probes'
+// query vectors (bf16) form the MMA A operand (M = 128, K-major, 128-byte
+// swizzle) in shared memory; the partition's rows in the blocks any probe
+// selected arrive as 256-row bf16 tiles by 2-D TMA (K-major, 128-byte
+// swizzle, double-buffered), together with their attribute words, original
+// ids and fp32 squared norms (1-D bulk copies).  tcgen05.mma (kind::f16,
+// bf16 x bf16 -> fp32, M = 128, N = 256, K = 16 per instruction) writes the
+// 128 x 256 dot products into tensor memory; two 256-column accumulators let
+// the MMA of the next tile run while the epilogue reads this one.  In the
+// epilogue two threads own probe p (TMEM lane p), one per half of the tile's
+// 256 rows: for every row the thread checks the block selection and the
+// attribute filter, forms the approximate score (L2: |x|^2 + |q|^2 - 2 q.x in
+// fp32; IP: -q.x) and, if it beats the thread's current threshold, appends
+// the key to a small queue in shared memory; when any lane's queue fills,
+// the warp merges every queue into the lanes' sorted KP-key register lists
+// with a fixed compare-exchange network (no divergent insertion).  Each
+// partition so contributes its KP best keys per probe (KP >= k); per query
+// the best rerank_factor * k of the m lists are re-scored exactly (fp32,
+// coordinates in order, one fma each) before the final top-k.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "caps_internal.cuh"
+
+namespace caps {
+namespace {
+
+constexpr int TC_M = 128;     // probes per work item (MMA M, TMEM lanes)
+constexpr int TC_N = 256;     // rows per tile (MMA N)
+constexpr int TC_T = 256;     // threads: two per probe (one per half tile)
+constexpr int TC_Q = 16;      // per-thread candidate queue (merged when > 8 wait)
+constexpr int TC_RA = TC_N + 8;
+constexpr uint64_t kTcWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)));
+}
+__device__ __forceinline__ bool mbar_wait_t(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = su32(bar);
+  const uint64_t t0 = gtimer();
+  while (true) {
+    for (int i = 0; i < 256; i++) {
+      uint32_t done;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(a), "r"(parity)
+          : "memory");
+      if (done) return true;
+    }
+    if (gtimer() - t0 > kTcWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor: bf16 x bf16 -> f32, A and B K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t id,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcItem {
+  int32_t b, e0, ne, pad;
+};
+
+struct TcArgs {
+  const int32_t* ent;
+  const TcItem* items;
+  const int32_t* n_items;
+  const uint64_t* sel;
+  const uint32_t* qmask;
+  const uint32_t* qval;
+  const __nv_bfloat16* Qh;  // [nq*d]
+  const float* qn;          // [nq]
+  const uint32_t* Ap;
+  const int32_t* perm;
+  const float* xn;
+  const int32_t* offsets;
+  int m, h, d, kc, kp;
+  uint64_t* part;  // [nq*m*kp]
+  int32_t* err;
+};
+
+__host__ __device__ constexpr size_t tc_a_bytes(int kc) { return (size_t)kc * TC_M * 128; }
+__host__ __device__ constexpr size_t tc_b_bytes(int kc) { return (size_t)kc * TC_N * 128; }
+__host__ __device__ constexpr size_t tc_aux_bytes(int WP) {
+  return (size_t)TC_RA * WP * 4 + (size_t)TC_RA * 4 + (size_t)TC_RA * 4 + TC_N;
+}
+__host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int kp) {
+  // 1024-byte alignment slack + A + 2 B + candidate queues + 2 aux (the final
+  // merge of the two half lists reuses the B tiles)
+  return 1024 + tc_a_bytes(kc) + 2 * tc_b_bytes(kc) + (size_t)TC_Q * TC_T * 8 +
+         2 * ((tc_aux_bytes(WP) + 15) & ~(size_t)15) + 0 * (size_t)kp;
+}
+
+template <int KP>
+__device__ __forceinline__ void net_insert(uint64_t (&L)[KP], uint64_t x) {
+  // sorted ascending; x moves down until it finds its place, the largest
+  // key falls off the end (an empty key changes nothing)
+#pragma unroll
+  for (int i = 0; i < KP; i++) {
+    const uint64_t lo = L[i] < x ? L[i] : x;
+    x = L[i] < x ? x : L[i];
+    L[i] = lo;
+  }
+}
+
+template <int METRIC, int WP, int KP>
+__global__ void __launch_bounds__(TC_T, 1)
+k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  const int item_id = blockIdx.x;
+  if (item_id >= *a.n_items) return;
+  const TcItem it = a.items[item_id];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int d = a.d, kc = a.kc, kp = a.kp, nb = a.h + 1;
+
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = base;
+  unsigned char* sB[2] = {sA + tc_a_bytes(kc), sA + tc_a_bytes(kc) + tc_b_bytes(kc)};
+  uint64_t* queue = reinterpret_cast<uint64_t*>(sA + tc_a_bytes(kc) + 2 * tc_b_bytes(kc));
+  unsigned char* auxb = reinterpret_cast<unsigned char*>(queue + (size_t)TC_Q * TC_T);
+  const size_t aux_stride = (tc_aux_bytes(WP) + 15) & ~(size_t)15;
+  uint32_t* s_attr[2];
+  int32_t* s_perm[2];
+  float* s_xn[2];
+  uint8_t* s_blk[2];
+  for (int i = 0; i < 2; i++) {
+    unsigned char* p = auxb + i * aux_stride;
+    s_attr[i] = reinterpret_cast<uint32_t*>(p);
+    s_perm[i] = reinterpret_cast<int32_t*>(p + (size_t)TC_RA * WP * 4);
+    s_xn[i] = reinterpret_cast<float*>(p + (size_t)TC_RA * WP * 4 + TC_RA * 4);
+    s_blk[i] = p + (size_t)TC_RA * WP * 4 + 2 * TC_RA * 4;
+  }
+
+  __shared__ uint64_t tma_bar[2], mma_bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ uint64_t p_sel[TC_M];
+  __shared__ uint32_t p_qm[TC_M * WP], p_qv[TC_M * WP];
+  __shared__ float p_qn[TC_M];
+  __shared__ int32_t p_e[TC_M];
+  __shared__ int run_lo[64], run_hi[64], run_j0[64];
+  __shared__ int n_runs;
+  __shared__ int32_t boff[65];
+
+  if (tid == 0) {
+    mbar_init1(&tma_bar[0]);
+    mbar_init1(&tma_bar[1]);
+    mbar_init1(&mma_bar[0]);
+    mbar_init1(&mma_bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     su32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // probe data and the A operand: row t = probe t's query, bf16, zero-padded
+  // to kc*64 coordinates, 16-byte unit u of chunk c stored at unit u ^ (t%8)
+  if (tid < TC_M) {
+    const int t = tid;
+    int q = -1;
+    if (t < it.ne) {
+      const int e = a.ent[it.e0 + t];
+      q = e / a.m;
+      p_e[t] = e;
+      p_sel[t] = a.sel[e];
+      p_qn[t] = a.qn[q];
+#pragma unroll
+      for (int w = 0; w < WP; w++) {
+        p_qm[t * WP + w] = a.qmask[(int64_t)q * WP + w];
+        p_qv[t * WP + w] = a.qval[(int64_t)q * WP + w];
+      }
+    } else {
+      p_sel[t] = 0ull;
+    }
+    const int units = kc * 8;
+    const int dunits = d / 8;
+    for (int u = 0; u < units; u++) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (q >= 0 && u < dunits) v = *reinterpret_cast<const uint4*>(a.Qh + (int64_t)q * d + 8 * u);
+      const int c = u >> 3, uu = u & 7;
+      *reinterpret_cast<uint4*>(sA + (size_t)c * TC_M * 128 + t * 128 + ((uu ^ (t & 7)) << 4)) = v;
+    }
+  }
+  fence_async_smem();
+  const int32_t* off = a.offsets + (int64_t)it.b * nb;
+  for (int j = tid; j <= nb; j += TC_T) boff[j] = off[j];
+  __syncthreads();
+  if (tid == 0) {
+    uint64_t U = 0ull;
+    for (int t = 0; t < it.ne; t++) U |= p_sel[t];
+    int nr = 0, j = 0;
+    while (j < nb) {
+      if (!((U >> j) & 1ull)) { j++; continue; }
+      int j2 = j;
+      while (j2 + 1 < nb && ((U >> (j2 + 1)) & 1ull)) j2++;
+      if (boff[j2 + 1] > boff[j]) {
+        run_lo[nr] = boff[j];
+        run_hi[nr] = boff[j2 + 1];
+        run_j0[nr] = j;
+        nr++;
+      }
+      j = j2 + 1;
+    }
+    n_runs = nr;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+
+  // tile schedule over the runs, TC_N rows per tile
+  int rr = 0, rlo = n_runs > 0 ? run_lo[0] : 0;
+  auto next_tile = [&](int& lo, int& n, int& j0) -> bool {
+    while (rr < n_runs && rlo >= run_hi[rr]) {
+      rr++;
+      if (rr < n_runs) rlo = run_lo[rr];
+    }
+    if (rr >= n_runs) return false;
+    lo = rlo;
+    n = min(TC_N, run_hi[rr] - rlo);
+    j0 = run_j0[rr];
+    rlo += n;
+    return true;
+  };
+  auto issue = [&](int bi, int lo, int n) {  // thread 0
+    const int alo = lo & ~3;
+    const int arows = ((lo + n + 3) & ~3) - alo;
+    const uint32_t ab = (uint32_t)(arows * WP * 4), pb = (uint32_t)(arows * 4);
+    fence_async_smem();
+    expect_tx(&tma_bar[bi], (uint32_t)(kc * TC_N * 128) + ab + 2 * pb);
+    for (int c = 0; c < kc; c++)
+      tma_2d(sB[bi] + (size_t)c * TC_N * 128, &tmX, 64 * c, lo, &tma_bar[bi]);
+    bulk_copy(s_attr[bi], a.Ap + (int64_t)alo * WP, ab, &tma_bar[bi]);
+    bulk_copy(s_perm[bi], a.perm + alo, pb, &tma_bar[bi]);
+    bulk_copy(s_xn[bi], a.xn + alo, pb, &tma_bar[bi]);
+  };
+  const uint32_t idesc = idesc_bf16(TC_M, TC_N);
+  auto issue_mma = [&](int bi) {  // thread 0: 128 x 256 x (kc*64) into accumulator bi
+    tc_fence_after();
+    const uint32_t a0 = su32(sA), b0 = su32(sB[bi]);
+    for (int ks = 0; ks < kc * 4; ks++) {
+      const int c = ks >> 2, kin = ks & 3;
+      const uint64_t ad = sdesc(a0 + (uint32_t)(c * TC_M * 128 + kin * 32));
+      const uint64_t bd = sdesc(b0 + (uint32_t)(c * TC_N * 128 + kin * 32));
+      mma_bf16(tbase + (uint32_t)(bi * TC_N), ad, bd, idesc, ks > 0 ? 1u : 0u);
+    }
+    mma_commit(&mma_bar[bi]);
+  };
+
+  // Pipeline.  Every thread waits on every barrier phase it needs and flips
+  // its own parity after the wait (tph: copies, mph: MMAs).  Thread 0 also
+  // waits early on the next tile's copy (without flipping) to issue its MMA
+  // while the epilogue of the current tile runs.
+  int t_lo[2], t_n[2], t_j0[2];
+  bool have[2];
+  have[0] = next_tile(t_lo[0], t_n[0], t_j0[0]);
+  have[1] = have[0] && next_tile(t_lo[1], t_n[1], t_j0[1]);
+  uint32_t tph[2] = {0u, 0u}, mph[2] = {0u, 0u};
+  bool tma_out[2] = {false, false}, mma_out[2] = {false, false};  // thread 0's view
+  bool fail_flag = false;
+  if (tid == 0) {
+    for (int i = 0; i < 2; i++)
+      if (have[i]) {
+        issue(i, t_lo[i], t_n[i]);
+        tma_out[i] = true;
+      }
+    if (have[0]) {
+      if (mbar_wait_t(&tma_bar[0], tph[0])) {
+        issue_mma(0);
+        mma_out[0] = true;
+      } else {
+        fail_flag = true;
+      }
+    }
+  }
+
+  const int probe = tid & (TC_M - 1), half = tid / TC_M;
+  const bool active = probe < it.ne;
+  const uint64_t my_sel = p_sel[probe];
+  uint32_t my_qm[WP], my_qv[WP];
+#pragma unroll
+  for (int w = 0; w < WP; w++) {
+    my_qm[w] = active ? p_qm[probe * WP + w] : 0u;
+    my_qv[w] = active ? p_qv[probe * WP + w] : 0u;
+  }
+  const float my_qn = active ? p_qn[probe] : 0.f;
+  uint64_t L[KP];
+#pragma unroll
+  for (int i = 0; i < KP; i++) L[i] = kEmptyKey;
+  uint64_t thr = kEmptyKey;
+  int qcnt = 0;
+  auto flush = [&]() {  // warp-uniform call: as many rounds as the fullest queue
+    const int mx = __reduce_max_sync(0xffffffffu, (unsigned)qcnt);
+#pragma unroll 1
+    for (int i = 0; i < mx; i++) {
+      const uint64_t x = i < qcnt ? queue[(size_t)i * TC_T + tid] : kEmptyKey;
+      net_insert<KP>(L, x);
+    }
+    qcnt = 0;
+    thr = L[KP - 1];
+  };
+
+  int bi = 0;
+  while (true) {
+    if (__syncthreads_or(fail_flag)) {
+      fail_flag = true;
+      break;
+    }
+    if (!have[bi]) break;
+    const int nb_ = bi ^ 1;
+    if (tid == 0 && have[nb_]) {
+      if (mbar_wait_t(&tma_bar[nb_], tph[nb_])) {
+        issue_mma(nb_);
+        mma_out[nb_] = true;
+      } else {
+        fail_flag = true;
+      }
+    }
+    const bool okm = mbar_wait_t(&mma_bar[bi], mph[bi]);
+    const bool okt = okm && mbar_wait_t(&tma_bar[bi], tph[bi]);
+    if (okm) {  // a phase that was not seen stays outstanding for the cleanup
+      mph[bi] ^= 1u;
+      if (tid == 0) mma_out[bi] = false;
+    }
+    if (okt) {
+      tph[bi] ^= 1u;
+      if (tid == 0) tma_out[bi] = false;
+    }
+    if (__syncthreads_or(!okt || fail_flag)) {
+      fail_flag = true;
+      break;
+    }
+    const int lo = t_lo[bi], n = t_n[bi];
+    const int alo = lo & ~3;
+    uint8_t* blk = s_blk[bi];
+    for (int r = tid; r < n; r += TC_T) {
+      int j = t_j0[bi];
+      while (j + 1 < nb && boff[j + 1] <= lo + r) j++;
+      blk[r] = (uint8_t)j;
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t* attr = s_attr[bi] + (lo - alo) * WP;
+    const int32_t* prm = s_perm[bi] + (lo - alo);
+    const float* xnr = s_xn[bi] + (lo - alo);
+    const uint32_t tacc =
+        tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(bi * TC_N);
+    const bool warp_live = __any_sync(0xffffffffu, active);
+#pragma unroll 1
+    for (int c0 = half * (TC_N / 2); warp_live && c0 < (half + 1) * (TC_N / 2); c0 += 8) {
+      uint32_t v[8];
+      __syncwarp();  // tcgen05.ld is warp-collective
+      tmem_ld8(tacc + (uint32_t)c0, v);
+      if (c0 < n) {  // warp-uniform
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          const int r = c0 + j;
+          if (active && r < n && ((my_sel >> blk[r]) & 1ull)) {
+            bool pass = true;
+#pragma unroll
+            for (int w = 0; w < WP; w++) pass = pass && ((attr[r * WP + w] & my_qm[w]) == my_qv[w]);
+            if (pass) {
+              const float dot = __uint_as_float(v[j]);
+              const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r] + my_qn) : -dot;
+              const uint64_t key = make_key(sc, (uint32_t)prm[r]);
+              if (key < thr) {
+                queue[(size_t)qcnt * TC_T + tid] = key;
+                qcnt++;
+              }
+            }
+          }
+        }
+      }
+      // at most 8 more keys per lane before the next check: merge once any
+      // queue holds more than TC_Q - 8
+      if (__any_sync(0xffffffffu, qcnt > TC_Q - 8)) flush();
+    }
+    tc_fence_before();
+    __syncthreads();
+    // refill this buffer with the tile after next
+    have[bi] = next_tile(t_lo[bi], t_n[bi], t_j0[bi]);
+    if (tid == 0 && have[bi]) {
+      issue(bi, t_lo[bi], t_n[bi]);
+      tma_out[bi] = true;
+    }
+    bi = nb_;
+  }
+  if (fail_flag) {
+    // a copy or an MMA did not complete in time: flag it, let what is in
+    // flight land (bounded waits), release tensor memory and leave
+    if (tid == 0) {
+      atomicExch(a.err, 1);
+      for (int i = 0; i < 2; i++) {
+        if (mma_out[i]) mbar_wait_t(&mma_bar[i], mph[i]);
+        if (tma_out[i]) mbar_wait_t(&tma_bar[i], tph[i]);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+    return;
+  }
+  flush();
+  // merge the two half lists of each probe (the B tiles are free now)
+  uint64_t* halves = reinterpret_cast<uint64_t*>(sB[0]);
+  if (half == 1) {
+#pragma unroll
+    for (int i = 0; i < KP; i++) halves[(size_t)i * TC_M + probe] = L[i];
+  }
+  __syncthreads();
+  if (half == 0 && active) {
+#pragma unroll
+    for (int i = 0; i < KP; i++) net_insert<KP>(L, halves[(size_t)i * TC_M + probe]);
+    uint64_t* dst = a.part + (int64_t)p_e[probe] * KP;
+#pragma unroll
+    for (int i = 0; i < KP; i++) dst[i] = L[i];
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+}
+
+// ---- bf16 query copy and fp32 squared norms -------------------------------
+__global__ void k_query_bf16(const float* __restrict__ Q, int64_t nq, int d,
+                             __nv_bfloat16* __restrict__ Qh, float* __restrict__ qn) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  float acc = 0.f;
+  for (int j = 0; j < d; j++) {
+    const float x = Q[q * d + j];
+    acc = fmaf(x, x, acc);
+    Qh[q * d + j] = __float2bfloat16_rn(x);
+  }
+  qn[q] = acc;
+}
+
+// ---- per-query merge of the m candidate lists (keys out) -------------------
+template <int KPL>
+struct TopKm {
+  uint64_t v[KPL];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int s = 0; s < KPL; s++) v[s] = kEmptyKey;
+  }
+  __device__ __forceinline__ uint64_t kth(int k) const {
+    const int P = k - 1, l = P / KPL, s = P % KPL;
+    uint64_t mine = v[0];
+#pragma unroll
+    for (int u = 1; u < KPL; u++)
+      if (u == s) mine = v[u];
+    return __shfl_sync(0xffffffffu, mine, l);
+  }
+  __device__ __forceinline__ void insert(uint64_t x, int lane) {
+    int p = 0;
+#pragma unroll
+    for (int s = 0; s < KPL; s++) p += __popc(__ballot_sync(0xffffffffu, v[s] < x));
+    const uint64_t prev_last = __shfl_up_sync(0xffffffffu, v[KPL - 1], 1);
+    uint64_t nv[KPL];
+#pragma unroll
+    for (int s = 0; s < KPL; s++) {
+      const int P = lane * KPL + s;
+      const uint64_t before = (s == 0) ? prev_last : v[s - 1];
+      nv[s] = P < p ? v[s] : (P == p ? x : before);
+    }
+#pragma unroll
+    for (int s = 0; s < KPL; s++) v[s] = nv[s];
+  }
+  __device__ __forceinline__ void offer(uint64_t key, uint64_t& kthv, int k, int lane) {
+    unsigned cand = __ballot_sync(0xffffffffu, key < kthv);
+    while (cand) {
+      const int src = __ffs(cand) - 1;
+      cand &= cand - 1;
+      const uint64_t x = __shfl_sync(0xffffffffu, key, src);
+      if (x < kthv) {
+        insert(x, lane);
+        kthv = kth(k);
+      }
+    }
+  }
+};
+
+// Merge each query's m lists of kp keys, re-score the kp best exactly in
+// fp32 (coordinates in order, one fma each) and keep the k best.
+template <int METRIC, int KPL_M, int KPL_K>
+__global__ void __launch_bounds__(128)
+k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ dead, int64_t nq,
+               int m, int lp, int kp, int k, const float* __restrict__ Q, int d,
+               const float* __restrict__ Xp, const int32_t* __restrict__ iperm,
+               int64_t* __restrict__ out_ids, float* __restrict__ out_dist) {
+  extern __shared__ float qsm[];  // [4][d]
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * 4 + wp;
+  if (q >= nq) return;
+  float* qs = qsm + (size_t)wp * d;
+  for (int j = lane; j < d; j += 32) qs[j] = Q[q * d + j];
+  __syncwarp();
+  TopKm<KPL_M> cand;
+  cand.init();
+  uint64_t kthv = kEmptyKey;
+  if (!dead[q]) {
+    const uint64_t* src = part + q * (int64_t)m * lp;
+    const int tot = m * lp;
+    for (int b0 = 0; b0 < tot; b0 += 32) {
+      const uint64_t key = (b0 + lane < tot) ? src[b0 + lane] : kEmptyKey;
+      cand.offer(key, kthv, kp, lane);
+    }
+  }
+  // exact fp32 scores of the kp candidates
+  TopKm<KPL_K> top;
+  top.init();
+  uint64_t kth2 = kEmptyKey;
+#pragma unroll
+  for (int s = 0; s < KPL_M; s++) {
+    const int P = lane * KPL_M + s;
+    uint64_t key = kEmptyKey;
+    const uint64_t ck = cand.v[s];
+    if (P < kp && ck != kEmptyKey) {
+      const uint32_t id = (uint32_t)(ck & 0xffffffffu);
+      const float* xr = Xp + (int64_t)iperm[id] * d;
+      float acc = 0.f;
+      for (int j = 0; j < d; j++) {
+        if (METRIC == CAPS_L2) {
+          const float t = xr[j] - qs[j];
+          acc = fmaf(t, t, acc);
+        } else {
+          acc = fmaf(xr[j], qs[j], acc);
+        }
+      }
+      key = make_key(METRIC == CAPS_L2 ? acc : -acc, id);
+    }
+    top.offer(key, kth2, k, lane);
+  }
+#pragma unroll
+  for (int s = 0; s < KPL_K; s++) {
+    const int P = lane * KPL_K + s;
+    if (P < k) {
+      const uint64_t key = top.v[s];
+      int64_t id = -1;
+      float dist = METRIC == CAPS_L2 ? INFINITY : -INFINITY;
+      if (key != kEmptyKey) {
+        id = (int64_t)(uint32_t)(key & 0xffffffffu);
+        const float sc = unord_bits((uint32_t)(key >> 32));
+        dist = METRIC == CAPS_L2 ? sc : -sc;
+      }
+      out_ids[q * k + P] = id;
+      out_dist[q * k + P] = dist;
+    }
+  }
+}
+
+__global__ void k_mask_key(const uint64_t* __restrict__ sel, int64_t ne, int32_t* __restrict__ key) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ne) key[i] = (int32_t)sel[i];
+}
+__global__ void k_gather_i32(const int32_t* __restrict__ src, const int32_t* __restrict__ idx,
+                             int64_t n, int32_t* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+__global__ void k_tc_items_count(const int32_t* __restrict__ bin_off, int B,
+                                 int32_t* __restrict__ cnt) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) cnt[b] = (bin_off[b + 1] - bin_off[b] + TC_M - 1) / TC_M;
+  if (b == B) cnt[B] = 0;
+}
+__global__ void k_tc_items_fill(const int32_t* __restrict__ bin_off,
+                                const int32_t* __restrict__ item_off, int B,
+                                TcItem* __restrict__ items, int32_t* __restrict__ n_items) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == B) *n_items = item_off[B];
+  if (b >= B) return;
+  const int c = bin_off[b + 1] - bin_off[b];
+  for (int t = 0; t * TC_M < c; t++) {
+    TcItem x;
+    x.b = b;
+    x.e0 = bin_off[b] + t * TC_M;
+    x.ne = min(TC_M, c - t * TC_M);
+    x.pad = 0;
+    items[item_off[b] + t] = x;
+  }
+}
+
+// ---- build-side helpers ----------------------------------------------------
+__global__ void k_rows_bf16_norms(const float* __restrict__ Xp, int64_t N, int d,
+                                  __nv_bfloat16* __restrict__ Xb, float* __restrict__ xn) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  float acc = 0.f;
+  for (int j = 0; j < d; j++) {
+    const float x = Xp[r * d + j];
+    acc = fmaf(x, x, acc);
+    Xb[r * d + j] = __float2bfloat16_rn(x);
+  }
+  xn[r] = acc;
+}
+__global__ void k_inverse_perm(const int32_t* __restrict__ perm, int64_t N,
+                               int32_t* __restrict__ iperm) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < N) iperm[perm[r]] = (int32_t)r;
+}
+
+template <int METRIC, int WP, int KP>
+int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem, cudaStream_t s) {
+  auto kern = k_scan_tc<METRIC, WP, KP>;
+  CAPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)grid, TC_T, smem, s>>>(map, a);
+  CAPS_LAUNCH("k_scan_tc");
+  return CAPS_OK;
+}
+
+}  // namespace
+
+int tc_kp(int k) { return k <= 16 ? 16 : 32; }
+int tc_rerank_depth(int k, int factor) {
+  const int f = factor > 0 ? factor : 4;
+  return std::min(64, std::max(k, f * k));
+}
+
+bool tc_scan_supported(int d, int k, int kp, int words_pad) {
+  if (d % 8 != 0 || d < 64 || d > 128 || k > 32 || (kp != 16 && kp != 32)) return false;
+  // leave room for ~5 KB of static shared memory under the 227 KB limit
+  return tc_smem_bytes((d + 63) / 64, words_pad, kp) <= 221 * 1024;
+}
+
+int tc_prepare_index(const float* Xp, int64_t N, int d, const int32_t* perm, void* Xb, float* xn,
+                     int32_t* iperm, void* tmap_out, cudaStream_t s) {
+  k_rows_bf16_norms<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
+      Xp, N, d, static_cast<__nv_bfloat16*>(Xb), xn);
+  CAPS_LAUNCH("k_rows_bf16_norms");
+  k_inverse_perm<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(perm, N, iperm);
+  CAPS_LAUNCH("k_inverse_perm");
+  // 2-D tensor map over the bf16 rows: inner dimension d, outer N rows;
+  // boxes of 64 coordinates (128 bytes) x 256 rows, 128-byte swizzle
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qres;
+  CAPS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &qres));
+  if (!fn || qres != cudaDriverEntryPointSuccess)
+    return fail(CAPS_ECUDA, "cuTensorMapEncodeTiled is not available");
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  cuuint64_t gdim[2] = {(cuuint64_t)d, (cuuint64_t)N};
+  cuuint64_t gstride[1] = {(cuuint64_t)d * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)TC_N};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(static_cast<CUtensorMap*>(tmap_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Xb,
+                      gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CAPS_ECUDA, "cuTensorMapEncodeTiled failed");
+  return CAPS_OK;
+}
+
+int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, cudaStream_t s) {
+  if (nq == 0) return CAPS_OK;
+  k_query_bf16<<<(unsigned)((nq + 127) / 128), 128, 0, s>>>(Q, nq, d,
+                                                            static_cast<__nv_bfloat16*>(Qh), qn);
+  CAPS_LAUNCH("k_query_bf16");
+  return CAPS_OK;
+}
+
+int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, BinWork* w,
+             Scratch& scr, cudaStream_t s) {
+  if (ne > INT_MAX) return fail(CAPS_EINVAL, "too many probes in one chunk");
+  int32_t *bin_off = nullptr, *cnt = nullptr;
+  if (int rc = scr.get(&w->ent, (size_t)ne)) return rc;
+  if (int rc = scr.get(&bin_off, (size_t)B + 1)) return rc;
+  if (h + 1 <= 16) {
+    // probes of a partition ordered by their selected-block mask, so that
+    // probes scanning the same blocks share a work item: sort by mask, then
+    // (stably) by partition
+    int32_t *mkey = nullptr, *p1 = nullptr, *moff = nullptr, *pkey = nullptr, *p2 = nullptr;
+    if (int rc = scr.get(&mkey, (size_t)ne)) return rc;
+    if (int rc = scr.get(&p1, (size_t)ne)) return rc;
+    if (int rc = scr.get(&moff, ((size_t)1 << (h + 1)) + 1)) return rc;
+    if (int rc = scr.get(&pkey, (size_t)ne)) return rc;
+    if (int rc = scr.get(&p2, (size_t)ne)) return rc;
+    const unsigned g = (unsigned)((ne + 255) / 256);
+    k_mask_key<<<g, 256, 0, s>>>(sel, ne, mkey);
+    CAPS_LAUNCH("k_mask_key");
+    if (int rc = stable_sort_by_key(mkey, ne, (int64_t)1 << (h + 1), p1, moff, scr, s)) return rc;
+    k_gather_i32<<<g, 256, 0, s>>>(probe, p1, ne, pkey);
+    CAPS_LAUNCH("k_gather_i32");
+    if (int rc = stable_sort_by_key(pkey, ne, B, p2, bin_off, scr, s)) return rc;
+    k_gather_i32<<<g, 256, 0, s>>>(p1, p2, ne, w->ent);
+    CAPS_LAUNCH("k_gather_i32");
+  } else {
+    if (int rc = stable_sort_by_key(probe, ne, B, w->ent, bin_off, scr, s)) return rc;
+  }
+  if (int rc = scr.get(&cnt, (size_t)B + 1)) return rc;
+  if (int rc = scr.get(&w->n_items, 1)) return rc;
+  k_tc_items_count<<<(B + 1 + 255) / 256, 256, 0, s>>>(bin_off, B, cnt);
+  CAPS_LAUNCH("k_tc_items_count");
+  if (int rc = scan_exclusive_i32(cnt, (int64_t)B + 1, scr, s)) return rc;
+  w->max_items = ne / TC_M + B + 1;
+  TcItem* items = nullptr;
+  if (int rc = scr.get(&items, (size_t)w->max_items)) return rc;
+  w->items = items;
+  k_tc_items_fill<<<(B + 1 + 255) / 256, 256, 0, s>>>(bin_off, cnt, B, items, w->n_items);
+  CAPS_LAUNCH("k_tc_items_fill");
+  return CAPS_OK;
+}
+
+int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
+  TcArgs a;
+  a.ent = w.ent;
+  a.items = static_cast<const TcItem*>(w.items);
+  a.n_items = w.n_items;
+  a.sel = t.sel;
+  a.qmask = t.qmask;
+  a.qval = t.qval;
+  a.Qh = static_cast<const __nv_bfloat16*>(t.Qh);
+  a.qn = t.qn;
+  a.Ap = t.Ap;
+  a.perm = t.perm;
+  a.xn = t.xn;
+  a.offsets = t.offsets;
+  a.m = t.m;
+  a.h = t.h;
+  a.d = t.d;
+  a.kc = (t.d + 63) / 64;
+  a.kp = t.kp;
+  a.part = t.part;
+  a.err = t.err;
+  const size_t smem = tc_smem_bytes(a.kc, t.words_pad, t.kp);
+  const CUtensorMap& map = *static_cast<const CUtensorMap*>(t.tmap);
+  const int64_t g = w.max_items;
+#define CAPS_TC(WPV, KPV)                                                 \
+  return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV>(map, a, g, smem, s) \
+                             : launch_tc<CAPS_IP, WPV, KPV>(map, a, g, smem, s)
+  if (t.kp == 16) {
+    switch (t.words_pad) {
+      case 1: CAPS_TC(1, 16);
+      case 2: CAPS_TC(2, 16);
+      case 4: CAPS_TC(4, 16);
+    }
+  } else if (t.kp == 32) {
+    switch (t.words_pad) {
+      case 1: CAPS_TC(1, 32);
+      case 2: CAPS_TC(2, 32);
+      case 4: CAPS_TC(4, 32);
+    }
+  }
+#undef CAPS_TC
+  return fail(CAPS_EINVAL, "unsupported attribute word count or list length");
+}
+
+int tc_merge_rerank(const TcScanArgs& t, const uint8_t* dead, int64_t nq, int k, const float* Q,
+                    const float* Xp, const int32_t* iperm, int64_t* out_ids, float* out_dist,
+                    cudaStream_t s) {
+  if (nq == 0) return CAPS_OK;
+  const int depth = std::min(t.rerank, t.m * t.kp);  // candidates re-scored per query
+  const unsigned grid = (unsigned)((nq + 3) / 4);
+  const size_t smem = sizeof(float) * 4 * (size_t)t.d;
+#define CAPS_MR(MET, KM, KK)                                                                   \
+  k_merge_rerank<MET, KM, KK><<<grid, 128, smem, s>>>(t.part, dead, nq, t.m, t.kp, depth, k, Q, \
+                                                       t.d, Xp, iperm, out_ids, out_dist)
+  const int km = depth <= 32 ? 1 : 2;
+  if (t.metric == CAPS_L2) {
+    if (km == 1) CAPS_MR(CAPS_L2, 1, 1);
+    else CAPS_MR(CAPS_L2, 2, 1);
+  } else {
+    if (km == 1) CAPS_MR(CAPS_IP, 1, 1);
+    else CAPS_MR(CAPS_IP, 2, 1);
+  }
+#undef CAPS_MR
+  CAPS_LAUNCH("k_merge_rerank");
+  return CAPS_OK;
+}
+
+}  // namespace caps
