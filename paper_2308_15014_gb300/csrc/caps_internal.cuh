@@ -48,6 +48,53 @@ __device__ __forceinline__ uint64_t make_key(float score, uint32_t id) {
 }
 constexpr uint64_t kEmptyKey = ~0ull;
 
+// Running k smallest keys of a warp: positions lane*KPL + s, ascending, the
+// k-th at position k-1 (k <= 32*KPL).  offer() takes one key per lane and
+// inserts every key that beats the current k-th, one at a time.
+template <int KPL>
+struct WarpTopK {
+  uint64_t v[KPL];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int s = 0; s < KPL; s++) v[s] = kEmptyKey;
+  }
+  __device__ __forceinline__ uint64_t kth(int k) const {
+    const int P = k - 1, l = P / KPL, s = P % KPL;
+    uint64_t mine = v[0];
+#pragma unroll
+    for (int u = 1; u < KPL; u++)
+      if (u == s) mine = v[u];
+    return __shfl_sync(0xffffffffu, mine, l);
+  }
+  __device__ __forceinline__ void insert(uint64_t x, int lane) {
+    int p = 0;
+#pragma unroll
+    for (int s = 0; s < KPL; s++) p += __popc(__ballot_sync(0xffffffffu, v[s] < x));
+    const uint64_t prev_last = __shfl_up_sync(0xffffffffu, v[KPL - 1], 1);
+    uint64_t nv[KPL];
+#pragma unroll
+    for (int s = 0; s < KPL; s++) {
+      const int P = lane * KPL + s;
+      const uint64_t before = (s == 0) ? prev_last : v[s - 1];
+      nv[s] = P < p ? v[s] : (P == p ? x : before);
+    }
+#pragma unroll
+    for (int s = 0; s < KPL; s++) v[s] = nv[s];
+  }
+  __device__ __forceinline__ void offer(uint64_t key, uint64_t& kthv, int k, int lane) {
+    unsigned cand = __ballot_sync(0xffffffffu, key < kthv);
+    while (cand) {
+      const int src = __ffs(cand) - 1;
+      cand &= cand - 1;
+      const uint64_t x = __shfl_sync(0xffffffffu, key, src);
+      if (x < kthv) {
+        insert(x, lane);
+        kthv = kth(k);
+      }
+    }
+  }
+};
+
 // ---- error handling --------------------------------------------------------
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);

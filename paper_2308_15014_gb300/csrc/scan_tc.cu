@@ -169,7 +169,7 @@ struct TcArgs {
 __host__ __device__ constexpr size_t tc_a_bytes(int kc) { return (size_t)kc * TC_M * 128; }
 __host__ __device__ constexpr size_t tc_b_bytes(int kc) { return (size_t)kc * TC_N * 128; }
 __host__ __device__ constexpr size_t tc_aux_bytes(int WP) {
-  return (size_t)TC_RA * WP * 4 + (size_t)TC_RA * 4 + (size_t)TC_RA * 4 + TC_N;
+  return (size_t)TC_RA * WP * 4 + (size_t)TC_RA * 4 + (size_t)TC_RA * 4 + TC_N + 8;
 }
 __host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int kp) {
   // 1024-byte alignment slack + A + 2 B + candidate queues + 2 aux (the final
@@ -441,21 +441,35 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       __syncwarp();  // tcgen05.ld is warp-collective
       tmem_ld8(tacc + (uint32_t)c0, v);
       if (c0 < n) {  // warp-uniform
+        // the 8 rows' block ids and attribute words in few wide loads
+        // (the same addresses for every lane: broadcast)
+        const uint2 bw = *reinterpret_cast<const uint2*>(blk + c0);
+        const uint32_t bb[2] = {bw.x, bw.y};
+        uint32_t aw[8 * WP];
+        if (WP == 1 && ((lo - alo + c0) & 3) == 0) {
+          const uint4 a0 = *reinterpret_cast<const uint4*>(attr + c0);
+          const uint4 a1 = *reinterpret_cast<const uint4*>(attr + c0 + 4);
+          aw[0] = a0.x; aw[1] = a0.y; aw[2] = a0.z; aw[3] = a0.w;
+          aw[4] = a1.x; aw[5] = a1.y; aw[6] = a1.z; aw[7] = a1.w;
+        } else {
+#pragma unroll
+          for (int x = 0; x < 8 * WP; x++) aw[x] = attr[c0 * WP + x];
+        }
+        const int lim = n - c0;  // rows of this group inside the tile
 #pragma unroll
         for (int j = 0; j < 8; j++) {
-          const int r = c0 + j;
-          if (active && r < n && ((my_sel >> blk[r]) & 1ull)) {
-            bool pass = true;
+          const int bj = (bb[j >> 2] >> (8 * (j & 3))) & 0xff;
+          bool pass = active && j < lim && ((my_sel >> bj) & 1ull);
 #pragma unroll
-            for (int w = 0; w < WP; w++) pass = pass && ((attr[r * WP + w] & my_qm[w]) == my_qv[w]);
-            if (pass) {
-              const float dot = __uint_as_float(v[j]);
-              const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r] + my_qn) : -dot;
-              const uint64_t key = make_key(sc, (uint32_t)prm[r]);
-              if (key < thr) {
-                queue[(size_t)qcnt * TC_T + tid] = key;
-                qcnt++;
-              }
+          for (int w = 0; w < WP; w++) pass = pass && ((aw[j * WP + w] & my_qm[w]) == my_qv[w]);
+          if (pass) {
+            const int r = c0 + j;
+            const float dot = __uint_as_float(v[j]);
+            const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r] + my_qn) : -dot;
+            const uint64_t key = make_key(sc, (uint32_t)prm[r]);
+            if (key < thr) {
+              queue[(size_t)qcnt * TC_T + tid] = key;
+              qcnt++;
             }
           }
         }
@@ -703,14 +717,15 @@ int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem
 
 }  // namespace
 
-int tc_kp(int k) { return k <= 16 ? 16 : 32; }
+int tc_kp(int k) { return k <= 12 ? 12 : (k <= 16 ? 16 : 32); }
 int tc_rerank_depth(int k, int factor) {
   const int f = factor > 0 ? factor : 4;
   return std::min(64, std::max(k, f * k));
 }
 
 bool tc_scan_supported(int d, int k, int kp, int words_pad) {
-  if (d % 8 != 0 || d < 64 || d > 128 || k > 32 || (kp != 16 && kp != 32)) return false;
+  if (d % 8 != 0 || d < 64 || d > 128 || k > 32 || (kp != 12 && kp != 16 && kp != 32))
+    return false;
   // leave room for ~5 KB of static shared memory under the 227 KB limit
   return tc_smem_bytes((d + 63) / 64, words_pad, kp) <= 221 * 1024;
 }
@@ -820,7 +835,13 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
 #define CAPS_TC(WPV, KPV)                                                 \
   return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV>(map, a, g, smem, s) \
                              : launch_tc<CAPS_IP, WPV, KPV>(map, a, g, smem, s)
-  if (t.kp == 16) {
+  if (t.kp == 12) {
+    switch (t.words_pad) {
+      case 1: CAPS_TC(1, 12);
+      case 2: CAPS_TC(2, 12);
+      case 4: CAPS_TC(4, 12);
+    }
+  } else if (t.kp == 16) {
     switch (t.words_pad) {
       case 1: CAPS_TC(1, 16);
       case 2: CAPS_TC(2, 16);

@@ -97,9 +97,46 @@ k_topm(const float* __restrict__ scores, int B, int P2, int m, int metric,
 }
 }  // namespace
 
+// Warp per query: running top-m of the B keys (same keys and order as the
+// bitonic kernel, so the same partitions in the same order).
+template <int KPL>
+__global__ void __launch_bounds__(128)
+k_topm_warp(const float* __restrict__ scores, int64_t nq, int B, int m, int metric,
+            int32_t* __restrict__ probe) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (q >= nq) return;
+  const float* sc = scores + q * B;
+  WarpTopK<KPL> top;
+  top.init();
+  uint64_t kthv = kEmptyKey;
+  for (int b0 = 0; b0 < B; b0 += 32) {
+    const int c = b0 + lane;
+    uint64_t key = kEmptyKey;
+    if (c < B) {
+      const float v = sc[c];
+      key = make_key(metric == CAPS_L2 ? v : -v, (uint32_t)c);
+    }
+    top.offer(key, kthv, m, lane);
+  }
+#pragma unroll
+  for (int s = 0; s < KPL; s++) {
+    const int P = lane * KPL + s;
+    if (P < m) probe[q * m + P] = (int32_t)(top.v[s] & 0xffffffffu);
+  }
+}
+
 int launch_topm(const float* scores, int64_t nq, int B, int m, int metric, int32_t* probe,
                 cudaStream_t s) {
   if (nq == 0) return CAPS_OK;
+  if (m <= 128) {
+    const unsigned g = (unsigned)((nq + 3) / 4);
+    if (m <= 32) k_topm_warp<1><<<g, 128, 0, s>>>(scores, nq, B, m, metric, probe);
+    else if (m <= 64) k_topm_warp<2><<<g, 128, 0, s>>>(scores, nq, B, m, metric, probe);
+    else k_topm_warp<4><<<g, 128, 0, s>>>(scores, nq, B, m, metric, probe);
+    CAPS_LAUNCH("k_topm_warp");
+    return CAPS_OK;
+  }
   int P2 = 1;
   while (P2 < B) P2 <<= 1;
   const size_t smem = sizeof(unsigned long long) * (size_t)P2;

@@ -296,3 +296,12 @@ def test_recall_rises_with_probes_and_reaches_one():
         ids, _ = gi.search(w.Q, w.Qb, 10, m)
         rec.append(O.recall(ids, gt, g64, cnt, 10, X=w.X, Q=w.Q)[1])
     assert rec[0] <= rec[1] <= rec[2] and rec[2] == 1.0
+
+
+@pytest.mark.parametrize("m", [33, 100, 150, 200])
+def test_probe_wide_m_both_selection_kernels(m):
+    # m <= 128 takes the warp running-top-m kernel, m > 128 the bitonic one
+    w = tiny(81, N=4000, d=16, B=200, h=3, integer=True, nq=25)
+    oi = oracle_index(w, iters=2)
+    gi = gpu_index(w, iters=2)
+    np.testing.assert_array_equal(gi.probe(w.Q, m), O.probe(w.Q, oi.C, m))
