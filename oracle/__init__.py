@@ -17,6 +17,9 @@ Function map (paper passage -> function):
   Alg. 2 full query ................. search
   Def. 2 / appendix ground truth .... bruteforce
   appendix RecallK@K ................ recall
+  Sec. 5.2 learned partitioner ...... mlp_forward64, mlp_loss_grad, adam,
+                                      mlp_assign32, mlp_logits32, mlp_labels,
+                                      mlp_train, probe_logits
 """
 from __future__ import annotations
 
@@ -58,6 +61,13 @@ def lib():
                                         P, P, P, i32, i32, i32, P, P, P, P]
         _lib.orc_set_threads.argtypes = [i32]
         _lib.orc_set_threads.restype = i32
+        _lib.orc_mlp_forward64.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P, P]
+        _lib.orc_mlp_loss_grad.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P, P, P, P, P]
+        _lib.orc_mlp_loss_grad.restype = ct.c_double
+        _lib.orc_adam.argtypes = [P, P, P, P, i64, ct.c_double, ct.c_double, ct.c_double,
+                                  ct.c_double, i32]
+        _lib.orc_mlp_assign32.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P]
+        _lib.orc_mlp_logits32.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P]
     return _lib
 
 
@@ -324,3 +334,126 @@ def recall(ids, gt_ids, gt_d64, gt_count, k, X=None, Q=None, metric=L2):
                     hits += 1
             tie[q] = min(hits, denom) / denom
     return float(strict.mean()), float(tie.mean()), strict, tie
+
+
+# ---- Sec. 5.2: learned partitioner (BLISS-style MLP) -------------------------
+
+@dataclasses.dataclass
+class MLP:
+    """f(x) = W2 relu(W1 x + b1) + b2; W1 [H,d], b1 [H], W2 [B,H], b2 [B]."""
+    W1: np.ndarray
+    b1: np.ndarray
+    W2: np.ndarray
+    b2: np.ndarray
+
+    @property
+    def dims(self):
+        return self.W1.shape[1], self.W1.shape[0], self.W2.shape[0]
+
+    def astype(self, dt):
+        return MLP(*(np.ascontiguousarray(a, dtype=dt) for a in (self.W1, self.b1, self.W2, self.b2)))
+
+
+def mlp_forward64(X, net: MLP):
+    X = _c(X, np.float32)
+    d, H, B = net.dims
+    n64 = net.astype(np.float64)
+    Z = np.empty((X.shape[0], B))
+    Hd = np.empty((X.shape[0], H))
+    lib().orc_mlp_forward64(_p(X), X.shape[0], d, H, B, _p(n64.W1), _p(n64.b1), _p(n64.W2),
+                            _p(n64.b2), _p(Z), _p(Hd))
+    return Z, Hd
+
+
+def mlp_loss_grad(X, Y, net: MLP):
+    """Mean softmax cross-entropy and its fp64 gradients (gW1, gb1, gW2, gb2)."""
+    X = _c(X, np.float32)
+    Y = _c(Y, np.float32)
+    d, H, B = net.dims
+    n64 = net.astype(np.float64)
+    g = MLP(np.empty((H, d)), np.empty(H), np.empty((B, H)), np.empty(B))
+    loss = lib().orc_mlp_loss_grad(_p(X), X.shape[0], d, H, B, _p(n64.W1), _p(n64.b1),
+                                   _p(n64.W2), _p(n64.b2), _p(Y), _p(g.W1), _p(g.b1), _p(g.W2),
+                                   _p(g.b2))
+    return loss, g
+
+
+def adam(w, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in place on fp64 arrays (t counts from 1)."""
+    for a in (w, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().orc_adam(_p(w), _p(g), _p(m), _p(v), w.size, lr, beta1, beta2, eps, int(t))
+
+
+def mlp_logits32(X, net: MLP):
+    X = _c(X, np.float32)
+    d, H, B = net.dims
+    n32 = net.astype(np.float32)
+    Z = np.empty((X.shape[0], B), np.float32)
+    lib().orc_mlp_logits32(_p(X), X.shape[0], d, H, B, _p(n32.W1), _p(n32.b1), _p(n32.W2),
+                           _p(n32.b2), _p(Z))
+    return Z
+
+
+def mlp_assign32(X, net: MLP):
+    X = _c(X, np.float32)
+    d, H, B = net.dims
+    n32 = net.astype(np.float32)
+    out = np.empty(X.shape[0], np.int32)
+    lib().orc_mlp_assign32(_p(X), X.shape[0], d, H, B, _p(n32.W1), _p(n32.b1), _p(n32.W2),
+                           _p(n32.b2), _p(out))
+    return out
+
+
+def probe_logits(Q, net: MLP, m):
+    """Top-m partitions by fp32 logit, largest first, ties to the lower id."""
+    Z = mlp_logits32(Q, net)
+    out = np.empty((Z.shape[0], m), np.int32)
+    idx = np.arange(Z.shape[1])
+    for q in range(Z.shape[0]):
+        out[q] = np.lexsort((idx, -Z[q].astype(np.float64)))[:m]
+    return out
+
+
+def mlp_labels(X, attrs: Attrs, bins, samples, sample_cons, B, k=10, metric=L2):
+    """Label of sample s: normalised histogram of the partitions (bins) of its
+    k exact filtered nearest neighbours, the filter being the sample's own
+    attributes on a chosen subset of fields (sample_cons row, -1 = free) and
+    the sample itself excluded; a sample with no neighbour gets its own bin."""
+    samples = np.asarray(samples, np.int64)
+    Qs = np.ascontiguousarray(np.asarray(X, np.float32)[samples])
+    ids, _, _, cnt = bruteforce(X, attrs, Qs, Cons(Qb=sample_cons), k + 1, metric=metric,
+                                order64=False)
+    Y = np.zeros((len(samples), B), np.float32)
+    for r, s in enumerate(samples):
+        nb = [int(i) for i in ids[r] if i >= 0 and i != s][:k]
+        if not nb:
+            Y[r, bins[s]] = 1.0
+            continue
+        for i in nb:
+            Y[r, bins[i]] += 1.0
+        Y[r] /= len(nb)
+    return Y
+
+
+def mlp_train(X, Y, net: MLP, epochs, batch, lr, order=None):
+    """Adam on the mean cross-entropy, fp64, minibatches in the given order
+    (default: sample order); returns the trained net and the loss per step."""
+    X = _c(X, np.float32)
+    Y = _c(Y, np.float32)
+    w = net.astype(np.float64)
+    params = [w.W1, w.b1, w.W2, w.b2]
+    ms = [np.zeros_like(a) for a in params]
+    vs = [np.zeros_like(a) for a in params]
+    n = X.shape[0]
+    losses, t = [], 0
+    for e in range(epochs):
+        idx = np.arange(n) if order is None else np.asarray(order[e])
+        for b0 in range(0, n, batch):
+            sel = idx[b0:b0 + batch]
+            loss, g = mlp_loss_grad(X[sel], Y[sel], w)
+            t += 1
+            for a, ga, ma, va in zip(params, [g.W1, g.b1, g.W2, g.b2], ms, vs):
+                adam(a, np.ascontiguousarray(ga), ma, va, lr, t)
+            losses.append(loss)
+    return w, losses

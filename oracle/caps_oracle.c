@@ -542,3 +542,145 @@ int orc_set_threads(int n) {
   return 1;
 #endif
 }
+
+/* ---- Sec. 5.2 learned partitioner (BLISS-style MLP) ------------------------
+ * f(x) = W2 relu(W1 x + b1) + b2, W1 [H x d], b1 [H], W2 [B x H], b2 [B]
+ * (row-major, output index first).  Training minimises the mean softmax
+ * cross-entropy between f(x_s) and a label distribution Y[s] over the B
+ * partitions; the partition of x is argmax f(x) (ties to the lower index). */
+
+/* fp64 forward: Z [n x B]; Hd [n x H] (post-ReLU) if not NULL */
+void orc_mlp_forward64(const float* X, int64_t n, int d, int H, int B,
+                       const double* W1, const double* b1, const double* W2,
+                       const double* b2, double* Z, double* Hd) {
+  double* h = (double*)malloc(sizeof(double) * (size_t)H);
+  for (int64_t i = 0; i < n; i++) {
+    for (int u = 0; u < H; u++) {
+      double a = b1[u];
+      for (int j = 0; j < d; j++) a += W1[(int64_t)u * d + j] * (double)X[i * d + j];
+      h[u] = a > 0.0 ? a : 0.0;
+      if (Hd) Hd[i * H + u] = h[u];
+    }
+    for (int c = 0; c < B; c++) {
+      double a = b2[c];
+      for (int u = 0; u < H; u++) a += W2[(int64_t)c * H + u] * h[u];
+      Z[i * B + c] = a;
+    }
+  }
+  free(h);
+}
+
+/* Mean softmax cross-entropy and its gradients (fp64). */
+double orc_mlp_loss_grad(const float* X, int64_t n, int d, int H, int B,
+                         const double* W1, const double* b1, const double* W2,
+                         const double* b2, const float* Y, double* gW1, double* gb1,
+                         double* gW2, double* gb2) {
+  double* Z = (double*)malloc(sizeof(double) * (size_t)(n * B));
+  double* Hd = (double*)malloc(sizeof(double) * (size_t)(n * H));
+  double* dz = (double*)malloc(sizeof(double) * (size_t)B);
+  double* dh = (double*)malloc(sizeof(double) * (size_t)H);
+  orc_mlp_forward64(X, n, d, H, B, W1, b1, W2, b2, Z, Hd);
+  memset(gW1, 0, sizeof(double) * (size_t)H * d);
+  memset(gb1, 0, sizeof(double) * (size_t)H);
+  memset(gW2, 0, sizeof(double) * (size_t)B * H);
+  memset(gb2, 0, sizeof(double) * (size_t)B);
+  double loss = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    const double* z = Z + i * B;
+    double mx = z[0];
+    for (int c = 1; c < B; c++) mx = z[c] > mx ? z[c] : mx;
+    double se = 0.0;
+    for (int c = 0; c < B; c++) se += exp(z[c] - mx);
+    const double lse = mx + log(se);
+    double ysum = 0.0;
+    for (int c = 0; c < B; c++) ysum += (double)Y[i * B + c];
+    for (int c = 0; c < B; c++) {
+      const double p = exp(z[c] - lse);
+      loss -= (double)Y[i * B + c] * (z[c] - lse);
+      /* d/dz of -sum_c y_c log p_c = p * sum(y) - y */
+      dz[c] = (p * ysum - (double)Y[i * B + c]) / (double)n;
+    }
+    const double* h = Hd + i * H;
+    for (int c = 0; c < B; c++) {
+      gb2[c] += dz[c];
+      for (int u = 0; u < H; u++) gW2[(int64_t)c * H + u] += dz[c] * h[u];
+    }
+    for (int u = 0; u < H; u++) {
+      double a = 0.0;
+      for (int c = 0; c < B; c++) a += dz[c] * W2[(int64_t)c * H + u];
+      dh[u] = h[u] > 0.0 ? a : 0.0;
+    }
+    for (int u = 0; u < H; u++) {
+      gb1[u] += dh[u];
+      for (int j = 0; j < d; j++) gW1[(int64_t)u * d + j] += dh[u] * (double)X[i * d + j];
+    }
+  }
+  free(Z);
+  free(Hd);
+  free(dz);
+  free(dh);
+  return loss / (double)n;
+}
+
+/* Adam (Kingma & Ba 2015) with bias correction; t counts from 1. */
+void orc_adam(double* w, const double* g, double* m, double* v, int64_t n, double lr,
+              double beta1, double beta2, double eps, int t) {
+  const double c1 = 1.0 - pow(beta1, t), c2 = 1.0 - pow(beta2, t);
+  for (int64_t i = 0; i < n; i++) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+    w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
+}
+
+/* fp32 forward in a fixed order (bias, then coordinates in order with one
+ * fma each; ReLU), used to take the argmax decision the GPU takes. */
+void orc_mlp_assign32(const float* X, int64_t n, int d, int H, int B, const float* W1,
+                      const float* b1, const float* W2, const float* b2, int32_t* bin) {
+#pragma omp parallel
+  {
+    float* h = (float*)malloc(sizeof(float) * (size_t)H);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+      for (int u = 0; u < H; u++) {
+        float a = 0.0f;
+        for (int j = 0; j < d; j++) a = fmaf(W1[(int64_t)u * d + j], X[i * d + j], a);
+        a = a + b1[u];
+        h[u] = a > 0.0f ? a : 0.0f;
+      }
+      int best = 0;
+      float bs = 0.0f;
+      for (int c = 0; c < B; c++) {
+        float a = 0.0f;
+        for (int u = 0; u < H; u++) a = fmaf(W2[(int64_t)c * H + u], h[u], a);
+        a = a + b2[c];
+        if (c == 0 || a > bs) {
+          bs = a;
+          best = c;
+        }
+      }
+      bin[i] = best;
+    }
+    free(h);
+  }
+}
+
+/* fp32 logits in the same fixed order (queries' partition scores). */
+void orc_mlp_logits32(const float* X, int64_t n, int d, int H, int B, const float* W1,
+                      const float* b1, const float* W2, const float* b2, float* Z) {
+  float* h = (float*)malloc(sizeof(float) * (size_t)H);
+  for (int64_t i = 0; i < n; i++) {
+    for (int u = 0; u < H; u++) {
+      float a = 0.0f;
+      for (int j = 0; j < d; j++) a = fmaf(W1[(int64_t)u * d + j], X[i * d + j], a);
+      a = a + b1[u];
+      h[u] = a > 0.0f ? a : 0.0f;
+    }
+    for (int c = 0; c < B; c++) {
+      float a = 0.0f;
+      for (int u = 0; u < H; u++) a = fmaf(W2[(int64_t)c * H + u], h[u], a);
+      Z[i * B + c] = a + b2[c];
+    }
+  }
+  free(h);
+}

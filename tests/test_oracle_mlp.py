@@ -1,0 +1,97 @@
+"""Pins for the oracle's learned partitioner (Sec. 5.2): gradients against
+central finite differences, closed forms of the loss and of Adam's first
+step, and the fp32 fixed-order argmax against the fp64 forward."""
+import numpy as np
+
+import oracle as O
+
+
+def _net(rng, d, H, B, scale=0.3):
+    return O.MLP(scale * rng.standard_normal((H, d)), 0.1 * rng.standard_normal(H),
+                 scale * rng.standard_normal((B, H)), 0.1 * rng.standard_normal(B))
+
+
+def test_loss_closed_forms():
+    rng = np.random.default_rng(1)
+    d, H, B = 3, 4, 5
+    X = rng.standard_normal((6, d)).astype(np.float32)
+    zero = O.MLP(np.zeros((H, d)), np.zeros(H), np.zeros((B, H)), np.zeros(B))
+    Y = np.eye(B, dtype=np.float32)[rng.integers(0, B, 6)]
+    loss, g = O.mlp_loss_grad(X, Y, zero)
+    # all logits equal: p = 1/B, loss = log B; dL/db2 = mean(p - y)
+    assert abs(loss - np.log(B)) < 1e-12
+    np.testing.assert_allclose(g.b2, (1.0 / B - Y.astype(np.float64)).mean(0), atol=1e-12)
+    np.testing.assert_array_equal(g.W1, 0.0)  # relu(0) = 0 blocks the first layer
+
+
+def test_gradients_match_central_differences():
+    rng = np.random.default_rng(2)
+    d, H, B, n = 5, 7, 6, 9
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = rng.random((n, B)).astype(np.float32)
+    Y /= Y.sum(1, keepdims=True)
+    net = _net(rng, d, H, B)
+    loss, g = O.mlp_loss_grad(X, Y, net)
+    eps = 1e-6
+    for name in ("W1", "b1", "W2", "b2"):
+        P = getattr(net, name)
+        G = getattr(g, name)
+        for idx in list(np.ndindex(P.shape))[:: max(1, P.size // 12)]:
+            old = P[idx]
+            P[idx] = old + eps
+            lp, _ = O.mlp_loss_grad(X, Y, net)
+            P[idx] = old - eps
+            lm, _ = O.mlp_loss_grad(X, Y, net)
+            P[idx] = old
+            num = (lp - lm) / (2 * eps)
+            assert abs(num - G[idx]) <= 1e-6 * max(1.0, abs(num)), (name, idx, num, G[idx])
+
+
+def test_adam_first_step_is_lr_times_sign():
+    w = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    m = np.zeros(3)
+    v = np.zeros(3)
+    O.adam(w, g, m, v, lr=0.01, t=1, eps=1e-12)
+    # bias-corrected first moment g and second moment g^2 -> step lr*sign(g)
+    np.testing.assert_allclose(w, [1.0 - 0.01, -2.0 + 0.01, 0.5 - 0.01], rtol=1e-9)
+
+
+def test_fp32_assign_matches_fp64_argmax_when_separated():
+    rng = np.random.default_rng(3)
+    d, H, B = 8, 16, 10
+    X = rng.standard_normal((200, d)).astype(np.float32)
+    net = _net(rng, d, H, B, scale=1.0)
+    Z, _ = O.mlp_forward64(X, net)
+    srt = np.sort(Z, 1)
+    clear = (srt[:, -1] - srt[:, -2]) > 1e-3
+    got = O.mlp_assign32(X, net)
+    np.testing.assert_array_equal(got[clear], Z.argmax(1)[clear])
+    Z32 = O.mlp_logits32(X, net)
+    np.testing.assert_allclose(Z32, Z, rtol=1e-4, atol=1e-4)
+
+
+def test_training_reduces_loss_and_labels_are_distributions():
+    from workloads import make_dense_workload
+    w = make_dense_workload(name="mlp", N=1500, d=8, ncomp=5, center=("normal", 3.0), sigma=1.0,
+                            vocab=[3, 4], zipf_s=1.0, nq=5, cmin=1, cmax=2, B=5, h=2, iters=5, m=2,
+                            k=5, seed=9)
+    at = O.Attrs.of(w)
+    C, bins = O.kmeans(w.X, w.B, w.iters, w.init_idx)
+    rng = np.random.default_rng(4)
+    samples = rng.choice(w.N, 120, replace=False)
+    cons = np.where(rng.random((120, 2)) < 0.5, w.A[samples], -1).astype(np.int32)
+    Y = O.mlp_labels(w.X, at, bins, samples, cons, w.B, k=5)
+    np.testing.assert_allclose(Y.sum(1), 1.0, rtol=1e-6)
+    # a sample's neighbours share its constraint: check one label by hand
+    s0 = int(samples[0])
+    ok = np.all((cons[0] < 0) | (w.A == cons[0]), axis=1)
+    ok[s0] = False
+    cand = np.nonzero(ok)[0]
+    dd = ((w.X[cand].astype(np.float64) - w.X[s0]) ** 2).sum(1)
+    nb = cand[np.lexsort((cand, dd))[:5]]
+    want = np.bincount(bins[nb], minlength=w.B) / len(nb)
+    np.testing.assert_allclose(Y[0], want, rtol=1e-6)
+    net = _net(np.random.default_rng(5), 8, 16, w.B, scale=0.3)
+    _, losses = O.mlp_train(w.X[samples], Y, net, epochs=30, batch=40, lr=1e-2)
+    assert losses[-1] < 0.7 * losses[0]
