@@ -88,7 +88,16 @@ typedef struct {
  *   metric       CAPS_L2 (squared Euclidean, smaller is better) or CAPS_IP
  *                (inner product, larger is better; k-means then normalises
  *                each centroid to unit length).
- *   part         CAPS_PART_KMEANS.
+ *   part         CAPS_PART_KMEANS: f(x) = nearest centroid (Sec. 5.2).
+ *                CAPS_PART_MLP: learned partitioner (Sec. 5.2, BLISS-style):
+ *                k-means first, then labels = normalised histogram of the
+ *                k-means partitions of each training point's mlp_label_k
+ *                exact filtered neighbours (the filter being the point's own
+ *                attributes on a subset of fields), an MLP
+ *                d -> mlp_hidden -> B (ReLU) trained with Adam on the mean
+ *                softmax cross-entropy, and f(x) = argmax of its logits
+ *                (ties to the lower partition); queries probe the m largest
+ *                logits.
  *   prec         CAPS_FP32: every distance in fp32.
  *                CAPS_BF16: the index also keeps a bf16 copy of the rows;
  *                searches score all selected rows with bf16 tensor-core
@@ -99,7 +108,22 @@ typedef struct {
  *                64) use the fp32 scan instead.
  *   rerank_factor candidates re-scored per result in the bf16 form
  *                (0 = 4, at most 16).
- *   mlp_hidden, mlp_epochs: reserved, pass 0.
+ *   mlp_hidden   hidden units H (0 = 512).
+ *   mlp_epochs   passes over the training points (0 = use mlp_init as the
+ *                trained network).
+ *   mlp_samples  training points S (0 = min(N, 32768)).
+ *   mlp_batch    minibatch size (0 = 4096); minibatches follow the sample
+ *                order, the same every epoch.
+ *   mlp_lr       Adam step size (0 = 1e-3; beta 0.9/0.999, eps 1e-8).
+ *   mlp_label_k  neighbours per label (0 = 10).
+ *   mlp_sample_idx  optional [S] int64 training point ids (else drawn with
+ *                SplitMix64(seed + 1)).
+ *   mlp_sample_cons optional [S*L] int32 label filters, -1 = free field
+ *                (else each field kept with probability 1/2, at least one).
+ *   mlp_init     optional initial weights, fp32, W1 [H*d] | b1 [H] |
+ *                W2 [B*H] | b2 [B] (row-major, output index first); else
+ *                U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and zero biases
+ *                from SplitMix64(seed + 2).
  *   init_idx     optional [B] int64: k-means seed point ids (distinct).
  *   centroids    optional [B*d] fp32: fixed first-level centroids; k-means is
  *                skipped and f(x) = best centroid (Alg. 1 first loop).
@@ -114,6 +138,12 @@ typedef struct {
   int32_t mlp_hidden, mlp_epochs;
   const int64_t* init_idx;
   const float* centroids;
+  int32_t mlp_samples, mlp_batch;
+  float mlp_lr;
+  int32_t mlp_label_k;
+  const int64_t* mlp_sample_idx;
+  const int32_t* mlp_sample_cons;
+  const float* mlp_init;
 } caps_build_params;
 
 /*
@@ -125,8 +155,9 @@ typedef struct {
  * sum(vocab[0..f-1]) + value), then a stable sort by (partition, block, id)
  * into contiguous sub-partitions.  Inputs may be freed on return.
  * Returns CAPS_EINVAL for N < 1, d < 1, B outside [1, N], h outside [0, 63],
- * bad attribute values, a dense packing wider than 128 bits, or sparse
- * attributes (not yet supported by this build).
+ * bad attribute values, a dense packing wider than 128 bits, sparse
+ * attributes (not yet supported by this build), or an MLP build without
+ * epochs and without initial weights.
  */
 int caps_build(const caps_build_params* params, const float* X, int64_t N,
                int32_t d, const caps_attrs* attrs, void* stream,
@@ -175,6 +206,9 @@ typedef struct {
   int64_t n_codes;       /* dense: sum(vocab); sparse: sp_vocab */
   int32_t attr_words;    /* packed 32-bit attribute words per row */
   int64_t device_bytes;  /* device memory held by the index */
+  int32_t part;          /* caps_partitioner of the index */
+  int32_t mlp_hidden;    /* H of the learned partitioner (0 for k-means) */
+  int64_t n_labels;      /* training points of the learned partitioner */
 } caps_index_info;
 
 int caps_get_info(const caps_index* index, caps_index_info* out);
@@ -196,7 +230,9 @@ enum {
   CAPS_ARR_TAGS = 2,
   CAPS_ARR_KEY = 3,
   CAPS_ARR_PERM = 4,
-  CAPS_ARR_OFFSETS = 5
+  CAPS_ARR_OFFSETS = 5,
+  CAPS_ARR_MLP = 6,     /* [H*d + H + B*H + B] fp32 W1|b1|W2|b2 (MLP index) */
+  CAPS_ARR_LABELS = 7   /* [S*B] fp32 training labels (MLP index) */
 };
 int caps_export(const caps_index* index, int32_t which, void* dst,
                 size_t bytes, void* stream);
@@ -227,6 +263,31 @@ int caps_probe(const caps_index* index, const float* Q, int64_t nq, int32_t m,
 int caps_select(const caps_index* index, const int32_t* probe, int64_t nq,
                 int32_t m, const caps_attrs* constraints, uint64_t* out_sel,
                 void* stream);
+
+/* ---- learned partitioner steps (Sec. 5.2), for checking each alone -------- */
+
+/* Mean softmax cross-entropy of the MLP on n rows X [n*d] against label
+ * distributions Y [n*B], and its gradients (same layouts as the weights).
+ * All fp32; loss = one float. */
+int caps_mlp_loss_grad(int32_t d, int32_t H, int32_t B, const float* W1,
+                       const float* b1, const float* W2, const float* b2,
+                       const float* X, int64_t n, const float* Y, float* gW1,
+                       float* gb1, float* gW2, float* gb2, float* loss,
+                       void* stream);
+
+/* Adam training in place: W = [H*d + H + B*H + B] fp32 (W1|b1|W2|b2),
+ * minibatches of `batch` rows of X/Y in order, `epochs` passes, step lr
+ * (beta 0.9/0.999, eps 1e-8).  losses (optional, host) receives the loss of
+ * every step (epochs * ceil(n / batch) floats). */
+int caps_mlp_train(int32_t d, int32_t H, int32_t B, float* W, const float* X,
+                   int64_t n, const float* Y, int32_t epochs, int32_t batch,
+                   float lr, float* losses, void* stream);
+
+/* f(x) = argmax of the logits (ties to the lower partition) for n rows;
+ * every logit accumulates its products in index order with one fma each,
+ * bias added last, ReLU on the hidden layer. */
+int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W,
+                    const float* X, int64_t n, int32_t* out_bin, void* stream);
 
 /* ---- batched query without device allocation ------------------------------ */
 

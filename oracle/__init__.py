@@ -56,7 +56,7 @@ def lib():
         _lib.orc_probe.argtypes = [P, i64, i32, P, i32, i32, i32, P]
         _lib.orc_select.argtypes = [P, i32, i32, P, ct.c_int32, P, i64, i32, P, P, P, P]
         _lib.orc_search.argtypes = [P, i64, i32, i32, P, P, P, P, ct.c_int32, P, i32, i32,
-                                    P, i32, P, P, P, i64, P, P, P, i32, i32, P, P, P, P]
+                                    P, i32, P, P, P, i64, P, P, P, i32, i32, P, P, P, P, P]
         _lib.orc_bruteforce.argtypes = [P, i64, i32, i32, P, P, P, P, ct.c_int32, P, i64,
                                         P, P, P, i32, i32, i32, P, P, P, P]
         _lib.orc_set_threads.argtypes = [i32]
@@ -256,9 +256,13 @@ class Index:
     metric: int
 
 
-def build(X, attrs: Attrs, B, h, iters, init_idx, metric=L2, C=None) -> Index:
-    """Alg. 1: k-means first level (or given centroids), AFT, layout."""
-    if C is None:
+def build(X, attrs: Attrs, B, h, iters, init_idx, metric=L2, C=None, bins=None) -> Index:
+    """Alg. 1: k-means first level (or given centroids, or given partitions
+    `bins` from a learned f), AFT, layout."""
+    if bins is not None:
+        C = np.zeros((B, np.asarray(X).shape[1]), np.float32) if C is None else _c(C, np.float32)
+        bin = _c(bins, np.int32)
+    elif C is None:
         C, bin = kmeans(X, B, iters, init_idx, metric)
     else:
         C = _c(C, np.float32)
@@ -269,9 +273,11 @@ def build(X, attrs: Attrs, B, h, iters, init_idx, metric=L2, C=None) -> Index:
                  metric=metric)
 
 
-def search(X, attrs: Attrs, index: Index, Q, cons: Cons, k, m):
+def search(X, attrs: Attrs, index: Index, Q, cons: Cons, k, m, probe_in=None):
     """Alg. 2 for every query: returns ids [nq,k] (original ids, -1 pad),
-    fp32 distances [nq,k], rows attribute-tested and rows matched per query."""
+    fp32 distances [nq,k], rows attribute-tested and rows matched per query.
+    probe_in [nq,m] (optional): the partitions to probe (e.g. from a learned
+    f(q)); by default the m nearest centroids."""
     X = _c(X, np.float32)
     Q = _c(Q, np.float32)
     nq = Q.shape[0]
@@ -285,7 +291,8 @@ def search(X, attrs: Attrs, index: Index, Q, cons: Cons, k, m):
     offsets = _c(index.offsets, np.int32)
     lib().orc_search(_p(X), X.shape[0], X.shape[1], *attrs.args(), _p(C), index.B,
                      index.metric, _p(tags), index.h, _p(perm), _p(offsets), _p(Q), nq,
-                     *cons.args(), k, m, _p(ids), _p(dist), _p(n_scan), _p(n_match))
+                     *cons.args(), k, m, _p(ids), _p(dist), _p(n_scan), _p(n_match),
+                     _p(_c(probe_in, np.int32)))
     return ids, dist, n_scan, n_match
 
 

@@ -447,7 +447,9 @@ void orc_search(const float* X, int64_t N, int d, int L, const int32_t* A,
                 const int32_t* offsets, const float* Q, int64_t nq,
                 const int32_t* Qb, const int64_t* q_off, const int32_t* q_lab,
                 int k, int m, int64_t* out_ids, float* out_dist, int64_t* n_scan,
-                int64_t* n_match) {
+                int64_t* n_match, const int32_t* probe_in) {
+  /* probe_in (optional [nq*m]): partitions to probe (a learned f(q)); else
+     the m nearest centroids */
   attrs_t a = mk_attrs(L, A, vocab, sp_off, sp_lab, sp_vocab);
   (void)N;
 #pragma omp parallel
@@ -458,7 +460,8 @@ void orc_search(const float* X, int64_t N, int d, int L, const int32_t* A,
     g_metric_cmp = metric;
 #pragma omp for schedule(dynamic, 1)
     for (int64_t q = 0; q < nq; q++) {
-      orc_probe(Q + q * d, 1, d, C, B, metric, m, probe);
+      if (probe_in) memcpy(probe, probe_in + q * m, sizeof(int32_t) * (size_t)m);
+      else orc_probe(Q + q * d, 1, d, C, B, metric, m, probe);
       const int32_t* b = A ? Qb + q * L : NULL;
       const int32_t* lab = A ? NULL : q_lab + q_off[q];
       int64_t nlab = A ? 0 : q_off[q + 1] - q_off[q];

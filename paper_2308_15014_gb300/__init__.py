@@ -22,12 +22,14 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcaps_gb300.so")
 CAPS_OK, CAPS_EINVAL, CAPS_ENOMEM, CAPS_ECUDA, CAPS_ETIMEOUT = 0, 1, 2, 3, 4
 L2, IP = 0, 1
 FP32, BF16 = 0, 1
-ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS = range(6)
+KMEANS, MLP = 0, 1
+ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS, ARR_MLP, ARR_LABELS = range(8)
 
 # Every symbol declared in include/caps.h.
 EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "caps_get_info",
            "caps_export", "caps_assign", "caps_probe", "caps_select", "caps_set_timing",
-           "caps_get_stage_times", "caps_search_batch_noalloc", "caps_device_status")
+           "caps_get_stage_times", "caps_search_batch_noalloc", "caps_device_status",
+           "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign")
 
 
 class CapsError(RuntimeError):
@@ -45,7 +47,10 @@ class caps_build_params(ct.Structure):
     _fields_ = [("B", ct.c_int32), ("h", ct.c_int32), ("kmeans_iters", ct.c_int32),
                 ("seed", ct.c_uint64), ("metric", ct.c_int), ("part", ct.c_int),
                 ("prec", ct.c_int), ("rerank_factor", ct.c_int32), ("mlp_hidden", ct.c_int32),
-                ("mlp_epochs", ct.c_int32), ("init_idx", ct.c_void_p), ("centroids", ct.c_void_p)]
+                ("mlp_epochs", ct.c_int32), ("init_idx", ct.c_void_p), ("centroids", ct.c_void_p),
+                ("mlp_samples", ct.c_int32), ("mlp_batch", ct.c_int32), ("mlp_lr", ct.c_float),
+                ("mlp_label_k", ct.c_int32), ("mlp_sample_idx", ct.c_void_p),
+                ("mlp_sample_cons", ct.c_void_p), ("mlp_init", ct.c_void_p)]
 
 
 class caps_stage_times(ct.Structure):
@@ -57,7 +62,8 @@ class caps_stage_times(ct.Structure):
 class caps_index_info(ct.Structure):
     _fields_ = [("N", ct.c_int64), ("d", ct.c_int32), ("B", ct.c_int32), ("h", ct.c_int32),
                 ("L", ct.c_int32), ("metric", ct.c_int32), ("n_codes", ct.c_int64),
-                ("attr_words", ct.c_int32), ("device_bytes", ct.c_int64)]
+                ("attr_words", ct.c_int32), ("device_bytes", ct.c_int64), ("part", ct.c_int32),
+                ("mlp_hidden", ct.c_int32), ("n_labels", ct.c_int64)]
 
 
 _lib = None
@@ -88,6 +94,9 @@ def lib(path: Optional[str] = None):
     L.caps_search_batch_noalloc.argtypes = [P, P, i64, ct.POINTER(caps_attrs), i32, i32, P, P,
                                             P]
     L.caps_device_status.argtypes = [P, P]
+    L.caps_mlp_loss_grad.argtypes = [i32, i32, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]
+    L.caps_mlp_train.argtypes = [i32, i32, i32, P, P, i64, P, i32, i32, ct.c_float, P, P]
+    L.caps_mlp_assign.argtypes = [i32, i32, i32, P, P, i64, P, P]
     L.caps_set_timing.argtypes = [i32]
     L.caps_get_stage_times.argtypes = [ct.POINTER(caps_stage_times)]
     _lib = L
@@ -179,6 +188,48 @@ def stage_times() -> dict:
     return {f: getattr(t, f) for f, _ in caps_stage_times._fields_}
 
 
+def mlp_flat(W1, b1, W2, b2):
+    """Concatenate the MLP weights in the library's order W1|b1|W2|b2."""
+    return np.ascontiguousarray(np.concatenate([np.ravel(W1), np.ravel(b1), np.ravel(W2),
+                                                np.ravel(b2)]).astype(np.float32))
+
+
+def mlp_loss_grad(W1, b1, W2, b2, X, Y, stream=None):
+    """caps_mlp_loss_grad: loss and fp32 gradients (gW1, gb1, gW2, gb2)."""
+    W1, b1, W2, b2 = (np.ascontiguousarray(a, np.float32) for a in (W1, b1, W2, b2))
+    X = np.ascontiguousarray(X, np.float32)
+    Y = np.ascontiguousarray(Y, np.float32)
+    H, d = W1.shape
+    B = W2.shape[0]
+    g = [np.empty_like(a) for a in (W1, b1, W2, b2)]
+    loss = ct.c_float()
+    _check(lib().caps_mlp_loss_grad(d, H, B, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2), _ptr(X),
+                                    X.shape[0], _ptr(Y), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]),
+                                    _ptr(g[3]), ct.byref(loss), _stream(stream)))
+    return float(loss.value), g
+
+
+def mlp_train(W, d, H, B, X, Y, epochs, batch, lr, stream=None):
+    """caps_mlp_train on a flat W1|b1|W2|b2 copy; returns (W, losses)."""
+    W = np.array(W, np.float32, copy=True)
+    X = np.ascontiguousarray(X, np.float32)
+    Y = np.ascontiguousarray(Y, np.float32)
+    steps = epochs * ((X.shape[0] + batch - 1) // batch)
+    losses = np.zeros(max(1, steps), np.float32)
+    _check(lib().caps_mlp_train(d, H, B, _ptr(W), _ptr(X), X.shape[0], _ptr(Y), epochs, batch,
+                                lr, _ptr(losses), _stream(stream)))
+    return W, losses[:steps]
+
+
+def mlp_assign(W, d, H, B, X, stream=None):
+    """caps_mlp_assign: argmax partition of every row of X."""
+    W = np.ascontiguousarray(W, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    out = np.empty(X.shape[0], np.int32)
+    _check(lib().caps_mlp_assign(d, H, B, _ptr(W), _ptr(X), X.shape[0], _ptr(out), _stream(stream)))
+    return out
+
+
 class Index:
     """A CAPS index living in GPU memory (caps_build / caps_free)."""
 
@@ -190,13 +241,27 @@ class Index:
 
     @classmethod
     def build(cls, X, A, vocab, B, h=15, iters=20, metric=L2, init_idx=None, centroids=None,
-              seed=0, prec=FP32, rerank_factor=0, stream=None) -> "Index":
+              seed=0, prec=FP32, rerank_factor=0, part=KMEANS, mlp_hidden=0, mlp_epochs=0,
+              mlp_samples=0, mlp_batch=0, mlp_lr=0.0, mlp_label_k=0, mlp_sample_idx=None,
+              mlp_sample_cons=None, mlp_init=None, stream=None) -> "Index":
         X = _np_or_keep(X, np.float32)
         N, d = X.shape
         at, keep = _dense_attrs(A, vocab)
         p = caps_build_params()
         p.B, p.h, p.kmeans_iters, p.seed, p.metric = B, h, iters, seed, metric
-        p.part, p.prec, p.rerank_factor = 0, prec, rerank_factor
+        p.part, p.prec, p.rerank_factor = part, prec, rerank_factor
+        p.mlp_hidden, p.mlp_epochs, p.mlp_samples, p.mlp_batch = (mlp_hidden, mlp_epochs,
+                                                                  mlp_samples, mlp_batch)
+        p.mlp_lr, p.mlp_label_k = mlp_lr, mlp_label_k
+        if mlp_sample_idx is not None:
+            mlp_sample_idx = _np_or_keep(mlp_sample_idx, np.int64)
+            p.mlp_sample_idx = _ptr(mlp_sample_idx)
+        if mlp_sample_cons is not None:
+            mlp_sample_cons = _np_or_keep(mlp_sample_cons, np.int32)
+            p.mlp_sample_cons = _ptr(mlp_sample_cons)
+        if mlp_init is not None:
+            mlp_init = _np_or_keep(mlp_init, np.float32)
+            p.mlp_init = _ptr(mlp_init)
         if init_idx is not None:
             init_idx = _np_or_keep(init_idx, np.int64)
             p.init_idx = _ptr(init_idx)
@@ -229,6 +294,9 @@ class Index:
                   ARR_TAGS: ((i.B, i.h), np.int32), ARR_KEY: ((i.N,), np.uint8),
                   ARR_PERM: ((i.N,), np.int32),
                   ARR_OFFSETS: ((i.B * (i.h + 1) + 1,), np.int32)}
+        Hm = i.mlp_hidden
+        shapes[ARR_MLP] = ((Hm * i.d + Hm + i.B * Hm + i.B,), np.float32)
+        shapes[ARR_LABELS] = ((i.n_labels, i.B), np.float32)
         shape, dt = shapes[which]
         out = np.empty(shape, dtype=dt)
         _check(lib().caps_export(self._h, which, _ptr(out) if out.size else 1, out.nbytes,

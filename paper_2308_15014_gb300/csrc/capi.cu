@@ -187,6 +187,155 @@ using namespace caps;
 
 extern "C" const char* caps_last_error(void) { return g_err.c_str(); }
 
+namespace caps {
+namespace {
+// Label of training point s: normalised histogram of the partitions of its
+// first label_k search results other than itself (its own partition when it
+// has none).
+__global__ void k_mlp_labels(const int64_t* __restrict__ ids, int kq, const int64_t* __restrict__ samples,
+                             int64_t S, int label_k, const int32_t* __restrict__ bin, int B,
+                             float* __restrict__ Y) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= S) return;
+  const int64_t self = samples[r];
+  int cnt = 0;
+  for (int j = 0; j < kq && cnt < label_k; j++) {
+    const int64_t i = ids[r * kq + j];
+    if (i < 0 || i == self) continue;
+    cnt++;
+  }
+  float* y = Y + r * B;
+  if (cnt == 0) {
+    y[bin[self]] = 1.f;
+    return;
+  }
+  const float w = 1.f / (float)cnt;
+  int seen = 0;
+  for (int j = 0; j < kq && seen < cnt; j++) {
+    const int64_t i = ids[r * kq + j];
+    if (i < 0 || i == self) continue;
+    y[bin[i]] += w;
+    seen++;
+  }
+}
+__global__ void k_mlp_cons(const int32_t* __restrict__ A, int L, const int64_t* __restrict__ samples,
+                           const uint8_t* __restrict__ keep, int64_t S, int32_t* __restrict__ cons) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= S * L) return;
+  const int64_t r = t / L, f = t % L;
+  cons[t] = keep[t] ? A[samples[r] * L + f] : -1;
+}
+double u01(uint64_t* st) { return (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0); }
+}  // namespace
+}  // namespace caps
+
+// Learned partitioner (Sec. 5.2): labels from exact filtered neighbours over
+// the k-means index, Adam training, f(x) = argmax logits into ix->bin.
+static int build_mlp(const caps_build_params* p, const float* dX, const int32_t* dA, int64_t N,
+                     int d, const DenseMeta& meta, cudaStream_t s, caps_index* ix) {
+  const int B = p->B, L = meta.L;
+  const int H = p->mlp_hidden > 0 ? p->mlp_hidden : 512;
+  const int64_t S = p->mlp_samples > 0 ? std::min<int64_t>(p->mlp_samples, N)
+                                       : std::min<int64_t>(N, 32768);
+  const int batch = p->mlp_batch > 0 ? p->mlp_batch : 4096;
+  const float lr = p->mlp_lr > 0.f ? p->mlp_lr : 1e-3f;
+  const int lk = p->mlp_label_k > 0 ? p->mlp_label_k : 10;
+  Scratch scr(s);
+  // training points
+  std::vector<int64_t> samp;
+  if (p->mlp_sample_idx) {
+    if (int rc = to_host(p->mlp_sample_idx, (size_t)S, &samp, s)) return rc;
+    for (int64_t v : samp)
+      if (v < 0 || v >= N) return fail(CAPS_EINVAL, "mlp_sample_idx entry outside [0, N)");
+  } else {
+    samp = floyd_sample(N, S, p->seed + 1);
+  }
+  int64_t* dS = nullptr;
+  if (int rc = scr.get(&dS, (size_t)S)) return rc;
+  CAPS_CUDA(cudaMemcpyAsync(dS, samp.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, s));
+  // label filters
+  const int32_t* dCons = nullptr;
+  int32_t* cons_buf = nullptr;
+  if (p->mlp_sample_cons) {
+    if (int rc = stage_in(p->mlp_sample_cons, (size_t)S * L, scr, s, &dCons)) return rc;
+  } else {
+    std::vector<uint8_t> keep((size_t)S * L, 0);
+    uint64_t st = p->seed + 3;
+    for (int64_t r = 0; r < S; r++) {
+      int any = 0;
+      for (int f = 0; f < L; f++) {
+        keep[r * L + f] = u01(&st) < 0.5 ? 1 : 0;
+        any |= keep[r * L + f];
+      }
+      if (!any) keep[r * L + (int)(splitmix64(&st) % (uint64_t)L)] = 1;
+    }
+    uint8_t* dkeep = nullptr;
+    if (int rc = scr.get(&dkeep, (size_t)S * L)) return rc;
+    if (int rc = scr.get(&cons_buf, (size_t)S * L)) return rc;
+    CAPS_CUDA(cudaMemcpyAsync(dkeep, keep.data(), keep.size(), cudaMemcpyHostToDevice, s));
+    k_mlp_cons<<<(unsigned)((S * L + 255) / 256), 256, 0, s>>>(dA, L, dS, dkeep, S, cons_buf);
+    CAPS_LAUNCH("k_mlp_cons");
+    CAPS_CUDA(cudaStreamSynchronize(s));  // `keep` leaves scope
+    dCons = cons_buf;
+  }
+  // exact filtered neighbours of the training points (m = B, fp32 scan)
+  float* Xs = nullptr;
+  if (int rc = scr.get(&Xs, (size_t)S * d)) return rc;
+  if (int rc = mlp_gather_rows(dX, dS, S, d, Xs, s)) return rc;
+  const int kq = lk + 1;
+  int64_t* nid = nullptr;
+  float* ndist = nullptr;
+  if (int rc = scr.get(&nid, (size_t)S * kq)) return rc;
+  if (int rc = scr.get(&ndist, (size_t)S * kq)) return rc;
+  caps_attrs ca;
+  ca.L = L;
+  ca.dense = dCons;
+  ca.vocab = nullptr;
+  ca.sp_offsets = nullptr;
+  ca.sp_labels = nullptr;
+  ca.sp_vocab = 0;
+  const int keep_prec = ix->prec;
+  ix->prec = CAPS_FP32;
+  const int rc_s = caps_search_batch(ix, Xs, S, &ca, kq, B, nid, ndist, s);
+  ix->prec = keep_prec;
+  if (rc_s) return rc_s;
+  if (int rc = ix->alloc(&ix->labels, (size_t)S * B)) return rc;
+  ix->n_labels = S;
+  CAPS_CUDA(cudaMemsetAsync(ix->labels, 0, sizeof(float) * S * B, s));
+  k_mlp_labels<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(nid, kq, dS, S, lk, ix->bin, B,
+                                                           ix->labels);
+  CAPS_LAUNCH("k_mlp_labels");
+  // network
+  ix->mlp.d = d;
+  ix->mlp.H = H;
+  ix->mlp.B = B;
+  float* wbase = nullptr;
+  if (int rc = ix->alloc(&wbase, (size_t)ix->mlp.size())) return rc;
+  ix->mlp.bind(wbase);
+  if (p->mlp_init) {
+    const float* dW = nullptr;
+    if (int rc = stage_in(p->mlp_init, (size_t)ix->mlp.size(), scr, s, &dW)) return rc;
+    CAPS_CUDA(cudaMemcpyAsync(wbase, dW, sizeof(float) * ix->mlp.size(), cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::vector<float> w((size_t)ix->mlp.size(), 0.f);
+    uint64_t st = p->seed + 2;
+    const double a1 = 1.0 / std::sqrt((double)d), a2 = 1.0 / std::sqrt((double)H);
+    for (int64_t i = 0; i < (int64_t)H * d; i++) w[i] = (float)((2.0 * u01(&st) - 1.0) * a1);
+    float* w2 = w.data() + (int64_t)H * d + H;
+    for (int64_t i = 0; i < (int64_t)B * H; i++) w2[i] = (float)((2.0 * u01(&st) - 1.0) * a2);
+    CAPS_CUDA(cudaMemcpyAsync(wbase, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, s));
+    CAPS_CUDA(cudaStreamSynchronize(s));
+  }
+  if (p->mlp_epochs > 0)
+    if (int rc = mlp_train(ix->mlp, Xs, S, ix->labels, p->mlp_epochs, batch, lr, nullptr, s))
+      return rc;
+  // f(x) = argmax logits for every point
+  if (int rc = mlp_assign(ix->mlp, dX, N, ix->bin, scr, s)) return rc;
+  ix->part = CAPS_PART_MLP;
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
 static int build_impl(const caps_build_params* p, const float* X, int64_t N, int32_t d,
                       const caps_attrs* attrs, cudaStream_t s, caps_index* ix) {
   if (!p || !X || !attrs) return fail(CAPS_EINVAL, "null argument");
@@ -197,7 +346,15 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   if ((int64_t)p->B * (p->h + 1) >= (int64_t)INT32_MAX) return fail(CAPS_EINVAL, "B*(h+1) too large");
   if (p->kmeans_iters < 0) return fail(CAPS_EINVAL, "kmeans_iters must be >= 0");
   if (p->metric != CAPS_L2 && p->metric != CAPS_IP) return fail(CAPS_EINVAL, "unknown metric");
-  if (p->part != CAPS_PART_KMEANS) return fail(CAPS_EINVAL, "only the k-means partitioner is built");
+  if (p->part != CAPS_PART_KMEANS && p->part != CAPS_PART_MLP)
+    return fail(CAPS_EINVAL, "unknown partitioner");
+  if (p->part == CAPS_PART_MLP) {
+    if (p->mlp_hidden < 0 || p->mlp_epochs < 0 || p->mlp_samples < 0 || p->mlp_batch < 0 ||
+        p->mlp_label_k < 0 || p->mlp_label_k > kMaxK - 1 || !(p->mlp_lr >= 0.f))
+      return fail(CAPS_EINVAL, "bad MLP parameters");
+    if (p->mlp_epochs == 0 && !p->mlp_init)
+      return fail(CAPS_EINVAL, "an MLP build needs mlp_epochs > 0 or mlp_init");
+  }
   if (p->prec != CAPS_FP32 && p->prec != CAPS_BF16)
     return fail(CAPS_EINVAL, "precision must be CAPS_FP32 or CAPS_BF16");
   if (p->prec == CAPS_BF16 && (d % 8 != 0 || d < 64 || d > 128))
@@ -284,19 +441,28 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   }
   // ---- f(x_i) for every point (Alg. 1, first loop) ----
   if (int rc = launch_assign(dX, N, d, ix->C, B, p->metric, ix->bin, s)) return rc;
-  if (int rc = stable_sort_by_key(ix->bin, N, B, perm_bin, bin_off, scr, s)) return rc;
-  // ---- attribute frequency tree per partition (Alg. 1, second loop) ----
-  CAPS_CUDA(cudaMemsetAsync(ix->key, 0, (size_t)N, s));
-  if (int rc = launch_aft(perm_bin, bin_off, B, h, dA, meta, ix->code_field, ix->tags, ix->key, s))
-    return rc;
-  // ---- contiguous sub-partitions: stable order by (partition, block, id) ----
   int32_t* seg = nullptr;
   if (int rc = scr.get(&seg, (size_t)N)) return rc;
-  if (int rc = launch_segment_keys(ix->bin, ix->key, N, h, seg, s)) return rc;
-  if (int rc = stable_sort_by_key(seg, N, nseg, ix->perm, ix->offsets, scr, s)) return rc;
-  if (int rc = launch_layout(dX, dA, ix->perm, N, d, meta, ix->Xp, ix->Ap, s)) return rc;
-  CAPS_CUDA(cudaMemsetAsync(ix->pos, 0, (size_t)B * meta.n_codes, s));
-  if (int rc = launch_pos_table(ix->tags, B, h, meta.n_codes, ix->pos, s)) return rc;
+  // partitions -> attribute frequency tree -> contiguous layout
+  auto finish = [&]() -> int {
+    if (int rc = stable_sort_by_key(ix->bin, N, B, perm_bin, bin_off, scr, s)) return rc;
+    // ---- attribute frequency tree per partition (Alg. 1, second loop) ----
+    CAPS_CUDA(cudaMemsetAsync(ix->key, 0, (size_t)N, s));
+    if (int rc = launch_aft(perm_bin, bin_off, B, h, dA, meta, ix->code_field, ix->tags, ix->key, s))
+      return rc;
+    // ---- contiguous sub-partitions: stable order by (partition, block, id) ----
+    if (int rc = launch_segment_keys(ix->bin, ix->key, N, h, seg, s)) return rc;
+    if (int rc = stable_sort_by_key(seg, N, nseg, ix->perm, ix->offsets, scr, s)) return rc;
+    if (int rc = launch_layout(dX, dA, ix->perm, N, d, meta, ix->Xp, ix->Ap, s)) return rc;
+    CAPS_CUDA(cudaMemsetAsync(ix->pos, 0, (size_t)B * meta.n_codes, s));
+    if (int rc = launch_pos_table(ix->tags, B, h, meta.n_codes, ix->pos, s)) return rc;
+    return CAPS_OK;
+  };
+  if (int rc = finish()) return rc;
+  if (p->part == CAPS_PART_MLP) {
+    if (int rc = build_mlp(p, dX, dA, N, d, meta, s, ix)) return rc;
+    if (int rc = finish()) return rc;
+  }
   if (p->prec == CAPS_BF16) {
     // bf16 form: bf16 rows + fp32 squared norms + inverse permutation
     uint16_t* xb = nullptr;
@@ -345,6 +511,9 @@ extern "C" int caps_get_info(const caps_index* ix, caps_index_info* out) {
   out->n_codes = ix->meta.n_codes;
   out->attr_words = ix->meta.words_pad;
   out->device_bytes = ix->bytes;
+  out->part = ix->part;
+  out->mlp_hidden = ix->part == CAPS_PART_MLP ? ix->mlp.H : 0;
+  out->n_labels = ix->n_labels;
   return CAPS_OK;
 }
 
@@ -362,6 +531,16 @@ extern "C" int caps_export(const caps_index* ix, int32_t which, void* dst, size_
     case CAPS_ARR_OFFSETS:
       src = ix->offsets;
       want = sizeof(int32_t) * ((size_t)ix->B * (ix->h + 1) + 1);
+      break;
+    case CAPS_ARR_MLP:
+      if (ix->part != CAPS_PART_MLP) return fail(CAPS_EINVAL, "not an MLP index");
+      src = ix->mlp.W1;
+      want = sizeof(float) * (size_t)ix->mlp.size();
+      break;
+    case CAPS_ARR_LABELS:
+      if (ix->part != CAPS_PART_MLP) return fail(CAPS_EINVAL, "not an MLP index");
+      src = ix->labels;
+      want = sizeof(float) * (size_t)ix->n_labels * ix->B;
       break;
     default: return fail(CAPS_EINVAL, "unknown array id");
   }
@@ -430,6 +609,18 @@ int64_t chunk_rows(const caps_index* ix, int64_t nq, int m = 1, int k = 1) {
 }
 }  // namespace
 
+// Alg. 2 "select top m partitions": scores of every partition for each
+// query -- centroid distances (k-means) or MLP logits (learned) -- and the
+// order in which they rank (smaller L2 distance / larger IP or logit).
+static int partition_scores(const caps_index* ix, const float* Q, int64_t n, float* scores,
+                            float* hid, cudaStream_t s) {
+  if (ix->part == CAPS_PART_MLP) return mlp_logits(ix->mlp, Q, n, hid, scores, s);
+  return launch_scores(Q, n, ix->d, ix->C, ix->B, ix->metric, scores, s);
+}
+static int probe_metric(const caps_index* ix) {
+  return ix->part == CAPS_PART_MLP ? CAPS_IP : ix->metric;
+}
+
 extern "C" int caps_probe(const caps_index* ix, const float* Q, int64_t nq, int32_t m,
                           int32_t* out_probe, void* stream) {
   if (!ix) return fail(CAPS_EINVAL, "null index");
@@ -444,11 +635,13 @@ extern "C" int caps_probe(const caps_index* ix, const float* Q, int64_t nq, int3
   const int64_t qc = chunk_rows(ix, nq);
   float* scores = nullptr;
   if (int rc = scr.get(&scores, (size_t)qc * ix->B)) return rc;
+  float* hid = nullptr;
+  if (ix->part == CAPS_PART_MLP)
+    if (int rc = scr.get(&hid, (size_t)qc * ix->mlp.H)) return rc;
   for (int64_t c0 = 0; c0 < nq; c0 += qc) {
     const int64_t n = std::min(qc, nq - c0);
-    if (int rc = launch_scores(dQ + c0 * ix->d, n, ix->d, ix->C, ix->B, ix->metric, scores, s))
-      return rc;
-    if (int rc = launch_topm(scores, n, ix->B, m, ix->metric, op.dev + c0 * m, s)) return rc;
+    if (int rc = partition_scores(ix, dQ + c0 * ix->d, n, scores, hid, s)) return rc;
+    if (int rc = launch_topm(scores, n, ix->B, m, probe_metric(ix), op.dev + c0 * m, s)) return rc;
   }
   if (int rc = op.finish(s)) return rc;
   if (op.host) CAPS_CUDA(cudaStreamSynchronize(s));
@@ -586,6 +779,9 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
   Batch bt;
   if (int rc = alloc_batch(ix, qc, m, scr, &bt)) return rc;
   const bool binmajor = !tc && bin_scan_supported(ix->d);
+  float* mlp_hidden = nullptr;
+  if (ix->part == CAPS_PART_MLP)
+    if (int rc = scr.get(&mlp_hidden, (size_t)qc * ix->mlp.H)) return rc;
   uint64_t* part = nullptr;
   if (binmajor || tc)
     if (int rc = scr.get(&part, (size_t)qc * m * kp)) return rc;
@@ -609,9 +805,9 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
     if (int rc = tm.record(s)) return rc;
     if (int rc = launch_query_prep(Qbc, n, ix->meta, bt.qp, s)) return rc;
     if (int rc = tm.record(s)) return rc;
-    if (int rc = launch_scores(Qc, n, ix->d, ix->C, ix->B, ix->metric, bt.scores, s)) return rc;
+    if (int rc = partition_scores(ix, Qc, n, bt.scores, mlp_hidden, s)) return rc;
     if (int rc = tm.record(s)) return rc;
-    if (int rc = launch_topm(bt.scores, n, ix->B, m, ix->metric, bt.probe, s)) return rc;
+    if (int rc = launch_topm(bt.scores, n, ix->B, m, probe_metric(ix), bt.probe, s)) return rc;
     if (int rc = tm.record(s)) return rc;
     if (int rc = launch_select(bt.probe, n, m, ix->h, ix->tags, ix->pos, ix->meta.n_codes,
                                ix->code_field, Qbc, ix->meta, bt.qp.qcode, bt.sel, s))
@@ -687,5 +883,113 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
     CAPS_CUDA(cudaStreamSynchronize(s));
     return caps_device_status(ix, stream);
   }
+  return CAPS_OK;
+}
+
+// ---- learned partitioner step entry points ---------------------------------
+
+static int mlp_dims_ok(int32_t d, int32_t H, int32_t B) {
+  if (d < 1 || H < 1 || B < 1) return fail(CAPS_EINVAL, "MLP dimensions must be >= 1");
+  return CAPS_OK;
+}
+
+extern "C" int caps_mlp_loss_grad(int32_t d, int32_t H, int32_t B, const float* W1,
+                                  const float* b1, const float* W2, const float* b2,
+                                  const float* X, int64_t n, const float* Y, float* gW1,
+                                  float* gb1, float* gW2, float* gb2, float* loss, void* stream) {
+  if (int rc = mlp_dims_ok(d, H, B)) return rc;
+  if (n < 1) return fail(CAPS_EINVAL, "n must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  keep_pool_warm();
+  Scratch scr(s);
+  MlpNet net;
+  net.d = d;
+  net.H = H;
+  net.B = B;
+  float* w = nullptr;
+  if (int rc = scr.get(&w, (size_t)net.size())) return rc;
+  net.bind(w);
+  const float *t1, *t2, *t3, *t4, *dX, *dY;
+  if (int rc = stage_in(W1, (size_t)H * d, scr, s, &t1)) return rc;
+  if (int rc = stage_in(b1, (size_t)H, scr, s, &t2)) return rc;
+  if (int rc = stage_in(W2, (size_t)B * H, scr, s, &t3)) return rc;
+  if (int rc = stage_in(b2, (size_t)B, scr, s, &t4)) return rc;
+  if (int rc = stage_in(X, (size_t)n * d, scr, s, &dX)) return rc;
+  if (int rc = stage_in(Y, (size_t)n * B, scr, s, &dY)) return rc;
+  CAPS_CUDA(cudaMemcpyAsync(net.W1, t1, sizeof(float) * H * d, cudaMemcpyDeviceToDevice, s));
+  CAPS_CUDA(cudaMemcpyAsync(net.b1, t2, sizeof(float) * H, cudaMemcpyDeviceToDevice, s));
+  CAPS_CUDA(cudaMemcpyAsync(net.W2, t3, sizeof(float) * B * H, cudaMemcpyDeviceToDevice, s));
+  CAPS_CUDA(cudaMemcpyAsync(net.b2, t4, sizeof(float) * B, cudaMemcpyDeviceToDevice, s));
+  Out<float> o1, o2, o3, o4;
+  if (int rc = o1.init(gW1, (size_t)H * d, scr)) return rc;
+  if (int rc = o2.init(gb1, (size_t)H, scr)) return rc;
+  if (int rc = o3.init(gW2, (size_t)B * H, scr)) return rc;
+  if (int rc = o4.init(gb2, (size_t)B, scr)) return rc;
+  MlpNet g = net;
+  g.W1 = o1.dev;
+  g.b1 = o2.dev;
+  g.W2 = o3.dev;
+  g.b2 = o4.dev;
+  double* dl = nullptr;
+  if (int rc = scr.get(&dl, 1)) return rc;
+  if (int rc = mlp_loss_grad(net, dX, n, dY, &g, dl, scr, s)) return rc;
+  if (int rc = o1.finish(s)) return rc;
+  if (int rc = o2.finish(s)) return rc;
+  if (int rc = o3.finish(s)) return rc;
+  if (int rc = o4.finish(s)) return rc;
+  double lh = 0.0;
+  CAPS_CUDA(cudaMemcpyAsync(&lh, dl, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  if (loss) *loss = (float)lh;
+  return CAPS_OK;
+}
+
+extern "C" int caps_mlp_train(int32_t d, int32_t H, int32_t B, float* W, const float* X,
+                              int64_t n, const float* Y, int32_t epochs, int32_t batch, float lr,
+                              float* losses, void* stream) {
+  if (int rc = mlp_dims_ok(d, H, B)) return rc;
+  if (n < 1 || epochs < 0 || batch < 1 || !(lr > 0.f)) return fail(CAPS_EINVAL, "bad training arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  keep_pool_warm();
+  Scratch scr(s);
+  MlpNet net;
+  net.d = d;
+  net.H = H;
+  net.B = B;
+  Out<float> ow;
+  if (int rc = ow.init(W, (size_t)net.size(), scr)) return rc;
+  if (ow.host)
+    CAPS_CUDA(cudaMemcpyAsync(ow.dev, W, sizeof(float) * net.size(), cudaMemcpyHostToDevice, s));
+  net.bind(ow.dev);
+  const float *dX, *dY;
+  if (int rc = stage_in(X, (size_t)n * d, scr, s, &dX)) return rc;
+  if (int rc = stage_in(Y, (size_t)n * B, scr, s, &dY)) return rc;
+  if (int rc = mlp_train(net, dX, n, dY, epochs, batch, lr, losses, s)) return rc;
+  if (int rc = ow.finish(s)) return rc;
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
+extern "C" int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W, const float* X,
+                               int64_t n, int32_t* out_bin, void* stream) {
+  if (int rc = mlp_dims_ok(d, H, B)) return rc;
+  if (n < 0) return fail(CAPS_EINVAL, "n < 0");
+  if (n == 0) return CAPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  keep_pool_warm();
+  Scratch scr(s);
+  MlpNet net;
+  net.d = d;
+  net.H = H;
+  net.B = B;
+  const float *dW, *dX;
+  if (int rc = stage_in(W, (size_t)net.size(), scr, s, &dW)) return rc;
+  if (int rc = stage_in(X, (size_t)n * d, scr, s, &dX)) return rc;
+  net.bind(const_cast<float*>(dW));
+  Out<int32_t> ob;
+  if (int rc = ob.init(out_bin, (size_t)n, scr)) return rc;
+  if (int rc = mlp_assign(net, dX, n, ob.dev, scr, s)) return rc;
+  if (int rc = ob.finish(s)) return rc;
+  if (ob.host) CAPS_CUDA(cudaStreamSynchronize(s));
   return CAPS_OK;
 }

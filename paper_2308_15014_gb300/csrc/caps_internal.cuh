@@ -217,6 +217,32 @@ int bin_group(const int32_t* probe, int64_t ne, int B, BinWork* w, Scratch& scr,
 int bin_scan(const ScanArgs& a, const BinWork& w, uint64_t* part, int32_t* err, cudaStream_t s);
 int bin_merge(const ScanArgs& a, const uint64_t* part, cudaStream_t s);
 
+// ---- learned partitioner (mlp.cu) ------------------------------------------
+// W1 [H,d] | b1 [H] | W2 [B,H] | b2 [B], one contiguous device block.
+struct MlpNet {
+  int d = 0, H = 0, B = 0;
+  float* W1 = nullptr;
+  float* b1 = nullptr;
+  float* W2 = nullptr;
+  float* b2 = nullptr;
+  int64_t size() const { return (int64_t)H * d + H + (int64_t)B * H + B; }
+  void bind(float* base) {
+    W1 = base;
+    b1 = W1 + (int64_t)H * d;
+    W2 = b1 + H;
+    b2 = W2 + (int64_t)B * H;
+  }
+};
+int mlp_logits(const MlpNet& net, const float* X, int64_t n, float* Hd, float* Z, cudaStream_t s);
+int mlp_assign(const MlpNet& net, const float* X, int64_t n, int32_t* bin, Scratch& scr,
+               cudaStream_t s);
+int mlp_loss_grad(const MlpNet& net, const float* X, int64_t n, const float* Y, MlpNet* grad,
+                  double* loss_dev, Scratch& scr, cudaStream_t s);
+int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs, int batch,
+              float lr, float* losses_host, cudaStream_t s);
+int mlp_gather_rows(const float* X, const int64_t* idx, int64_t n, int d, float* out,
+                    cudaStream_t s);
+
 // ---- bf16 tensor-core scan + exact re-rank (scan_tc.cu) ---------------------
 struct TcScanArgs {
   const uint64_t* sel;
@@ -270,6 +296,11 @@ struct caps_index {
   // norms, row of each original id, and a TMA tensor map over the bf16 rows
   int prec = CAPS_FP32;
   int rerank_factor = 4;
+  // learned partitioner (part = CAPS_PART_MLP): weights and training labels
+  int part = CAPS_PART_KMEANS;
+  caps::MlpNet mlp;
+  float* labels = nullptr;
+  int64_t n_labels = 0;
   void* Xb = nullptr;
   float* xn = nullptr;
   int32_t* iperm = nullptr;

@@ -1,0 +1,316 @@
+// Learned first-level partitioner (Sec. 5.2, BLISS-style): a two-layer MLP
+// f(x) = W2 relu(W1 x + b1) + b2 trained on the GPU with the library's own
+// forward, backward and Adam kernels; the partition of x is argmax f(x).
+//
+// Every GEMM output element accumulates its products in index order with one
+// fused multiply-add each and adds the bias afterwards, so the fp32 forward
+// (and hence the argmax decision) is reproducible term for term.  Gradients
+// are the mean softmax cross-entropy against a label distribution Y over the
+// B partitions: dz = (softmax(z) * sum(y) - y) / n.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "caps_internal.cuh"
+
+namespace caps {
+namespace {
+
+constexpr int GM = 64, GN = 64, GK = 16, GP = 4;
+
+// op(A)[m][k]: TA = false -> A[m*lda + k]; TA = true -> A[k*lda + m]
+// op(B)[k][n]: TB = false -> B[n*ldb + k] (B stored [N,K]); TB = true -> B[k*ldb + n]
+// EPI: 0 = plain, 1 = + bias[n] then relu, 2 = + bias[n], 3 = * (mask[m*ldm + n] > 0)
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(256)
+k_gemm(const float* __restrict__ A, int lda, const float* __restrict__ Bm, int ldb,
+       float* __restrict__ C, int ldc, int M, int N, int K, const float* __restrict__ bias,
+       const float* __restrict__ mask, int ldm) {
+  __shared__ __align__(16) float As[GK][GM + GP];
+  __shared__ __align__(16) float Bs[GK][GN + GP];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    // 64 x 16 of op(A) and 16 x 64 of op(B): 1024 elements each, 4 per thread
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int x = tid + 256 * e;
+      int mm, kk;
+      if (TA) { kk = x >> 6; mm = x & 63; } else { mm = x >> 4; kk = x & 15; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      float v = 0.f;
+      if (gm < M && gk < K) v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+      As[kk][mm] = v;
+      int nn, kb;
+      if (TB) { kb = x >> 6; nn = x & 63; } else { nn = x >> 4; kb = x & 15; }
+      const int gn = n0 + nn, gkb = k0 + kb;
+      float w = 0.f;
+      if (gn < N && gkb < K) w = TB ? Bm[(int64_t)gkb * ldb + gn] : Bm[(int64_t)gn * ldb + gkb];
+      Bs[kb][nn] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; kk++) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (EPI == 1) {
+        v = v + bias[n];
+        v = v > 0.f ? v : 0.f;
+      } else if (EPI == 2) {
+        v = v + bias[n];
+      } else if (EPI == 3) {
+        v = mask[(int64_t)m * ldm + n] > 0.f ? v : 0.f;
+      }
+      C[(int64_t)m * ldc + n] = v;
+    }
+  }
+}
+
+// Softmax cross-entropy per row (warp per row): dz and the loss (summed).
+__global__ void k_softmax_xent(const float* __restrict__ Z, const float* __restrict__ Y, int n,
+                               int B, float inv_n, float* __restrict__ dZ,
+                               double* __restrict__ loss) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const float* z = Z + (int64_t)i * B;
+  const float* y = Y + (int64_t)i * B;
+  float mx = -INFINITY;
+  for (int c = lane; c < B; c += 32) mx = fmaxf(mx, z[c]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  float se = 0.f, ys = 0.f;
+  for (int c = lane; c < B; c += 32) {
+    se += expf(z[c] - mx);
+    ys += y[c];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+    ys += __shfl_xor_sync(0xffffffffu, ys, o);
+  }
+  const float lse = mx + logf(se);
+  float l = 0.f;
+  for (int c = lane; c < B; c += 32) {
+    const float p = expf(z[c] - lse);
+    dZ[(int64_t)i * B + c] = (p * ys - y[c]) * inv_n;
+    l -= y[c] * (z[c] - lse);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if (lane == 0) atomicAdd(loss, (double)l * (double)inv_n);
+}
+
+// Column sums (bias gradients), rows in order.
+__global__ void k_colsum(const float* __restrict__ D, int n, int ncol, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  float s = 0.f;
+  for (int i = 0; i < n; i++) s += D[(int64_t)i * ncol + c];
+  out[c] = s;
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// argmax per row, ties to the lower index (warp per row).
+__global__ void k_argmax_rows(const float* __restrict__ Z, int64_t n, int B,
+                              int32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const float* z = Z + i * B;
+  float best = -INFINITY;
+  int bi = INT_MAX;
+  for (int c = lane; c < B; c += 32) {
+    const float v = z[c];
+    if (v > best || (v == best && c < bi)) {
+      best = v;
+      bi = c;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float v2 = __shfl_xor_sync(0xffffffffu, best, o);
+    const int c2 = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (v2 > best || (v2 == best && c2 < bi)) {
+      best = v2;
+      bi = c2;
+    }
+  }
+  if (lane == 0) out[i] = bi == INT_MAX ? 0 : bi;
+}
+
+__global__ void k_gather_rows_f(const float* __restrict__ X, const int64_t* __restrict__ idx,
+                                int64_t n, int d, float* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * d) return;
+  out[t] = X[idx[t / d] * d + t % d];
+}
+
+template <bool TA, bool TB, int EPI>
+int gemm(const float* A, int lda, const float* Bm, int ldb, float* C, int ldc, int M, int N, int K,
+         const float* bias, const float* mask, int ldm, cudaStream_t s) {
+  if (M == 0 || N == 0) return CAPS_OK;
+  dim3 grid((unsigned)((N + GN - 1) / GN), (unsigned)((M + GM - 1) / GM));
+  if (grid.y > 65535) return fail(CAPS_EINVAL, "gemm: too many rows in one call");
+  k_gemm<TA, TB, EPI><<<grid, 256, 0, s>>>(A, lda, Bm, ldb, C, ldc, M, N, K, bias, mask, ldm);
+  CAPS_LAUNCH("k_gemm");
+  return CAPS_OK;
+}
+
+}  // namespace
+
+// logits Z [n, B] of rows X [n, d]; Hd [n, H] scratch.  Rows in chunks.
+int mlp_logits(const MlpNet& net, const float* X, int64_t n, float* Hd, float* Z, cudaStream_t s) {
+  const int64_t chunk = 65535LL * GM;
+  for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+    const int rows = (int)std::min(chunk, n - r0);
+    if (int rc = gemm<false, false, 1>(X + r0 * net.d, net.d, net.W1, net.d, Hd + r0 * net.H,
+                                       net.H, rows, net.H, net.d, net.b1, nullptr, 0, s))
+      return rc;
+    if (int rc = gemm<false, false, 2>(Hd + r0 * net.H, net.H, net.W2, net.H, Z + r0 * net.B,
+                                       net.B, rows, net.B, net.H, net.b2, nullptr, 0, s))
+      return rc;
+  }
+  return CAPS_OK;
+}
+
+int mlp_assign(const MlpNet& net, const float* X, int64_t n, int32_t* bin, Scratch& scr,
+               cudaStream_t s) {
+  if (n == 0) return CAPS_OK;
+  // rows per pass so that hidden + logits stay under ~256 MB
+  const int64_t per = std::max<int64_t>(1, ((int64_t)1 << 26) / (net.H + net.B));
+  const int64_t pass = std::min(n, per);
+  float *Hd = nullptr, *Z = nullptr;
+  if (int rc = scr.get(&Hd, (size_t)pass * net.H)) return rc;
+  if (int rc = scr.get(&Z, (size_t)pass * net.B)) return rc;
+  for (int64_t r0 = 0; r0 < n; r0 += pass) {
+    const int64_t rows = std::min(pass, n - r0);
+    if (int rc = mlp_logits(net, X + r0 * net.d, rows, Hd, Z, s)) return rc;
+    k_argmax_rows<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(Z, rows, net.B, bin + r0);
+    CAPS_LAUNCH("k_argmax_rows");
+  }
+  return CAPS_OK;
+}
+
+int mlp_loss_grad(const MlpNet& net, const float* X, int64_t n, const float* Y, MlpNet* grad,
+                  double* loss_dev, Scratch& scr, cudaStream_t s) {
+  if (n < 1 || n > INT_MAX) return fail(CAPS_EINVAL, "mlp: batch size out of range");
+  const int d = net.d, H = net.H, B = net.B, nn = (int)n;
+  float *Hd = nullptr, *Z = nullptr, *dZ = nullptr, *dH = nullptr;
+  if (int rc = scr.get(&Hd, (size_t)n * H)) return rc;
+  if (int rc = scr.get(&Z, (size_t)n * B)) return rc;
+  if (int rc = scr.get(&dZ, (size_t)n * B)) return rc;
+  if (int rc = scr.get(&dH, (size_t)n * H)) return rc;
+  if (int rc = mlp_logits(net, X, n, Hd, Z, s)) return rc;
+  CAPS_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(double), s));
+  k_softmax_xent<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(Z, Y, nn, B, 1.f / (float)n, dZ, loss_dev);
+  CAPS_LAUNCH("k_softmax_xent");
+  // gW2 [B,H] = dZ^T [B,n] . Hd [n,H];  gb2 = column sums of dZ
+  if (int rc = gemm<true, true, 0>(dZ, B, Hd, H, grad->W2, H, B, H, nn, nullptr, nullptr, 0, s))
+    return rc;
+  k_colsum<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(dZ, nn, B, grad->b2);
+  CAPS_LAUNCH("k_colsum");
+  // dH [n,H] = dZ [n,B] . W2 [B,H], zero where the hidden unit was off
+  if (int rc = gemm<false, true, 3>(dZ, B, net.W2, H, dH, H, nn, H, B, nullptr, Hd, H, s)) return rc;
+  // gW1 [H,d] = dH^T [H,n] . X [n,d];  gb1 = column sums of dH
+  if (int rc = gemm<true, true, 0>(dH, H, X, d, grad->W1, d, H, d, nn, nullptr, nullptr, 0, s))
+    return rc;
+  k_colsum<<<(unsigned)((H + 127) / 128), 128, 0, s>>>(dH, nn, H, grad->b1);
+  CAPS_LAUNCH("k_colsum");
+  return CAPS_OK;
+}
+
+int mlp_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr, int t,
+             cudaStream_t s) {
+  const double b1 = 0.9, b2 = 0.999;
+  const float c1 = (float)(1.0 - std::pow(b1, t)), c2 = (float)(1.0 - std::pow(b2, t));
+  k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, g, m, v, n, lr, (float)b1, (float)b2,
+                                                     1e-8f, c1, c2);
+  CAPS_LAUNCH("k_adam");
+  return CAPS_OK;
+}
+
+int mlp_gather_rows(const float* X, const int64_t* idx, int64_t n, int d, float* out,
+                    cudaStream_t s) {
+  if (n == 0) return CAPS_OK;
+  k_gather_rows_f<<<(unsigned)((n * d + 255) / 256), 256, 0, s>>>(X, idx, n, d, out);
+  CAPS_LAUNCH("k_gather_rows_f");
+  return CAPS_OK;
+}
+
+// Minibatches of `batch` samples in sample order, the same every epoch.
+int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs, int batch,
+              float lr, float* losses_host, cudaStream_t s) {
+  const int64_t P1 = (int64_t)net.H * net.d, P2 = (int64_t)net.B * net.H;
+  const int64_t total = P1 + net.H + P2 + net.B;
+  Scratch scr(s);
+  float *g = nullptr, *mo = nullptr, *ve = nullptr;
+  double* loss = nullptr;
+  if (int rc = scr.get(&g, (size_t)total)) return rc;
+  if (int rc = scr.get(&mo, (size_t)total)) return rc;
+  if (int rc = scr.get(&ve, (size_t)total)) return rc;
+  if (int rc = scr.get(&loss, 1)) return rc;
+  CAPS_CUDA(cudaMemsetAsync(mo, 0, sizeof(float) * total, s));
+  CAPS_CUDA(cudaMemsetAsync(ve, 0, sizeof(float) * total, s));
+  MlpNet gr = net;
+  gr.W1 = g;
+  gr.b1 = g + P1;
+  gr.W2 = g + P1 + net.H;
+  gr.b2 = g + P1 + net.H + P2;
+  float* w = net.W1;  // W1|b1|W2|b2 are one contiguous block
+  int t = 0;
+  for (int e = 0; e < epochs; e++) {
+    for (int64_t b0 = 0; b0 < n; b0 += batch) {
+      const int64_t nb = std::min<int64_t>(batch, n - b0);
+      Scratch step(s);
+      if (int rc = mlp_loss_grad(net, X + b0 * net.d, nb, Y + b0 * net.B, &gr, loss, step, s))
+        return rc;
+      t++;
+      if (int rc = mlp_adam(w, g, mo, ve, total, lr, t, s)) return rc;
+      if (losses_host) {
+        double lh = 0.0;
+        CAPS_CUDA(cudaMemcpyAsync(&lh, loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CAPS_CUDA(cudaStreamSynchronize(s));
+        losses_host[t - 1] = (float)lh;
+      }
+    }
+  }
+  return CAPS_OK;
+}
+
+}  // namespace caps

@@ -94,6 +94,8 @@ extern "C" int caps_search_batch_noalloc(const caps_index* ix, const float* Q, i
   if (m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
   if (!cons || cons->dense == nullptr || cons->L != ix->meta.L)
     return fail(CAPS_EINVAL, "constraints must be dense with the index's L fields");
+  if (ix->part != CAPS_PART_KMEANS)
+    return fail(CAPS_EINVAL, "the no-allocation query serves k-means indexes only");
   if (nq == 0) return CAPS_OK;
   if (int rc = require_device(Q, "Q")) return rc;
   if (int rc = require_device(cons->dense, "constraints")) return rc;
