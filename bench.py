@@ -30,7 +30,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "filtered QPS at recall@10>=0.9 (k-means + BF16 tensor-core path; plain FP32 path alongside)"
+METRIC = ("filtered QPS at recall@10>=0.9 (learned partitioner + BF16 tensor-core path; "
+          "plain FP32 k-means path alongside)")
 UNIT = "queries/s"
 M_SWEEP = (8, 12, 16, 24, 32, 48, 64)
 RECALL_SAMPLE = 500
@@ -62,8 +63,9 @@ def parse():
     ap.add_argument("--config", choices=["sift1m", "small"], default="sift1m")
     ap.add_argument("--m", type=int, default=0, help="fixed probe count (0 = sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--paths", default="bf16,fp32",
-                    help="comma list of search paths to measure; the first is the headline")
+    ap.add_argument("--paths", default="mlp_bf16,fp32,bf16",
+                    help="comma list of search paths (fp32, bf16, mlp_fp32, mlp_bf16); "
+                         "the first is the headline")
     return ap.parse_args()
 
 
@@ -302,16 +304,24 @@ def run_reference(args):
     return 0
 
 
-def measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world, local):
-    """Build the index in the given precision, pick m, time the batch."""
+# learned partitioner: 128 -> 512 -> 1024 (ReLU), 131,072 training points,
+# 10-NN filtered labels, Adam lr 2e-3, batches of 4096, 20 epochs
+MLP_ARGS = dict(mlp_hidden=512, mlp_epochs=20, mlp_samples=131072, mlp_batch=4096, mlp_lr=2e-3,
+                mlp_label_k=10, seed=17)
+
+
+def measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world, local, part=0):
+    """Build the index in the given precision and partitioner, pick m, time
+    the batch."""
     import torch
     import torch.distributed as dist
     X = torch.from_numpy(w.X).cuda()
     A = torch.from_numpy(w.A).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    extra = MLP_ARGS if part == caps.MLP else {}
     ix = caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, metric=w.metric,
-                          init_idx=w.init_idx, prec=prec)
+                          init_idx=w.init_idx, prec=prec, part=part, **extra)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     del X, A
@@ -405,12 +415,14 @@ def run_caps(args):
     O.set_threads(0)
     gt, _, g64, cnt = O.bruteforce(w.X, O.Attrs.of(w), w.Q[samp], O.Cons(Qb=w.Qb[samp]), w.k)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    precs = {"bf16": caps.BF16, "fp32": caps.FP32}
+    kinds = {"fp32": (caps.FP32, caps.KMEANS), "bf16": (caps.BF16, caps.KMEANS),
+             "mlp_fp32": (caps.FP32, caps.MLP), "mlp_bf16": (caps.BF16, caps.MLP)}
     paths = [p for p in args.paths.split(",") if p]
     res = {}
     for pth in paths:
-        res[pth] = measure_path(args, w, caps, O, precs[pth], samp, gt, g64, cnt, flush, world,
-                                local)
+        prec, part = kinds[pth]
+        res[pth] = measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world,
+                                local, part=part)
     head = res[paths[0]]
     ix, m, stage = head["ix"], head["m"], head["stage"]
 
@@ -420,12 +432,12 @@ def run_caps(args):
     probe = ix.probe(w.Q, m)
     sel = ix.select(probe, w.Qb)
     union, per_query, rows_scanned, rows_passed = scan_traffic_bytes(
-        w, perm, offsets, probe, sel, ix.info.attr_words, bf16=paths[0] == "bf16")
+        w, perm, offsets, probe, sel, ix.info.attr_words, bf16=paths[0].endswith("bf16"))
     hbm, hbm_src = peaks()
     scan_s = stage["scan_ms"] / 1e3
-    d_items, d_rows, d_pairs = dense_item_stats(w, offsets, probe, sel,
-                                                128 if paths[0] == "bf16" else 32)
-    if paths[0] == "bf16":
+    tc_head = paths[0].endswith("bf16")
+    d_items, d_rows, d_pairs = dense_item_stats(w, offsets, probe, sel, 128 if tc_head else 32)
+    if tc_head:
         # every selected (probe, row) pair: one d-long bf16 dot product
         flops = rows_scanned * w.d * 2
         tflops = flops / scan_s / 1e12
@@ -483,10 +495,11 @@ def run_caps(args):
         "metric": METRIC, "value": round(head["value"], 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms"], 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if paths[0] == "bf16" else "f32", "data": "synthetic",
+        "dtype": "bf16" if paths[0].endswith("bf16") else "f32", "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "d": w.d, "L": int(w.A.shape[1]),
                    "B": w.B, "h": w.h, "kmeans_iters": w.iters, "m": m, "k": w.k,
-                   "path": paths[0], "queries_per_step": w.nq,
+                   "path": paths[0], "partitioner": "mlp 128-512-1024" if paths[0].startswith("mlp")
+                   else "k-means", "queries_per_step": w.nq,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "recall_at_10": {"tie_aware": head["rec"]["recall_tie"],

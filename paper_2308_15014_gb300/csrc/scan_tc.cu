@@ -34,8 +34,9 @@ namespace {
 
 constexpr int TC_M = 128;     // probes per work item (MMA M, TMEM lanes)
 constexpr int TC_N = 256;     // rows per tile (MMA N)
-constexpr int TC_T = 256;     // threads: two per probe (one per half tile)
-constexpr int TC_Q = 16;      // per-thread candidate queue (merged when > 8 wait)
+constexpr int TC_T = 512;     // threads: four per probe (one per quarter tile)
+constexpr int TC_PARTS = TC_T / TC_M;
+constexpr int TC_Q = 12;      // per-thread candidate queue (merged when > 4 wait)
 constexpr int TC_RA = TC_N + 8;
 constexpr uint64_t kTcWaitNs = 1000000000ull;
 
@@ -363,7 +364,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     }
   }
 
-  const int probe = tid & (TC_M - 1), half = tid / TC_M;
+  const int probe = tid & (TC_M - 1), half = tid / TC_M;  // half: which quarter of the tile
   const bool active = probe < it.ne;
   const uint64_t my_sel = p_sel[probe];
   uint32_t my_qm[WP], my_qv[WP];
@@ -436,7 +437,8 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(bi * TC_N);
     const bool warp_live = __any_sync(0xffffffffu, active);
 #pragma unroll 1
-    for (int c0 = half * (TC_N / 2); warp_live && c0 < (half + 1) * (TC_N / 2); c0 += 8) {
+    for (int c0 = half * (TC_N / TC_PARTS); warp_live && c0 < (half + 1) * (TC_N / TC_PARTS);
+         c0 += 8) {
       uint32_t v[8];
       __syncwarp();  // tcgen05.ld is warp-collective
       tmem_ld8(tacc + (uint32_t)c0, v);
@@ -506,16 +508,17 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     return;
   }
   flush();
-  // merge the two half lists of each probe (the B tiles are free now)
-  uint64_t* halves = reinterpret_cast<uint64_t*>(sB[0]);
-  if (half == 1) {
+  // merge the quarter lists of each probe (the B tiles are free now)
+  uint64_t* parts = reinterpret_cast<uint64_t*>(sB[0]);
+  if (half > 0) {
 #pragma unroll
-    for (int i = 0; i < KP; i++) halves[(size_t)i * TC_M + probe] = L[i];
+    for (int i = 0; i < KP; i++) parts[((size_t)(half - 1) * KP + i) * TC_M + probe] = L[i];
   }
   __syncthreads();
   if (half == 0 && active) {
+    for (int q = 0; q < TC_PARTS - 1; q++)
 #pragma unroll
-    for (int i = 0; i < KP; i++) net_insert<KP>(L, halves[(size_t)i * TC_M + probe]);
+      for (int i = 0; i < KP; i++) net_insert<KP>(L, parts[((size_t)q * KP + i) * TC_M + probe]);
     uint64_t* dst = a.part + (int64_t)p_e[probe] * KP;
 #pragma unroll
     for (int i = 0; i < KP; i++) dst[i] = L[i];
