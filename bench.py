@@ -8,7 +8,7 @@ iterations), AFT height 15, 10,000 queries with 1-3 AND constraints
 all 10,000 queries (Alg. 2: filter packing, centroid scores, top-m, block
 selection, fused scan + top-k) with queries resident in HBM; the index build
 (Alg. 1) runs once before and is reported as build time.  m is the smallest
-probe count in {8,12,16,24,32,48,64} whose tie-aware recall@10 (against the
+probe count in {8,12,16,24,32,40,48,64} whose tie-aware recall@10 (against the
 CPU oracle's exact filtered kNN on a seeded sample of queries) is >= 0.9.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = ("filtered QPS at recall@10>=0.9 (learned partitioner + BF16 tensor-core path; "
           "plain FP32 k-means path alongside)")
 UNIT = "queries/s"
-M_SWEEP = (8, 12, 16, 24, 32, 48, 64)
+M_SWEEP = (8, 12, 16, 24, 32, 40, 48, 64)
 RECALL_SAMPLE = 500
 FALLBACK_HBM_GBS = 6800.0
 # fp32 peak from unit counts and clock: 152 SMs x 128 fp32 lanes x 2 flop
