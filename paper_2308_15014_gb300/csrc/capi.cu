@@ -834,7 +834,7 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
     if (tc) {
       BinWork w;
       if (int rc = tc_query_prep(Qc, n, ix->d, Qh, qn, s)) return rc;
-      if (int rc = tc_group(bt.probe, bt.sel, ix->h, n * m, ix->B, &w, cscr, s)) return rc;
+      if (int rc = tc_group(bt.probe, bt.sel, ix->h, n * m, ix->B, 0, &w, cscr, s)) return rc;
       if (int rc = tm.record(s)) return rc;
       TcScanArgs t;
       t.sel = bt.sel;
@@ -852,6 +852,7 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
       t.d = ix->d;
       t.kp = kp;
       t.rerank = tc_rerank_depth(k, ix->rerank_factor);
+      t.tile_n = 256;
       t.words_pad = ix->meta.words_pad;
       t.metric = ix->metric;
       t.part = part;

@@ -209,6 +209,7 @@ struct BinWork {
   int32_t* ent = nullptr;      // [nq*m] probe entries sorted by partition
   void* items = nullptr;       // work items
   int32_t* n_items = nullptr;  // device count of work items
+  int32_t* next_item = nullptr;  // work counter of a persistent scan (zeroed with the items)
   int64_t max_items = 0;       // grid bound
 };
 bool bin_scan_supported(int d);
@@ -257,6 +258,7 @@ struct TcScanArgs {
   const void* tmap;     // CUtensorMap over the bf16 rows
   int m, h, d, kp, words_pad, metric;  // kp: keys kept per probe (16 or 32)
   int rerank;           // candidates re-scored exactly per query
+  int tile_n;           // rows per tensor-core tile: 128 or 256 (0: 256)
   uint64_t* part;       // [nq*m*kp]
   int32_t* err;
 };
@@ -266,8 +268,9 @@ bool tc_scan_supported(int d, int k, int kp, int words_pad);
 int tc_prepare_index(const float* Xp, int64_t N, int d, const int32_t* perm, void* Xb, float* xn,
                      int32_t* iperm, void* tmap_out, cudaStream_t s);
 int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, cudaStream_t s);
-int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, BinWork* w,
-             Scratch& scr, cudaStream_t s);
+// item_cap: most probes per work item (1..128; 0: 128)
+int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, int item_cap,
+             BinWork* w, Scratch& scr, cudaStream_t s);
 int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s);
 int tc_merge_rerank(const TcScanArgs& t, const uint8_t* dead, int64_t nq, int k, const float* Q,
                     const float* Xp, const int32_t* iperm, int64_t* out_ids, float* out_dist,

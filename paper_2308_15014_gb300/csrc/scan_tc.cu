@@ -33,11 +33,13 @@ namespace caps {
 namespace {
 
 constexpr int TC_M = 128;     // probes per work item (MMA M, TMEM lanes)
-constexpr int TC_N = 256;     // rows per tile (MMA N)
-constexpr int TC_T = 512;     // threads: four per probe (one per quarter tile)
-constexpr int TC_PARTS = TC_T / TC_M;
+constexpr int TC_C = 512;     // epilogue threads: four per probe (one per quarter tile)
+constexpr int TC_T = TC_C + 32;  // + one producer warp (copies and MMAs)
+constexpr int TC_PARTS = TC_C / TC_M;
 constexpr int TC_Q = 12;      // per-thread candidate queue (merged when > 4 wait)
-constexpr int TC_RA = TC_N + 8;
+constexpr int TC_BOX = 128;   // rows per 2-D copy (the tensor map's box)
+constexpr int TC_COLS = 512;  // tensor-memory columns: TC_COLS / N accumulator stages
+constexpr int TC_PRODUCER = TC_C / 32;  // warp index of the producer
 constexpr uint64_t kTcWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -48,14 +50,16 @@ __device__ __forceinline__ uint64_t gtimer() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)));
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
 }
-__device__ __forceinline__ bool mbar_wait_t(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the completion of the barrier phase with the given parity.
+// Gives up after kTcWaitNs, or early once *fail is set (fail may be null).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* fail) {
   const uint32_t a = su32(bar);
   const uint64_t t0 = gtimer();
   while (true) {
-    for (int i = 0; i < 256; i++) {
+    for (int i = 0; i < 64; i++) {
       uint32_t done;
       asm volatile(
           "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -65,8 +69,12 @@ __device__ __forceinline__ bool mbar_wait_t(uint64_t* bar, uint32_t parity) {
           : "memory");
       if (done) return true;
     }
+    if (fail != nullptr && *fail) return false;
     if (gtimer() - t0 > kTcWaitNs) return false;
   }
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
 }
 __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
@@ -94,6 +102,9 @@ __device__ __forceinline__ void tc_fence_before() {
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void consumers_sync() {  // named barrier 1: the 16 epilogue warps
+  asm volatile("bar.sync 1, %0;" ::"n"(TC_C) : "memory");
 }
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart.
@@ -123,26 +134,22 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                    su32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+// Eight accumulator columns of this warp's 32 lanes; the load is only issued
+// here, tmem_wait() completes it (no use of v before that).
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&v)[8]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Completes the outstanding loads; v is tied in so that no use of it moves above.
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7])
+               :
+               : "memory");
 }
 
 struct TcItem {
@@ -153,6 +160,7 @@ struct TcArgs {
   const int32_t* ent;
   const TcItem* items;
   const int32_t* n_items;
+  int32_t* next_item;  // work counter, zeroed by the grouping step
   const uint64_t* sel;
   const uint32_t* qmask;
   const uint32_t* qval;
@@ -167,16 +175,19 @@ struct TcArgs {
   int32_t* err;
 };
 
+__host__ __device__ constexpr int tc_stages(int N) { return TC_COLS / N; }
 __host__ __device__ constexpr size_t tc_a_bytes(int kc) { return (size_t)kc * TC_M * 128; }
-__host__ __device__ constexpr size_t tc_b_bytes(int kc) { return (size_t)kc * TC_N * 128; }
-__host__ __device__ constexpr size_t tc_aux_bytes(int WP) {
-  return (size_t)TC_RA * WP * 4 + (size_t)TC_RA * 4 + (size_t)TC_RA * 4 + TC_N + 8;
+__host__ __device__ constexpr size_t tc_b_bytes(int kc, int N) { return (size_t)kc * N * 128; }
+// per stage: attribute words, ids and norms of N + 8 rows (4-row aligned
+// superset of the tile), block id of each row
+__host__ __device__ constexpr size_t tc_aux_bytes(int WP, int N) {
+  return (((size_t)(N + 8) * WP * 4 + (size_t)(N + 8) * 8 + (size_t)(N + 8)) + 15) & ~(size_t)15;
 }
-__host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int kp) {
-  // 1024-byte alignment slack + A + 2 B + candidate queues + 2 aux (the final
-  // merge of the two half lists reuses the B tiles)
-  return 1024 + tc_a_bytes(kc) + 2 * tc_b_bytes(kc) + (size_t)TC_Q * TC_T * 8 +
-         2 * ((tc_aux_bytes(WP) + 15) & ~(size_t)15) + 0 * (size_t)kp;
+__host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N) {
+  // 1024-byte alignment slack + A + B stages + candidate queues + aux stages
+  // (the final merge of the quarter lists reuses the B stages)
+  return 1024 + tc_a_bytes(kc) + (size_t)tc_stages(N) * tc_b_bytes(kc, N) +
+         (size_t)TC_Q * TC_C * 8 + (size_t)tc_stages(N) * tc_aux_bytes(WP, N);
 }
 
 template <int KP>
@@ -191,38 +202,50 @@ __device__ __forceinline__ void net_insert(uint64_t (&L)[KP], uint64_t x) {
   }
 }
 
-template <int METRIC, int WP, int KP>
+// One persistent CTA per SM walks the work items (partition, <= 128 probes)
+// in the order a global counter hands them out, so partitions of very
+// different sizes balance across the SMs within one launch.  Warp 16 is the
+// producer: for each tile of an item it waits until the epilogue has released
+// the stage, writes the rows' block ids, starts the copies and, once they
+// have landed, issues the MMAs of that tile into the stage's accumulator.
+// Warps 0-15 are the epilogue; they meet the producer only through the
+// stage barriers (full: copies landed; mma: accumulator written; empty: all
+// 16 warps done with the stage), and each other only at item boundaries.
+template <int METRIC, int WP, int KP, int N>
 __global__ void __launch_bounds__(TC_T, 1)
 k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
+  constexpr int S = tc_stages(N);
+  constexpr int RA = N + 8;
+  constexpr int CPT = N / TC_PARTS;  // accumulator columns per epilogue thread and tile
   extern __shared__ unsigned char smem_raw[];
-  const int item_id = blockIdx.x;
-  if (item_id >= *a.n_items) return;
-  const TcItem it = a.items[item_id];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int d = a.d, kc = a.kc, kp = a.kp, nb = a.h + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kc = a.kc, nb = a.h + 1;
+  const int n_items = *a.n_items;
 
   unsigned char* base =
       reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = base;
-  unsigned char* sB[2] = {sA + tc_a_bytes(kc), sA + tc_a_bytes(kc) + tc_b_bytes(kc)};
-  uint64_t* queue = reinterpret_cast<uint64_t*>(sA + tc_a_bytes(kc) + 2 * tc_b_bytes(kc));
-  unsigned char* auxb = reinterpret_cast<unsigned char*>(queue + (size_t)TC_Q * TC_T);
-  const size_t aux_stride = (tc_aux_bytes(WP) + 15) & ~(size_t)15;
-  uint32_t* s_attr[2];
-  int32_t* s_perm[2];
-  float* s_xn[2];
-  uint8_t* s_blk[2];
-  for (int i = 0; i < 2; i++) {
-    unsigned char* p = auxb + i * aux_stride;
-    s_attr[i] = reinterpret_cast<uint32_t*>(p);
-    s_perm[i] = reinterpret_cast<int32_t*>(p + (size_t)TC_RA * WP * 4);
-    s_xn[i] = reinterpret_cast<float*>(p + (size_t)TC_RA * WP * 4 + TC_RA * 4);
-    s_blk[i] = p + (size_t)TC_RA * WP * 4 + 2 * TC_RA * 4;
-  }
+  unsigned char* sB0 = sA + tc_a_bytes(kc);
+  const size_t bstride = tc_b_bytes(kc, N);
+  uint64_t* queue = reinterpret_cast<uint64_t*>(sB0 + S * bstride);
+  unsigned char* aux0 = reinterpret_cast<unsigned char*>(queue + (size_t)TC_Q * TC_C);
+  constexpr size_t astride = tc_aux_bytes(WP, N);
+  auto s_attr = [&](int b) { return reinterpret_cast<uint32_t*>(aux0 + b * astride); };
+  auto s_perm = [&](int b) {
+    return reinterpret_cast<int32_t*>(aux0 + b * astride + (size_t)RA * WP * 4);
+  };
+  auto s_xn = [&](int b) {
+    return reinterpret_cast<float*>(aux0 + b * astride + (size_t)RA * WP * 4 + RA * 4);
+  };
+  auto s_blk = [&](int b) { return aux0 + b * astride + (size_t)RA * WP * 4 + RA * 8; };
 
-  __shared__ uint64_t tma_bar[2], mma_bar[2];
+  __shared__ uint64_t full_bar[S], mma_bar[S], empty_bar[S];
   __shared__ uint32_t tmem_base;
-  __shared__ uint64_t p_sel[TC_M];
+  __shared__ volatile int s_fail;
+  __shared__ int s_item[2];
+  __shared__ int s_ntiles;
+  __shared__ int s_tlo[S], s_tn[S];
+  __shared__ uint64_t p_sel[TC_M], p_thr[TC_M];
   __shared__ uint32_t p_qm[TC_M * WP], p_qv[TC_M * WP];
   __shared__ float p_qn[TC_M];
   __shared__ int32_t p_e[TC_M];
@@ -231,302 +254,307 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   __shared__ int32_t boff[65];
 
   if (tid == 0) {
-    mbar_init1(&tma_bar[0]);
-    mbar_init1(&tma_bar[1]);
-    mbar_init1(&mma_bar[0]);
-    mbar_init1(&mma_bar[1]);
+    for (int i = 0; i < S; i++) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&mma_bar[i], 1);
+      mbar_init(&empty_bar[i], TC_C / 32);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    fence_async_smem();
+    s_fail = 0;
+    s_item[0] = atomicAdd(a.next_item, 1);
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                     su32(&tmem_base)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&tmem_base)),
+                 "n"(TC_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  // probe data and the A operand: row t = probe t's query, bf16, zero-padded
-  // to kc*64 coordinates, 16-byte unit u of chunk c stored at unit u ^ (t%8)
-  if (tid < TC_M) {
-    const int t = tid;
-    int q = -1;
-    if (t < it.ne) {
-      const int e = a.ent[it.e0 + t];
-      q = e / a.m;
-      p_e[t] = e;
-      p_sel[t] = a.sel[e];
-      p_qn[t] = a.qn[q];
-#pragma unroll
-      for (int w = 0; w < WP; w++) {
-        p_qm[t * WP + w] = a.qmask[(int64_t)q * WP + w];
-        p_qv[t * WP + w] = a.qval[(int64_t)q * WP + w];
-      }
-    } else {
-      p_sel[t] = 0ull;
-    }
-    const int units = kc * 8;
-    const int dunits = d / 8;
-    for (int u = 0; u < units; u++) {
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (q >= 0 && u < dunits) v = *reinterpret_cast<const uint4*>(a.Qh + (int64_t)q * d + 8 * u);
-      const int c = u >> 3, uu = u & 7;
-      *reinterpret_cast<uint4*>(sA + (size_t)c * TC_M * 128 + t * 128 + ((uu ^ (t & 7)) << 4)) = v;
-    }
-  }
-  fence_async_smem();
-  const int32_t* off = a.offsets + (int64_t)it.b * nb;
-  for (int j = tid; j <= nb; j += TC_T) boff[j] = off[j];
-  __syncthreads();
-  if (tid == 0) {
-    uint64_t U = 0ull;
-    for (int t = 0; t < it.ne; t++) U |= p_sel[t];
-    int nr = 0, j = 0;
-    while (j < nb) {
-      if (!((U >> j) & 1ull)) { j++; continue; }
-      int j2 = j;
-      while (j2 + 1 < nb && ((U >> (j2 + 1)) & 1ull)) j2++;
-      if (boff[j2 + 1] > boff[j]) {
-        run_lo[nr] = boff[j];
-        run_hi[nr] = boff[j2 + 1];
-        run_j0[nr] = j;
-        nr++;
-      }
-      j = j2 + 1;
-    }
-    n_runs = nr;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
+  const uint32_t idesc = idesc_bf16(TC_M, N);
 
-  // tile schedule over the runs, TC_N rows per tile
-  int rr = 0, rlo = n_runs > 0 ? run_lo[0] : 0;
-  auto next_tile = [&](int& lo, int& n, int& j0) -> bool {
-    while (rr < n_runs && rlo >= run_hi[rr]) {
-      rr++;
-      if (rr < n_runs) rlo = run_lo[rr];
-    }
-    if (rr >= n_runs) return false;
-    lo = rlo;
-    n = min(TC_N, run_hi[rr] - rlo);
-    j0 = run_j0[rr];
-    rlo += n;
-    return true;
-  };
-  auto issue = [&](int bi, int lo, int n) {  // thread 0
-    const int alo = lo & ~3;
-    const int arows = ((lo + n + 3) & ~3) - alo;
-    const uint32_t ab = (uint32_t)(arows * WP * 4), pb = (uint32_t)(arows * 4);
-    fence_async_smem();
-    expect_tx(&tma_bar[bi], (uint32_t)(kc * TC_N * 128) + ab + 2 * pb);
-    for (int c = 0; c < kc; c++)
-      tma_2d(sB[bi] + (size_t)c * TC_N * 128, &tmX, 64 * c, lo, &tma_bar[bi]);
-    bulk_copy(s_attr[bi], a.Ap + (int64_t)alo * WP, ab, &tma_bar[bi]);
-    bulk_copy(s_perm[bi], a.perm + alo, pb, &tma_bar[bi]);
-    bulk_copy(s_xn[bi], a.xn + alo, pb, &tma_bar[bi]);
-  };
-  const uint32_t idesc = idesc_bf16(TC_M, TC_N);
-  auto issue_mma = [&](int bi) {  // thread 0: 128 x 256 x (kc*64) into accumulator bi
-    tc_fence_after();
-    const uint32_t a0 = su32(sA), b0 = su32(sB[bi]);
-    for (int ks = 0; ks < kc * 4; ks++) {
-      const int c = ks >> 2, kin = ks & 3;
-      const uint64_t ad = sdesc(a0 + (uint32_t)(c * TC_M * 128 + kin * 32));
-      const uint64_t bd = sdesc(b0 + (uint32_t)(c * TC_N * 128 + kin * 32));
-      mma_bf16(tbase + (uint32_t)(bi * TC_N), ad, bd, idesc, ks > 0 ? 1u : 0u);
-    }
-    mma_commit(&mma_bar[bi]);
-  };
-
-  // Pipeline.  Every thread waits on every barrier phase it needs and flips
-  // its own parity after the wait (tph: copies, mph: MMAs).  Thread 0 also
-  // waits early on the next tile's copy (without flipping) to issue its MMA
-  // while the epilogue of the current tile runs.
-  int t_lo[2], t_n[2], t_j0[2];
-  bool have[2];
-  have[0] = next_tile(t_lo[0], t_n[0], t_j0[0]);
-  have[1] = have[0] && next_tile(t_lo[1], t_n[1], t_j0[1]);
-  uint32_t tph[2] = {0u, 0u}, mph[2] = {0u, 0u};
-  bool tma_out[2] = {false, false}, mma_out[2] = {false, false};  // thread 0's view
-  bool fail_flag = false;
-  if (tid == 0) {
-    for (int i = 0; i < 2; i++)
-      if (have[i]) {
-        issue(i, t_lo[i], t_n[i]);
-        tma_out[i] = true;
-      }
-    if (have[0]) {
-      if (mbar_wait_t(&tma_bar[0], tph[0])) {
-        issue_mma(0);
-        mma_out[0] = true;
-      } else {
-        fail_flag = true;
-      }
-    }
-  }
-
-  const int probe = tid & (TC_M - 1), half = tid / TC_M;  // half: which quarter of the tile
-  const bool active = probe < it.ne;
-  const uint64_t my_sel = p_sel[probe];
-  uint32_t my_qm[WP], my_qv[WP];
-#pragma unroll
-  for (int w = 0; w < WP; w++) {
-    my_qm[w] = active ? p_qm[probe * WP + w] : 0u;
-    my_qv[w] = active ? p_qv[probe * WP + w] : 0u;
-  }
-  const float my_qn = active ? p_qn[probe] : 0.f;
-  uint64_t L[KP];
-#pragma unroll
-  for (int i = 0; i < KP; i++) L[i] = kEmptyKey;
-  uint64_t thr = kEmptyKey;
-  int qcnt = 0;
-  auto flush = [&]() {  // warp-uniform call: as many rounds as the fullest queue
-    const int mx = __reduce_max_sync(0xffffffffu, (unsigned)qcnt);
-#pragma unroll 1
-    for (int i = 0; i < mx; i++) {
-      const uint64_t x = i < qcnt ? queue[(size_t)i * TC_T + tid] : kEmptyKey;
-      net_insert<KP>(L, x);
-    }
-    qcnt = 0;
-    thr = L[KP - 1];
-  };
-
-  int bi = 0;
+  int g0 = 0;           // tiles this CTA finished before the current item
+  int slot = 0;
+  int tma_hi = -1, mma_hi = -1;  // producer: last tile whose copies / MMAs were issued
   while (true) {
-    if (__syncthreads_or(fail_flag)) {
-      fail_flag = true;
-      break;
-    }
-    if (!have[bi]) break;
-    const int nb_ = bi ^ 1;
-    if (tid == 0 && have[nb_]) {
-      if (mbar_wait_t(&tma_bar[nb_], tph[nb_])) {
-        issue_mma(nb_);
-        mma_out[nb_] = true;
+    const int item_id = s_item[slot];
+    if (item_id >= n_items || s_fail) break;
+    const TcItem it = a.items[item_id];
+
+    // ---- item setup ------------------------------------------------------
+    if (warp == TC_PRODUCER) {
+      if (lane == 0) s_item[slot ^ 1] = atomicAdd(a.next_item, 1);
+      const int32_t* off = a.offsets + (int64_t)it.b * nb;
+      for (int j = lane; j <= nb; j += 32) boff[j] = off[j];
+      uint64_t U = 0ull;
+      for (int t = lane; t < it.ne; t += 32) U |= a.sel[a.ent[it.e0 + t]];
+      const uint32_t ulo = __reduce_or_sync(0xffffffffu, (uint32_t)U);
+      const uint32_t uhi = __reduce_or_sync(0xffffffffu, (uint32_t)(U >> 32));
+      U = ((uint64_t)uhi << 32) | ulo;
+      __syncwarp();
+      if (lane == 0) {
+        int nr = 0, nt = 0, j = 0;
+        while (j < nb) {
+          if (!((U >> j) & 1ull)) {
+            j++;
+            continue;
+          }
+          int j2 = j;
+          while (j2 + 1 < nb && ((U >> (j2 + 1)) & 1ull)) j2++;
+          if (boff[j2 + 1] > boff[j]) {
+            run_lo[nr] = boff[j];
+            run_hi[nr] = boff[j2 + 1];
+            run_j0[nr] = j;
+            nt += (boff[j2 + 1] - boff[j] + N - 1) / N;
+            nr++;
+          }
+          j = j2 + 1;
+        }
+        n_runs = nr;
+        s_ntiles = nt;
+      }
+    } else if (tid < TC_M) {
+      // probe data and the A operand: row t = probe t's query, bf16,
+      // zero-padded to kc*64 coordinates, 16-byte unit u of chunk c stored at
+      // unit u ^ (t%8)
+      const int t = tid;
+      int q = -1;
+      p_thr[t] = kEmptyKey;
+      if (t < it.ne) {
+        const int e = a.ent[it.e0 + t];
+        q = e / a.m;
+        p_e[t] = e;
+        p_sel[t] = a.sel[e];
+        p_qn[t] = a.qn[q];
+#pragma unroll
+        for (int w = 0; w < WP; w++) {
+          p_qm[t * WP + w] = a.qmask[(int64_t)q * WP + w];
+          p_qv[t * WP + w] = a.qval[(int64_t)q * WP + w];
+        }
       } else {
-        fail_flag = true;
+        p_sel[t] = 0ull;
+#pragma unroll
+        for (int w = 0; w < WP; w++) p_qm[t * WP + w] = p_qv[t * WP + w] = 0u;
+        p_qn[t] = 0.f;
+      }
+      const int units = kc * 8, dunits = a.d / 8;
+      for (int u = 0; u < units; u++) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (q >= 0 && u < dunits)
+          v = *reinterpret_cast<const uint4*>(a.Qh + (int64_t)q * a.d + 8 * u);
+        const int c = u >> 3, uu = u & 7;
+        *reinterpret_cast<uint4*>(sA + (size_t)c * TC_M * 128 + t * 128 + ((uu ^ (t & 7)) << 4)) = v;
       }
     }
-    const bool okm = mbar_wait_t(&mma_bar[bi], mph[bi]);
-    const bool okt = okm && mbar_wait_t(&tma_bar[bi], tph[bi]);
-    if (okm) {  // a phase that was not seen stays outstanding for the cleanup
-      mph[bi] ^= 1u;
-      if (tid == 0) mma_out[bi] = false;
-    }
-    if (okt) {
-      tph[bi] ^= 1u;
-      if (tid == 0) tma_out[bi] = false;
-    }
-    if (__syncthreads_or(!okt || fail_flag)) {
-      fail_flag = true;
-      break;
-    }
-    const int lo = t_lo[bi], n = t_n[bi];
-    const int alo = lo & ~3;
-    uint8_t* blk = s_blk[bi];
-    for (int r = tid; r < n; r += TC_T) {
-      int j = t_j0[bi];
-      while (j + 1 < nb && boff[j + 1] <= lo + r) j++;
-      blk[r] = (uint8_t)j;
-    }
+    fence_async_smem();  // the A operand (generic stores) before the MMAs read it
     __syncthreads();
-    tc_fence_after();
-    const uint32_t* attr = s_attr[bi] + (lo - alo) * WP;
-    const int32_t* prm = s_perm[bi] + (lo - alo);
-    const float* xnr = s_xn[bi] + (lo - alo);
-    const uint32_t tacc =
-        tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(bi * TC_N);
-    const bool warp_live = __any_sync(0xffffffffu, active);
-#pragma unroll 1
-    for (int c0 = half * (TC_N / TC_PARTS); warp_live && c0 < (half + 1) * (TC_N / TC_PARTS);
-         c0 += 8) {
-      uint32_t v[8];
-      __syncwarp();  // tcgen05.ld is warp-collective
-      tmem_ld8(tacc + (uint32_t)c0, v);
-      if (c0 < n) {  // warp-uniform
-        // the 8 rows' block ids and attribute words in few wide loads
-        // (the same addresses for every lane: broadcast)
-        const uint2 bw = *reinterpret_cast<const uint2*>(blk + c0);
-        const uint32_t bb[2] = {bw.x, bw.y};
-        uint32_t aw[8 * WP];
-        if (WP == 1 && ((lo - alo + c0) & 3) == 0) {
-          const uint4 a0 = *reinterpret_cast<const uint4*>(attr + c0);
-          const uint4 a1 = *reinterpret_cast<const uint4*>(attr + c0 + 4);
-          aw[0] = a0.x; aw[1] = a0.y; aw[2] = a0.z; aw[3] = a0.w;
-          aw[4] = a1.x; aw[5] = a1.y; aw[6] = a1.z; aw[7] = a1.w;
-        } else {
-#pragma unroll
-          for (int x = 0; x < 8 * WP; x++) aw[x] = attr[c0 * WP + x];
+    const int n_tiles = s_ntiles;
+
+    if (warp == TC_PRODUCER) {
+      // ---- producer ------------------------------------------------------
+      int rr = 0, rlo = n_runs > 0 ? run_lo[0] : 0;
+      for (int t = 0; t < n_tiles; t++) {
+        const int g = g0 + t, b = g % S, u = g / S;
+        while (rlo >= run_hi[rr]) {
+          rr++;
+          rlo = run_lo[rr];
         }
-        const int lim = n - c0;  // rows of this group inside the tile
+        const int lo = rlo, n = min(N, run_hi[rr] - rlo), j0 = run_j0[rr];
+        rlo += n;
+        bool ok = true;
+        if (u > 0) ok = mbar_wait(&empty_bar[b], (uint32_t)((u - 1) & 1), &s_fail);
+        if (!__all_sync(0xffffffffu, ok)) {
+          if (lane == 0) s_fail = 1;
+          break;
+        }
+        uint8_t* blk = s_blk(b);
+        for (int r = lane; r < n; r += 32) {
+          int j = j0;
+          while (j + 1 < nb && boff[j + 1] <= lo + r) j++;
+          blk[r] = (uint8_t)j;
+        }
+        if (lane == 0) {
+          s_tlo[b] = lo;
+          s_tn[b] = n;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          const int alo = lo & ~3;
+          const int arows = ((lo + n + 3) & ~3) - alo;
+          const uint32_t ab = (uint32_t)(arows * WP * 4), pb = (uint32_t)(arows * 4);
+          unsigned char* sB = sB0 + b * bstride;
+          expect_tx(&full_bar[b], (uint32_t)(kc * N * 128) + ab + 2 * pb);
+          for (int c = 0; c < kc; c++)
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-          const int bj = (bb[j >> 2] >> (8 * (j & 3))) & 0xff;
-          bool pass = active && j < lim && ((my_sel >> bj) & 1ull);
-#pragma unroll
-          for (int w = 0; w < WP; w++) pass = pass && ((aw[j * WP + w] & my_qm[w]) == my_qv[w]);
-          if (pass) {
-            const int r = c0 + j;
-            const float dot = __uint_as_float(v[j]);
-            const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r] + my_qn) : -dot;
-            const uint64_t key = make_key(sc, (uint32_t)prm[r]);
-            if (key < thr) {
-              queue[(size_t)qcnt * TC_T + tid] = key;
-              qcnt++;
+            for (int hb = 0; hb < N / TC_BOX; hb++)
+              tma_2d(sB + (size_t)c * N * 128 + (size_t)hb * TC_BOX * 128, &tmX, 64 * c,
+                     lo + hb * TC_BOX, &full_bar[b]);
+          bulk_copy(s_attr(b), a.Ap + (int64_t)alo * WP, ab, &full_bar[b]);
+          bulk_copy(s_perm(b), a.perm + alo, pb, &full_bar[b]);
+          bulk_copy(s_xn(b), a.xn + alo, pb, &full_bar[b]);
+          tma_hi = g;
+          ok = mbar_wait(&full_bar[b], (uint32_t)(u & 1), &s_fail);
+          if (ok) {
+            tc_fence_after();
+            const uint32_t a0 = su32(sA), b0 = su32(sB);
+            for (int ks = 0; ks < kc * 4; ks++) {
+              const int c = ks >> 2, kin = ks & 3;
+              const uint64_t ad = sdesc(a0 + (uint32_t)(c * TC_M * 128 + kin * 32));
+              const uint64_t bd = sdesc(b0 + (uint32_t)(c * N * 128 + kin * 32));
+              mma_bf16(tbase + (uint32_t)(b * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
             }
+            mma_commit(&mma_bar[b]);
+            mma_hi = g;
           }
         }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          if (lane == 0) s_fail = 1;
+          break;
+        }
       }
-      // at most 8 more keys per lane before the next check: merge once any
-      // queue holds more than TC_Q - 8
-      if (__any_sync(0xffffffffu, qcnt > TC_Q - 8)) flush();
+    } else {
+      // ---- epilogue ------------------------------------------------------
+      const int probe = tid & (TC_M - 1), part = tid / TC_M;
+      const bool active = probe < it.ne;
+      const uint64_t my_sel = p_sel[probe];
+      uint32_t my_qm[WP], my_qv[WP];
+#pragma unroll
+      for (int w = 0; w < WP; w++) {
+        my_qm[w] = p_qm[probe * WP + w];
+        my_qv[w] = p_qv[probe * WP + w];
+      }
+      const float my_qn = p_qn[probe];
+      uint64_t L[KP];
+#pragma unroll
+      for (int i = 0; i < KP; i++) L[i] = kEmptyKey;
+      uint64_t thr = kEmptyKey;
+      int qcnt = 0;
+      auto flush = [&]() {  // warp-uniform call: as many rounds as the fullest queue
+        const int mx = __reduce_max_sync(0xffffffffu, (unsigned)qcnt);
+#pragma unroll 1
+        for (int i = 0; i < mx; i++) {
+          const uint64_t x = i < qcnt ? queue[(size_t)i * TC_C + tid] : kEmptyKey;
+          net_insert<KP>(L, x);
+        }
+        qcnt = 0;
+        thr = L[KP - 1];
+        // the four threads of a probe share the smallest of their KP-th keys:
+        // a key above it has KP better keys in one quarter list already
+        if (thr != kEmptyKey) atomicMin(reinterpret_cast<unsigned long long*>(&p_thr[probe]), thr);
+      };
+      const bool warp_live = __any_sync(0xffffffffu, active);
+      const int cbeg = part * CPT;
+      for (int t = 0; t < n_tiles; t++) {
+        const int g = g0 + t, b = g % S, u = g / S;
+        const bool ok = mbar_wait(&full_bar[b], (uint32_t)(u & 1), &s_fail) &&
+                        mbar_wait(&mma_bar[b], (uint32_t)(u & 1), &s_fail);
+        if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform: the loads below are collective
+          s_fail = 1;
+          break;
+        }
+        tc_fence_after();
+        const int lo = s_tlo[b], n = s_tn[b];
+        const int alo = lo & ~3;
+        const uint32_t* attr = s_attr(b) + (lo - alo) * WP;
+        const int32_t* prm = s_perm(b) + (lo - alo);
+        const float* xnr = s_xn(b) + (lo - alo);
+        const uint8_t* blk = s_blk(b);
+        const uint32_t tacc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * N + cbeg);
+        const int ncol = warp_live ? min(CPT, n - cbeg) : 0;  // warp-uniform
+        const int ngr = ncol > 0 ? (ncol + 7) >> 3 : 0;
+#pragma unroll 1
+        for (int gi = 0; gi < ngr; gi++) {
+          uint32_t cur[8];
+          tmem_ld8_issue(tacc + (uint32_t)(8 * gi), cur);
+          tmem_wait(cur);
+          const int c0 = cbeg + 8 * gi;
+          {
+            const uint64_t st = p_thr[probe];
+            if (st < thr) thr = st;
+          }
+          // the 8 rows' block ids and attribute words in few wide loads
+          // (the same addresses for every lane: broadcast)
+          const uint2 bw = *reinterpret_cast<const uint2*>(blk + c0);
+          const uint32_t bb[2] = {bw.x, bw.y};
+          uint32_t aw[8 * WP];
+          if (WP == 1 && ((lo - alo + c0) & 3) == 0) {
+            const uint4 a0 = *reinterpret_cast<const uint4*>(attr + c0);
+            const uint4 a1 = *reinterpret_cast<const uint4*>(attr + c0 + 4);
+            aw[0] = a0.x; aw[1] = a0.y; aw[2] = a0.z; aw[3] = a0.w;
+            aw[4] = a1.x; aw[5] = a1.y; aw[6] = a1.z; aw[7] = a1.w;
+          } else {
+#pragma unroll
+            for (int x = 0; x < 8 * WP; x++) aw[x] = attr[c0 * WP + x];
+          }
+          const int lim = n - c0;  // rows of this group inside the tile
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            const int bj = (bb[j >> 2] >> (8 * (j & 3))) & 0xff;
+            bool pass = j < lim && ((my_sel >> bj) & 1ull);
+#pragma unroll
+            for (int w = 0; w < WP; w++) pass = pass && ((aw[j * WP + w] & my_qm[w]) == my_qv[w]);
+            if (pass) {
+              const int r = c0 + j;
+              const float dot = __uint_as_float(cur[j]);
+              const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r] + my_qn) : -dot;
+              const uint64_t key = make_key(sc, (uint32_t)prm[r]);
+              if (key < thr) {
+                queue[(size_t)qcnt * TC_C + tid] = key;
+                qcnt++;
+              }
+            }
+          }
+          // at most 8 more keys per lane before the next check: merge once
+          // any queue holds more than TC_Q - 8
+          if (__any_sync(0xffffffffu, qcnt > TC_Q - 8)) flush();
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_bar[b]);
+      }
+      flush();
+      // merge the quarter lists of each probe (the B stages are free: every
+      // MMA of the item has completed)
+      uint64_t* parts = reinterpret_cast<uint64_t*>(sB0);
+      const bool fine = s_fail == 0;
+      if (fine && part > 0) {
+#pragma unroll
+        for (int i = 0; i < KP; i++) parts[((size_t)(part - 1) * KP + i) * TC_M + probe] = L[i];
+      }
+      consumers_sync();
+      if (fine && part == 0 && active) {
+        for (int q = 0; q < TC_PARTS - 1; q++)
+#pragma unroll
+          for (int i = 0; i < KP; i++) net_insert<KP>(L, parts[((size_t)q * KP + i) * TC_M + probe]);
+        uint64_t* dst = a.part + (int64_t)p_e[probe] * KP;
+#pragma unroll
+        for (int i = 0; i < KP; i++) dst[i] = L[i];
+      }
     }
-    tc_fence_before();
+    g0 += n_tiles;
+    fence_async_smem();  // generic stores into the B stages before later copies land there
     __syncthreads();
-    // refill this buffer with the tile after next
-    have[bi] = next_tile(t_lo[bi], t_n[bi], t_j0[bi]);
-    if (tid == 0 && have[bi]) {
-      issue(bi, t_lo[bi], t_n[bi]);
-      tma_out[bi] = true;
-    }
-    bi = nb_;
+    slot ^= 1;
   }
-  if (fail_flag) {
+
+  if (s_fail) {
     // a copy or an MMA did not complete in time: flag it, let what is in
     // flight land (bounded waits), release tensor memory and leave
-    if (tid == 0) {
+    if (warp == TC_PRODUCER && lane == 0) {
       atomicExch(a.err, 1);
-      for (int i = 0; i < 2; i++) {
-        if (mma_out[i]) mbar_wait_t(&mma_bar[i], mph[i]);
-        if (tma_out[i]) mbar_wait_t(&tma_bar[i], tph[i]);
-      }
+      for (int g = max(0, tma_hi - S + 1); g <= tma_hi; g++)
+        mbar_wait(&full_bar[g % S], (uint32_t)((g / S) & 1), nullptr);
+      for (int g = max(0, mma_hi - S + 1); g <= mma_hi; g++)
+        mbar_wait(&mma_bar[g % S], (uint32_t)((g / S) & 1), nullptr);
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
-    return;
-  }
-  flush();
-  // merge the quarter lists of each probe (the B tiles are free now)
-  uint64_t* parts = reinterpret_cast<uint64_t*>(sB[0]);
-  if (half > 0) {
-#pragma unroll
-    for (int i = 0; i < KP; i++) parts[((size_t)(half - 1) * KP + i) * TC_M + probe] = L[i];
-  }
-  __syncthreads();
-  if (half == 0 && active) {
-    for (int q = 0; q < TC_PARTS - 1; q++)
-#pragma unroll
-      for (int i = 0; i < KP; i++) net_insert<KP>(L, parts[((size_t)q * KP + i) * TC_M + probe]);
-    uint64_t* dst = a.part + (int64_t)p_e[probe] * KP;
-#pragma unroll
-    for (int i = 0; i < KP; i++) dst[i] = L[i];
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(TC_COLS));
 }
 
 // ---- bf16 query copy and fp32 squared norms -------------------------------
@@ -667,24 +695,28 @@ __global__ void k_gather_i32(const int32_t* __restrict__ src, const int32_t* __r
   if (i < n) dst[i] = src[idx[i]];
 }
 
-__global__ void k_tc_items_count(const int32_t* __restrict__ bin_off, int B,
+__global__ void k_tc_items_count(const int32_t* __restrict__ bin_off, int B, int cap,
                                  int32_t* __restrict__ cnt) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < B) cnt[b] = (bin_off[b + 1] - bin_off[b] + TC_M - 1) / TC_M;
+  if (b < B) cnt[b] = (bin_off[b + 1] - bin_off[b] + cap - 1) / cap;
   if (b == B) cnt[B] = 0;
 }
 __global__ void k_tc_items_fill(const int32_t* __restrict__ bin_off,
-                                const int32_t* __restrict__ item_off, int B,
-                                TcItem* __restrict__ items, int32_t* __restrict__ n_items) {
+                                const int32_t* __restrict__ item_off, int B, int cap,
+                                TcItem* __restrict__ items, int32_t* __restrict__ n_items,
+                                int32_t* __restrict__ next_item) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b == B) *n_items = item_off[B];
+  if (b == B) {
+    *n_items = item_off[B];
+    *next_item = 0;
+  }
   if (b >= B) return;
   const int c = bin_off[b + 1] - bin_off[b];
-  for (int t = 0; t * TC_M < c; t++) {
+  for (int t = 0; t * cap < c; t++) {
     TcItem x;
     x.b = b;
-    x.e0 = bin_off[b] + t * TC_M;
-    x.ne = min(TC_M, c - t * TC_M);
+    x.e0 = bin_off[b] + t * cap;
+    x.ne = min(cap, c - t * cap);
     x.pad = 0;
     items[item_off[b] + t] = x;
   }
@@ -709,13 +741,31 @@ __global__ void k_inverse_perm(const int32_t* __restrict__ perm, int64_t N,
   if (r < N) iperm[perm[r]] = (int32_t)r;
 }
 
-template <int METRIC, int WP, int KP>
+template <int METRIC, int WP, int KP, int N>
 int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem, cudaStream_t s) {
-  auto kern = k_scan_tc<METRIC, WP, KP>;
+  auto kern = k_scan_tc<METRIC, WP, KP, N>;
   CAPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<(unsigned)grid, TC_T, smem, s>>>(map, a);
   CAPS_LAUNCH("k_scan_tc");
   return CAPS_OK;
+}
+
+int sm_count() {
+  static int n[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (n[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 1;
+    }
+    n[dev] = v;
+  }
+  return n[dev];
 }
 
 }  // namespace
@@ -729,8 +779,10 @@ int tc_rerank_depth(int k, int factor) {
 bool tc_scan_supported(int d, int k, int kp, int words_pad) {
   if (d % 8 != 0 || d < 64 || d > 128 || k > 32 || (kp != 12 && kp != 16 && kp != 32))
     return false;
-  // leave room for ~5 KB of static shared memory under the 227 KB limit
-  return tc_smem_bytes((d + 63) / 64, words_pad, kp) <= 221 * 1024;
+  // leave room for ~7 KB of static shared memory under the 227 KB limit
+  const int kc = (d + 63) / 64;
+  return std::max(tc_smem_bytes(kc, words_pad, 256), tc_smem_bytes(kc, words_pad, 128)) <=
+         220 * 1024;
 }
 
 int tc_prepare_index(const float* Xp, int64_t N, int d, const int32_t* perm, void* Xb, float* xn,
@@ -741,7 +793,7 @@ int tc_prepare_index(const float* Xp, int64_t N, int d, const int32_t* perm, voi
   k_inverse_perm<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(perm, N, iperm);
   CAPS_LAUNCH("k_inverse_perm");
   // 2-D tensor map over the bf16 rows: inner dimension d, outer N rows;
-  // boxes of 64 coordinates (128 bytes) x 256 rows, 128-byte swizzle
+  // boxes of 64 coordinates (128 bytes) x 128 rows, 128-byte swizzle
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult qres;
   CAPS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
@@ -751,7 +803,7 @@ int tc_prepare_index(const float* Xp, int64_t N, int d, const int32_t* perm, voi
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   cuuint64_t gdim[2] = {(cuuint64_t)d, (cuuint64_t)N};
   cuuint64_t gstride[1] = {(cuuint64_t)d * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)TC_N};
+  cuuint32_t box[2] = {64, (cuuint32_t)TC_BOX};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(static_cast<CUtensorMap*>(tmap_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Xb,
                       gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -769,9 +821,10 @@ int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, cudaSt
   return CAPS_OK;
 }
 
-int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, BinWork* w,
-             Scratch& scr, cudaStream_t s) {
+int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, int item_cap,
+             BinWork* w, Scratch& scr, cudaStream_t s) {
   if (ne > INT_MAX) return fail(CAPS_EINVAL, "too many probes in one chunk");
+  const int cap = item_cap > 0 ? std::min(item_cap, TC_M) : TC_M;
   int32_t *bin_off = nullptr, *cnt = nullptr;
   if (int rc = scr.get(&w->ent, (size_t)ne)) return rc;
   if (int rc = scr.get(&bin_off, (size_t)B + 1)) return rc;
@@ -798,15 +851,17 @@ int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B
     if (int rc = stable_sort_by_key(probe, ne, B, w->ent, bin_off, scr, s)) return rc;
   }
   if (int rc = scr.get(&cnt, (size_t)B + 1)) return rc;
-  if (int rc = scr.get(&w->n_items, 1)) return rc;
-  k_tc_items_count<<<(B + 1 + 255) / 256, 256, 0, s>>>(bin_off, B, cnt);
+  if (int rc = scr.get(&w->n_items, 2)) return rc;
+  w->next_item = w->n_items + 1;
+  k_tc_items_count<<<(B + 1 + 255) / 256, 256, 0, s>>>(bin_off, B, cap, cnt);
   CAPS_LAUNCH("k_tc_items_count");
   if (int rc = scan_exclusive_i32(cnt, (int64_t)B + 1, scr, s)) return rc;
-  w->max_items = ne / TC_M + B + 1;
+  w->max_items = ne / cap + B + 1;
   TcItem* items = nullptr;
   if (int rc = scr.get(&items, (size_t)w->max_items)) return rc;
   w->items = items;
-  k_tc_items_fill<<<(B + 1 + 255) / 256, 256, 0, s>>>(bin_off, cnt, B, items, w->n_items);
+  k_tc_items_fill<<<(B + 1 + 255) / 256, 256, 0, s>>>(bin_off, cnt, B, cap, items, w->n_items,
+                                                       w->next_item);
   CAPS_LAUNCH("k_tc_items_fill");
   return CAPS_OK;
 }
@@ -816,6 +871,7 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   a.ent = w.ent;
   a.items = static_cast<const TcItem*>(w.items);
   a.n_items = w.n_items;
+  a.next_item = w.next_item;
   a.sel = t.sel;
   a.qmask = t.qmask;
   a.qval = t.qval;
@@ -832,12 +888,18 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   a.kp = t.kp;
   a.part = t.part;
   a.err = t.err;
-  const size_t smem = tc_smem_bytes(a.kc, t.words_pad, t.kp);
+  const int N = t.tile_n == 128 ? 128 : 256;
+  const size_t smem = tc_smem_bytes(a.kc, t.words_pad, N);
   const CUtensorMap& map = *static_cast<const CUtensorMap*>(t.tmap);
-  const int64_t g = w.max_items;
-#define CAPS_TC(WPV, KPV)                                                 \
-  return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV>(map, a, g, smem, s) \
-                             : launch_tc<CAPS_IP, WPV, KPV>(map, a, g, smem, s)
+  // persistent: one CTA per SM (the shared memory admits no second), never
+  // more CTAs than work items
+  const int64_t g = std::max<int64_t>(1, std::min<int64_t>(w.max_items, sm_count()));
+#define CAPS_TC(WPV, KPV)                                                                   \
+  if (N == 128)                                                                             \
+    return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 128>(map, a, g, smem, s)      \
+                               : launch_tc<CAPS_IP, WPV, KPV, 128>(map, a, g, smem, s);     \
+  return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 256>(map, a, g, smem, s)        \
+                             : launch_tc<CAPS_IP, WPV, KPV, 256>(map, a, g, smem, s)
   if (t.kp == 12) {
     switch (t.words_pad) {
       case 1: CAPS_TC(1, 12);
