@@ -323,6 +323,67 @@ int caps_search_batch_noalloc(const caps_index* index, const float* Q,
                               int32_t k, int32_t m, int64_t* out_ids,
                               float* out_dist, void* stream);
 
+/* ---- tuned, graph-captured query plans -------------------------------------
+ *
+ * One batch shape (nq queries, k, m) against one index, prepared once and
+ * then replayed: the whole batched query of Alg. 2 (filter packing, probe,
+ * sub-partition selection, grouping, the persistent scan, merge and
+ * re-rank) is captured into one CUDA graph, so a later batch costs two input
+ * copies, one graph launch and two output copies.  Before the capture an
+ * autotuner times the scan's launch shapes on the batch given to
+ * caps_plan_create and keeps the fastest: rows per tensor-core tile (256 or
+ * 128, i.e. 2 or 4 accumulator stages in tensor memory) and the most probes
+ * per work item (128 or 64).  All shapes compute the same per-probe lists, so
+ * the tuner also checks that their results agree to the bit.  The index
+ * remembers the chosen shape for this (k, m): later caps_search_batch calls
+ * with the same k and m use it too.  Indexes that do not use the tensor-core
+ * scan have nothing to tune; their plan is only the captured graph.
+ *
+ * The plan owns device copies of one batch's inputs and outputs
+ * (nq*(4d + 4L + 12k) bytes); the graph owns its temporaries.  The index must
+ * outlive the plan.  Calls on one plan must be ordered (one stream, or
+ * synchronised): they share those buffers.
+ */
+typedef struct caps_plan caps_plan;
+
+#define CAPS_PLAN_MAX_CANDIDATES 8
+typedef struct {
+  int64_t nq;
+  int32_t k, m;
+  int32_t tile_n;        /* chosen rows per tensor-core tile; 0 without that scan */
+  int32_t item_cap;      /* chosen most probes per work item; 0 without that scan */
+  int32_t n_candidates;  /* launch shapes the autotuner timed (0: none) */
+  int32_t cand_tile_n[CAPS_PLAN_MAX_CANDIDATES];
+  int32_t cand_item_cap[CAPS_PLAN_MAX_CANDIDATES];
+  float cand_ms[CAPS_PLAN_MAX_CANDIDATES]; /* median device ms of one search each */
+  int32_t graph_nodes;   /* nodes of the captured graph */
+} caps_plan_info;
+
+/* Prepare a plan for batches of nq queries (Q [nq*d] fp32, constraints dense
+ * [nq*L], host or device).  These queries are the autotuner's sample: it
+ * runs the full search 4 times per candidate shape on them (autotune = 0:
+ * keep the default shape, 256 rows and 128 probes).  The call synchronises
+ * `stream`.  CAPS_EINVAL on bad arguments, CAPS_ECUDA if the capture or the
+ * instantiation fails; *out is set only on success. */
+int caps_plan_create(const caps_index* index, const float* Q, int64_t nq,
+                     const caps_attrs* constraints, int32_t k, int32_t m,
+                     int32_t autotune, void* stream, caps_plan** out);
+
+/* Run the plan on a batch of nq <= plan nq queries (arguments as in
+ * caps_search_batch; host or device).  The graph always processes the
+ * plan's nq rows (rows beyond this call's nq hold earlier inputs and their
+ * results are not copied out).  Asynchronous on `stream` when both outputs
+ * are device memory; with a host output the call waits and also reports an
+ * expired bounded device wait as CAPS_ETIMEOUT. */
+int caps_plan_search(caps_plan* plan, const float* Q, int64_t nq,
+                     const caps_attrs* constraints, int64_t* out_ids,
+                     float* out_dist, void* stream);
+
+int caps_plan_get_info(const caps_plan* plan, caps_plan_info* out);
+
+/* Destroys the graph and frees the plan's buffers (synchronises the device). */
+void caps_plan_free(caps_plan* plan);
+
 /* ---- stage timing (measurement aid, off by default) ---------------------- */
 
 /* Per-stage device time of the last caps_search_batch call made on this

@@ -29,7 +29,8 @@ ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS, ARR_MLP, ARR_L
 EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "caps_get_info",
            "caps_export", "caps_assign", "caps_probe", "caps_select", "caps_set_timing",
            "caps_get_stage_times", "caps_search_batch_noalloc", "caps_device_status",
-           "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign")
+           "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign", "caps_plan_create",
+           "caps_plan_search", "caps_plan_get_info", "caps_plan_free")
 
 
 class CapsError(RuntimeError):
@@ -66,6 +67,13 @@ class caps_index_info(ct.Structure):
                 ("mlp_hidden", ct.c_int32), ("n_labels", ct.c_int64)]
 
 
+class caps_plan_info(ct.Structure):
+    _fields_ = [("nq", ct.c_int64), ("k", ct.c_int32), ("m", ct.c_int32),
+                ("tile_n", ct.c_int32), ("item_cap", ct.c_int32), ("n_candidates", ct.c_int32),
+                ("cand_tile_n", ct.c_int32 * 8), ("cand_item_cap", ct.c_int32 * 8),
+                ("cand_ms", ct.c_float * 8), ("graph_nodes", ct.c_int32)]
+
+
 _lib = None
 
 
@@ -97,6 +105,12 @@ def lib(path: Optional[str] = None):
     L.caps_mlp_loss_grad.argtypes = [i32, i32, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]
     L.caps_mlp_train.argtypes = [i32, i32, i32, P, P, i64, P, i32, i32, ct.c_float, P, P]
     L.caps_mlp_assign.argtypes = [i32, i32, i32, P, P, i64, P, P]
+    L.caps_plan_create.argtypes = [P, P, i64, ct.POINTER(caps_attrs), i32, i32, i32, P,
+                                   ct.POINTER(P)]
+    L.caps_plan_search.argtypes = [P, P, i64, ct.POINTER(caps_attrs), P, P, P]
+    L.caps_plan_get_info.argtypes = [P, ct.POINTER(caps_plan_info)]
+    L.caps_plan_free.argtypes = [P]
+    L.caps_plan_free.restype = None
     L.caps_set_timing.argtypes = [i32]
     L.caps_get_stage_times.argtypes = [ct.POINTER(caps_stage_times)]
     _lib = L
@@ -350,3 +364,59 @@ class Index:
         _check(lib().caps_search_batch_noalloc(self._h, _ptr(Q), Q.shape[0], ct.byref(at), k, m,
                                                _ptr(out_ids), _ptr(out_dist), _stream(stream)))
         return out_ids, out_dist
+
+    def plan(self, Q, Qb, k, m, autotune=True, stream=None) -> "Plan":
+        """caps_plan_create: a tuned, graph-captured plan for batches shaped
+        like Q (its rows are the autotuner's sample)."""
+        Q = _np_or_keep(Q, np.float32)
+        at, keep = _dense_attrs(Qb)
+        h = ct.c_void_p()
+        _check(lib().caps_plan_create(self._h, _ptr(Q), Q.shape[0], ct.byref(at), k, m,
+                                      1 if autotune else 0, _stream(stream), ct.byref(h)))
+        return Plan(h, self, k)
+
+
+class Plan:
+    """A tuned, graph-captured batch query (caps_plan_*); keeps its index alive."""
+
+    def __init__(self, handle, index, k):
+        self._h = handle
+        self._index = index
+        self.k = k
+        inf = caps_plan_info()
+        _check(lib().caps_plan_get_info(self._h, ct.byref(inf)))
+        self.nq = inf.nq
+        n = inf.n_candidates
+        self.info = {"nq": inf.nq, "k": inf.k, "m": inf.m, "tile_n": inf.tile_n,
+                     "item_cap": inf.item_cap, "graph_nodes": inf.graph_nodes,
+                     "candidates": [{"tile_n": inf.cand_tile_n[i],
+                                     "item_cap": inf.cand_item_cap[i],
+                                     "ms": round(float(inf.cand_ms[i]), 4)} for i in range(n)]}
+
+    def search(self, Q, Qb, out_ids=None, out_dist=None, stream=None):
+        """Replay the plan on a batch of <= nq queries; returns (ids, dist)."""
+        Q = _np_or_keep(Q, np.float32)
+        nq = Q.shape[0]
+        at, keep = _dense_attrs(Qb)
+        t = _torch()
+        if out_ids is None:
+            if t is not None and isinstance(Q, t.Tensor) and Q.is_cuda:
+                out_ids = t.empty((nq, self.k), dtype=t.int64, device=Q.device)
+                out_dist = t.empty((nq, self.k), dtype=t.float32, device=Q.device)
+            else:
+                out_ids = np.empty((nq, self.k), dtype=np.int64)
+                out_dist = np.empty((nq, self.k), dtype=np.float32)
+        _check(lib().caps_plan_search(self._h, _ptr(Q), nq, ct.byref(at), _ptr(out_ids),
+                                      _ptr(out_dist), _stream(stream)))
+        return out_ids, out_dist
+
+    def close(self):
+        if self._h:
+            lib().caps_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,7 +1,9 @@
 // C ABI of the CAPS GB300 library: argument checks, host/device staging and
 // the order of the kernels for index construction (Alg. 1) and batched query
 // (Alg. 2).  All arithmetic of the method runs in the kernels.
+#include <algorithm>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <unordered_set>
 #include <vector>
@@ -752,16 +754,42 @@ extern "C" int caps_device_status(const caps_index* ix, void* stream) {
   return CAPS_OK;
 }
 
+namespace {
+// Launch-shape choices of one batched search (the autotuner's search space).
+struct SearchOpts {
+  int tile_n = 256;    // rows per tensor-core tile (128 or 256)
+  int item_cap = 0;    // most probes per tensor-core work item (0: 128)
+  bool timed = true;   // stage events allowed (not while a graph is captured)
+  bool cached = false; // use the shape the autotuner chose for this (k, m), if any
+};
+
+int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_attrs* cons,
+                int32_t k, int32_t m, int64_t* out_ids, float* out_dist, cudaStream_t s,
+                const SearchOpts& o);
+
+bool uses_tc(const caps_index* ix, int k) {
+  return ix->prec == CAPS_BF16 && tc_scan_supported(ix->d, k, tc_kp(k), ix->meta.words_pad);
+}
+}  // namespace
+
 extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t nq,
                                  const caps_attrs* cons, int32_t k, int32_t m, int64_t* out_ids,
                                  float* out_dist, void* stream) {
+  SearchOpts o;
+  o.cached = true;
+  return search_impl(ix, Q, nq, cons, k, m, out_ids, out_dist, (cudaStream_t)stream, o);
+}
+
+namespace {
+int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_attrs* cons,
+                int32_t k, int32_t m, int64_t* out_ids, float* out_dist, cudaStream_t s,
+                const SearchOpts& o) {
   if (!ix) return fail(CAPS_EINVAL, "null index");
   if (nq < 0) return fail(CAPS_EINVAL, "nq < 0");
   if (k < 1 || k > kMaxK) return fail(CAPS_EINVAL, "k must be in [1, 128]");
   if (m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
   if (int rc = check_cons(ix, cons)) return rc;
   if (nq == 0) return CAPS_OK;
-  cudaStream_t s = (cudaStream_t)stream;
   keep_pool_warm();
   Scratch scr(s);
   const float* dQ = nullptr;
@@ -772,9 +800,17 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
   Out<float> od;
   if (int rc = oi.init(out_ids, (size_t)nq * k, scr)) return rc;
   if (int rc = od.init(out_dist, (size_t)nq * k, scr)) return rc;
-  const bool tc = ix->prec == CAPS_BF16 &&
-                  tc_scan_supported(ix->d, k, tc_kp(k), ix->meta.words_pad);
+  const bool tc = uses_tc(ix, k);
   const int kp = tc ? tc_kp(k) : k;
+  int tile_n = o.tile_n, item_cap = o.item_cap;
+  if (o.cached) {
+    std::lock_guard<std::mutex> lock(ix->tune_mu);
+    auto f = ix->tuned.find({k, m});
+    if (f != ix->tuned.end()) {
+      tile_n = f->second.first;
+      item_cap = f->second.second;
+    }
+  }
   const int64_t qc = chunk_rows(ix, nq, m, kp);
   Batch bt;
   if (int rc = alloc_batch(ix, qc, m, scr, &bt)) return rc;
@@ -793,6 +829,13 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
   }
   const int L = ix->meta.L;
   StageTimer& tm = g_timer;
+  const bool timer_on = tm.on;
+  if (!o.timed) tm.on = false;  // no event records inside a graph capture
+  struct Restore {
+    StageTimer& t;
+    bool on;
+    ~Restore() { t.on = on; }
+  } restore{tm, timer_on};
   tm.used = 0;
   tm.launches = 0;
   tm.valid = false;
@@ -834,7 +877,8 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
     if (tc) {
       BinWork w;
       if (int rc = tc_query_prep(Qc, n, ix->d, Qh, qn, s)) return rc;
-      if (int rc = tc_group(bt.probe, bt.sel, ix->h, n * m, ix->B, 0, &w, cscr, s)) return rc;
+      if (int rc = tc_group(bt.probe, bt.sel, ix->h, n * m, ix->B, item_cap, &w, cscr, s))
+        return rc;
       if (int rc = tm.record(s)) return rc;
       TcScanArgs t;
       t.sel = bt.sel;
@@ -852,7 +896,7 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
       t.d = ix->d;
       t.kp = kp;
       t.rerank = tc_rerank_depth(k, ix->rerank_factor);
-      t.tile_n = 256;
+      t.tile_n = tile_n;
       t.words_pad = ix->meta.words_pad;
       t.metric = ix->metric;
       t.part = part;
@@ -882,10 +926,217 @@ extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t n
   if (int rc = od.finish(s)) return rc;
   if (oi.host || od.host) {
     CAPS_CUDA(cudaStreamSynchronize(s));
-    return caps_device_status(ix, stream);
+    return caps_device_status(ix, s);
   }
   return CAPS_OK;
 }
+}  // namespace
+
+// ---- tuned, graph-captured query plans -------------------------------------
+
+struct caps_plan {
+  const caps_index* ix = nullptr;
+  int64_t nq = 0;
+  int32_t k = 0, m = 0;
+  float* Q = nullptr;        // [nq*d]
+  int32_t* cons = nullptr;   // [nq*L]
+  int64_t* ids = nullptr;    // [nq*k]
+  float* dist = nullptr;     // [nq*k]
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  caps_plan_info info{};
+  ~caps_plan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaFree(Q);
+    cudaFree(cons);
+    cudaFree(ids);
+    cudaFree(dist);
+    cudaGetLastError();
+  }
+};
+
+namespace {
+template <class T>
+int plan_alloc(T** p, size_t count) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(1, count) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(CAPS_ENOMEM, "cudaMalloc failed for a plan buffer");
+  }
+  return CAPS_OK;
+}
+
+// Median device time (ms) of `reps` searches with launch shape o, after one
+// untimed run.
+int time_shape(caps_plan* p, const caps_attrs& pc, const SearchOpts& o, cudaStream_t s, int reps,
+               float* ms_out) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CAPS_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce, "cudaEventCreate");
+  }
+  std::vector<float> t;
+  int rc = search_impl(p->ix, p->Q, p->nq, &pc, p->k, p->m, p->ids, p->dist, s, o);
+  for (int r = 0; rc == CAPS_OK && r < reps; r++) {
+    if (cudaEventRecord(e0, s) != cudaSuccess) rc = fail(CAPS_ECUDA, "cudaEventRecord");
+    if (rc == CAPS_OK) rc = search_impl(p->ix, p->Q, p->nq, &pc, p->k, p->m, p->ids, p->dist, s, o);
+    if (rc == CAPS_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = fail(CAPS_ECUDA, "cudaEventRecord");
+    float ms = 0.f;
+    if (rc == CAPS_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(CAPS_ECUDA, "cudaEventSynchronize");
+    if (rc == CAPS_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      rc = fail(CAPS_ECUDA, "cudaEventElapsedTime");
+    t.push_back(ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  if (rc) return rc;
+  std::sort(t.begin(), t.end());
+  *ms_out = t[t.size() / 2];
+  return CAPS_OK;
+}
+}  // namespace
+
+extern "C" int caps_plan_create(const caps_index* ix, const float* Q, int64_t nq,
+                                const caps_attrs* cons, int32_t k, int32_t m, int32_t autotune,
+                                void* stream, caps_plan** out) {
+  if (!out) return fail(CAPS_EINVAL, "null output handle");
+  *out = nullptr;
+  if (!ix || !Q) return fail(CAPS_EINVAL, "null argument");
+  if (nq < 1) return fail(CAPS_EINVAL, "a plan needs nq >= 1");
+  if (k < 1 || k > kMaxK) return fail(CAPS_EINVAL, "k must be in [1, 128]");
+  if (m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
+  if (int rc = check_cons(ix, cons)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<caps_plan> p(new caps_plan());
+  p->ix = ix;
+  p->nq = nq;
+  p->k = k;
+  p->m = m;
+  const int L = ix->meta.L;
+  if (int rc = plan_alloc(&p->Q, (size_t)nq * ix->d)) return rc;
+  if (int rc = plan_alloc(&p->cons, (size_t)nq * L)) return rc;
+  if (int rc = plan_alloc(&p->ids, (size_t)nq * k)) return rc;
+  if (int rc = plan_alloc(&p->dist, (size_t)nq * k)) return rc;
+  CAPS_CUDA(cudaMemcpyAsync(p->Q, Q, sizeof(float) * nq * ix->d, cudaMemcpyDefault, s));
+  CAPS_CUDA(cudaMemcpyAsync(p->cons, cons->dense, sizeof(int32_t) * nq * L, cudaMemcpyDefault, s));
+  caps_attrs pc = *cons;
+  pc.dense = p->cons;
+  caps_plan_info& inf = p->info;
+  inf.nq = nq;
+  inf.k = k;
+  inf.m = m;
+  SearchOpts best;
+  best.timed = false;
+  if (uses_tc(ix, k)) {
+    inf.tile_n = best.tile_n;
+    inf.item_cap = 128;
+    if (autotune) {
+      // the scan's launch shapes: rows per tile (accumulator stages) x most
+      // probes per work item
+      const int shapes[4][2] = {{256, 128}, {128, 128}, {256, 64}, {128, 64}};
+      float best_ms = 0.f;
+      // every shape computes the same per-probe lists, so the results must
+      // agree to the bit: the tuner checks that against the first shape
+      std::vector<int64_t> ref_i((size_t)nq * k), got_i((size_t)nq * k);
+      std::vector<float> ref_d((size_t)nq * k), got_d((size_t)nq * k);
+      for (int c = 0; c < 4; c++) {
+        SearchOpts o;
+        o.timed = false;
+        o.tile_n = shapes[c][0];
+        o.item_cap = shapes[c][1];
+        float ms = 0.f;
+        if (int rc = time_shape(p.get(), pc, o, s, 3, &ms)) return rc;
+        std::vector<int64_t>& vi = c == 0 ? ref_i : got_i;
+        std::vector<float>& vd = c == 0 ? ref_d : got_d;
+        CAPS_CUDA(cudaMemcpyAsync(vi.data(), p->ids, sizeof(int64_t) * vi.size(),
+                                  cudaMemcpyDeviceToHost, s));
+        CAPS_CUDA(cudaMemcpyAsync(vd.data(), p->dist, sizeof(float) * vd.size(),
+                                  cudaMemcpyDeviceToHost, s));
+        CAPS_CUDA(cudaStreamSynchronize(s));
+        if (c > 0 && (std::memcmp(vi.data(), ref_i.data(), sizeof(int64_t) * vi.size()) != 0 ||
+                      std::memcmp(vd.data(), ref_d.data(), sizeof(float) * vd.size()) != 0))
+          return fail(CAPS_ECUDA, "tensor-core launch shapes disagree on the tuning batch");
+        inf.cand_tile_n[c] = o.tile_n;
+        inf.cand_item_cap[c] = o.item_cap;
+        inf.cand_ms[c] = ms;
+        inf.n_candidates = c + 1;
+        if (c == 0 || ms < best_ms) {
+          best_ms = ms;
+          best = o;
+        }
+      }
+      inf.tile_n = best.tile_n;
+      inf.item_cap = best.item_cap;
+      std::lock_guard<std::mutex> lock(ix->tune_mu);
+      ix->tuned[{k, m}] = {best.tile_n, best.item_cap};
+    }
+  }
+  CAPS_CUDA(cudaStreamSynchronize(s));  // the input copies, and any tuning runs
+  if (int rc = caps_device_status(ix, s)) return rc;
+  // capture on a private stream (the legacy default stream cannot be captured)
+  cudaStream_t cs = nullptr;
+  CAPS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(ce, "cudaStreamBeginCapture");
+  }
+  int rc = search_impl(ix, p->Q, nq, &pc, k, m, p->ids, p->dist, cs, best);
+  cudaGraph_t g = nullptr;
+  ce = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (rc != CAPS_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc;
+  }
+  if (ce != cudaSuccess || !g) return cuda_fail(ce, "cudaStreamEndCapture");
+  p->graph = g;
+  CAPS_CUDA(cudaGraphInstantiate(&p->exec, g, 0));
+  size_t nodes = 0;
+  CAPS_CUDA(cudaGraphGetNodes(g, nullptr, &nodes));
+  inf.graph_nodes = (int32_t)nodes;
+  *out = p.release();
+  return CAPS_OK;
+}
+
+extern "C" int caps_plan_search(caps_plan* p, const float* Q, int64_t nq, const caps_attrs* cons,
+                                int64_t* out_ids, float* out_dist, void* stream) {
+  if (!p) return fail(CAPS_EINVAL, "null plan");
+  if (nq < 0 || nq > p->nq) return fail(CAPS_EINVAL, "nq must be in [0, plan nq]");
+  if (int rc = check_cons(p->ix, cons)) return rc;
+  if (nq == 0) return CAPS_OK;
+  if (!Q || !out_ids || !out_dist) return fail(CAPS_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int L = p->ix->meta.L;
+  CAPS_CUDA(cudaMemcpyAsync(p->Q, Q, sizeof(float) * nq * p->ix->d, cudaMemcpyDefault, s));
+  CAPS_CUDA(cudaMemcpyAsync(p->cons, cons->dense, sizeof(int32_t) * nq * L, cudaMemcpyDefault, s));
+  CAPS_CUDA(cudaGraphLaunch(p->exec, s));
+  ++g_kernel_launches;
+  CAPS_CUDA(cudaMemcpyAsync(out_ids, p->ids, sizeof(int64_t) * nq * p->k, cudaMemcpyDefault, s));
+  CAPS_CUDA(cudaMemcpyAsync(out_dist, p->dist, sizeof(float) * nq * p->k, cudaMemcpyDefault, s));
+  bool di = false, dd = false;
+  if (int rc = is_device_ptr(out_ids, &di)) return rc;
+  if (int rc = is_device_ptr(out_dist, &dd)) return rc;
+  if (!di || !dd) {
+    CAPS_CUDA(cudaStreamSynchronize(s));
+    return caps_device_status(p->ix, s);
+  }
+  return CAPS_OK;
+}
+
+extern "C" int caps_plan_get_info(const caps_plan* p, caps_plan_info* out) {
+  if (!p || !out) return fail(CAPS_EINVAL, "null argument");
+  *out = p->info;
+  return CAPS_OK;
+}
+
+extern "C" void caps_plan_free(caps_plan* p) { delete p; }
 
 // ---- learned partitioner step entry points ---------------------------------
 

@@ -4,7 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "caps.h"
@@ -308,6 +311,10 @@ struct caps_index {
   float* xn = nullptr;
   int32_t* iperm = nullptr;
   alignas(128) unsigned char tmap[128] = {};
+  // launch shapes the autotuner chose, per (k, m): (rows per tile, probes per
+  // item); later caps_search_batch calls with that (k, m) use them
+  mutable std::mutex tune_mu;
+  mutable std::map<std::pair<int, int>, std::pair<int, int>> tuned;
   int64_t bytes = 0;
   std::vector<void*> allocs;
 
