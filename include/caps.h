@@ -331,9 +331,11 @@ int caps_search_batch_noalloc(const caps_index* index, const float* Q,
  * re-rank) is captured into one CUDA graph, so a later batch costs two input
  * copies, one graph launch and two output copies.  Before the capture an
  * autotuner times the scan's launch shapes on the batch given to
- * caps_plan_create and keeps the fastest: rows per tensor-core tile (256 or
- * 128, i.e. 2 or 4 accumulator stages in tensor memory) and the most probes
- * per work item (128 or 64).  All shapes compute the same per-probe lists, so
+ * caps_plan_create and keeps the fastest: where the block selection and the
+ * attribute filter are applied (per pair in the epilogue, with 256 or 128
+ * rows per tensor-core tile, i.e. 2 or 4 accumulator stages in tensor memory;
+ * or folded into the MMA through a one-hot code chunk, 128 rows, when the
+ * index has that chunk) and the most probes per work item (128 or 64).  All shapes compute the same per-probe lists, so
  * the tuner also checks that their results agree to the bit.  The index
  * remembers the chosen shape for this (k, m): later caps_search_batch calls
  * with the same k and m use it too.  Indexes that do not use the tensor-core
@@ -357,6 +359,8 @@ typedef struct {
   int32_t cand_item_cap[CAPS_PLAN_MAX_CANDIDATES];
   float cand_ms[CAPS_PLAN_MAX_CANDIDATES]; /* median device ms of one search each */
   int32_t graph_nodes;   /* nodes of the captured graph */
+  int32_t pen;           /* chosen: 1 = block selection and filter folded into the MMA */
+  int32_t cand_pen[CAPS_PLAN_MAX_CANDIDATES];
 } caps_plan_info;
 
 /* Prepare a plan for batches of nq queries (Q [nq*d] fp32, constraints dense

@@ -71,7 +71,8 @@ class caps_plan_info(ct.Structure):
     _fields_ = [("nq", ct.c_int64), ("k", ct.c_int32), ("m", ct.c_int32),
                 ("tile_n", ct.c_int32), ("item_cap", ct.c_int32), ("n_candidates", ct.c_int32),
                 ("cand_tile_n", ct.c_int32 * 8), ("cand_item_cap", ct.c_int32 * 8),
-                ("cand_ms", ct.c_float * 8), ("graph_nodes", ct.c_int32)]
+                ("cand_ms", ct.c_float * 8), ("graph_nodes", ct.c_int32), ("pen", ct.c_int32),
+                ("cand_pen", ct.c_int32 * 8)]
 
 
 _lib = None
@@ -388,9 +389,9 @@ class Plan:
         self.nq = inf.nq
         n = inf.n_candidates
         self.info = {"nq": inf.nq, "k": inf.k, "m": inf.m, "tile_n": inf.tile_n,
-                     "item_cap": inf.item_cap, "graph_nodes": inf.graph_nodes,
+                     "item_cap": inf.item_cap, "pen": inf.pen, "graph_nodes": inf.graph_nodes,
                      "candidates": [{"tile_n": inf.cand_tile_n[i],
-                                     "item_cap": inf.cand_item_cap[i],
+                                     "item_cap": inf.cand_item_cap[i], "pen": inf.cand_pen[i],
                                      "ms": round(float(inf.cand_ms[i]), 4)} for i in range(n)]}
 
     def search(self, Q, Qb, out_ids=None, out_dist=None, stream=None):

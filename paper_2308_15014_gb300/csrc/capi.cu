@@ -467,13 +467,42 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   }
   if (p->prec == CAPS_BF16) {
     // bf16 form: bf16 rows + fp32 squared norms + inverse permutation
+    // penalty form when the one-hot code of the packed attribute bits (two
+    // columns per bit) and of the blocks fits one 64-column chunk
+    int T = 0;
+    uint32_t um[4] = {};
+    for (int f = 0; f < meta.L; f++) {
+      um[meta.word[f]] |= ((1u << meta.bits[f]) - 1u) << meta.shift[f];
+      T += meta.bits[f];
+    }
+    ix->pen = 2 * T + (h + 1) <= 64 ? 1 : 0;
+    ix->pen_bits = T;
+    for (int w = 0; w < 4; w++) ix->pen_mask[w] = um[w];
+    const int cols = ix->pen ? ((d + 63) / 64 + 1) * 64 : d;
     uint16_t* xb = nullptr;
-    if (int rc = ix->alloc(&xb, (size_t)N * d)) return rc;
+    if (int rc = ix->alloc(&xb, (size_t)N * cols)) return rc;
     ix->Xb = xb;
     if (int rc = ix->alloc(&ix->xn, (size_t)N + 4)) return rc;
     if (int rc = ix->alloc(&ix->iperm, (size_t)N)) return rc;
-    if (int rc = tc_prepare_index(ix->Xp, N, d, ix->perm, ix->Xb, ix->xn, ix->iperm, ix->tmap, s))
-      return rc;
+    TcIndexPrep tp;
+    tp.Xp = ix->Xp;
+    tp.N = N;
+    tp.d = d;
+    tp.perm = ix->perm;
+    tp.Ap = ix->Ap;
+    tp.words_pad = meta.words_pad;
+    tp.offsets = ix->offsets;
+    tp.B = B;
+    tp.nb = h + 1;
+    tp.pen = ix->pen;
+    tp.pen_bits = T;
+    for (int w = 0; w < 4; w++) tp.pen_mask[w] = um[w];
+    tp.Xb = ix->Xb;
+    tp.xn = ix->xn;
+    tp.iperm = ix->iperm;
+    tp.xn_max = &ix->xn_max;
+    tp.tmap = ix->tmap;
+    if (int rc = tc_prepare_index(tp, s)) return rc;
   }
   CAPS_CUDA(cudaStreamSynchronize(s));
   return CAPS_OK;
@@ -759,6 +788,7 @@ namespace {
 struct SearchOpts {
   int tile_n = 256;    // rows per tensor-core tile (128 or 256)
   int item_cap = 0;    // most probes per tensor-core work item (0: 128)
+  int pen = -1;        // filter folded into the MMA: 1 yes, 0 no, -1 when the index has it
   bool timed = true;   // stage events allowed (not while a graph is captured)
   bool cached = false; // use the shape the autotuner chose for this (k, m), if any
 };
@@ -769,6 +799,9 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
 
 bool uses_tc(const caps_index* ix, int k) {
   return ix->prec == CAPS_BF16 && tc_scan_supported(ix->d, k, tc_kp(k), ix->meta.words_pad);
+}
+bool uses_pen(const caps_index* ix, int k) {
+  return uses_tc(ix, k) && ix->pen && tc_pen_supported(ix->d, tc_kp(k), ix->meta.words_pad);
 }
 }  // namespace
 
@@ -802,15 +835,18 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
   if (int rc = od.init(out_dist, (size_t)nq * k, scr)) return rc;
   const bool tc = uses_tc(ix, k);
   const int kp = tc ? tc_kp(k) : k;
-  int tile_n = o.tile_n, item_cap = o.item_cap;
+  int tile_n = o.tile_n, item_cap = o.item_cap, pen = o.pen;
   if (o.cached) {
     std::lock_guard<std::mutex> lock(ix->tune_mu);
     auto f = ix->tuned.find({k, m});
     if (f != ix->tuned.end()) {
-      tile_n = f->second.first;
-      item_cap = f->second.second;
+      tile_n = f->second.tile_n;
+      item_cap = f->second.item_cap;
+      pen = f->second.pen;
     }
   }
+  const bool pen_ok = tc && ix->pen && tc_pen_supported(ix->d, kp, ix->meta.words_pad);
+  const bool use_pen = pen_ok && pen != 0;
   const int64_t qc = chunk_rows(ix, nq, m, kp);
   Batch bt;
   if (int rc = alloc_batch(ix, qc, m, scr, &bt)) return rc;
@@ -897,6 +933,10 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
       t.kp = kp;
       t.rerank = tc_rerank_depth(k, ix->rerank_factor);
       t.tile_n = tile_n;
+      t.pen = use_pen ? 1 : 0;
+      t.pen_bits = ix->pen_bits;
+      for (int i = 0; i < 4; i++) t.pen_mask[i] = ix->pen_mask[i];
+      t.xn_max = ix->xn_max;
       t.words_pad = ix->meta.words_pad;
       t.metric = ix->metric;
       t.part = part;
@@ -1033,22 +1073,30 @@ extern "C" int caps_plan_create(const caps_index* ix, const float* Q, int64_t nq
   SearchOpts best;
   best.timed = false;
   if (uses_tc(ix, k)) {
+    const bool pen_ok = uses_pen(ix, k);
+    best.pen = pen_ok ? 1 : 0;
+    best.tile_n = pen_ok ? 128 : 256;
     inf.tile_n = best.tile_n;
     inf.item_cap = 128;
+    inf.pen = best.pen;
     if (autotune) {
-      // the scan's launch shapes: rows per tile (accumulator stages) x most
-      // probes per work item
-      const int shapes[4][2] = {{256, 128}, {128, 128}, {256, 64}, {128, 64}};
+      // the scan's launch shapes: filter in the epilogue (rows per tile:
+      // accumulator stages) or folded into the MMA (128 rows), x most probes
+      // per work item
+      const int shapes[6][3] = {{256, 128, 0}, {128, 128, 0}, {256, 64, 0},
+                                {128, 64, 0},  {128, 128, 1}, {128, 64, 1}};
+      const int n_shapes = pen_ok ? 6 : 4;
       float best_ms = 0.f;
       // every shape computes the same per-probe lists, so the results must
       // agree to the bit: the tuner checks that against the first shape
       std::vector<int64_t> ref_i((size_t)nq * k), got_i((size_t)nq * k);
       std::vector<float> ref_d((size_t)nq * k), got_d((size_t)nq * k);
-      for (int c = 0; c < 4; c++) {
+      for (int c = 0; c < n_shapes; c++) {
         SearchOpts o;
         o.timed = false;
         o.tile_n = shapes[c][0];
         o.item_cap = shapes[c][1];
+        o.pen = shapes[c][2];
         float ms = 0.f;
         if (int rc = time_shape(p.get(), pc, o, s, 3, &ms)) return rc;
         std::vector<int64_t>& vi = c == 0 ? ref_i : got_i;
@@ -1063,6 +1111,7 @@ extern "C" int caps_plan_create(const caps_index* ix, const float* Q, int64_t nq
           return fail(CAPS_ECUDA, "tensor-core launch shapes disagree on the tuning batch");
         inf.cand_tile_n[c] = o.tile_n;
         inf.cand_item_cap[c] = o.item_cap;
+        inf.cand_pen[c] = o.pen;
         inf.cand_ms[c] = ms;
         inf.n_candidates = c + 1;
         if (c == 0 || ms < best_ms) {
@@ -1072,8 +1121,9 @@ extern "C" int caps_plan_create(const caps_index* ix, const float* Q, int64_t nq
       }
       inf.tile_n = best.tile_n;
       inf.item_cap = best.item_cap;
+      inf.pen = best.pen;
       std::lock_guard<std::mutex> lock(ix->tune_mu);
-      ix->tuned[{k, m}] = {best.tile_n, best.item_cap};
+      ix->tuned[{k, m}] = {best.tile_n, best.item_cap, best.pen};
     }
   }
   CAPS_CUDA(cudaStreamSynchronize(s));  // the input copies, and any tuning runs

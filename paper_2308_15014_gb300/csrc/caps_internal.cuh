@@ -262,14 +262,36 @@ struct TcScanArgs {
   int m, h, d, kp, words_pad, metric;  // kp: keys kept per probe (16 or 32)
   int rerank;           // candidates re-scored exactly per query
   int tile_n;           // rows per tensor-core tile: 128 or 256 (0: 256)
+  int pen;              // 1: filter folded into the MMA (the index has the code chunk)
+  int pen_bits;         // packed attribute bits in the code chunk
+  uint32_t pen_mask[4]; // which bits of each packed word are encoded
+  float xn_max;         // largest squared row norm
   uint64_t* part;       // [nq*m*kp]
   int32_t* err;
 };
 int tc_kp(int k);
 int tc_rerank_depth(int k, int factor);
 bool tc_scan_supported(int d, int k, int kp, int words_pad);
-int tc_prepare_index(const float* Xp, int64_t N, int d, const int32_t* perm, void* Xb, float* xn,
-                     int32_t* iperm, void* tmap_out, cudaStream_t s);
+bool tc_pen_supported(int d, int kp, int words_pad);
+// What the bf16 form of an index is made from, and where it goes.
+struct TcIndexPrep {
+  const float* Xp;         // [N*d] rows in layout order
+  int64_t N;
+  int d;
+  const int32_t* perm;     // layout row -> original id
+  const uint32_t* Ap;      // [N*words_pad] packed attributes
+  int words_pad;
+  const int32_t* offsets;  // [B*nb+1] block offsets
+  int B, nb;
+  int pen, pen_bits;       // code chunk for the penalty form
+  uint32_t pen_mask[4];
+  void* Xb;                // out: [N*cols] bf16 rows, cols = d, or (ceil(d/64)+1)*64 with pen
+  float* xn;               // out: [N] squared norms
+  int32_t* iperm;          // out: original id -> layout row
+  float* xn_max;           // out (host): largest squared norm
+  void* tmap;              // out: CUtensorMap over Xb
+};
+int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s);
 int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, cudaStream_t s);
 // item_cap: most probes per work item (1..128; 0: 128)
 int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, int item_cap,
@@ -311,10 +333,19 @@ struct caps_index {
   float* xn = nullptr;
   int32_t* iperm = nullptr;
   alignas(128) unsigned char tmap[128] = {};
-  // launch shapes the autotuner chose, per (k, m): (rows per tile, probes per
-  // item); later caps_search_batch calls with that (k, m) use them
+  // penalty form of the bf16 scan: each bf16 row carries a 64-column one-hot
+  // code of its packed attribute bits and its block
+  int pen = 0;
+  int pen_bits = 0;
+  uint32_t pen_mask[4] = {};
+  float xn_max = 0.f;
+  // launch shapes the autotuner chose, per (k, m): rows per tile, probes per
+  // item, penalty form; later caps_search_batch calls with that (k, m) use them
+  struct Shape {
+    int tile_n, item_cap, pen;
+  };
   mutable std::mutex tune_mu;
-  mutable std::map<std::pair<int, int>, std::pair<int, int>> tuned;
+  mutable std::map<std::pair<int, int>, Shape> tuned;
   int64_t bytes = 0;
   std::vector<void*> allocs;
 

@@ -1,561 +1,17 @@
-// BF16 tensor-core form of the CAPS scan (Alg. 2 "attribute match" +
-// "top-k vector match"), with an exact fp32 re-rank of 4k candidates.
-//
-// One CTA takes one partition and up to 128 of its probes.  The probes'
-// query vectors (bf16) form the MMA A operand (M = 128, K-major, 128-byte
-// swizzle) in shared memory; the partition's rows in the blocks any probe
-// selected arrive as 256-row bf16 tiles by 2-D TMA (K-major, 128-byte
-// swizzle, double-buffered), together with their attribute words, original
-// ids and fp32 squared norms (1-D bulk copies).  tcgen05.mma (kind::f16,
-// bf16 x bf16 -> fp32, M = 128, N = 256, K = 16 per instruction) writes the
-// 128 x 256 dot products into tensor memory; two 256-column accumulators let
-// the MMA of the next tile run while the epilogue reads this one.  In the
-// epilogue two threads own probe p (TMEM lane p), one per half of the tile's
-// 256 rows: for every row the thread checks the block selection and the
-// attribute filter, forms the approximate score (L2: |x|^2 + |q|^2 - 2 q.x in
-// fp32; IP: -q.x) and, if it beats the thread's current threshold, appends
-// the key to a small queue in shared memory; when any lane's queue fills,
-// the warp merges every queue into the lanes' sorted KP-key register lists
-// with a fixed compare-exchange network (no divergent insertion).  Each
-// partition so contributes its KP best keys per probe (KP >= k); per query
-// the best rerank_factor * k of the m lists are re-scored exactly (fp32,
-// coordinates in order, one fma each) before the final top-k.
-#include <cuda.h>
-#include <cuda_bf16.h>
-#include <cudaTypedefs.h>
-
+// Host side of the BF16 tensor-core form of the CAPS scan: bf16 copies of
+// the queries and rows, grouping of the probes into work items, the
+// persistent scan launch (explicit-filter instantiations here, the penalty
+// form in scan_tc_pen.cu), and the per-query merge with an exact fp32
+// re-rank of the best rerank_factor * k candidates (coordinates in order,
+// one fma each) before the final top-k.
 #include <algorithm>
 #include <climits>
+#include <cstring>
 
-#include "caps_internal.cuh"
+#include "scan_tc_kernel.cuh"
 
 namespace caps {
 namespace {
-
-constexpr int TC_M = 128;     // probes per work item (MMA M, TMEM lanes)
-constexpr int TC_C = 512;     // epilogue threads: four per probe (one per quarter tile)
-constexpr int TC_T = TC_C + 32;  // + one producer warp (copies and MMAs)
-constexpr int TC_PARTS = TC_C / TC_M;
-constexpr int TC_Q = 12;      // per-thread candidate queue (merged when > 4 wait)
-constexpr int TC_BOX = 128;   // rows per 2-D copy (the tensor map's box)
-constexpr int TC_COLS = 512;  // tensor-memory columns: TC_COLS / N accumulator stages
-constexpr int TC_PRODUCER = TC_C / 32;  // warp index of the producer
-constexpr uint64_t kTcWaitNs = 1000000000ull;
-
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
-}
-// Bounded wait for the completion of the barrier phase with the given parity.
-// Gives up after kTcWaitNs, or early once *fail is set (fail may be null).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* fail) {
-  const uint32_t a = su32(bar);
-  const uint64_t t0 = gtimer();
-  while (true) {
-    for (int i = 0; i < 64; i++) {
-      uint32_t done;
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-          " selp.u32 %0, 1, 0, p;\n}\n"
-          : "=r"(done)
-          : "r"(a), "r"(parity)
-          : "memory");
-      if (done) return true;
-    }
-    if (fail != nullptr && *fail) return false;
-    if (gtimer() - t0 > kTcWaitNs) return false;
-  }
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
-}
-__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          su32(dst)),
-      "l"(src), "r"(bytes), "r"(su32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void consumers_sync() {  // named barrier 1: the 16 epilogue warps
-  asm volatile("bar.sync 1, %0;" ::"n"(TC_C) : "memory");
-}
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // 128-byte swizzle
-  return d;
-}
-// Instruction descriptor: bf16 x bf16 -> f32, A and B K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t id,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-      "l"(ad), "l"(bd), "r"(id), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   su32(bar))
-               : "memory");
-}
-// Eight accumulator columns of this warp's 32 lanes; the load is only issued
-// here, tmem_wait() completes it (no use of v before that).
-__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&v)[8]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7])
-      : "r"(taddr));
-}
-// Completes the outstanding loads; v is tied in so that no use of it moves above.
-__device__ __forceinline__ void tmem_wait(uint32_t (&v)[8]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
-                 "+r"(v[6]), "+r"(v[7])
-               :
-               : "memory");
-}
-
-struct TcItem {
-  int32_t b, e0, ne, pad;
-};
-
-struct TcArgs {
-  const int32_t* ent;
-  const TcItem* items;
-  const int32_t* n_items;
-  int32_t* next_item;  // work counter, zeroed by the grouping step
-  const uint64_t* sel;
-  const uint32_t* qmask;
-  const uint32_t* qval;
-  const __nv_bfloat16* Qh;  // [nq*d]
-  const float* qn;          // [nq]
-  const uint32_t* Ap;
-  const int32_t* perm;
-  const float* xn;
-  const int32_t* offsets;
-  int m, h, d, kc, kp;
-  uint64_t* part;  // [nq*m*kp]
-  int32_t* err;
-};
-
-__host__ __device__ constexpr int tc_stages(int N) { return TC_COLS / N; }
-__host__ __device__ constexpr size_t tc_a_bytes(int kc) { return (size_t)kc * TC_M * 128; }
-__host__ __device__ constexpr size_t tc_b_bytes(int kc, int N) { return (size_t)kc * N * 128; }
-// per stage: attribute words, ids and norms of N + 8 rows (4-row aligned
-// superset of the tile), block id of each row
-__host__ __device__ constexpr size_t tc_aux_bytes(int WP, int N) {
-  return (((size_t)(N + 8) * WP * 4 + (size_t)(N + 8) * 8 + (size_t)(N + 8)) + 15) & ~(size_t)15;
-}
-__host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N) {
-  // 1024-byte alignment slack + A + B stages + candidate queues + aux stages
-  // (the final merge of the quarter lists reuses the B stages)
-  return 1024 + tc_a_bytes(kc) + (size_t)tc_stages(N) * tc_b_bytes(kc, N) +
-         (size_t)TC_Q * TC_C * 8 + (size_t)tc_stages(N) * tc_aux_bytes(WP, N);
-}
-
-template <int KP>
-__device__ __forceinline__ void net_insert(uint64_t (&L)[KP], uint64_t x) {
-  // sorted ascending; x moves down until it finds its place, the largest
-  // key falls off the end (an empty key changes nothing)
-#pragma unroll
-  for (int i = 0; i < KP; i++) {
-    const uint64_t lo = L[i] < x ? L[i] : x;
-    x = L[i] < x ? x : L[i];
-    L[i] = lo;
-  }
-}
-
-// One persistent CTA per SM walks the work items (partition, <= 128 probes)
-// in the order a global counter hands them out, so partitions of very
-// different sizes balance across the SMs within one launch.  Warp 16 is the
-// producer: for each tile of an item it waits until the epilogue has released
-// the stage, writes the rows' block ids, starts the copies and, once they
-// have landed, issues the MMAs of that tile into the stage's accumulator.
-// Warps 0-15 are the epilogue; they meet the producer only through the
-// stage barriers (full: copies landed; mma: accumulator written; empty: all
-// 16 warps done with the stage), and each other only at item boundaries.
-template <int METRIC, int WP, int KP, int N>
-__global__ void __launch_bounds__(TC_T, 1)
-k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
-  constexpr int S = tc_stages(N);
-  constexpr int RA = N + 8;
-  constexpr int CPT = N / TC_PARTS;  // accumulator columns per epilogue thread and tile
-  extern __shared__ unsigned char smem_raw[];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int kc = a.kc, nb = a.h + 1;
-  const int n_items = *a.n_items;
-
-  unsigned char* base =
-      reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = base;
-  unsigned char* sB0 = sA + tc_a_bytes(kc);
-  const size_t bstride = tc_b_bytes(kc, N);
-  uint64_t* queue = reinterpret_cast<uint64_t*>(sB0 + S * bstride);
-  unsigned char* aux0 = reinterpret_cast<unsigned char*>(queue + (size_t)TC_Q * TC_C);
-  constexpr size_t astride = tc_aux_bytes(WP, N);
-  auto s_attr = [&](int b) { return reinterpret_cast<uint32_t*>(aux0 + b * astride); };
-  auto s_perm = [&](int b) {
-    return reinterpret_cast<int32_t*>(aux0 + b * astride + (size_t)RA * WP * 4);
-  };
-  auto s_xn = [&](int b) {
-    return reinterpret_cast<float*>(aux0 + b * astride + (size_t)RA * WP * 4 + RA * 4);
-  };
-  auto s_blk = [&](int b) { return aux0 + b * astride + (size_t)RA * WP * 4 + RA * 8; };
-
-  __shared__ uint64_t full_bar[S], mma_bar[S], empty_bar[S];
-  __shared__ uint32_t tmem_base;
-  __shared__ volatile int s_fail;
-  __shared__ int s_item[2];
-  __shared__ int s_ntiles;
-  __shared__ int s_tlo[S], s_tn[S];
-  __shared__ uint64_t p_sel[TC_M], p_thr[TC_M];
-  __shared__ uint32_t p_qm[TC_M * WP], p_qv[TC_M * WP];
-  __shared__ float p_qn[TC_M];
-  __shared__ int32_t p_e[TC_M];
-  __shared__ int run_lo[64], run_hi[64], run_j0[64];
-  __shared__ int n_runs;
-  __shared__ int32_t boff[65];
-
-  if (tid == 0) {
-    for (int i = 0; i < S; i++) {
-      mbar_init(&full_bar[i], 1);
-      mbar_init(&mma_bar[i], 1);
-      mbar_init(&empty_bar[i], TC_C / 32);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_fail = 0;
-    s_item[0] = atomicAdd(a.next_item, 1);
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     su32(&tmem_base)),
-                 "n"(TC_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tbase = tmem_base;
-  const uint32_t idesc = idesc_bf16(TC_M, N);
-
-  int g0 = 0;           // tiles this CTA finished before the current item
-  int slot = 0;
-  int tma_hi = -1, mma_hi = -1;  // producer: last tile whose copies / MMAs were issued
-  while (true) {
-    const int item_id = s_item[slot];
-    if (item_id >= n_items || s_fail) break;
-    const TcItem it = a.items[item_id];
-
-    // ---- item setup ------------------------------------------------------
-    if (warp == TC_PRODUCER) {
-      if (lane == 0) s_item[slot ^ 1] = atomicAdd(a.next_item, 1);
-      const int32_t* off = a.offsets + (int64_t)it.b * nb;
-      for (int j = lane; j <= nb; j += 32) boff[j] = off[j];
-      uint64_t U = 0ull;
-      for (int t = lane; t < it.ne; t += 32) U |= a.sel[a.ent[it.e0 + t]];
-      const uint32_t ulo = __reduce_or_sync(0xffffffffu, (uint32_t)U);
-      const uint32_t uhi = __reduce_or_sync(0xffffffffu, (uint32_t)(U >> 32));
-      U = ((uint64_t)uhi << 32) | ulo;
-      __syncwarp();
-      if (lane == 0) {
-        int nr = 0, nt = 0, j = 0;
-        while (j < nb) {
-          if (!((U >> j) & 1ull)) {
-            j++;
-            continue;
-          }
-          int j2 = j;
-          while (j2 + 1 < nb && ((U >> (j2 + 1)) & 1ull)) j2++;
-          if (boff[j2 + 1] > boff[j]) {
-            run_lo[nr] = boff[j];
-            run_hi[nr] = boff[j2 + 1];
-            run_j0[nr] = j;
-            nt += (boff[j2 + 1] - boff[j] + N - 1) / N;
-            nr++;
-          }
-          j = j2 + 1;
-        }
-        n_runs = nr;
-        s_ntiles = nt;
-      }
-    } else if (tid < TC_M) {
-      // probe data and the A operand: row t = probe t's query, bf16,
-      // zero-padded to kc*64 coordinates, 16-byte unit u of chunk c stored at
-      // unit u ^ (t%8)
-      const int t = tid;
-      int q = -1;
-      p_thr[t] = kEmptyKey;
-      if (t < it.ne) {
-        const int e = a.ent[it.e0 + t];
-        q = e / a.m;
-        p_e[t] = e;
-        p_sel[t] = a.sel[e];
-        p_qn[t] = a.qn[q];
-#pragma unroll
-        for (int w = 0; w < WP; w++) {
-          p_qm[t * WP + w] = a.qmask[(int64_t)q * WP + w];
-          p_qv[t * WP + w] = a.qval[(int64_t)q * WP + w];
-        }
-      } else {
-        p_sel[t] = 0ull;
-#pragma unroll
-        for (int w = 0; w < WP; w++) p_qm[t * WP + w] = p_qv[t * WP + w] = 0u;
-        p_qn[t] = 0.f;
-      }
-      const int units = kc * 8, dunits = a.d / 8;
-      for (int u = 0; u < units; u++) {
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (q >= 0 && u < dunits)
-          v = *reinterpret_cast<const uint4*>(a.Qh + (int64_t)q * a.d + 8 * u);
-        const int c = u >> 3, uu = u & 7;
-        *reinterpret_cast<uint4*>(sA + (size_t)c * TC_M * 128 + t * 128 + ((uu ^ (t & 7)) << 4)) = v;
-      }
-    }
-    fence_async_smem();  // the A operand (generic stores) before the MMAs read it
-    __syncthreads();
-    const int n_tiles = s_ntiles;
-
-    if (warp == TC_PRODUCER) {
-      // ---- producer ------------------------------------------------------
-      int rr = 0, rlo = n_runs > 0 ? run_lo[0] : 0;
-      for (int t = 0; t < n_tiles; t++) {
-        const int g = g0 + t, b = g % S, u = g / S;
-        while (rlo >= run_hi[rr]) {
-          rr++;
-          rlo = run_lo[rr];
-        }
-        const int lo = rlo, n = min(N, run_hi[rr] - rlo), j0 = run_j0[rr];
-        rlo += n;
-        bool ok = true;
-        if (u > 0) ok = mbar_wait(&empty_bar[b], (uint32_t)((u - 1) & 1), &s_fail);
-        if (!__all_sync(0xffffffffu, ok)) {
-          if (lane == 0) s_fail = 1;
-          break;
-        }
-        uint8_t* blk = s_blk(b);
-        for (int r = lane; r < n; r += 32) {
-          int j = j0;
-          while (j + 1 < nb && boff[j + 1] <= lo + r) j++;
-          blk[r] = (uint8_t)j;
-        }
-        if (lane == 0) {
-          s_tlo[b] = lo;
-          s_tn[b] = n;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          const int alo = lo & ~3;
-          const int arows = ((lo + n + 3) & ~3) - alo;
-          const uint32_t ab = (uint32_t)(arows * WP * 4), pb = (uint32_t)(arows * 4);
-          unsigned char* sB = sB0 + b * bstride;
-          expect_tx(&full_bar[b], (uint32_t)(kc * N * 128) + ab + 2 * pb);
-          for (int c = 0; c < kc; c++)
-#pragma unroll
-            for (int hb = 0; hb < N / TC_BOX; hb++)
-              tma_2d(sB + (size_t)c * N * 128 + (size_t)hb * TC_BOX * 128, &tmX, 64 * c,
-                     lo + hb * TC_BOX, &full_bar[b]);
-          bulk_copy(s_attr(b), a.Ap + (int64_t)alo * WP, ab, &full_bar[b]);
-          bulk_copy(s_perm(b), a.perm + alo, pb, &full_bar[b]);
-          bulk_copy(s_xn(b), a.xn + alo, pb, &full_bar[b]);
-          tma_hi = g;
-          ok = mbar_wait(&full_bar[b], (uint32_t)(u & 1), &s_fail);
-          if (ok) {
-            tc_fence_after();
-            const uint32_t a0 = su32(sA), b0 = su32(sB);
-            for (int ks = 0; ks < kc * 4; ks++) {
-              const int c = ks >> 2, kin = ks & 3;
-              const uint64_t ad = sdesc(a0 + (uint32_t)(c * TC_M * 128 + kin * 32));
-              const uint64_t bd = sdesc(b0 + (uint32_t)(c * N * 128 + kin * 32));
-              mma_bf16(tbase + (uint32_t)(b * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
-            }
-            mma_commit(&mma_bar[b]);
-            mma_hi = g;
-          }
-        }
-        if (!__shfl_sync(0xffffffffu, ok, 0)) {
-          if (lane == 0) s_fail = 1;
-          break;
-        }
-      }
-    } else {
-      // ---- epilogue ------------------------------------------------------
-      const int probe = tid & (TC_M - 1), part = tid / TC_M;
-      const bool active = probe < it.ne;
-      const uint64_t my_sel = p_sel[probe];
-      uint32_t my_qm[WP], my_qv[WP];
-#pragma unroll
-      for (int w = 0; w < WP; w++) {
-        my_qm[w] = p_qm[probe * WP + w];
-        my_qv[w] = p_qv[probe * WP + w];
-      }
-      const float my_qn = p_qn[probe];
-      uint64_t L[KP];
-#pragma unroll
-      for (int i = 0; i < KP; i++) L[i] = kEmptyKey;
-      uint64_t thr = kEmptyKey;
-      int qcnt = 0;
-      auto flush = [&]() {  // warp-uniform call: as many rounds as the fullest queue
-        const int mx = __reduce_max_sync(0xffffffffu, (unsigned)qcnt);
-#pragma unroll 1
-        for (int i = 0; i < mx; i++) {
-          const uint64_t x = i < qcnt ? queue[(size_t)i * TC_C + tid] : kEmptyKey;
-          net_insert<KP>(L, x);
-        }
-        qcnt = 0;
-        thr = L[KP - 1];
-        // the four threads of a probe share the smallest of their KP-th keys:
-        // a key above it has KP better keys in one quarter list already
-        if (thr != kEmptyKey) atomicMin(reinterpret_cast<unsigned long long*>(&p_thr[probe]), thr);
-      };
-      const bool warp_live = __any_sync(0xffffffffu, active);
-      const int cbeg = part * CPT;
-      for (int t = 0; t < n_tiles; t++) {
-        const int g = g0 + t, b = g % S, u = g / S;
-        const bool ok = mbar_wait(&full_bar[b], (uint32_t)(u & 1), &s_fail) &&
-                        mbar_wait(&mma_bar[b], (uint32_t)(u & 1), &s_fail);
-        if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform: the loads below are collective
-          s_fail = 1;
-          break;
-        }
-        tc_fence_after();
-        const int lo = s_tlo[b], n = s_tn[b];
-        const int alo = lo & ~3;
-        const uint32_t* attr = s_attr(b) + (lo - alo) * WP;
-        const int32_t* prm = s_perm(b) + (lo - alo);
-        const float* xnr = s_xn(b) + (lo - alo);
-        const uint8_t* blk = s_blk(b);
-        const uint32_t tacc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * N + cbeg);
-        const int ncol = warp_live ? min(CPT, n - cbeg) : 0;  // warp-uniform
-        const int ngr = ncol > 0 ? (ncol + 7) >> 3 : 0;
-#pragma unroll 1
-        for (int gi = 0; gi < ngr; gi++) {
-          uint32_t cur[8];
-          tmem_ld8_issue(tacc + (uint32_t)(8 * gi), cur);
-          tmem_wait(cur);
-          const int c0 = cbeg + 8 * gi;
-          {
-            const uint64_t st = p_thr[probe];
-            if (st < thr) thr = st;
-          }
-          // the 8 rows' block ids and attribute words in few wide loads
-          // (the same addresses for every lane: broadcast)
-          const uint2 bw = *reinterpret_cast<const uint2*>(blk + c0);
-          const uint32_t bb[2] = {bw.x, bw.y};
-          uint32_t aw[8 * WP];
-          if (WP == 1 && ((lo - alo + c0) & 3) == 0) {
-            const uint4 a0 = *reinterpret_cast<const uint4*>(attr + c0);
-            const uint4 a1 = *reinterpret_cast<const uint4*>(attr + c0 + 4);
-            aw[0] = a0.x; aw[1] = a0.y; aw[2] = a0.z; aw[3] = a0.w;
-            aw[4] = a1.x; aw[5] = a1.y; aw[6] = a1.z; aw[7] = a1.w;
-          } else {
-#pragma unroll
-            for (int x = 0; x < 8 * WP; x++) aw[x] = attr[c0 * WP + x];
-          }
-          const int lim = n - c0;  // rows of this group inside the tile
-#pragma unroll
-          for (int j = 0; j < 8; j++) {
-            const int bj = (bb[j >> 2] >> (8 * (j & 3))) & 0xff;
-            bool pass = j < lim && ((my_sel >> bj) & 1ull);
-#pragma unroll
-            for (int w = 0; w < WP; w++) pass = pass && ((aw[j * WP + w] & my_qm[w]) == my_qv[w]);
-            if (pass) {
-              const int r = c0 + j;
-              const float dot = __uint_as_float(cur[j]);
-              const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r] + my_qn) : -dot;
-              const uint64_t key = make_key(sc, (uint32_t)prm[r]);
-              if (key < thr) {
-                queue[(size_t)qcnt * TC_C + tid] = key;
-                qcnt++;
-              }
-            }
-          }
-          // at most 8 more keys per lane before the next check: merge once
-          // any queue holds more than TC_Q - 8
-          if (__any_sync(0xffffffffu, qcnt > TC_Q - 8)) flush();
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty_bar[b]);
-      }
-      flush();
-      // merge the quarter lists of each probe (the B stages are free: every
-      // MMA of the item has completed)
-      uint64_t* parts = reinterpret_cast<uint64_t*>(sB0);
-      const bool fine = s_fail == 0;
-      if (fine && part > 0) {
-#pragma unroll
-        for (int i = 0; i < KP; i++) parts[((size_t)(part - 1) * KP + i) * TC_M + probe] = L[i];
-      }
-      consumers_sync();
-      if (fine && part == 0 && active) {
-        for (int q = 0; q < TC_PARTS - 1; q++)
-#pragma unroll
-          for (int i = 0; i < KP; i++) net_insert<KP>(L, parts[((size_t)q * KP + i) * TC_M + probe]);
-        uint64_t* dst = a.part + (int64_t)p_e[probe] * KP;
-#pragma unroll
-        for (int i = 0; i < KP; i++) dst[i] = L[i];
-      }
-    }
-    g0 += n_tiles;
-    fence_async_smem();  // generic stores into the B stages before later copies land there
-    __syncthreads();
-    slot ^= 1;
-  }
-
-  if (s_fail) {
-    // a copy or an MMA did not complete in time: flag it, let what is in
-    // flight land (bounded waits), release tensor memory and leave
-    if (warp == TC_PRODUCER && lane == 0) {
-      atomicExch(a.err, 1);
-      for (int g = max(0, tma_hi - S + 1); g <= tma_hi; g++)
-        mbar_wait(&full_bar[g % S], (uint32_t)((g / S) & 1), nullptr);
-      for (int g = max(0, mma_hi - S + 1); g <= mma_hi; g++)
-        mbar_wait(&mma_bar[g % S], (uint32_t)((g / S) & 1), nullptr);
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(TC_COLS));
-}
 
 // ---- bf16 query copy and fp32 squared norms -------------------------------
 __global__ void k_query_bf16(const float* __restrict__ Q, int64_t nq, int d,
@@ -723,31 +179,55 @@ __global__ void k_tc_items_fill(const int32_t* __restrict__ bin_off,
 }
 
 // ---- build-side helpers ----------------------------------------------------
-__global__ void k_rows_bf16_norms(const float* __restrict__ Xp, int64_t N, int d,
-                                  __nv_bfloat16* __restrict__ Xb, float* __restrict__ xn) {
+// bf16 copy of each row in `cols` columns (vector, zero padding, and in the
+// penalty form the 64-column one-hot code of the row's packed attribute bits
+// and of its block), its fp32 squared norm (coordinates in order, one fma
+// each) and the largest squared norm
+__global__ void k_rows_bf16(const float* __restrict__ Xp, int64_t N, int d, int cols, int kcd,
+                            const uint32_t* __restrict__ Ap, int WP, int pen, int pen_bits,
+                            uint4 pen_mask, const int32_t* __restrict__ offsets, int n_blocks,
+                            int nb, __nv_bfloat16* __restrict__ Xb, float* __restrict__ xn,
+                            unsigned int* __restrict__ xn_max_bits) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
+  __nv_bfloat16* row = Xb + r * cols;
   float acc = 0.f;
   for (int j = 0; j < d; j++) {
     const float x = Xp[r * d + j];
     acc = fmaf(x, x, acc);
-    Xb[r * d + j] = __float2bfloat16_rn(x);
+    row[j] = __float2bfloat16_rn(x);
   }
+  for (int j = d; j < cols; j++) row[j] = __float2bfloat16_rn(0.f);
   xn[r] = acc;
+  if (!(acc != acc)) atomicMax(xn_max_bits, __float_as_uint(acc));  // acc >= 0: bits order as floats
+  if (!pen) return;
+  __nv_bfloat16* code = row + (size_t)kcd * 64;
+  const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
+  const uint32_t um[4] = {pen_mask.x, pen_mask.y, pen_mask.z, pen_mask.w};
+  int gb = 0;
+  for (int w = 0; w < WP; w++) {
+    uint32_t m = um[w];
+    const uint32_t a = Ap[r * WP + w];
+    while (m) {
+      const int i = __ffs(m) - 1;
+      m &= m - 1;
+      code[2 * gb + ((a >> i) & 1u)] = one;
+      gb++;
+    }
+  }
+  // block of row r: the last offset <= r (offsets[n_blocks] = N)
+  int lo = 0, hi = n_blocks;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (offsets[mid] <= r) lo = mid;
+    else hi = mid;
+  }
+  code[2 * pen_bits + lo % nb] = one;
 }
 __global__ void k_inverse_perm(const int32_t* __restrict__ perm, int64_t N,
                                int32_t* __restrict__ iperm) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < N) iperm[perm[r]] = (int32_t)r;
-}
-
-template <int METRIC, int WP, int KP, int N>
-int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem, cudaStream_t s) {
-  auto kern = k_scan_tc<METRIC, WP, KP, N>;
-  CAPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<(unsigned)grid, TC_T, smem, s>>>(map, a);
-  CAPS_LAUNCH("k_scan_tc");
-  return CAPS_OK;
 }
 
 int sm_count() {
@@ -781,18 +261,40 @@ bool tc_scan_supported(int d, int k, int kp, int words_pad) {
     return false;
   // leave room for ~7 KB of static shared memory under the 227 KB limit
   const int kc = (d + 63) / 64;
-  return std::max(tc_smem_bytes(kc, words_pad, 256), tc_smem_bytes(kc, words_pad, 128)) <=
-         220 * 1024;
+  return std::max(tc_smem_bytes(kc, words_pad, 256, false),
+                  tc_smem_bytes(kc, words_pad, 128, false)) <= 220 * 1024;
 }
 
-int tc_prepare_index(const float* Xp, int64_t N, int d, const int32_t* perm, void* Xb, float* xn,
-                     int32_t* iperm, void* tmap_out, cudaStream_t s) {
-  k_rows_bf16_norms<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
-      Xp, N, d, static_cast<__nv_bfloat16*>(Xb), xn);
-  CAPS_LAUNCH("k_rows_bf16_norms");
-  k_inverse_perm<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(perm, N, iperm);
+bool tc_pen_supported(int d, int kp, int words_pad) {
+  if (d % 8 != 0 || d < 64 || d > 128 || (kp != 12 && kp != 16)) return false;
+  return tc_smem_bytes((d + 63) / 64 + 1, words_pad, 128, true) <= 220 * 1024;
+}
+
+int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
+  const int64_t N = p.N;
+  const int kcd = (p.d + 63) / 64;
+  const int cols = p.pen ? (kcd + 1) * 64 : p.d;
+  unsigned int* xmax = nullptr;
+  CAPS_CUDA(cudaMallocAsync(&xmax, sizeof(unsigned int), s));
+  CAPS_CUDA(cudaMemsetAsync(xmax, 0, sizeof(unsigned int), s));
+  const uint4 pm = make_uint4(p.pen_mask[0], p.pen_mask[1], p.pen_mask[2], p.pen_mask[3]);
+  k_rows_bf16<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
+      p.Xp, N, p.d, cols, kcd, p.Ap, p.words_pad, p.pen, p.pen_bits, pm, p.offsets,
+      p.B * p.nb, p.nb, static_cast<__nv_bfloat16*>(p.Xb), p.xn, xmax);
+  cudaError_t le = cudaGetLastError();
+  unsigned int xmax_h = 0;
+  if (le == cudaSuccess) le = cudaMemcpyAsync(&xmax_h, xmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+  if (le == cudaSuccess) le = cudaStreamSynchronize(s);
+  cudaFreeAsync(xmax, s);
+  if (le != cudaSuccess) return cuda_fail(le, "k_rows_bf16");
+  ++g_kernel_launches;
+  uint32_t bits = xmax_h;
+  float xm;
+  std::memcpy(&xm, &bits, sizeof(float));
+  *p.xn_max = xm;
+  k_inverse_perm<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(p.perm, N, p.iperm);
   CAPS_LAUNCH("k_inverse_perm");
-  // 2-D tensor map over the bf16 rows: inner dimension d, outer N rows;
+  // 2-D tensor map over the bf16 rows: inner dimension cols, outer N rows;
   // boxes of 64 coordinates (128 bytes) x 128 rows, 128-byte swizzle
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult qres;
@@ -801,11 +303,11 @@ int tc_prepare_index(const float* Xp, int64_t N, int d, const int32_t* perm, voi
   if (!fn || qres != cudaDriverEntryPointSuccess)
     return fail(CAPS_ECUDA, "cuTensorMapEncodeTiled is not available");
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  cuuint64_t gdim[2] = {(cuuint64_t)d, (cuuint64_t)N};
-  cuuint64_t gstride[1] = {(cuuint64_t)d * 2};
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)N};
+  cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
   cuuint32_t box[2] = {64, (cuuint32_t)TC_BOX};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode(static_cast<CUtensorMap*>(tmap_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Xb,
+  CUresult r = encode(static_cast<CUtensorMap*>(p.tmap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p.Xb,
                       gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                       CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -884,22 +386,32 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   a.m = t.m;
   a.h = t.h;
   a.d = t.d;
-  a.kc = (t.d + 63) / 64;
+  a.kcd = (t.d + 63) / 64;
+  a.kc = a.kcd + (t.pen ? 1 : 0);
   a.kp = t.kp;
+  a.pen_bits = t.pen_bits;
+  for (int i = 0; i < 4; i++) a.pen_mask[i] = t.pen_mask[i];
+  a.xn_max = t.xn_max;
   a.part = t.part;
   a.err = t.err;
-  const int N = t.tile_n == 128 ? 128 : 256;
-  const size_t smem = tc_smem_bytes(a.kc, t.words_pad, N);
   const CUtensorMap& map = *static_cast<const CUtensorMap*>(t.tmap);
   // persistent: one CTA per SM (the shared memory admits no second), never
   // more CTAs than work items
   const int64_t g = std::max<int64_t>(1, std::min<int64_t>(w.max_items, sm_count()));
-#define CAPS_TC(WPV, KPV)                                                                   \
-  if (N == 128)                                                                             \
-    return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 128>(map, a, g, smem, s)      \
-                               : launch_tc<CAPS_IP, WPV, KPV, 128>(map, a, g, smem, s);     \
-  return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 256>(map, a, g, smem, s)        \
-                             : launch_tc<CAPS_IP, WPV, KPV, 256>(map, a, g, smem, s)
+  if (t.pen) {
+    if (!tc_pen_supported(t.d, t.kp, t.words_pad))
+      return fail(CAPS_EINVAL, "the penalty form does not fit this index or k");
+    return tc_launch_pen(map, a, t.metric, t.words_pad, t.kp, g,
+                         tc_smem_bytes(a.kc, t.words_pad, 128, true), s);
+  }
+  const int N = t.tile_n == 128 ? 128 : 256;
+  const size_t smem = tc_smem_bytes(a.kc, t.words_pad, N, false);
+#define CAPS_TC(WPV, KPV)                                                                      \
+  if (N == 128)                                                                                \
+    return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 128, false>(map, a, g, smem, s)  \
+                               : launch_tc<CAPS_IP, WPV, KPV, 128, false>(map, a, g, smem, s); \
+  return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 256, false>(map, a, g, smem, s)    \
+                             : launch_tc<CAPS_IP, WPV, KPV, 256, false>(map, a, g, smem, s)
   if (t.kp == 12) {
     switch (t.words_pad) {
       case 1: CAPS_TC(1, 12);

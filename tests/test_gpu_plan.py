@@ -6,7 +6,8 @@ batch (the graph replays the same kernels), and the byte-valued bf16 case
 must still equal the CPU oracle bit for bit.  The autotuner itself checks
 that all four launch shapes (256 or 128 rows per tile x 128 or 64 probes per
 work item) agree to the bit on the tuning batch, so a successful plan
-creation covers every shape.
+creation covers every shape, the penalty form (block selection and filter
+folded into the MMA) against the per-pair filter included.
 """
 import numpy as np
 import pytest
@@ -53,12 +54,14 @@ def test_plan_bf16_autotuned_equals_direct_and_oracle():
     plan = gi.plan(Q, Qb, k, m, autotune=True)
     inf = plan.info
     assert inf["nq"] == w.nq and inf["k"] == k and inf["m"] == m
-    assert len(inf["candidates"]) == 4
-    assert {(c["tile_n"], c["item_cap"]) for c in inf["candidates"]} == {
-        (256, 128), (128, 128), (256, 64), (128, 64)}
+    # filter per pair in the epilogue (256 or 128 rows per tile) or folded
+    # into the MMA (128 rows), x 128 or 64 probes per item; the vocabularies
+    # 5/7/11 (10 packed bits) and 8 blocks fit the one-hot code chunk
+    assert {(c["tile_n"], c["item_cap"], c["pen"]) for c in inf["candidates"]} == {
+        (256, 128, 0), (128, 128, 0), (256, 64, 0), (128, 64, 0), (128, 128, 1), (128, 64, 1)}
     assert all(c["ms"] > 0 for c in inf["candidates"])
-    assert (inf["tile_n"], inf["item_cap"]) in {(c["tile_n"], c["item_cap"])
-                                                for c in inf["candidates"]}
+    assert (inf["tile_n"], inf["item_cap"], inf["pen"]) in {
+        (c["tile_n"], c["item_cap"], c["pen"]) for c in inf["candidates"]}
     assert inf["graph_nodes"] > 5
     d_ids, d_dist = gi.search(Q, Qb, k, m)
     for _ in range(3):  # replays are repeatable
@@ -78,7 +81,7 @@ def test_plan_host_buffers_and_short_batch():
     w = wl(902, nq=400)
     gi = gpu_index(w, caps.BF16)
     plan = gi.plan(w.Q, w.Qb, 10, 5, autotune=False)
-    assert plan.info["candidates"] == [] and plan.info["tile_n"] == 256
+    assert plan.info["candidates"] == [] and plan.info["pen"] == 1 and plan.info["tile_n"] == 128
     ids, dist = plan.search(w.Q, w.Qb)  # numpy in, numpy out
     r_ids, r_dist = gi.search(w.Q, w.Qb, 10, 5)
     np.testing.assert_array_equal(ids, r_ids)
