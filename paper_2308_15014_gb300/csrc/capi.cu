@@ -797,12 +797,15 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
                 int32_t k, int32_t m, int64_t* out_ids, float* out_dist, cudaStream_t s,
                 const SearchOpts& o);
 
-bool uses_tc(const caps_index* ix, int k) {
+// which forms of the tensor-core scan serve this index and k
+bool tc_explicit_ok(const caps_index* ix, int k) {
   return ix->prec == CAPS_BF16 && tc_scan_supported(ix->d, k, tc_kp(k), ix->meta.words_pad);
 }
 bool uses_pen(const caps_index* ix, int k) {
-  return uses_tc(ix, k) && ix->pen && tc_pen_supported(ix->d, tc_kp(k), ix->meta.words_pad);
+  return ix->prec == CAPS_BF16 && k <= 32 && ix->pen &&
+         tc_pen_supported(ix->d, tc_kp(k), ix->meta.words_pad);
 }
+bool uses_tc(const caps_index* ix, int k) { return tc_explicit_ok(ix, k) || uses_pen(ix, k); }
 }  // namespace
 
 extern "C" int caps_search_batch(const caps_index* ix, const float* Q, int64_t nq,
@@ -845,8 +848,8 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
       pen = f->second.pen;
     }
   }
-  const bool pen_ok = tc && ix->pen && tc_pen_supported(ix->d, kp, ix->meta.words_pad);
-  const bool use_pen = pen_ok && pen != 0;
+  const bool pen_ok = tc && uses_pen(ix, k);
+  const bool use_pen = pen_ok && (pen != 0 || !tc_explicit_ok(ix, k));
   const int64_t qc = chunk_rows(ix, nq, m, kp);
   Batch bt;
   if (int rc = alloc_batch(ix, qc, m, scr, &bt)) return rc;
@@ -937,6 +940,10 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
       t.pen_bits = ix->pen_bits;
       for (int i = 0; i < 4; i++) t.pen_mask[i] = ix->pen_mask[i];
       t.xn_max = ix->xn_max;
+      uint64_t* qslot = nullptr;
+      if (int rc = cscr.get(&qslot, (size_t)n * 8)) return rc;
+      CAPS_CUDA(cudaMemsetAsync(qslot, 0xFF, sizeof(uint64_t) * (size_t)n * 8, s));
+      t.qslot = qslot;
       t.words_pad = ix->meta.words_pad;
       t.metric = ix->metric;
       t.part = part;
@@ -1083,9 +1090,15 @@ extern "C" int caps_plan_create(const caps_index* ix, const float* Q, int64_t nq
       // the scan's launch shapes: filter in the epilogue (rows per tile:
       // accumulator stages) or folded into the MMA (128 rows), x most probes
       // per work item
-      const int shapes[6][3] = {{256, 128, 0}, {128, 128, 0}, {256, 64, 0},
-                                {128, 64, 0},  {128, 128, 1}, {128, 64, 1}};
-      const int n_shapes = pen_ok ? 6 : 4;
+      const int all[6][3] = {{256, 128, 0}, {128, 128, 0}, {256, 64, 0},
+                             {128, 64, 0},  {128, 128, 1}, {128, 64, 1}};
+      int shapes[6][3];
+      int n_shapes = 0;
+      for (const auto& sh : all)
+        if (sh[2] ? pen_ok : tc_explicit_ok(ix, k)) {
+          for (int j = 0; j < 3; j++) shapes[n_shapes][j] = sh[j];
+          n_shapes++;
+        }
       float best_ms = 0.f;
       // every shape computes the same per-probe lists, so the results must
       // agree to the bit: the tuner checks that against the first shape

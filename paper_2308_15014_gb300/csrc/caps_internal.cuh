@@ -266,6 +266,7 @@ struct TcScanArgs {
   int pen_bits;         // packed attribute bits in the code chunk
   uint32_t pen_mask[4]; // which bits of each packed word are encoded
   float xn_max;         // largest squared row norm
+  uint64_t* qslot;      // [nq*8] bound slots per query, set to all ones before the scan
   uint64_t* part;       // [nq*m*kp]
   int32_t* err;
 };

@@ -259,15 +259,12 @@ int tc_rerank_depth(int k, int factor) {
 bool tc_scan_supported(int d, int k, int kp, int words_pad) {
   if (d % 8 != 0 || d < 64 || d > 128 || k > 32 || (kp != 12 && kp != 16 && kp != 32))
     return false;
-  // leave room for ~7 KB of static shared memory under the 227 KB limit
-  const int kc = (d + 63) / 64;
-  return std::max(tc_smem_bytes(kc, words_pad, 256, false),
-                  tc_smem_bytes(kc, words_pad, 128, false)) <= 220 * 1024;
+  return tc_fits((d + 63) / 64, words_pad, 128, false);
 }
 
 bool tc_pen_supported(int d, int kp, int words_pad) {
   if (d % 8 != 0 || d < 64 || d > 128 || (kp != 12 && kp != 16)) return false;
-  return tc_smem_bytes((d + 63) / 64 + 1, words_pad, 128, true) <= 220 * 1024;
+  return tc_fits((d + 63) / 64 + 1, words_pad, 128, true);
 }
 
 int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
@@ -392,6 +389,11 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   a.pen_bits = t.pen_bits;
   for (int i = 0; i < 4; i++) a.pen_mask[i] = t.pen_mask[i];
   a.xn_max = t.xn_max;
+  a.qslot = t.qslot;
+  {
+    const int depth = std::min(t.rerank, t.m * t.kp);  // keys the merge keeps per query
+    a.nslot = std::min(TC_SLOTS, std::max(1, (depth + t.kp - 1) / t.kp));
+  }
   a.part = t.part;
   a.err = t.err;
   const CUtensorMap& map = *static_cast<const CUtensorMap*>(t.tmap);
@@ -404,7 +406,10 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
     return tc_launch_pen(map, a, t.metric, t.words_pad, t.kp, g,
                          tc_smem_bytes(a.kc, t.words_pad, 128, true), s);
   }
-  const int N = t.tile_n == 128 ? 128 : 256;
+  if (!tc_fits(a.kc, t.words_pad, 128, false))
+    return fail(CAPS_EINVAL, "the per-pair filter form does not fit this index");
+  // 256-row tiles where they fit, else 128
+  const int N = t.tile_n != 128 && tc_fits(a.kc, t.words_pad, 256, false) ? 256 : 128;
   const size_t smem = tc_smem_bytes(a.kc, t.words_pad, N, false);
 #define CAPS_TC(WPV, KPV)                                                                      \
   if (N == 128)                                                                                \

@@ -69,6 +69,8 @@ struct TcArgs {
   int pen_bits;          // penalty form: packed attribute bits encoded (two columns each)
   uint32_t pen_mask[4];  // which bits of each packed word are encoded
   float xn_max;          // largest squared row norm
+  uint64_t* qslot;       // [nq*8] per-query bound slots, all ones at the start
+  int nslot;             // slots in use: ceil(rerank depth / kp)
   uint64_t* part;        // [nq*m*kp]
   int32_t* err;
 };
@@ -83,6 +85,7 @@ constexpr int TC_Q = 12;      // per-thread candidate queue (merged when > 4 wai
 constexpr int TC_BOX = 128;   // rows per 2-D copy (the tensor map's box)
 constexpr int TC_COLS = 512;  // tensor-memory columns: TC_COLS / N accumulator stages
 constexpr int TC_PRODUCER = TC_C / 32;  // warp index of the producer
+constexpr int TC_SLOTS = 8;   // per-query bound slots (stride)
 constexpr uint64_t kTcWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -149,6 +152,17 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void consumers_sync() {  // named barrier 1: the 16 epilogue warps
   asm volatile("bar.sync 1, %0;" ::"n"(TC_C) : "memory");
 }
+// named barrier 1 with an AND over the 16 epilogue warps' predicates
+__device__ __forceinline__ bool consumers_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(TC_C)
+      : "memory");
+  return r != 0;
+}
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -203,6 +217,14 @@ __host__ __device__ constexpr size_t tc_b_bytes(int kc, int N) { return (size_t)
 __host__ __device__ constexpr size_t tc_aux_bytes(int WP, int N) {
   return (((size_t)(N + 8) * WP * 4 + (size_t)(N + 8) * 8 + (size_t)(N + 8)) + 15) & ~(size_t)15;
 }
+// shared memory one CTA may hold (227 KB), and an upper bound of the
+// kernel's static part (barriers, per-probe arrays, the tile schedule)
+constexpr size_t kTcSmemLimit = 227 * 1024;
+__host__ __device__ constexpr size_t tc_static_bound(int WP) { return 7168 + 1024 * (size_t)WP; }
+__host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N, bool pen);
+__host__ __device__ constexpr bool tc_fits(int kc, int WP, int N, bool pen) {
+  return tc_smem_bytes(kc, WP, N, pen) + tc_static_bound(WP) <= kTcSmemLimit;
+}
 __host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N, bool pen) {
   // 1024-byte alignment slack + A + B stages + candidate queues + aux stages
   // (the final merge of the quarter lists reuses the B stages)
@@ -227,10 +249,21 @@ __device__ __forceinline__ void net_insert(uint64_t (&L)[KP], uint64_t x) {
 // different sizes balance across the SMs within one launch.  Warp 16 is the
 // producer: for each tile of an item it waits until the epilogue has released
 // the stage, writes the rows' block ids, starts the copies and, once they
-// have landed, issues the MMAs of that tile into the stage's accumulator.
-// Warps 0-15 are the epilogue; they meet the producer only through the
-// stage barriers (full: copies landed; mma: accumulator written; empty: all
-// 16 warps done with the stage), and each other only at item boundaries.
+// have landed, issues the MMAs of that tile into the stage's accumulator;
+// after the item's last tile it already takes and prepares the next item
+// (its rows' ranges and the probes' data) while the epilogue finishes the
+// current one.  Warps 0-15 are the epilogue; they meet the producer only
+// through mbarriers (full: copies landed; mma: accumulator written; empty:
+// all 16 warps done with the stage; taken: the probes' data read; meta: the
+// next item's data ready), and at item boundaries, where they have built the
+// next item's A operand.
+//
+// Bound across a query's partitions: the rerank keeps the best R keys of the
+// query's m lists.  Each finished list offers its KP-th key to one of the
+// query's ns = ceil(R / KP) slots (slot = partition mod ns, atomic min).  Once
+// every slot holds a key, the largest of them, T, has at least ns * KP >= R
+// keys of distinct lists at or below it, so a later partition of that query
+// drops every key above T: such a key cannot be among the R best.
 template <int METRIC, int WP, int KP, int N, bool PEN>
 __global__ void __launch_bounds__(TC_T, 1)
 k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
@@ -259,17 +292,20 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   };
   auto s_blk = [&](int b) { return aux0 + b * astride + (size_t)RA * WP * 4 + RA * 8; };
 
-  __shared__ uint64_t full_bar[S], mma_bar[S], empty_bar[S];
+  __shared__ uint64_t full_bar[S], mma_bar[S], empty_bar[S], taken_bar, meta_bar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_fail;
-  __shared__ int s_item[2];
-  __shared__ int s_ntiles;
-  __shared__ int s_tlo[S], s_tn[S];
-  __shared__ uint64_t p_sel[TC_M], p_thr[TC_M];
+  // the current and the next item (index: item parity)
+  __shared__ int s_ne[2], s_ntiles[2], s_bin[2];
+  __shared__ uint64_t p_thr[2][TC_M];
+  __shared__ int32_t p_e[2][TC_M];
+  // probe data of the item about to start (read once into registers)
+  __shared__ uint64_t p_sel[TC_M];
   __shared__ uint32_t p_qm[TC_M * WP], p_qv[TC_M * WP];
   __shared__ float p_qn[TC_M];
   __shared__ float p_cut[TC_M];  // penalty form: scores at or above are masked pairs
-  __shared__ int32_t p_e[TC_M];
+  // producer only: tile schedule of its item
+  __shared__ int s_tlo[S], s_tn[S];
   __shared__ int run_lo[64], run_hi[64], run_j0[64];
   __shared__ int n_runs;
   __shared__ int32_t boff[65];
@@ -280,9 +316,10 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       mbar_init(&mma_bar[i], 1);
       mbar_init(&empty_bar[i], TC_C / 32);
     }
+    mbar_init(&taken_bar, TC_C / 32);
+    mbar_init(&meta_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
-    s_item[0] = atomicAdd(a.next_item, 1);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -296,120 +333,165 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   const uint32_t tbase = tmem_base;
   const uint32_t idesc = idesc_bf16(TC_M, N);
 
-  int g0 = 0;           // tiles this CTA finished before the current item
-  int slot = 0;
-  int tma_hi = -1, mma_hi = -1;  // producer: last tile whose copies / MMAs were issued
-  while (true) {
-    const int item_id = s_item[slot];
-    if (item_id >= n_items || s_fail) break;
-    const TcItem it = a.items[item_id];
-
-    // ---- item setup ------------------------------------------------------
-    if (warp == TC_PRODUCER) {
-      if (lane == 0) s_item[slot ^ 1] = atomicAdd(a.next_item, 1);
-      const int32_t* off = a.offsets + (int64_t)it.b * nb;
-      for (int j = lane; j <= nb; j += 32) boff[j] = off[j];
-      uint64_t U = 0ull;
-      for (int t = lane; t < it.ne; t += 32) U |= a.sel[a.ent[it.e0 + t]];
-      const uint32_t ulo = __reduce_or_sync(0xffffffffu, (uint32_t)U);
-      const uint32_t uhi = __reduce_or_sync(0xffffffffu, (uint32_t)(U >> 32));
-      U = ((uint64_t)uhi << 32) | ulo;
-      __syncwarp();
-      if (lane == 0) {
-        int nr = 0, nt = 0, j = 0;
-        while (j < nb) {
-          if (!((U >> j) & 1ull)) {
-            j++;
-            continue;
-          }
-          int j2 = j;
-          while (j2 + 1 < nb && ((U >> (j2 + 1)) & 1ull)) j2++;
-          if (boff[j2 + 1] > boff[j]) {
-            run_lo[nr] = boff[j];
-            run_hi[nr] = boff[j2 + 1];
-            run_j0[nr] = j;
-            nt += (boff[j2 + 1] - boff[j] + N - 1) / N;
-            nr++;
-          }
-          j = j2 + 1;
-        }
-        n_runs = nr;
-        s_ntiles = nt;
-      }
-    } else if (tid < TC_M) {
-      // probe data and the A operand: row t = probe t's query, bf16,
-      // zero-padded to kc*64 coordinates, 16-byte unit u of chunk c stored at
-      // unit u ^ (t%8)
-      const int t = tid;
-      int q = -1;
-      p_thr[t] = kEmptyKey;
-      if (t < it.ne) {
-        const int e = a.ent[it.e0 + t];
-        q = e / a.m;
-        p_e[t] = e;
-        p_sel[t] = a.sel[e];
-        p_qn[t] = a.qn[q];
+  // ---- producer: take the next item and prepare everything but A ----------
+  // (fills s_ne/s_ntiles/s_bin/p_e/p_thr[par], the probe data, the runs)
+  TcItem pit;  // producer: the item it prepared last
+  auto prep_meta = [&](int par) -> bool {
+    int id = 0;
+    if (lane == 0) id = atomicAdd(a.next_item, 1);
+    id = __shfl_sync(0xffffffffu, id, 0);
+    if (id >= n_items) {
+      if (lane == 0) s_ne[par] = -1;
+      return false;
+    }
+    pit = a.items[id];
+    const int32_t* off = a.offsets + (int64_t)pit.b * nb;
+    for (int j = lane; j <= nb; j += 32) boff[j] = off[j];
+    uint64_t U = 0ull;
+#pragma unroll
+    for (int i = 0; i < TC_M / 32; i++) {
+      const int t = lane + 32 * i;
+      uint64_t sel = 0ull, T = kEmptyKey;
+      float qn = 0.f;
+      int e = 0;
+      uint32_t qm[WP], qv[WP];
+#pragma unroll
+      for (int w = 0; w < WP; w++) qm[w] = qv[w] = 0u;
+      if (t < pit.ne) {
+        e = a.ent[pit.e0 + t];
+        const int q = e / a.m;
+        sel = a.sel[e];
+        qn = a.qn[q];
 #pragma unroll
         for (int w = 0; w < WP; w++) {
-          p_qm[t * WP + w] = a.qmask[(int64_t)q * WP + w];
-          p_qv[t * WP + w] = a.qval[(int64_t)q * WP + w];
+          qm[w] = a.qmask[(int64_t)q * WP + w];
+          qv[w] = a.qval[(int64_t)q * WP + w];
         }
-      } else {
-        p_sel[t] = 0ull;
-#pragma unroll
-        for (int w = 0; w < WP; w++) p_qm[t * WP + w] = p_qv[t * WP + w] = 0u;
-        p_qn[t] = 0.f;
+        const uint64_t* sl = a.qslot + (int64_t)q * TC_SLOTS;
+        T = 0ull;
+        for (int i = 0; i < a.nslot; i++) {
+          const uint64_t v = sl[i];
+          T = v > T ? v : T;
+        }
       }
-      const int units = a.kcd * 8, dunits = a.d / 8;
-      for (int u = 0; u < units; u++) {
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (q >= 0 && u < dunits)
-          v = *reinterpret_cast<const uint4*>(a.Qh + (int64_t)q * a.d + 8 * u);
-        const int c = u >> 3, uu = u & 7;
-        *reinterpret_cast<uint4*>(sA + (size_t)c * TC_M * 128 + t * 128 + ((uu ^ (t & 7)) << 4)) = v;
+      U |= sel;
+      p_e[par][t] = e;
+      p_thr[par][t] = T;
+      p_sel[t] = sel;
+      p_qn[t] = qn;
+#pragma unroll
+      for (int w = 0; w < WP; w++) {
+        p_qm[t * WP + w] = qm[w];
+        p_qv[t * WP + w] = qv[w];
       }
-      if (PEN) {
-        // penalty chunk: -P in the column of every attribute bit value the
-        // probe's filter rules out and of every block it does not select,
-        // 0 elsewhere; P = 2^e >= 4 (max |x|^2 + |q|^2) (see the epilogue)
-        unsigned char* rowp = sA + (size_t)a.kcd * TC_M * 128 + t * 128;
+      float cut = 0.f;
+      if (PEN && t < pit.ne) {
+        const float bound = 4.f * (a.xn_max + qn);
+        int ex = (int)((__float_as_uint(bound) >> 23) & 0xffu) - 126;  // 2^ex >= bound
+        ex = max(0, min(126, ex));
+        cut = __uint_as_float((uint32_t)(METRIC == CAPS_L2 ? ex + 127 : ex + 126) << 23);
+      }
+      p_cut[t] = cut;
+    }
+    const uint32_t ulo = __reduce_or_sync(0xffffffffu, (uint32_t)U);
+    const uint32_t uhi = __reduce_or_sync(0xffffffffu, (uint32_t)(U >> 32));
+    U = ((uint64_t)uhi << 32) | ulo;
+    __syncwarp();
+    if (lane == 0) {
+      int nr = 0, nt = 0, j = 0;
+      while (j < nb) {
+        if (!((U >> j) & 1ull)) {
+          j++;
+          continue;
+        }
+        int j2 = j;
+        while (j2 + 1 < nb && ((U >> (j2 + 1)) & 1ull)) j2++;
+        if (boff[j2 + 1] > boff[j]) {
+          run_lo[nr] = boff[j];
+          run_hi[nr] = boff[j2 + 1];
+          run_j0[nr] = j;
+          nt += (boff[j2 + 1] - boff[j] + N - 1) / N;
+          nr++;
+        }
+        j = j2 + 1;
+      }
+      n_runs = nr;
+      s_ntiles[par] = nt;
+      s_ne[par] = pit.ne;
+      s_bin[par] = pit.b;
+    }
+    __syncwarp();
+    return true;
+  };
+  // ---- epilogue threads: the A operand of the prepared item ---------------
+  // row t = probe t's query, bf16, zero-padded to kcd*64 coordinates, 16-byte
+  // unit u of chunk c stored at unit u ^ (t%8); four threads per row, one per
+  // quarter of the units.  In the penalty form one more chunk: -P in the
+  // column of every attribute bit value the probe's filter rules out and of
+  // every block it does not select, 0 elsewhere.
+  auto build_a = [&](int par) {
+    const int t = tid & (TC_M - 1), qq = tid / TC_M;
+    const int ne_n = s_ne[par];
+    const int q = t < ne_n ? p_e[par][t] / a.m : -1;
+    const int units = a.kcd * 8, dunits = a.d / 8;
+    const int u0 = qq * units / TC_PARTS, u1 = (qq + 1) * units / TC_PARTS;
+#pragma unroll 4
+    for (int u = u0; u < u1; u++) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (q >= 0 && u < dunits) v = *reinterpret_cast<const uint4*>(a.Qh + (int64_t)q * a.d + 8 * u);
+      const int c = u >> 3, uu = u & 7;
+      *reinterpret_cast<uint4*>(sA + (size_t)c * TC_M * 128 + t * 128 + ((uu ^ (t & 7)) << 4)) = v;
+    }
+    if (PEN) {
+      unsigned char* rowp = sA + (size_t)a.kcd * TC_M * 128 + t * 128;
+      *reinterpret_cast<uint4*>(rowp + ((2 * qq) << 4)) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(rowp + ((2 * qq + 1) << 4)) = make_uint4(0u, 0u, 0u, 0u);
+      consumers_sync();  // the chunk is zero before the -P entries go in
+      if (qq == 0 && q >= 0) {
+        const float bound = 4.f * (a.xn_max + p_qn[t]);
+        int ex = (int)((__float_as_uint(bound) >> 23) & 0xffu) - 126;  // 2^ex >= bound
+        ex = max(0, min(126, ex));
+        const uint16_t negP = (uint16_t)(0x8000u | ((uint32_t)(ex + 127) << 7));
+        auto put = [&](int col) {
+          *reinterpret_cast<uint16_t*>(rowp + (((col >> 3) ^ (t & 7)) << 4) + (col & 7) * 2) = negP;
+        };
+        int gb = 0;
 #pragma unroll
-        for (int uu = 0; uu < 8; uu++)
-          *reinterpret_cast<uint4*>(rowp + (uu << 4)) = make_uint4(0u, 0u, 0u, 0u);
-        float cut = 0.f;
-        if (q >= 0) {
-          const float bound = 4.f * (a.xn_max + p_qn[t]);
-          int e = (int)((__float_as_uint(bound) >> 23) & 0xffu) - 126;  // 2^e >= bound
-          e = max(0, min(126, e));
-          const uint16_t negP = (uint16_t)(0x8000u | ((uint32_t)(e + 127) << 7));
-          cut = __uint_as_float((uint32_t)(METRIC == CAPS_L2 ? e + 127 : e + 126) << 23);
-          auto put = [&](int col) {
-            *reinterpret_cast<uint16_t*>(rowp + (((col >> 3) ^ (t & 7)) << 4) + (col & 7) * 2) = negP;
-          };
-          int gb = 0;
-#pragma unroll
-          for (int w = 0; w < WP; w++) {
-            uint32_t um = a.pen_mask[w];
-            while (um) {
-              const int i = __ffs(um) - 1;
-              um &= um - 1;
-              if ((p_qm[t * WP + w] >> i) & 1u) put(2 * gb + 1 - (int)((p_qv[t * WP + w] >> i) & 1u));
-              gb++;
-            }
+        for (int w = 0; w < WP; w++) {
+          uint32_t um = a.pen_mask[w];
+          const uint32_t qm = p_qm[t * WP + w], qv = p_qv[t * WP + w];
+          while (um) {
+            const int i = __ffs(um) - 1;
+            um &= um - 1;
+            if ((qm >> i) & 1u) put(2 * gb + 1 - (int)((qv >> i) & 1u));
+            gb++;
           }
-          for (int j = 0; j < a.h + 1; j++)
-            if (!((p_sel[t] >> j) & 1ull)) put(2 * a.pen_bits + j);
         }
-        p_cut[t] = cut;
+        const uint64_t sel = p_sel[t];
+        for (int j = 0; j < nb; j++)
+          if (!((sel >> j) & 1ull)) put(2 * a.pen_bits + j);
       }
     }
-    fence_async_smem();  // the A operand (generic stores) before the MMAs read it
-    __syncthreads();
-    const int n_tiles = s_ntiles;
+    fence_async_smem();  // generic stores of A before the MMAs read it
+  };
+
+  if (warp == TC_PRODUCER) prep_meta(0);
+  __syncthreads();
+  if (warp != TC_PRODUCER && s_ne[0] >= 0) build_a(0);
+  __syncthreads();
+
+  int g0 = 0;           // tiles this CTA finished before the current item
+  int par = 0, n_done = 0;
+  int tma_hi = -1, mma_hi = -1;  // producer: last tile whose copies / MMAs were issued
+  while (true) {
+    const int ne = s_ne[par];
+    if (ne < 0 || s_fail) break;
+    const int n_tiles = s_ntiles[par];
 
     if (warp == TC_PRODUCER) {
       // ---- producer ------------------------------------------------------
       int rr = 0, rlo = n_runs > 0 ? run_lo[0] : 0;
+      bool ok = true;
       for (int t = 0; t < n_tiles; t++) {
         const int g = g0 + t, b = g % S, u = g / S;
         while (rlo >= run_hi[rr]) {
@@ -418,10 +500,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         }
         const int lo = rlo, n = min(N, run_hi[rr] - rlo), j0 = run_j0[rr];
         rlo += n;
-        bool ok = true;
         if (u > 0) ok = mbar_wait(&empty_bar[b], (uint32_t)((u - 1) & 1), &s_fail);
         if (!__all_sync(0xffffffffu, ok)) {
-          if (lane == 0) s_fail = 1;
+          ok = false;
           break;
         }
         if (!PEN) {
@@ -466,15 +547,24 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
             mma_hi = g;
           }
         }
-        if (!__shfl_sync(0xffffffffu, ok, 0)) {
-          if (lane == 0) s_fail = 1;
-          break;
-        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
       }
+      // prepare the next item's metadata while the epilogue finishes this
+      // one, once the epilogue has taken this item's probe data
+      if (ok) {
+        ok = mbar_wait(&taken_bar, (uint32_t)(n_done & 1), &s_fail);
+        ok = __all_sync(0xffffffffu, ok);
+      }
+      if (ok) {
+        prep_meta(par ^ 1);
+        if (lane == 0) mbar_arrive(&meta_bar);  // the epilogue may build the next A operand
+      }
+      if (!ok && lane == 0) s_fail = 1;
     } else {
       // ---- epilogue ------------------------------------------------------
       const int probe = tid & (TC_M - 1), part = tid / TC_M;
-      const bool active = probe < it.ne;
+      const bool active = probe < ne;
       const uint64_t my_sel = p_sel[probe];
       uint32_t my_qm[WP], my_qv[WP];
 #pragma unroll
@@ -484,6 +574,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       }
       const float my_qn = p_qn[probe];
       const float my_cut = PEN ? p_cut[probe] : 0.f;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&taken_bar);  // the producer may refill the probe data
+      uint64_t* pthr = p_thr[par];
       uint64_t L[KP];
 #pragma unroll
       for (int i = 0; i < KP; i++) L[i] = kEmptyKey;
@@ -500,7 +593,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         thr = L[KP - 1];
         // the four threads of a probe share the smallest of their KP-th keys:
         // a key above it has KP better keys in one quarter list already
-        if (thr != kEmptyKey) atomicMin(reinterpret_cast<unsigned long long*>(&p_thr[probe]), thr);
+        if (thr != kEmptyKey) atomicMin(reinterpret_cast<unsigned long long*>(&pthr[probe]), thr);
       };
       const bool warp_live = __any_sync(0xffffffffu, active);
       const int cbeg = part * CPT;
@@ -529,7 +622,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
           tmem_wait(cur);
           const int c0 = cbeg + 8 * gi;
           {
-            const uint64_t st = p_thr[probe];
+            const uint64_t st = pthr[probe];
             if (st < thr) thr = st;
           }
           const int lim = n - c0;  // rows of this group inside the tile
@@ -615,15 +708,28 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         for (int q = 0; q < TC_PARTS - 1; q++)
 #pragma unroll
           for (int i = 0; i < KP; i++) net_insert<KP>(L, parts[((size_t)q * KP + i) * TC_M + probe]);
-        uint64_t* dst = a.part + (int64_t)p_e[probe] * KP;
+        const int e = p_e[par][probe];
+        uint64_t* dst = a.part + (int64_t)e * KP;
 #pragma unroll
         for (int i = 0; i < KP; i++) dst[i] = L[i];
+        // offer the list's KP-th key to the query's bound
+        if (L[KP - 1] != kEmptyKey)
+          atomicMin(reinterpret_cast<unsigned long long*>(
+                        a.qslot + (int64_t)(e / a.m) * TC_SLOTS + s_bin[par] % a.nslot),
+                    (unsigned long long)L[KP - 1]);
       }
+      // the next item's A operand: every MMA of this item has completed (each
+      // tile's accumulator was waited for), so A may be overwritten once the
+      // producer has the next item's probe data
+      const bool meta = fine && mbar_wait(&meta_bar, (uint32_t)(n_done & 1), &s_fail);
+      if (fine && !meta) s_fail = 1;
+      if (consumers_all(meta) && s_ne[par ^ 1] >= 0) build_a(par ^ 1);
     }
     g0 += n_tiles;
+    n_done++;
     fence_async_smem();  // generic stores into the B stages before later copies land there
     __syncthreads();
-    slot ^= 1;
+    par ^= 1;
   }
 
   if (s_fail) {
@@ -647,6 +753,10 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
 template <int METRIC, int WP, int KP, int N, bool PEN>
 int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem, cudaStream_t s) {
   auto kern = k_scan_tc<METRIC, WP, KP, N, PEN>;
+  cudaFuncAttributes fa;
+  CAPS_CUDA(cudaFuncGetAttributes(&fa, kern));
+  if (smem + fa.sharedSizeBytes > kTcSmemLimit)
+    return fail(CAPS_EINVAL, "tensor-core tile shape does not fit in shared memory");
   CAPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<(unsigned)grid, TC_T, smem, s>>>(map, a);
   CAPS_LAUNCH("k_scan_tc");
