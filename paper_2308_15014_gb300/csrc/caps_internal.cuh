@@ -49,6 +49,39 @@ __device__ __forceinline__ float unord_bits(uint32_t u) {
 __device__ __forceinline__ uint64_t make_key(float score, uint32_t id) {
   return ((uint64_t)ord_bits(score) << 32) | (uint64_t)id;
 }
+
+// Ascending bitonic sort of 32 * V keys held V per lane (key P = V * lane + s).
+template <int V>
+__device__ __forceinline__ void warp_sort(uint64_t (&v)[V], int lane) {
+#pragma unroll
+  for (int size = 2; size <= 32 * V; size <<= 1)
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride < V) {
+#pragma unroll
+        for (int s = 0; s < V; s++) {
+          const int o = s ^ stride;
+          if (o > s) {
+            const bool up = ((V * lane + s) & size) == 0;
+            const uint64_t a = v[s], b = v[o];
+            if ((a > b) == up) {
+              v[s] = b;
+              v[o] = a;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < V; s++) {
+          const int P = V * lane + s;
+          const uint64_t o = __shfl_xor_sync(0xffffffffu, v[s], stride / V);
+          const bool up = (P & size) == 0, lower = (P & stride) == 0;
+          v[s] = (lower == up) ? (o < v[s] ? o : v[s]) : (o > v[s] ? o : v[s]);
+        }
+      }
+    }
+}
+
 constexpr uint64_t kEmptyKey = ~0ull;
 
 // Running k smallest keys of a warp: positions lane*KPL + s, ascending, the

@@ -16,15 +16,18 @@ namespace {
 // ---- bf16 query copy and fp32 squared norms -------------------------------
 __global__ void k_query_bf16(const float* __restrict__ Q, int64_t nq, int d,
                              __nv_bfloat16* __restrict__ Qh, float* __restrict__ qn) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per query: coalesced bf16 conversion, then lane 0 forms the
+  // squared norm over the coordinates in order (one fma each)
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (q >= nq) return;
-  float acc = 0.f;
-  for (int j = 0; j < d; j++) {
-    const float x = Q[q * d + j];
-    acc = fmaf(x, x, acc);
-    Qh[q * d + j] = __float2bfloat16_rn(x);
+  const float* x = Q + q * d;
+  for (int j = lane; j < d; j += 32) Qh[q * d + j] = __float2bfloat16_rn(x[j]);
+  if (lane == 0) {
+    float acc = 0.f;
+    for (int j = 0; j < d; j++) acc = fmaf(x[j], x[j], acc);
+    qn[q] = acc;
   }
-  qn[q] = acc;
 }
 
 // ---- per-query merge of the m candidate lists (keys out) -------------------
@@ -73,50 +76,107 @@ struct TopKm {
 };
 
 // Merge each query's m lists of kp keys, re-score the kp best exactly in
-// fp32 (coordinates in order, one fma each) and keep the k best.
-template <int METRIC, int KPL_M, int KPL_K>
+// fp32 (coordinates in order, one fma each) and keep the k best.  The scan's
+// per-query bound T (the largest of the query's bound slots, once all are
+// set) has at least kp keys of the lists at or below it, so only those keys
+// compete: they are compacted and sorted in the warp (up to 128), else the
+// lists are merged by insertion.
+template <int METRIC, int KPL_K>
 __global__ void __launch_bounds__(128)
 k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ dead, int64_t nq,
-               int m, int lp, int kp, int k, const float* __restrict__ Q, int d,
-               const float* __restrict__ Xp, const int32_t* __restrict__ iperm,
-               int64_t* __restrict__ out_ids, float* __restrict__ out_dist) {
-  extern __shared__ float qsm[];  // [4][d]
+               int m, int lp, int kp, int k, const uint64_t* __restrict__ qslot, int nslot,
+               const float* __restrict__ Q, int d, const float* __restrict__ Xp,
+               const int32_t* __restrict__ iperm, int64_t* __restrict__ out_ids,
+               float* __restrict__ out_dist) {
+  // [4][d] queries, [4][128] candidate keys
+  extern __shared__ float qsm[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * 4 + wp;
   if (q >= nq) return;
   float* qs = qsm + (size_t)wp * d;
+  uint64_t* cbuf = reinterpret_cast<uint64_t*>(qsm + 4 * (size_t)d) + (size_t)wp * 128;
   for (int j = lane; j < d; j += 32) qs[j] = Q[q * d + j];
-  __syncwarp();
-  TopKm<KPL_M> cand;
-  cand.init();
-  uint64_t kthv = kEmptyKey;
-  if (!dead[q]) {
-    const uint64_t* src = part + q * (int64_t)m * lp;
-    const int tot = m * lp;
-    for (int b0 = 0; b0 < tot; b0 += 32) {
-      const uint64_t key = (b0 + lane < tot) ? src[b0 + lane] : kEmptyKey;
-      cand.offer(key, kthv, kp, lane);
+  const uint64_t* src = part + q * (int64_t)m * lp;
+  const int tot = m * lp;
+  const bool live = !dead[q];
+  uint64_t T = kEmptyKey;
+  if (nslot > 0) {
+    T = 0ull;
+    for (int i = 0; i < nslot; i++) {
+      const uint64_t v = qslot[q * 8 + i];
+      T = v > T ? v : T;
     }
   }
-  // exact fp32 scores of the kp candidates
+  int cnt = 0;
+  if (live && T != kEmptyKey) {
+    const unsigned lt = (1u << lane) - 1u;
+    for (int b0 = 0; b0 < tot; b0 += 32) {
+      const uint64_t key = (b0 + lane < tot) ? src[b0 + lane] : kEmptyKey;
+      const bool keep = key <= T;
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      const int pos = cnt + __popc(bal & lt);
+      if (keep && pos < 128) cbuf[pos] = key;
+      cnt += __popc(bal);
+    }
+  }
+  __syncwarp();
+  if (live && T != kEmptyKey && cnt <= 128) {
+    uint64_t v[4];
+#pragma unroll
+    for (int s = 0; s < 4; s++) v[s] = (4 * lane + s < cnt) ? cbuf[4 * lane + s] : kEmptyKey;
+    warp_sort<4>(v, lane);
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 4; s++) cbuf[4 * lane + s] = v[s];
+  } else {
+    TopKm<2> cand;
+    cand.init();
+    uint64_t kthv = kEmptyKey;
+    if (live) {
+      for (int b0 = 0; b0 < tot; b0 += 32) {
+        const uint64_t key = (b0 + lane < tot) ? src[b0 + lane] : kEmptyKey;
+        cand.offer(key, kthv, kp, lane);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; s++) cbuf[2 * lane + s] = cand.v[s];
+  }
+  __syncwarp();
+  // exact fp32 scores of the kp candidates, one per lane (32 at a time):
+  // 16-byte loads of the candidate's row, eight in flight, and the fma chain
+  // over the coordinates in order
   TopKm<KPL_K> top;
   top.init();
   uint64_t kth2 = kEmptyKey;
-#pragma unroll
-  for (int s = 0; s < KPL_M; s++) {
-    const int P = lane * KPL_M + s;
+  for (int r0 = 0; r0 < kp; r0 += 32) {
+    const int c = r0 + lane;  // this lane's candidate
+    const uint64_t ck = c < kp ? cbuf[c] : kEmptyKey;
     uint64_t key = kEmptyKey;
-    const uint64_t ck = cand.v[s];
-    if (P < kp && ck != kEmptyKey) {
+    if (ck != kEmptyKey) {
       const uint32_t id = (uint32_t)(ck & 0xffffffffu);
-      const float* xr = Xp + (int64_t)iperm[id] * d;
+      const float4* xr = reinterpret_cast<const float4*>(Xp + (int64_t)iperm[id] * d);
       float acc = 0.f;
-      for (int j = 0; j < d; j++) {
-        if (METRIC == CAPS_L2) {
-          const float t = xr[j] - qs[j];
-          acc = fmaf(t, t, acc);
-        } else {
-          acc = fmaf(xr[j], qs[j], acc);
+      for (int j0 = 0; j0 < d / 4; j0 += 8) {
+        float4 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+          if (j0 + u < d / 4) x[u] = xr[j0 + u];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+          if (j0 + u < d / 4) {
+            const float* qv = qs + 4 * (j0 + u);
+            const float xv[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              if (METRIC == CAPS_L2) {
+                const float t = xv[e] - qv[e];
+                acc = fmaf(t, t, acc);
+              } else {
+                acc = fmaf(xv[e], qv[e], acc);
+              }
+            }
+          }
         }
       }
       key = make_key(METRIC == CAPS_L2 ? acc : -acc, id);
@@ -141,14 +201,69 @@ k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ de
   }
 }
 
-__global__ void k_mask_key(const uint64_t* __restrict__ sel, int64_t ne, int32_t* __restrict__ key) {
+// ---- grouping of the probes by partition -----------------------------------
+__global__ void k_bin_count(const int32_t* __restrict__ probe, int64_t ne, int32_t* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < ne) key[i] = (int32_t)sel[i];
+  if (i < ne) atomicAdd(&cnt[probe[i]], 1);
 }
-__global__ void k_gather_i32(const int32_t* __restrict__ src, const int32_t* __restrict__ idx,
-                             int64_t n, int32_t* __restrict__ dst) {
+__global__ void k_bin_scatter(const int32_t* __restrict__ probe, int64_t ne,
+                              int32_t* __restrict__ cursor, int32_t* __restrict__ ent) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = src[idx[i]];
+  if (i < ne) ent[atomicAdd(&cursor[probe[i]], 1)] = (int32_t)i;
+}
+// Within each partition, order the probe entries by a 12-bit code of their
+// selected-block mask (lowest block, highest block, number of blocks): probes
+// that scan the same blocks end up in the same work item.  One CTA per
+// partition: count the codes in shared memory, scan, scatter.  Only the speed
+// of the scan depends on this order (equal codes land in any order), never its
+// results.
+constexpr int TC_MCODES = 4096;
+__device__ __forceinline__ int mask_code(uint64_t m) {
+  if (m == 0) return 0;
+  const int lo = min(15, __ffsll((long long)m) - 1), hi = min(15, 63 - __clzll((long long)m));
+  const int n = min(15, __popcll(m));
+  return lo | (hi << 4) | (n << 8);
+}
+__global__ void __launch_bounds__(512)
+k_bin_group_mask(const int32_t* __restrict__ bin_off, const uint64_t* __restrict__ sel,
+                 const int32_t* __restrict__ ent_in, int32_t* __restrict__ ent_out) {
+  __shared__ int cnt[TC_MCODES];
+  __shared__ int wsum[16];
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int beg = bin_off[b], end = bin_off[b + 1];
+  if (end - beg <= 1) {
+    if (end > beg && tid == 0) ent_out[beg] = ent_in[beg];
+    return;
+  }
+  for (int i = tid; i < TC_MCODES; i += 512) cnt[i] = 0;
+  __syncthreads();
+  for (int i = beg + tid; i < end; i += 512) atomicAdd(&cnt[mask_code(sel[ent_in[i]])], 1);
+  __syncthreads();
+  // exclusive scan of the 4096 counts: 8 per thread, then across threads
+  int loc[TC_MCODES / 512], run = 0;
+#pragma unroll
+  for (int j = 0; j < TC_MCODES / 512; j++) {
+    loc[j] = run;
+    run += cnt[tid * (TC_MCODES / 512) + j];
+  }
+  int inc = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  int wbase = 0;
+  for (int w = 0; w < warp; w++) wbase += wsum[w];
+  const int tbase = beg + wbase + inc - run;
+#pragma unroll
+  for (int j = 0; j < TC_MCODES / 512; j++) cnt[tid * (TC_MCODES / 512) + j] = tbase + loc[j];
+  __syncthreads();
+  for (int i = beg + tid; i < end; i += 512) {
+    const int e = ent_in[i];
+    ent_out[atomicAdd(&cnt[mask_code(sel[e])], 1)] = e;
+  }
 }
 
 __global__ void k_tc_items_count(const int32_t* __restrict__ bin_off, int B, int cap,
@@ -314,8 +429,8 @@ int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
 
 int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, cudaStream_t s) {
   if (nq == 0) return CAPS_OK;
-  k_query_bf16<<<(unsigned)((nq + 127) / 128), 128, 0, s>>>(Q, nq, d,
-                                                            static_cast<__nv_bfloat16*>(Qh), qn);
+  k_query_bf16<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, d,
+                                                        static_cast<__nv_bfloat16*>(Qh), qn);
   CAPS_LAUNCH("k_query_bf16");
   return CAPS_OK;
 }
@@ -323,31 +438,29 @@ int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, cudaSt
 int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, int item_cap,
              BinWork* w, Scratch& scr, cudaStream_t s) {
   if (ne > INT_MAX) return fail(CAPS_EINVAL, "too many probes in one chunk");
+  (void)h;
   const int cap = item_cap > 0 ? std::min(item_cap, TC_M) : TC_M;
-  int32_t *bin_off = nullptr, *cnt = nullptr;
+  int32_t *bin_off = nullptr, *cursor = nullptr, *cnt = nullptr;
   if (int rc = scr.get(&w->ent, (size_t)ne)) return rc;
   if (int rc = scr.get(&bin_off, (size_t)B + 1)) return rc;
-  if (h + 1 <= 16) {
-    // probes of a partition ordered by their selected-block mask, so that
-    // probes scanning the same blocks share a work item: sort by mask, then
-    // (stably) by partition
-    int32_t *mkey = nullptr, *p1 = nullptr, *moff = nullptr, *pkey = nullptr, *p2 = nullptr;
-    if (int rc = scr.get(&mkey, (size_t)ne)) return rc;
-    if (int rc = scr.get(&p1, (size_t)ne)) return rc;
-    if (int rc = scr.get(&moff, ((size_t)1 << (h + 1)) + 1)) return rc;
-    if (int rc = scr.get(&pkey, (size_t)ne)) return rc;
-    if (int rc = scr.get(&p2, (size_t)ne)) return rc;
-    const unsigned g = (unsigned)((ne + 255) / 256);
-    k_mask_key<<<g, 256, 0, s>>>(sel, ne, mkey);
-    CAPS_LAUNCH("k_mask_key");
-    if (int rc = stable_sort_by_key(mkey, ne, (int64_t)1 << (h + 1), p1, moff, scr, s)) return rc;
-    k_gather_i32<<<g, 256, 0, s>>>(probe, p1, ne, pkey);
-    CAPS_LAUNCH("k_gather_i32");
-    if (int rc = stable_sort_by_key(pkey, ne, B, p2, bin_off, scr, s)) return rc;
-    k_gather_i32<<<g, 256, 0, s>>>(p1, p2, ne, w->ent);
-    CAPS_LAUNCH("k_gather_i32");
-  } else {
-    if (int rc = stable_sort_by_key(probe, ne, B, w->ent, bin_off, scr, s)) return rc;
+  if (int rc = scr.get(&cursor, (size_t)B + 1)) return rc;
+  // partition histogram, offsets, scatter; then mask order inside each partition
+  CAPS_CUDA(cudaMemsetAsync(bin_off, 0, sizeof(int32_t) * ((size_t)B + 1), s));
+  const unsigned g = (unsigned)((ne + 255) / 256);
+  if (ne > 0) {
+    k_bin_count<<<g, 256, 0, s>>>(probe, ne, bin_off);
+    CAPS_LAUNCH("k_bin_count");
+  }
+  if (int rc = scan_exclusive_i32(bin_off, (int64_t)B + 1, scr, s)) return rc;
+  CAPS_CUDA(cudaMemcpyAsync(cursor, bin_off, sizeof(int32_t) * ((size_t)B + 1),
+                            cudaMemcpyDeviceToDevice, s));
+  if (ne > 0) {
+    int32_t* tmp = nullptr;
+    if (int rc = scr.get(&tmp, (size_t)ne)) return rc;
+    k_bin_scatter<<<g, 256, 0, s>>>(probe, ne, cursor, tmp);
+    CAPS_LAUNCH("k_bin_scatter");
+    k_bin_group_mask<<<(unsigned)B, 512, 0, s>>>(bin_off, sel, tmp, w->ent);
+    CAPS_LAUNCH("k_bin_group_mask");
   }
   if (int rc = scr.get(&cnt, (size_t)B + 1)) return rc;
   if (int rc = scr.get(&w->n_items, 2)) return rc;
@@ -445,19 +558,21 @@ int tc_merge_rerank(const TcScanArgs& t, const uint8_t* dead, int64_t nq, int k,
                     cudaStream_t s) {
   if (nq == 0) return CAPS_OK;
   const int depth = std::min(t.rerank, t.m * t.kp);  // candidates re-scored per query
+  const int nslot = t.qslot ? std::min(TC_SLOTS, std::max(1, (depth + t.kp - 1) / t.kp)) : 0;
   const unsigned grid = (unsigned)((nq + 3) / 4);
-  const size_t smem = sizeof(float) * 4 * (size_t)t.d;
-#define CAPS_MR(MET, KM, KK)                                                                   \
-  k_merge_rerank<MET, KM, KK><<<grid, 128, smem, s>>>(t.part, dead, nq, t.m, t.kp, depth, k, Q, \
-                                                       t.d, Xp, iperm, out_ids, out_dist)
-  const int km = depth <= 32 ? 1 : 2;
-  if (t.metric == CAPS_L2) {
-    if (km == 1) CAPS_MR(CAPS_L2, 1, 1);
-    else CAPS_MR(CAPS_L2, 2, 1);
-  } else {
-    if (km == 1) CAPS_MR(CAPS_IP, 1, 1);
-    else CAPS_MR(CAPS_IP, 2, 1);
-  }
+  if (t.d % 4 != 0 || t.d > 128) return fail(CAPS_EINVAL, "re-rank needs d % 4 == 0, d <= 128");
+  if (depth > 64) return fail(CAPS_EINVAL, "re-rank depth above 64");
+  const size_t smem = sizeof(float) * 4 * (size_t)t.d + sizeof(uint64_t) * 4 * 128;
+#define CAPS_MR(MET)                                                                            \
+  do {                                                                                          \
+    CAPS_CUDA(cudaFuncSetAttribute(k_merge_rerank<MET, 1>,                                      \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
+    k_merge_rerank<MET, 1><<<grid, 128, smem, s>>>(t.part, dead, nq, t.m, t.kp, depth, k,       \
+                                                   t.qslot, nslot, Q, t.d, Xp, iperm, out_ids,  \
+                                                   out_dist);                                   \
+  } while (0)
+  if (t.metric == CAPS_L2) CAPS_MR(CAPS_L2);
+  else CAPS_MR(CAPS_IP);
 #undef CAPS_MR
   CAPS_LAUNCH("k_merge_rerank");
   return CAPS_OK;

@@ -126,9 +126,91 @@ k_topm_warp(const float* __restrict__ scores, int64_t nq, int B, int m, int metr
   }
 }
 
+// m <= 64: each lane's two smallest keys; the m-th smallest of those 64 keys
+// has m keys at or below it, so it bounds the m-th smallest overall.  The keys
+// at or below it are compacted and sorted in the warp (up to 128 of them),
+// else the warp falls back to insertion.
+__global__ void __launch_bounds__(128)
+k_topm_thr(const float* __restrict__ scores, int64_t nq, int B, int m, int metric,
+           int32_t* __restrict__ probe) {
+  __shared__ uint64_t cbuf[4][128];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * 4 + wp;
+  if (q >= nq) return;
+  const float* sc = scores + q * B;
+  uint64_t a0 = kEmptyKey, a1 = kEmptyKey;
+  for (int c = lane; c < B; c += 32) {
+    const float v = sc[c];
+    const uint64_t key = make_key(metric == CAPS_L2 ? v : -v, (uint32_t)c);
+    if (key < a1) {
+      if (key < a0) {
+        a1 = a0;
+        a0 = key;
+      } else {
+        a1 = key;
+      }
+    }
+  }
+  uint64_t v2[2] = {a0, a1};
+  warp_sort<2>(v2, lane);
+  const int P = m - 1;
+  const uint64_t tl = __shfl_sync(0xffffffffu, (P & 1) ? v2[1] : v2[0], P >> 1);
+  const unsigned lt = (1u << lane) - 1u;
+  int cnt = 0;
+  uint64_t* cb = cbuf[wp];
+  for (int c0 = 0; c0 < B; c0 += 32) {
+    const int c = c0 + lane;
+    uint64_t key = kEmptyKey;
+    if (c < B) {
+      const float v = sc[c];
+      key = make_key(metric == CAPS_L2 ? v : -v, (uint32_t)c);
+    }
+    const bool keep = key <= tl && key != kEmptyKey;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int pos = cnt + __popc(bal & lt);
+    if (keep && pos < 128) cb[pos] = key;
+    cnt += __popc(bal);
+  }
+  __syncwarp();
+  if (cnt <= 128) {
+    uint64_t v4[4];
+#pragma unroll
+    for (int s2 = 0; s2 < 4; s2++) v4[s2] = (4 * lane + s2 < cnt) ? cb[4 * lane + s2] : kEmptyKey;
+    warp_sort<4>(v4, lane);
+#pragma unroll
+    for (int s2 = 0; s2 < 4; s2++) {
+      const int Pp = 4 * lane + s2;
+      if (Pp < m) probe[q * m + Pp] = (int32_t)(v4[s2] & 0xffffffffu);
+    }
+    return;
+  }
+  WarpTopK<2> top;
+  top.init();
+  uint64_t kthv = kEmptyKey;
+  for (int b0 = 0; b0 < B; b0 += 32) {
+    const int c = b0 + lane;
+    uint64_t key = kEmptyKey;
+    if (c < B) {
+      const float v = sc[c];
+      key = make_key(metric == CAPS_L2 ? v : -v, (uint32_t)c);
+    }
+    top.offer(key, kthv, m, lane);
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < 2; s2++) {
+    const int Pp = lane * 2 + s2;
+    if (Pp < m) probe[q * m + Pp] = (int32_t)(top.v[s2] & 0xffffffffu);
+  }
+}
+
 int launch_topm(const float* scores, int64_t nq, int B, int m, int metric, int32_t* probe,
                 cudaStream_t s) {
   if (nq == 0) return CAPS_OK;
+  if (m <= 64 && m <= B) {
+    k_topm_thr<<<(unsigned)((nq + 3) / 4), 128, 0, s>>>(scores, nq, B, m, metric, probe);
+    CAPS_LAUNCH("k_topm_thr");
+    return CAPS_OK;
+  }
   if (m <= 128) {
     const unsigned g = (unsigned)((nq + 3) / 4);
     if (m <= 32) k_topm_warp<1><<<g, 128, 0, s>>>(scores, nq, B, m, metric, probe);
