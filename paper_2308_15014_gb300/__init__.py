@@ -179,6 +179,26 @@ def _dense_attrs(A, vocab=None):
     return at, keep
 
 
+def _sparse_attrs(off, lab, vocab=0):
+    """Label-set attributes or constraints: CSR offsets [n+1] (int64) and
+    labels (int32); for data the labels of each point ascend strictly."""
+    off = _np_or_keep(off, np.int64)
+    lab = _np_or_keep(lab, np.int32)
+    at = caps_attrs()
+    at.L = 0
+    at.sp_offsets = _ptr(off)
+    at.sp_labels = _ptr(lab) if lab.shape[0] > 0 else None
+    at.sp_vocab = int(vocab)
+    return at, [off, lab]
+
+
+def _cons(Qb):
+    """Dense constraint rows [nq, L], or a (q_off, q_lab) pair of label sets."""
+    if isinstance(Qb, tuple):
+        return _sparse_attrs(Qb[0], Qb[1])
+    return _dense_attrs(Qb)
+
+
 def assign(X, C, metric=L2, out=None, stream=None):
     """f(x) = best centroid for every row of X (caps_assign)."""
     X = _np_or_keep(X, np.float32)
@@ -258,10 +278,15 @@ class Index:
     def build(cls, X, A, vocab, B, h=15, iters=20, metric=L2, init_idx=None, centroids=None,
               seed=0, prec=FP32, rerank_factor=0, part=KMEANS, mlp_hidden=0, mlp_epochs=0,
               mlp_samples=0, mlp_batch=0, mlp_lr=0.0, mlp_label_k=0, mlp_sample_idx=None,
-              mlp_sample_cons=None, mlp_init=None, stream=None) -> "Index":
+              mlp_sample_cons=None, mlp_init=None, labels=None, stream=None) -> "Index":
+        """labels = (sp_off, sp_lab, sp_vocab): label-set attributes instead of
+        the dense A / vocab."""
         X = _np_or_keep(X, np.float32)
         N, d = X.shape
-        at, keep = _dense_attrs(A, vocab)
+        if labels is not None:
+            at, keep = _sparse_attrs(*labels)
+        else:
+            at, keep = _dense_attrs(A, vocab)
         p = caps_build_params()
         p.B, p.h, p.kmeans_iters, p.seed, p.metric = B, h, iters, seed, metric
         p.part, p.prec, p.rerank_factor = part, prec, rerank_factor
@@ -333,7 +358,7 @@ class Index:
     def select(self, probe, Qb, out=None, stream=None):
         probe = _np_or_keep(probe, np.int32)
         nq, m = probe.shape
-        at, keep = _dense_attrs(Qb)
+        at, keep = _cons(Qb)
         if out is None:
             out = np.empty((nq, m), dtype=np.uint64)
         _check(lib().caps_select(self._h, _ptr(probe), nq, m, ct.byref(at), _ptr(out),
@@ -342,10 +367,11 @@ class Index:
 
     def search(self, Q, Qb, k, m, out_ids=None, out_dist=None, stream=None):
         """Alg. 2 for a batch; returns (ids [nq,k] int64, dist [nq,k] fp32).
-        Outputs land where the inputs live unless given explicitly."""
+        Qb: dense constraint rows, or (q_off, q_lab) label sets.  Outputs land
+        where the inputs live unless given explicitly."""
         Q = _np_or_keep(Q, np.float32)
         nq = Q.shape[0]
-        at, keep = _dense_attrs(Qb)
+        at, keep = _cons(Qb)
         t = _torch()
         if out_ids is None:
             if t is not None and isinstance(Q, t.Tensor) and Q.is_cuda:
@@ -370,7 +396,7 @@ class Index:
         """caps_plan_create: a tuned, graph-captured plan for batches shaped
         like Q (its rows are the autotuner's sample)."""
         Q = _np_or_keep(Q, np.float32)
-        at, keep = _dense_attrs(Qb)
+        at, keep = _cons(Qb)
         h = ct.c_void_p()
         _check(lib().caps_plan_create(self._h, _ptr(Q), Q.shape[0], ct.byref(at), k, m,
                                       1 if autotune else 0, _stream(stream), ct.byref(h)))

@@ -615,6 +615,7 @@ int launch_layout(const float* X, const int32_t* A, const int32_t* perm, int64_t
     k_layout_rows1<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, perm, N, d, Xp);
   }
   CAPS_LAUNCH("k_layout_rows");
+  if (meta.sparse) return CAPS_OK;  // label sets: launch_layout_sparse
   k_layout_attrs<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(A, perm, N, meta, Ap);
   CAPS_LAUNCH("k_layout_attrs");
   return CAPS_OK;
@@ -626,6 +627,165 @@ int launch_pos_table(const int32_t* tags, int B, int h, int64_t n_codes, uint8_t
   if (tot == 0) return CAPS_OK;
   k_pos_table<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(tags, B, h, n_codes, pos);
   CAPS_LAUNCH("k_pos_table");
+  return CAPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sparse label sets (Def. 1 with label-set attributes): validation, the
+// attribute frequency tree over label codes, and the layout-order copies.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_check_sparse(const int64_t* __restrict__ off, const int32_t* __restrict__ lab,
+                               int64_t N, int32_t V, int32_t* __restrict__ off32,
+                               int32_t* __restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > N) return;
+  const int64_t o = off[i];
+  if (o < 0 || o > INT_MAX) atomicExch(bad, 1);
+  off32[i] = (int32_t)o;
+  if (i == N) return;
+  const int64_t e = off[i + 1];
+  if (e < o) {
+    atomicExch(bad, 1);
+    return;
+  }
+  int32_t prev = -1;
+  for (int64_t r = o; r < e; r++) {
+    const int32_t c = lab[r];
+    if (c < 0 || c >= V || c <= prev) {
+      atomicExch(bad, 1);
+      return;
+    }
+    prev = c;
+  }
+}
+
+// One CTA per partition; as k_aft, but a point carries its labels as codes.
+__global__ void __launch_bounds__(AFT_T)
+k_aft_sparse(const int32_t* __restrict__ perm_bin, const int32_t* __restrict__ bin_off, int h,
+             const int32_t* __restrict__ off, const int32_t* __restrict__ lab, int32_t V,
+             int32_t* __restrict__ tags, uint8_t* __restrict__ key) {
+  extern __shared__ int hist[];  // [V]
+  __shared__ unsigned long long red[AFT_T / 32];
+  __shared__ int t_sh;
+  const int b = blockIdx.x;
+  const int beg = bin_off[b], end = bin_off[b + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  bool done = false;
+  for (int j = 1; j <= h; j++) {
+    if (done) {
+      if (threadIdx.x == 0) tags[(int64_t)b * h + j - 1] = -1;
+      continue;
+    }
+    for (int c = threadIdx.x; c < V; c += AFT_T) hist[c] = 0;
+    __syncthreads();
+    for (int u = beg + threadIdx.x; u < end; u += AFT_T) {
+      const int i = perm_bin[u];
+      if (key[i] != 0) continue;
+      for (int r = off[i]; r < off[i + 1]; r++) atomicAdd(&hist[lab[r]], 1);
+    }
+    __syncthreads();
+    unsigned long long best = 0ull;
+    for (int c = threadIdx.x; c < V; c += AFT_T) {
+      const unsigned long long cand =
+          ((unsigned long long)(unsigned)hist[c] << 32) | (unsigned long long)(0xffffffffu - (unsigned)c);
+      if (cand > best) best = cand;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(0xffffffffu, best, o);
+      if (x > best) best = x;
+    }
+    if (lane == 0) red[w] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long m = red[0];
+      for (int q = 1; q < AFT_T / 32; q++) m = red[q] > m ? red[q] : m;
+      const unsigned cnt = (unsigned)(m >> 32);
+      t_sh = cnt > 0 ? (int)(0xffffffffu - (unsigned)(m & 0xffffffffull)) : -1;
+      tags[(int64_t)b * h + j - 1] = t_sh;
+    }
+    __syncthreads();
+    const int t = t_sh;
+    if (t < 0) {
+      done = true;
+      continue;
+    }
+    for (int u = beg + threadIdx.x; u < end; u += AFT_T) {
+      const int i = perm_bin[u];
+      if (key[i] != 0) continue;
+      for (int r = off[i]; r < off[i + 1]; r++)
+        if (lab[r] == t) {
+          key[i] = (uint8_t)j;
+          break;
+        }
+    }
+    __syncthreads();
+  }
+  for (int u = beg + threadIdx.x; u < end; u += AFT_T) {
+    const int i = perm_bin[u];
+    if (key[i] == 0) key[i] = (uint8_t)(h + 1);
+  }
+}
+
+__global__ void k_layout_sparse_sig(const int32_t* __restrict__ off, const int32_t* __restrict__ lab,
+                                    const int32_t* __restrict__ perm, int64_t N,
+                                    uint32_t* __restrict__ Ap, int32_t* __restrict__ cnt) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > N) return;
+  if (r == N) {
+    cnt[N] = 0;
+    return;
+  }
+  const int i = perm[r];
+  uint64_t sig = 0ull;
+  for (int u = off[i]; u < off[i + 1]; u++) sig |= 1ull << sig_bit(lab[u]);
+  Ap[2 * r] = (uint32_t)sig;
+  Ap[2 * r + 1] = (uint32_t)(sig >> 32);
+  cnt[r] = off[i + 1] - off[i];
+}
+
+__global__ void k_layout_sparse_lab(const int32_t* __restrict__ off, const int32_t* __restrict__ lab,
+                                    const int32_t* __restrict__ perm, int64_t N,
+                                    const int32_t* __restrict__ off_p, int32_t* __restrict__ lab_p) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int i = perm[r];
+  const int o = off_p[r];
+  for (int u = off[i]; u < off[i + 1]; u++) lab_p[o + (u - off[i])] = lab[u];
+}
+}  // namespace
+
+int launch_check_sparse(const int64_t* off, const int32_t* lab, int64_t N, int32_t V,
+                        int32_t* off32, int32_t* bad, cudaStream_t s) {
+  k_check_sparse<<<(unsigned)((N + 1 + 255) / 256), 256, 0, s>>>(off, lab, N, V, off32, bad);
+  CAPS_LAUNCH("k_check_sparse");
+  return CAPS_OK;
+}
+
+int launch_aft_sparse(const int32_t* perm_bin, const int32_t* bin_off, int B, int h,
+                      const int32_t* off, const int32_t* lab, int32_t V, int32_t* tags,
+                      uint8_t* key, cudaStream_t s) {
+  const size_t smem = sizeof(int) * (size_t)std::max<int32_t>(1, V);
+  if (smem > 200 * 1024) return fail(CAPS_EINVAL, "label vocabulary too large for the AFT kernel");
+  if (smem > 48 * 1024)
+    CAPS_CUDA(cudaFuncSetAttribute(k_aft_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  k_aft_sparse<<<B, AFT_T, smem, s>>>(perm_bin, bin_off, h, off, lab, V, tags, key);
+  CAPS_LAUNCH("k_aft_sparse");
+  return CAPS_OK;
+}
+
+int launch_layout_sparse(const int32_t* off, const int32_t* lab, const int32_t* perm, int64_t N,
+                         uint32_t* Ap, int32_t* off_p, int32_t* lab_p, Scratch& scr,
+                         cudaStream_t s) {
+  k_layout_sparse_sig<<<(unsigned)((N + 1 + 255) / 256), 256, 0, s>>>(off, lab, perm, N, Ap, off_p);
+  CAPS_LAUNCH("k_layout_sparse_sig");
+  if (int rc = scan_exclusive_i32(off_p, N + 1, scr, s)) return rc;
+  if (N > 0) {
+    k_layout_sparse_lab<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(off, lab, perm, N, off_p, lab_p);
+    CAPS_LAUNCH("k_layout_sparse_lab");
+  }
   return CAPS_OK;
 }
 

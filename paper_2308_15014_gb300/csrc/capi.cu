@@ -27,6 +27,16 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 namespace {
 
+// int64 offsets -> int32, flagging negative, oversized or decreasing ones
+__global__ void k_offsets_i32(const int64_t* __restrict__ in, int64_t n, int32_t* __restrict__ out,
+                              int32_t* __restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t v = in[i];
+  if (v < 0 || v > INT32_MAX || (i > 0 && v < in[i - 1])) atomicExch(bad, 1);
+  out[i] = (int32_t)v;
+}
+
 // Is p a pointer the current device can dereference (device or managed)?
 int is_device_ptr(const void* p, bool* dev) {
   *dev = false;
@@ -148,8 +158,21 @@ std::vector<int64_t> floyd_sample(int64_t N, int64_t B, uint64_t seed) {
 
 int make_meta(const caps_attrs* at, cudaStream_t s, DenseMeta* meta) {
   if (!at) return fail(CAPS_EINVAL, "attributes are required");
-  if (at->dense == nullptr || at->L <= 0)
-    return fail(CAPS_EINVAL, "sparse label attributes are not supported by this build");
+  if (at->dense == nullptr) {
+    // sparse label sets: codes = labels, two packed words = the signature
+    if (!at->sp_offsets) return fail(CAPS_EINVAL, "attributes need dense values or sparse labels");
+    if (at->sp_vocab < 1 || at->sp_vocab > (1 << 24))
+      return fail(CAPS_EINVAL, "sp_vocab must be in [1, 2^24]");
+    DenseMeta m;
+    m.L = 0;
+    m.words = 2;
+    m.words_pad = 2;
+    m.n_codes = at->sp_vocab;
+    m.sparse = 1;
+    *meta = m;
+    return CAPS_OK;
+  }
+  if (at->L <= 0) return fail(CAPS_EINVAL, "dense attributes need L >= 1");
   if (at->L > kMaxFields) return fail(CAPS_EINVAL, "more than 16 attribute fields");
   std::vector<int32_t> vocab;
   if (int rc = to_host(at->vocab, (size_t)at->L, &vocab, s)) return rc;
@@ -366,6 +389,8 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   keep_pool_warm();
   DenseMeta meta;
   if (int rc = make_meta(attrs, s, &meta)) return rc;
+  if (meta.sparse && p->part == CAPS_PART_MLP)
+    return fail(CAPS_EINVAL, "the learned partitioner serves dense attributes only");
   const int B = p->B, h = p->h, L = meta.L;
   ix->N = N;
   ix->d = d;
@@ -380,15 +405,47 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   const float* dX = nullptr;
   const int32_t* dA = nullptr;
   if (int rc = stage_in(X, (size_t)N * d, scr, s, &dX)) return rc;
-  if (int rc = stage_in(attrs->dense, (size_t)N * L, scr, s, &dA)) return rc;
   int32_t* bad = nullptr;
   if (int rc = scr.get(&bad, 1)) return rc;
   CAPS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
-  if (int rc = launch_check_dense(dA, N, meta, bad, s)) return rc;
+  int32_t* sp_off32 = nullptr;  // sparse: int32 offsets of the input label lists
+  const int32_t* sp_lab_in = nullptr;
+  if (meta.sparse) {
+    int64_t nnz = 0;
+    bool dev = false;
+    if (int rc = is_device_ptr(attrs->sp_offsets, &dev)) return rc;
+    if (dev) {
+      CAPS_CUDA(cudaMemcpyAsync(&nnz, attrs->sp_offsets + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      CAPS_CUDA(cudaStreamSynchronize(s));
+    } else {
+      nnz = attrs->sp_offsets[N];
+    }
+    if (nnz < 0 || nnz >= (int64_t)INT32_MAX) return fail(CAPS_EINVAL, "bad sparse label offsets");
+    if (nnz > 0 && !attrs->sp_labels) return fail(CAPS_EINVAL, "null sp_labels");
+    const int64_t* doff = nullptr;
+    if (int rc = stage_in(attrs->sp_offsets, (size_t)N + 1, scr, s, &doff)) return rc;
+    if (nnz > 0) {
+      if (int rc = stage_in(attrs->sp_labels, (size_t)nnz, scr, s, &sp_lab_in)) return rc;
+    } else {
+      int32_t* z = nullptr;
+      if (int rc = scr.get(&z, 1)) return rc;
+      sp_lab_in = z;
+    }
+    if (int rc = scr.get(&sp_off32, (size_t)N + 1)) return rc;
+    if (int rc = launch_check_sparse(doff, sp_lab_in, N, (int32_t)meta.n_codes, sp_off32, bad, s))
+      return rc;
+    ix->sp_nnz = nnz;
+  } else {
+    if (int rc = stage_in(attrs->dense, (size_t)N * L, scr, s, &dA)) return rc;
+    if (int rc = launch_check_dense(dA, N, meta, bad, s)) return rc;
+  }
   int32_t bad_h = 0;
   CAPS_CUDA(cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CAPS_CUDA(cudaStreamSynchronize(s));
-  if (bad_h) return fail(CAPS_EINVAL, "attribute value outside [0, vocab[f])");
+  if (bad_h)
+    return fail(CAPS_EINVAL, meta.sparse ? "labels must lie in [0, sp_vocab) and ascend strictly "
+                                           "within each point"
+                                         : "attribute value outside [0, vocab[f])");
 
   const int64_t nseg = (int64_t)B * (h + 1);
   if (int rc = ix->alloc(&ix->C, (size_t)B * d)) return rc;
@@ -405,7 +462,13 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   if (int rc = ix->alloc(&ix->Ap, (size_t)(N + 4) * meta.words_pad)) return rc;
   if (int rc = ix->alloc(&ix->err, 1)) return rc;
   CAPS_CUDA(cudaMemsetAsync(ix->err, 0, sizeof(int32_t), s));
-  if (int rc = launch_code_field(meta, ix->code_field, s)) return rc;
+  if (meta.sparse) {
+    CAPS_CUDA(cudaMemsetAsync(ix->code_field, 0, (size_t)meta.n_codes, s));
+    if (int rc = ix->alloc(&ix->sp_off, (size_t)N + 1)) return rc;
+    if (int rc = ix->alloc(&ix->sp_lab, (size_t)std::max<int64_t>(1, ix->sp_nnz))) return rc;
+  } else {
+    if (int rc = launch_code_field(meta, ix->code_field, s)) return rc;
+  }
 
   int32_t *perm_bin = nullptr, *bin_off = nullptr;
   if (int rc = scr.get(&perm_bin, (size_t)N)) return rc;
@@ -450,12 +513,22 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     if (int rc = stable_sort_by_key(ix->bin, N, B, perm_bin, bin_off, scr, s)) return rc;
     // ---- attribute frequency tree per partition (Alg. 1, second loop) ----
     CAPS_CUDA(cudaMemsetAsync(ix->key, 0, (size_t)N, s));
-    if (int rc = launch_aft(perm_bin, bin_off, B, h, dA, meta, ix->code_field, ix->tags, ix->key, s))
+    if (meta.sparse) {
+      if (int rc = launch_aft_sparse(perm_bin, bin_off, B, h, sp_off32, sp_lab_in,
+                                     (int32_t)meta.n_codes, ix->tags, ix->key, s))
+        return rc;
+    } else if (int rc = launch_aft(perm_bin, bin_off, B, h, dA, meta, ix->code_field, ix->tags,
+                                   ix->key, s)) {
       return rc;
+    }
     // ---- contiguous sub-partitions: stable order by (partition, block, id) ----
     if (int rc = launch_segment_keys(ix->bin, ix->key, N, h, seg, s)) return rc;
     if (int rc = stable_sort_by_key(seg, N, nseg, ix->perm, ix->offsets, scr, s)) return rc;
     if (int rc = launch_layout(dX, dA, ix->perm, N, d, meta, ix->Xp, ix->Ap, s)) return rc;
+    if (meta.sparse)
+      if (int rc = launch_layout_sparse(sp_off32, sp_lab_in, ix->perm, N, ix->Ap, ix->sp_off,
+                                        ix->sp_lab, scr, s))
+        return rc;
     CAPS_CUDA(cudaMemsetAsync(ix->pos, 0, (size_t)B * meta.n_codes, s));
     if (int rc = launch_pos_table(ix->tags, B, h, meta.n_codes, ix->pos, s)) return rc;
     return CAPS_OK;
@@ -475,7 +548,8 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
       um[meta.word[f]] |= ((1u << meta.bits[f]) - 1u) << meta.shift[f];
       T += meta.bits[f];
     }
-    ix->pen = 2 * T + (h + 1) <= 64 ? 1 : 0;
+    // (label sets need the exact subset test per key: never the penalty form)
+    ix->pen = !meta.sparse && 2 * T + (h + 1) <= 64 ? 1 : 0;
     ix->pen_bits = T;
     for (int w = 0; w < 4; w++) ix->pen_mask[w] = um[w];
     const int cols = ix->pen ? ((d + 63) / 64 + 1) * 64 : d;
@@ -605,8 +679,56 @@ extern "C" int caps_assign(const float* X, int64_t N, int32_t d, const float* C,
 namespace {
 int check_cons(const caps_index* ix, const caps_attrs* cons) {
   if (!cons) return fail(CAPS_EINVAL, "constraints are required");
+  if (ix->meta.sparse) {
+    if (cons->sp_offsets == nullptr)
+      return fail(CAPS_EINVAL, "a label-set index needs sparse constraints (sp_offsets, sp_labels)");
+    return CAPS_OK;
+  }
   if (cons->dense == nullptr || cons->L != ix->meta.L)
     return fail(CAPS_EINVAL, "constraints must be dense with the index's L fields");
+  return CAPS_OK;
+}
+
+// Device int32 copy of sparse query constraints (offsets [nq+1], labels).
+struct SparseQueries {
+  int32_t* off = nullptr;
+  const int32_t* lab = nullptr;
+};
+int stage_sparse_queries(const caps_attrs* cons, int64_t nq, Scratch& scr, cudaStream_t s,
+                         SparseQueries* out) {
+  bool dev = false;
+  if (int rc = is_device_ptr(cons->sp_offsets, &dev)) return rc;
+  int64_t nnz = 0;
+  if (dev) {
+    CAPS_CUDA(cudaMemcpyAsync(&nnz, cons->sp_offsets + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CAPS_CUDA(cudaStreamSynchronize(s));
+  } else {
+    nnz = cons->sp_offsets[nq];
+  }
+  if (nnz < 0 || nnz > INT32_MAX) return fail(CAPS_EINVAL, "bad sparse constraint offsets");
+  if (nnz > 0 && !cons->sp_labels) return fail(CAPS_EINVAL, "null sp_labels");
+  const int64_t* doff = nullptr;
+  if (int rc = stage_in(cons->sp_offsets, (size_t)nq + 1, scr, s, &doff)) return rc;
+  const int32_t* dlab = nullptr;
+  if (nnz > 0) {
+    if (int rc = stage_in(cons->sp_labels, (size_t)nnz, scr, s, &dlab)) return rc;
+  } else {
+    int32_t* z = nullptr;
+    if (int rc = scr.get(&z, 1)) return rc;
+    dlab = z;
+  }
+  int32_t *o32 = nullptr, *bad = nullptr;
+  if (int rc = scr.get(&o32, (size_t)nq + 1)) return rc;
+  if (int rc = scr.get(&bad, 1)) return rc;
+  CAPS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
+  k_offsets_i32<<<(unsigned)((nq + 1 + 255) / 256), 256, 0, s>>>(doff, nq + 1, o32, bad);
+  CAPS_LAUNCH("k_offsets_i32");
+  int32_t bad_h = 0;
+  CAPS_CUDA(cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  if (bad_h) return fail(CAPS_EINVAL, "sparse constraint offsets must be non-decreasing");
+  out->off = o32;
+  out->lab = dlab;
   return CAPS_OK;
 }
 
@@ -693,9 +815,19 @@ extern "C" int caps_select(const caps_index* ix, const int32_t* probe, int64_t n
     if (b < 0 || b >= ix->B) return fail(CAPS_EINVAL, "probe entry outside [0, B)");
   const int32_t *dP = nullptr, *dQb = nullptr;
   if (int rc = stage_in(probe, (size_t)nq * m, scr, s, &dP)) return rc;
-  if (int rc = stage_in(cons->dense, (size_t)nq * ix->meta.L, scr, s, &dQb)) return rc;
   Out<uint64_t> os;
   if (int rc = os.init(out_sel, (size_t)nq * m, scr)) return rc;
+  if (ix->meta.sparse) {
+    SparseQueries sq;
+    if (int rc = stage_sparse_queries(cons, nq, scr, s, &sq)) return rc;
+    if (int rc = launch_select_sparse(dP, nq, m, ix->h, ix->tags, ix->pos, ix->meta.n_codes,
+                                      sq.off, sq.lab, os.dev, s))
+      return rc;
+    if (int rc = os.finish(s)) return rc;
+    if (os.host) CAPS_CUDA(cudaStreamSynchronize(s));
+    return CAPS_OK;
+  }
+  if (int rc = stage_in(cons->dense, (size_t)nq * ix->meta.L, scr, s, &dQb)) return rc;
   QueryPrep qp;
   const int WP = ix->meta.words_pad, L = ix->meta.L;
   if (int rc = scr.get(&qp.qmask, (size_t)nq * WP)) return rc;
@@ -830,8 +962,13 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
   Scratch scr(s);
   const float* dQ = nullptr;
   const int32_t* dQb = nullptr;
+  SparseQueries sq;
   if (int rc = stage_in(Q, (size_t)nq * ix->d, scr, s, &dQ)) return rc;
-  if (int rc = stage_in(cons->dense, (size_t)nq * ix->meta.L, scr, s, &dQb)) return rc;
+  if (ix->meta.sparse) {
+    if (int rc = stage_sparse_queries(cons, nq, scr, s, &sq)) return rc;
+  } else if (int rc = stage_in(cons->dense, (size_t)nq * ix->meta.L, scr, s, &dQb)) {
+    return rc;
+  }
   Out<int64_t> oi;
   Out<float> od;
   if (int rc = oi.init(out_ids, (size_t)nq * k, scr)) return rc;
@@ -882,20 +1019,37 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
   for (int64_t c0 = 0; c0 < nq; c0 += qc) {
     const int64_t n = std::min(qc, nq - c0);
     const float* Qc = dQ + c0 * ix->d;
-    const int32_t* Qbc = dQb + c0 * L;
+    const int32_t* Qbc = dQb ? dQb + c0 * L : nullptr;
+    SparseRef sp;  // label sets: rows (layout order) and this chunk's queries
+    if (ix->meta.sparse) {
+      sp.roff = ix->sp_off;
+      sp.rlab = ix->sp_lab;
+      sp.qoff = sq.off + c0;
+      sp.qlab = sq.lab;
+    }
     Scratch cscr(s);  // per-chunk grouping temporaries
     if (int rc = tm.record(s)) return rc;
-    if (int rc = launch_query_prep(Qbc, n, ix->meta, bt.qp, s)) return rc;
+    if (ix->meta.sparse) {
+      if (int rc = launch_query_prep_sparse(sp.qoff, sp.qlab, n, ix->meta, bt.qp, s)) return rc;
+    } else if (int rc = launch_query_prep(Qbc, n, ix->meta, bt.qp, s)) {
+      return rc;
+    }
     if (int rc = tm.record(s)) return rc;
     if (int rc = partition_scores(ix, Qc, n, bt.scores, mlp_hidden, s)) return rc;
     if (int rc = tm.record(s)) return rc;
     if (int rc = launch_topm(bt.scores, n, ix->B, m, probe_metric(ix), bt.probe, s)) return rc;
     if (int rc = tm.record(s)) return rc;
-    if (int rc = launch_select(bt.probe, n, m, ix->h, ix->tags, ix->pos, ix->meta.n_codes,
-                               ix->code_field, Qbc, ix->meta, bt.qp.qcode, bt.sel, s))
+    if (ix->meta.sparse) {
+      if (int rc = launch_select_sparse(bt.probe, n, m, ix->h, ix->tags, ix->pos,
+                                        ix->meta.n_codes, sp.qoff, sp.qlab, bt.sel, s))
+        return rc;
+    } else if (int rc = launch_select(bt.probe, n, m, ix->h, ix->tags, ix->pos, ix->meta.n_codes,
+                                      ix->code_field, Qbc, ix->meta, bt.qp.qcode, bt.sel, s)) {
       return rc;
+    }
     if (int rc = tm.record(s)) return rc;
     ScanArgs a;
+    a.sp = sp;
     a.Xp = ix->Xp;
     a.Ap = ix->Ap;
     a.perm = ix->perm;
@@ -944,6 +1098,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
       if (int rc = cscr.get(&qslot, (size_t)n * 8)) return rc;
       CAPS_CUDA(cudaMemsetAsync(qslot, 0xFF, sizeof(uint64_t) * (size_t)n * 8, s));
       t.qslot = qslot;
+      t.sp = sp;
       t.words_pad = ix->meta.words_pad;
       t.metric = ix->metric;
       t.part = part;
@@ -1057,6 +1212,7 @@ extern "C" int caps_plan_create(const caps_index* ix, const float* Q, int64_t nq
   if (nq < 1) return fail(CAPS_EINVAL, "a plan needs nq >= 1");
   if (k < 1 || k > kMaxK) return fail(CAPS_EINVAL, "k must be in [1, 128]");
   if (m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
+  if (ix->meta.sparse) return fail(CAPS_EINVAL, "plans serve dense constraints only");
   if (int rc = check_cons(ix, cons)) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   std::unique_ptr<caps_plan> p(new caps_plan());

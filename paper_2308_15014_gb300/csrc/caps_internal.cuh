@@ -33,7 +33,42 @@ struct DenseMeta {
   int words = 0;       // packed words actually used (1..4)
   int words_pad = 0;   // row stride in words: 1, 2 or 4 (vector loads)
   int64_t n_codes = 0;
+  // sparse label sets: L = 0, n_codes = the label vocabulary, and the two
+  // packed words of a row hold its 64-bit label signature (bit
+  // sig_bit(label) set for every label), so "(a & mask) == val" with
+  // mask = val = the query's signature is a necessary condition for b <= a
+  int sparse = 0;
 };
+
+// Signature bit of a sparse label (Fibonacci hashing of the label id).
+__host__ __device__ __forceinline__ int sig_bit(int32_t label) {
+  return (int)(((uint32_t)label * 2654435769u) >> 26);
+}
+
+// Sparse label filter (Def. 1, label sets): is every label the query requires
+// present in the row's sorted label list?  roff/rlab: rows in layout order;
+// qoff/qlab: the queries of the current chunk.  roff == nullptr: dense.
+struct SparseRef {
+  const int32_t* roff = nullptr;  // [N+1]
+  const int32_t* rlab = nullptr;
+  const int32_t* qoff = nullptr;  // [nq+1] (positions into qlab)
+  const int32_t* qlab = nullptr;
+};
+__device__ __forceinline__ bool sp_subset(const SparseRef& s, int64_t row, int64_t q) {
+  const int rb = s.roff[row], re = s.roff[row + 1];
+  const int qe = s.qoff[q + 1];
+  for (int i = s.qoff[q]; i < qe; i++) {
+    const int32_t c = s.qlab[i];
+    int lo = rb, hi = re;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (s.rlab[mid] < c) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo == re || s.rlab[lo] != c) return false;
+  }
+  return true;
+}
 
 // ---- orderable keys: (score, id) -> uint64, smaller key = better --------
 // score is the fp32 distance for L2 and minus the inner product for IP; the
@@ -195,6 +230,17 @@ int launch_centroid_update(const float* X, int d, const int32_t* perm_bin,
                            Scratch& scr, cudaStream_t s);
 int launch_check_dense(const int32_t* A, int64_t N, const DenseMeta& meta,
                        int32_t* bad, cudaStream_t s);
+// sparse label sets (CSR, int64 offsets): every label in [0, V), strictly
+// ascending per point; *bad = 1 otherwise.  Also writes int32 offsets.
+int launch_check_sparse(const int64_t* off, const int32_t* lab, int64_t N, int32_t V,
+                        int32_t* off32, int32_t* bad, cudaStream_t s);
+int launch_aft_sparse(const int32_t* perm_bin, const int32_t* bin_off, int B, int h,
+                      const int32_t* off, const int32_t* lab, int32_t V, int32_t* tags,
+                      uint8_t* key, cudaStream_t s);
+// signature words and label lists of the rows in layout order
+int launch_layout_sparse(const int32_t* off, const int32_t* lab, const int32_t* perm, int64_t N,
+                         uint32_t* Ap, int32_t* off_p, int32_t* lab_p, Scratch& scr,
+                         cudaStream_t s);
 int launch_aft(const int32_t* perm_bin, const int32_t* bin_off, int B, int h,
                const int32_t* A, const DenseMeta& meta, const uint8_t* code_field,
                int32_t* tags, uint8_t* key, cudaStream_t s);
@@ -216,6 +262,16 @@ struct QueryPrep {
 };
 int launch_query_prep(const int32_t* Qb, int64_t nq, const DenseMeta& meta,
                       QueryPrep qp, cudaStream_t s);
+// sparse constraints: qoff [nq+1] / qlab (int32, device); signature words,
+// dead = a label outside [0, vocab)
+int launch_query_prep_sparse(const int32_t* qoff, const int32_t* qlab, int64_t nq,
+                             const DenseMeta& meta, QueryPrep qp, cudaStream_t s);
+// sparse rule of Alg. 2: j* = the first block whose tag the query requires;
+// blocks 1..min(j*, h) that have a tag (every tag is compatible with a label
+// set) and h+1 iff j* = h+1
+int launch_select_sparse(const int32_t* probe, int64_t nq, int m, int h, const int32_t* tags,
+                         const uint8_t* pos, int64_t n_codes, const int32_t* qoff,
+                         const int32_t* qlab, uint64_t* sel, cudaStream_t s);
 int launch_topm(const float* scores, int64_t nq, int B, int m, int metric,
                 int32_t* probe, cudaStream_t s);
 int launch_select(const int32_t* probe, int64_t nq, int m, int h, const int32_t* tags,
@@ -236,6 +292,7 @@ struct ScanArgs {
   int m, h, d, k, metric, words_pad;
   int64_t* out_ids;
   float* out_dist;
+  SparseRef sp;  // sparse label sets: exact check after the signature test
 };
 int launch_scan_topk(const ScanArgs& a, cudaStream_t s);
 
@@ -300,6 +357,7 @@ struct TcScanArgs {
   uint32_t pen_mask[4]; // which bits of each packed word are encoded
   float xn_max;         // largest squared row norm
   uint64_t* qslot;      // [nq*8] bound slots per query, set to all ones before the scan
+  SparseRef sp;         // sparse label sets: exact check before a key is queued
   uint64_t* part;       // [nq*m*kp]
   int32_t* err;
 };
@@ -373,6 +431,10 @@ struct caps_index {
   int pen_bits = 0;
   uint32_t pen_mask[4] = {};
   float xn_max = 0.f;
+  // sparse label sets of the rows, in layout order (CSR)
+  int32_t* sp_off = nullptr;  // [N+1]
+  int32_t* sp_lab = nullptr;  // [nnz]
+  int64_t sp_nnz = 0;
   // launch shapes the autotuner chose, per (k, m): rows per tile, probes per
   // item, penalty form; later caps_search_batch calls with that (k, m) use them
   struct Shape {

@@ -92,6 +92,7 @@ extern "C" int caps_search_batch_noalloc(const caps_index* ix, const float* Q, i
   if (nq < 0) return fail(CAPS_EINVAL, "nq < 0");
   if (k < 1 || k > kMaxK) return fail(CAPS_EINVAL, "k must be in [1, 128]");
   if (m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
+  if (ix->meta.sparse) return fail(CAPS_EINVAL, "the no-allocation query serves dense attributes only");
   if (!cons || cons->dense == nullptr || cons->L != ix->meta.L)
     return fail(CAPS_EINVAL, "constraints must be dense with the index's L fields");
   if (ix->part != CAPS_PART_KMEANS)

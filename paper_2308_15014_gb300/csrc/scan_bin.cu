@@ -164,6 +164,7 @@ struct BinScanArgs {
   int m, h, d, k, R;
   uint64_t* part;          // [nq*m*k] keys
   int32_t* err;
+  SparseRef sp;            // label sets: exact check after the signature test
 };
 
 // DV = d / 32 float4 pieces per lane (d a multiple of 32).
@@ -358,6 +359,8 @@ k_scan_bin(BinScanArgs a) {
           bool pass = in && ((ps[u] >> bj) & 1ull);
 #pragma unroll
           for (int w = 0; w < WP; w++) pass = pass && ((aw[w] & pqm[u][w]) == pqv[u][w]);
+          // label sets: the signature test is necessary, this is exact
+          if (pass && a.sp.roff) pass = sp_subset(a.sp, lo + r, p_q[PPW * warp + u]);
           pm[u] |= (uint64_t)__ballot_sync(0xffffffffu, pass) << g0;
         }
       }
@@ -614,6 +617,7 @@ int bin_scan(const ScanArgs& a, const BinWork& w, uint64_t* part, int32_t* err, 
   b.R = a.d <= 128 ? 64 : 32;
   b.part = part;
   b.err = err;
+  b.sp = a.sp;
   const size_t smem = bin_smem_total(b.R, a.d, a.words_pad);
   return a.metric == CAPS_L2 ? launch_bin_w<CAPS_L2>(b, a.words_pad, w.max_items, smem, s)
                              : launch_bin_w<CAPS_IP>(b, a.words_pad, w.max_items, smem, s);

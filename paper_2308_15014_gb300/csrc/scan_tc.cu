@@ -503,6 +503,7 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   for (int i = 0; i < 4; i++) a.pen_mask[i] = t.pen_mask[i];
   a.xn_max = t.xn_max;
   a.qslot = t.qslot;
+  a.sp = t.sp;
   {
     const int depth = std::min(t.rerank, t.m * t.kp);  // keys the merge keeps per query
     a.nslot = std::min(TC_SLOTS, std::max(1, (depth + t.kp - 1) / t.kp));

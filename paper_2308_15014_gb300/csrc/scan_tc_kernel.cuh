@@ -71,6 +71,7 @@ struct TcArgs {
   float xn_max;          // largest squared row norm
   uint64_t* qslot;       // [nq*8] per-query bound slots, all ones at the start
   int nslot;             // slots in use: ceil(rerank depth / kp)
+  SparseRef sp;          // label sets: exact check before a key is queued
   uint64_t* part;        // [nq*m*kp]
   int32_t* err;
 };
@@ -574,6 +575,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       }
       const float my_qn = p_qn[probe];
       const float my_cut = PEN ? p_cut[probe] : 0.f;
+      const int my_q = active ? p_e[par][probe] / a.m : 0;
       __syncwarp();
       if (lane == 0) mbar_arrive(&taken_bar);  // the producer may refill the probe data
       uint64_t* pthr = p_thr[par];
@@ -679,7 +681,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
                 const float dot = __uint_as_float(cur[j]);
                 const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r] + my_qn) : -dot;
                 const uint64_t key = make_key(sc, (uint32_t)prm[r]);
-                if (key < thr) {
+                // label sets: the signature test above is necessary; the
+                // exact test runs only for keys that would enter the list
+                if (key < thr && (!a.sp.roff || sp_subset(a.sp, lo + r, my_q))) {
                   queue[(size_t)qcnt * TC_C + tid] = key;
                   qcnt++;
                 }

@@ -47,6 +47,69 @@ __global__ void k_query_prep(const int32_t* __restrict__ Qb, int64_t nq, DenseMe
 }
 }  // namespace
 
+namespace {
+__global__ void k_query_prep_sparse(const int32_t* __restrict__ qoff, const int32_t* __restrict__ qlab,
+                                    int64_t nq, int32_t V, QueryPrep qp) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  uint64_t sig = 0ull;
+  uint8_t dead = 0;
+  for (int i = qoff[q]; i < qoff[q + 1]; i++) {
+    const int32_t c = qlab[i];
+    if (c < 0 || c >= V) dead = 1;
+    else sig |= 1ull << sig_bit(c);
+  }
+  qp.qmask[2 * q] = qp.qval[2 * q] = (uint32_t)sig;
+  qp.qmask[2 * q + 1] = qp.qval[2 * q + 1] = (uint32_t)(sig >> 32);
+  qp.dead[q] = dead;
+}
+
+__global__ void k_select_sparse(const int32_t* __restrict__ probe, int64_t nq, int m, int h,
+                                const int32_t* __restrict__ tags,
+                                const uint8_t* __restrict__ pos, int64_t n_codes,
+                                const int32_t* __restrict__ qoff, const int32_t* __restrict__ qlab,
+                                uint64_t* __restrict__ sel) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nq * m) return;
+  const int64_t q = t / m;
+  const int b = probe[t];
+  int jstar = h + 1;
+  for (int i = qoff[q]; i < qoff[q + 1]; i++) {
+    const int32_t c = qlab[i];
+    if (c < 0 || c >= n_codes) continue;
+    const int p = pos[(int64_t)b * n_codes + c];
+    if (p > 0 && p < jstar) jstar = p;
+  }
+  // every tag is compatible with a label set; a block without a tag is empty
+  const int jmax = jstar < h ? jstar : h;
+  uint64_t s = 0;
+  for (int j = 1; j <= jmax; j++)
+    if (tags[(int64_t)b * h + j - 1] >= 0) s |= 1ull << (j - 1);
+  if (jstar == h + 1) s |= 1ull << h;
+  sel[t] = s;
+}
+}  // namespace
+
+int launch_query_prep_sparse(const int32_t* qoff, const int32_t* qlab, int64_t nq,
+                             const DenseMeta& meta, QueryPrep qp, cudaStream_t s) {
+  if (nq == 0) return CAPS_OK;
+  k_query_prep_sparse<<<(unsigned)((nq + 127) / 128), 128, 0, s>>>(qoff, qlab, nq,
+                                                                  (int32_t)meta.n_codes, qp);
+  CAPS_LAUNCH("k_query_prep_sparse");
+  return CAPS_OK;
+}
+
+int launch_select_sparse(const int32_t* probe, int64_t nq, int m, int h, const int32_t* tags,
+                         const uint8_t* pos, int64_t n_codes, const int32_t* qoff,
+                         const int32_t* qlab, uint64_t* sel, cudaStream_t s) {
+  const int64_t tot = nq * m;
+  if (tot == 0) return CAPS_OK;
+  k_select_sparse<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(probe, nq, m, h, tags, pos,
+                                                                n_codes, qoff, qlab, sel);
+  CAPS_LAUNCH("k_select_sparse");
+  return CAPS_OK;
+}
+
 int launch_query_prep(const int32_t* Qb, int64_t nq, const DenseMeta& meta, QueryPrep qp,
                       cudaStream_t s) {
   if (nq == 0) return CAPS_OK;
@@ -432,6 +495,8 @@ k_scan_topk(ScanArgs a) {
               pass = ((w.x & qm[0]) == qv[0]) && ((w.y & qm[1]) == qv[1]) &&
                      ((w.z & qm[2]) == qv[2]) && ((w.w & qm[3]) == qv[3]);
             }
+            // label sets: the signature test is necessary, this is exact
+            if (pass && a.sp.roff) pass = sp_subset(a.sp, r, q);
           }
           const unsigned bal = __ballot_sync(0xffffffffu, pass);
           if (pass) queue[qn + __popc(bal & ((1u << lane) - 1u))] = r;
