@@ -34,6 +34,7 @@ METRIC = ("filtered QPS at recall@10>=0.9 (learned partitioner + BF16 tensor-cor
           "plain FP32 k-means path alongside)")
 UNIT = "queries/s"
 M_SWEEP = (8, 12, 16, 24, 32, 40, 48, 64)
+SPARSE_M_SWEEP = (8, 16, 32, 64, 128, 256)
 RECALL_SAMPLE = 500
 FALLBACK_HBM_GBS = 6800.0
 # fp32 peak from unit counts and clock: 152 SMs x 128 fp32 lanes x 2 flop
@@ -43,7 +44,7 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_GHZ / 1e3
 SCAN_KERNEL = "k_scan_bin"
 SCAN_SRC = "scan_bin.cu"
 TC_KERNEL = "k_scan_tc"
-TC_SRC = "scan_tc.cu"
+TC_SRC = "scan_tc_kernel.cuh"
 
 
 def _json_default(o):
@@ -66,6 +67,9 @@ def parse():
     ap.add_argument("--paths", default="mlp_bf16,fp32,bf16",
                     help="comma list of search paths (fp32, bf16, mlp_fp32, mlp_bf16); "
                          "the first is the headline")
+    ap.add_argument("--sparse", action="store_true",
+                    help="also measure the label-set workload (2M x 128, 10,000 labels, "
+                         "4,096 queries); adds about two minutes")
     return ap.parse_args()
 
 
@@ -224,9 +228,10 @@ def dense_item_stats(w, offsets, probe, sel, group=128):
     return int(items), int(rows), int(pairs)
 
 
-def traffic_from_profile(kernel=SCAN_KERNEL, src_name=SCAN_SRC):
+def traffic_from_profile(kernel=SCAN_KERNEL, src_name=SCAN_SRC, m=None):
     """dram bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current source of that kernel (else None)."""
+    was taken on the current source of that kernel and, where the entry names
+    one, at the same probe count m (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2308_15014_gb300", "csrc", src_name)
     if not os.path.exists(p):
@@ -236,9 +241,94 @@ def traffic_from_profile(kernel=SCAN_KERNEL, src_name=SCAN_SRC):
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
     for e in entries:
-        if e.get("kernel") == kernel and e.get("src_sha") == sha:
+        if e.get("kernel") == kernel and e.get("src_sha") == sha and \
+                (m is None or e.get("m") in (None, m)):
             return e.get("dram_bytes_per_launch")
     return None
+
+
+def form1_error(w, rng_seed=11, nq=64, nrow=2048):
+    """Relative error of the BF16 tile score against the FP64 distance.
+
+    The tensor-core tile multiplies bf16-rounded vectors and accumulates in
+    fp32; the score is |x|^2 + |q|^2 - 2 q.x with fp32 norms.  Here the bf16
+    rounding is applied to x and q, the products are summed in fp64 (the
+    fp32 accumulation adds at most ~d * 2^-24 relative), and the result is
+    compared with the exact squared distance in fp64 on random (query, row)
+    pairs.  The returned distances themselves are exact fp32 (re-ranked)."""
+    rng = np.random.default_rng(rng_seed)
+    qi = rng.choice(w.Q.shape[0], min(nq, w.Q.shape[0]), replace=False)
+    ri = rng.choice(w.X.shape[0], min(nrow, w.X.shape[0]), replace=False)
+    X = w.X[ri].astype(np.float64)
+    Q = w.Q[qi].astype(np.float64)
+
+    def bf16(a):
+        u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+        u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000  # round to nearest even
+        return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+    xn = (X * X).sum(1)
+    qn = (Q * Q).sum(1)
+    approx = xn[None, :] + qn[:, None] - 2.0 * (bf16(Q) @ bf16(X).T)
+    exact = ((Q[:, None, :] - X[None, :, :]) ** 2).sum(-1)
+    rel = np.abs(approx - exact) / np.maximum(exact, 1e-30)
+    return {"pairs": int(rel.size), "max_rel": float(rel.max()), "mean_rel": float(rel.mean())}
+
+
+def sparse_line(args, caps, O, torch):
+    """Label-set workload (2M x 128 fp32 mixture, 10,000-label vocabulary,
+    1-20 labels per point, queries requiring 1-8 labels): build, probe sweep,
+    recall against the oracle's exact filtered kNN on a query sample, QPS of
+    the batched query (device buffers, CUDA events, L2 flushed)."""
+    from workloads import config_sparse2m
+    t0 = time.perf_counter()
+    w = config_sparse2m()
+    gen_s = time.perf_counter() - t0
+    rng = np.random.default_rng(6)
+    samp = np.sort(rng.choice(w.nq, 200, replace=False))
+    cons = O.Cons(q_off=w.q_off, q_lab=w.q_lab)
+    sub = cons.subset(samp)
+    gt, _, g64, cnt = O.bruteforce(w.X, O.Attrs.of(w), w.Q[samp], sub, w.k)
+    Qd = torch.from_numpy(w.Q).cuda()
+    qoff = torch.from_numpy(w.q_off).cuda()
+    qlab = torch.from_numpy(w.q_lab).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"workload": w.name, "N": w.N, "d": w.d, "labels": int(w.sp_vocab),
+           "queries_per_step": w.nq, "generate_s": round(gen_s, 1), "paths": {}}
+    for name, prec in (("fp32", caps.FP32), ("bf16", caps.BF16)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = caps.Index.build(torch.from_numpy(w.X).cuda(), None, None, w.B, h=w.h,
+                              iters=w.iters, init_idx=w.init_idx, prec=prec,
+                              labels=(w.sp_off, w.sp_lab, w.sp_vocab))
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        ids = torch.empty((w.nq, w.k), dtype=torch.int64, device="cuda")
+        dist = torch.empty((w.nq, w.k), dtype=torch.float32, device="cuda")
+        sweep, chosen = [], None
+        for m in SPARSE_M_SWEEP:
+            ix.search(Qd, (qoff, qlab), w.k, m, out_ids=ids, out_dist=dist)
+            strict, tie, _, _ = O.recall(ids.cpu().numpy()[samp], gt, g64, cnt, w.k, X=w.X,
+                                         Q=w.Q[samp])
+            evs = []
+            for _ in range(max(3, args.warmup)):
+                ix.search(Qd, (qoff, qlab), w.k, m, out_ids=ids, out_dist=dist)
+            for _ in range(5):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ix.search(Qd, (qoff, qlab), w.k, m, out_ids=ids, out_dist=dist)
+                e1.record()
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
+            sweep.append({"m": m, "recall_tie": round(tie, 4), "recall_strict": round(strict, 4),
+                          "qps": round(w.nq / (ms / 1e3), 1), "ms": round(ms, 4)})
+            if chosen is None and tie >= 0.9:
+                chosen = m
+        out["paths"][name] = {"build_s": round(build_s, 2), "m_at_0.9": chosen, "sweep": sweep}
+        ix.close()
+    return out
 
 
 def oracle_baseline(w, m, k, budget_s=15.0):
@@ -373,6 +463,7 @@ def measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world, local
     run(m)
     torch.cuda.synchronize()
     p_ids = out_ids.cpu().numpy()[samp]
+    p_dist = out_dist.cpu().numpy()[samp]
     search(m)
     assert np.array_equal(p_ids, out_ids.cpu().numpy()[samp]), "plan and direct call disagree"
 
@@ -415,7 +506,7 @@ def measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world, local
     launches = int(round(stage.pop("launches")))
     return dict(ix=ix, plan=plan, m=m, rec=rec, sweep=sweep, value=value, ms=ms, stage=stage,
                 launches=launches, build_s=build_s, clocks=clk.summary(),
-                direct_ms=direct_ms, tuning=plan.info)
+                direct_ms=direct_ms, tuning=plan.info, ids_s=p_ids, dist_s=p_dist)
 
 
 def run_caps(args):
@@ -468,7 +559,8 @@ def run_caps(args):
         bf16_peak, bf16_src = bf16_peak_tflops()
         roof = {"kernel": TC_KERNEL, "bound": "tensor", "achieved": round(tflops, 2),
                 "peak": bf16_peak, "peak_source": bf16_src, "unit": "TFLOP/s",
-                "frac": round(tflops / bf16_peak, 4), "traffic": traffic_from_profile(TC_KERNEL, TC_SRC),
+                "frac": round(tflops / bf16_peak, 4),
+                "traffic": traffic_from_profile(TC_KERNEL, TC_SRC, m),
                 "algorithmic_flops": flops, "rows_attr_tested": rows_scanned,
                 "rows_distance": rows_passed, "work_items": d_items,
                 "item_union_rows": d_rows, "item_dense_pairs": d_pairs}
@@ -503,6 +595,22 @@ def run_caps(args):
         plan.search(Qh, Qbh, out_ids=ids_h, out_dist=dist_h)  # returns after the D2H copies
         e2e_t.append(time.perf_counter() - t0)
     e2e_v = world * w.nq / float(np.mean(e2e_t))
+
+    # ---- form 1: bf16 tile scores and returned distances against fp64 -------
+    from workloads import make_dense_workload
+    wf = make_dense_workload(name="float_mixture", N=20_000, d=w.d, ncomp=100,
+                             center=("uniform", 128.0), sigma=16.0, vocab=[20, 50, 100],
+                             zipf_s=1.0, nq=200, cmin=1, cmax=3, B=64, h=15, iters=1, m=4,
+                             k=10, seed=77, integer=False)
+    hid, hdist = head["ids_s"], head["dist_s"]
+    okm = hid >= 0
+    qs = np.repeat(samp[:, None], hid.shape[1], 1)[okm]
+    d64 = ((w.X[hid[okm]].astype(np.float64) - w.Q[qs].astype(np.float64)) ** 2).sum(1)
+    rel = np.abs(hdist[okm].astype(np.float64) - d64) / np.maximum(d64, 1e-30)
+    form1 = {"tile_score_vs_fp64": {w.name: form1_error(w), "float_mixture_d128": form1_error(wf)},
+             "returned_dist_vs_fp64": {"pairs": int(rel.size), "max_rel": float(rel.max()),
+                                       "mean_rel": float(rel.mean())}}
+    sparse = sparse_line(args, caps, O, torch) if args.sparse and world == 1 else None
 
     if rank != 0:
         return 0
@@ -547,7 +655,10 @@ def run_caps(args):
         "gpu_launches": head["launches"] * args.steps,
         "clocks": head["clocks"],
         "cpu_baseline": cpu,
+        "form1_error": form1,
     }
+    if sparse is not None:
+        line["label_sets"] = sparse
     print(json.dumps(line, default=_json_default), flush=True)
     for r in res.values():
         r["plan"].close()

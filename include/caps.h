@@ -64,8 +64,15 @@ typedef enum { CAPS_FP32 = 0, CAPS_BF16 = 1, CAPS_FP8E4M3 = 2 } caps_precision;
  *   sparse: L = 0, dense = NULL; point i carries the label set
  *           sp_labels[sp_offsets[i] .. sp_offsets[i+1]) (int32 in
  *           [0, sp_vocab), sorted ascending, no repeats), sp_offsets = [N+1]
- *           int64.  For a query the set lists the REQUIRED labels; the
- *           filter holds when every required label is present.
+ *           int64.  For a query the set lists the REQUIRED labels (any
+ *           order; an empty set constrains nothing, a label outside
+ *           [0, sp_vocab) matches no point); the filter holds when every
+ *           required label is present.  sp_vocab may be 0 for queries.
+ *           On the GPU each row also carries a 64-bit signature of its
+ *           labels: the scans test it first and run the exact subset test
+ *           on the row's sorted labels only for the pairs that pass it.
+ *           The learned partitioner, query plans and the no-allocation
+ *           query serve dense attributes only (CAPS_EINVAL).
  */
 typedef struct {
   int32_t L;
@@ -155,9 +162,11 @@ typedef struct {
  * sum(vocab[0..f-1]) + value), then a stable sort by (partition, block, id)
  * into contiguous sub-partitions.  Inputs may be freed on return.
  * Returns CAPS_EINVAL for N < 1, d < 1, B outside [1, N], h outside [0, 63],
- * bad attribute values, a dense packing wider than 128 bits, sparse
- * attributes (not yet supported by this build), or an MLP build without
- * epochs and without initial weights.
+ * bad attribute values (dense: outside [0, vocab[f]); sparse: outside
+ * [0, sp_vocab) or not strictly ascending within a point), a dense packing
+ * wider than 128 bits, sparse attributes with the learned partitioner, or an
+ * MLP build without epochs and without initial weights.  For sparse
+ * attributes a code is the label itself and the peel counts labels.
  */
 int caps_build(const caps_build_params* params, const float* X, int64_t N,
                int32_t d, const caps_attrs* attrs, void* stream,
@@ -166,12 +175,14 @@ int caps_build(const caps_build_params* params, const float* X, int64_t N,
 /*
  * caps_search_batch -- Alg. 2 (CAPS query) for nq queries.
  * Q = [nq*d] fp32; constraints = the queries' attribute constraints in the
- * form the index was built with (dense: [nq*L], -1 = unconstrained).
+ * form the index was built with (dense: [nq*L], -1 = unconstrained;
+ * sparse: the required labels, CSR).
  * For each query: the m partitions with the best centroid score are probed
  * (ties to the lower partition); in each, the sub-partitions that can hold a
  * valid point are selected (Alg. 2; every block up to the first block whose
- * tag the query carries, skipping blocks whose tag contradicts the query, and
- * the remainder block only when no tag matches); every row of those blocks
+ * tag the query carries, skipping blocks whose tag contradicts the query (a
+ * label set contradicts no tag), and the remainder block only when no tag
+ * matches); every row of those blocks
  * is filtered with Def. 1 and its distance computed in fp32 (coordinates in
  * order, one fused multiply-add each); the k best are kept.
  * out_ids = [nq*k] int64 original point ids, best first, ties to the lower
