@@ -124,13 +124,112 @@ __global__ void k_softmax_xent(const float* __restrict__ Z, const float* __restr
   if (lane == 0) atomicAdd(loss, (double)l * (double)inv_n);
 }
 
-// Column sums (bias gradients), rows in order.
-__global__ void k_colsum(const float* __restrict__ D, int n, int ncol, float* __restrict__ out) {
+// Column sums (bias gradients) in a fixed order: chunks of CS_ROWS rows, in
+// each chunk 8 row lanes (rows r = lane, lane + 8, ...) summed in order and
+// then the 8 lanes in order; k_colsum_fin adds the chunks in order.
+constexpr int CS_ROWS = 256;
+__global__ void __launch_bounds__(256)
+k_colsum_part(const float* __restrict__ D, int n, int ncol, float* __restrict__ part) {
+  __shared__ float red[8][33];
+  const int cx = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + cx;
+  const int r0 = blockIdx.y * CS_ROWS, r1 = min(n, r0 + CS_ROWS);
+  float s = 0.f;
+  if (c < ncol)
+    for (int i = r0 + g; i < r1; i += 8) s += D[(int64_t)i * ncol + c];
+  red[g][cx] = s;
+  __syncthreads();
+  if (g == 0 && c < ncol) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; q++) t += red[q][cx];
+    part[(int64_t)blockIdx.y * ncol + c] = t;
+  }
+}
+__global__ void k_colsum_fin(const float* __restrict__ part, int nchunk, int ncol,
+                             float* __restrict__ out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncol) return;
   float s = 0.f;
-  for (int i = 0; i < n; i++) s += D[(int64_t)i * ncol + c];
+  for (int q = 0; q < nchunk; q++) s += part[(int64_t)q * ncol + c];
   out[c] = s;
+}
+
+// C[M,N] = A[M,K] . B[N,K]^T (+ bias, relu) for the forward pass: 128 x 128
+// tiles, 8 x 8 outputs per thread, k in steps of 8 through double-buffered
+// shared memory.  Every output is the same fma chain over k in order as in
+// k_gemm, so the two kernels agree bit for bit.  Needs K % 8 == 0 and
+// 16-byte aligned rows (lda, ldb multiples of 4).
+constexpr int TM = 128, TN = 128, TK = 8, TPAD = 4;
+template <int EPI>
+__global__ void __launch_bounds__(256)
+k_gemm_big(const float* __restrict__ A, int lda, const float* __restrict__ Bm, int ldb,
+           float* __restrict__ C, int ldc, int M, int N, int K, const float* __restrict__ bias) {
+  __shared__ __align__(16) float As[2][TK][TM + TPAD];
+  __shared__ __align__(16) float Bs[2][TK][TN + TPAD];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  // loader: thread t brings row t/2, k-offset 4*(t%2) of both tiles
+  const int lr = tid >> 1, lk = (tid & 1) * 4;
+  const bool am = m0 + lr < M, bn = n0 + lr < N;
+  const float* ap = A + (int64_t)(am ? m0 + lr : 0) * lda + lk;
+  const float* bp = Bm + (int64_t)(bn ? n0 + lr : 0) * ldb + lk;
+  float4 ra = am ? *reinterpret_cast<const float4*>(ap) : make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 rb = bn ? *reinterpret_cast<const float4*>(bp) : make_float4(0.f, 0.f, 0.f, 0.f);
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; i++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc[i][j] = 0.f;
+  int buf = 0;
+  As[0][lk + 0][lr] = ra.x; As[0][lk + 1][lr] = ra.y; As[0][lk + 2][lr] = ra.z; As[0][lk + 3][lr] = ra.w;
+  Bs[0][lk + 0][lr] = rb.x; Bs[0][lk + 1][lr] = rb.y; Bs[0][lk + 2][lr] = rb.z; Bs[0][lk + 3][lr] = rb.w;
+  __syncthreads();
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    const bool more = k0 + TK < K;
+    if (more) {
+      ra = am ? *reinterpret_cast<const float4*>(ap + k0 + TK) : make_float4(0.f, 0.f, 0.f, 0.f);
+      rb = bn ? *reinterpret_cast<const float4*>(bp + k0 + TK) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int kk = 0; kk < TK; kk++) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + 64]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4 + 64]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+      const int nb = buf ^ 1;
+      As[nb][lk + 0][lr] = ra.x; As[nb][lk + 1][lr] = ra.y; As[nb][lk + 2][lr] = ra.z; As[nb][lk + 3][lr] = ra.w;
+      Bs[nb][lk + 0][lr] = rb.x; Bs[nb][lk + 1][lr] = rb.y; Bs[nb][lk + 2][lr] = rb.z; Bs[nb][lk + 3][lr] = rb.w;
+      __syncthreads();
+      buf = nb;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const int m = m0 + ty * 4 + (i & 3) + (i >> 2) * 64;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int n = n0 + tx * 4 + (j & 3) + (j >> 2) * 64;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (EPI == 1) {
+        v = v + bias[n];
+        v = v > 0.f ? v : 0.f;
+      } else if (EPI == 2) {
+        v = v + bias[n];
+      }
+      C[(int64_t)m * ldc + n] = v;
+    }
+  }
 }
 
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
@@ -185,10 +284,29 @@ template <bool TA, bool TB, int EPI>
 int gemm(const float* A, int lda, const float* Bm, int ldb, float* C, int ldc, int M, int N, int K,
          const float* bias, const float* mask, int ldm, cudaStream_t s) {
   if (M == 0 || N == 0) return CAPS_OK;
+  if (!TA && !TB && EPI != 3 && K > 0 && K % TK == 0 && lda % 4 == 0 && ldb % 4 == 0 &&
+      (uintptr_t)A % 16 == 0 && (uintptr_t)Bm % 16 == 0 && M >= TM) {
+    dim3 g2((unsigned)((N + TN - 1) / TN), (unsigned)((M + TM - 1) / TM));
+    if (g2.y > 65535) return fail(CAPS_EINVAL, "gemm: too many rows in one call");
+    k_gemm_big<EPI == 3 ? 0 : EPI><<<g2, 256, 0, s>>>(A, lda, Bm, ldb, C, ldc, M, N, K, bias);
+    CAPS_LAUNCH("k_gemm_big");
+    return CAPS_OK;
+  }
   dim3 grid((unsigned)((N + GN - 1) / GN), (unsigned)((M + GM - 1) / GM));
   if (grid.y > 65535) return fail(CAPS_EINVAL, "gemm: too many rows in one call");
   k_gemm<TA, TB, EPI><<<grid, 256, 0, s>>>(A, lda, Bm, ldb, C, ldc, M, N, K, bias, mask, ldm);
   CAPS_LAUNCH("k_gemm");
+  return CAPS_OK;
+}
+
+int colsum(const float* D, int n, int ncol, float* out, Scratch& scr, cudaStream_t s) {
+  const int nchunk = std::max(1, (n + CS_ROWS - 1) / CS_ROWS);
+  float* part = nullptr;
+  if (int rc = scr.get(&part, (size_t)nchunk * ncol)) return rc;
+  k_colsum_part<<<dim3((unsigned)((ncol + 31) / 32), (unsigned)nchunk), 256, 0, s>>>(D, n, ncol, part);
+  CAPS_LAUNCH("k_colsum_part");
+  k_colsum_fin<<<(unsigned)((ncol + 127) / 128), 128, 0, s>>>(part, nchunk, ncol, out);
+  CAPS_LAUNCH("k_colsum_fin");
   return CAPS_OK;
 }
 
@@ -243,15 +361,13 @@ int mlp_loss_grad(const MlpNet& net, const float* X, int64_t n, const float* Y, 
   // gW2 [B,H] = dZ^T [B,n] . Hd [n,H];  gb2 = column sums of dZ
   if (int rc = gemm<true, true, 0>(dZ, B, Hd, H, grad->W2, H, B, H, nn, nullptr, nullptr, 0, s))
     return rc;
-  k_colsum<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(dZ, nn, B, grad->b2);
-  CAPS_LAUNCH("k_colsum");
+  if (int rc = colsum(dZ, nn, B, grad->b2, scr, s)) return rc;
   // dH [n,H] = dZ [n,B] . W2 [B,H], zero where the hidden unit was off
   if (int rc = gemm<false, true, 3>(dZ, B, net.W2, H, dH, H, nn, H, B, nullptr, Hd, H, s)) return rc;
   // gW1 [H,d] = dH^T [H,n] . X [n,d];  gb1 = column sums of dH
   if (int rc = gemm<true, true, 0>(dH, H, X, d, grad->W1, d, H, d, nn, nullptr, nullptr, 0, s))
     return rc;
-  k_colsum<<<(unsigned)((H + 127) / 128), 128, 0, s>>>(dH, nn, H, grad->b1);
-  CAPS_LAUNCH("k_colsum");
+  if (int rc = colsum(dH, nn, H, grad->b1, scr, s)) return rc;
   return CAPS_OK;
 }
 
