@@ -365,20 +365,20 @@ int sm_count() {
 
 }  // namespace
 
-int tc_kp(int k) { return k <= 12 ? 12 : (k <= 16 ? 16 : 32); }
+int tc_kp(int k) { return k <= 10 ? 10 : (k <= 16 ? 16 : 32); }
 int tc_rerank_depth(int k, int factor) {
   const int f = factor > 0 ? factor : 4;
   return std::min(64, std::max(k, f * k));
 }
 
 bool tc_scan_supported(int d, int k, int kp, int words_pad) {
-  if (d % 8 != 0 || d < 64 || d > 128 || k > 32 || (kp != 12 && kp != 16 && kp != 32))
+  if (d % 8 != 0 || d < 64 || d > 128 || k > 32 || (kp != 10 && kp != 16 && kp != 32))
     return false;
   return tc_fits((d + 63) / 64, words_pad, 128, false);
 }
 
 bool tc_pen_supported(int d, int kp, int words_pad) {
-  if (d % 8 != 0 || d < 64 || d > 128 || (kp != 12 && kp != 16)) return false;
+  if (d % 8 != 0 || d < 64 || d > 128 || (kp != 10 && kp != 16)) return false;
   return tc_fits((d + 63) / 64 + 1, words_pad, 128, true);
 }
 
@@ -531,11 +531,11 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
                                : launch_tc<CAPS_IP, WPV, KPV, 128, false>(map, a, g, smem, s); \
   return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 256, false>(map, a, g, smem, s)    \
                              : launch_tc<CAPS_IP, WPV, KPV, 256, false>(map, a, g, smem, s)
-  if (t.kp == 12) {
+  if (t.kp == 10) {
     switch (t.words_pad) {
-      case 1: CAPS_TC(1, 12);
-      case 2: CAPS_TC(2, 12);
-      case 4: CAPS_TC(4, 12);
+      case 1: CAPS_TC(1, 10);
+      case 2: CAPS_TC(2, 10);
+      case 4: CAPS_TC(4, 10);
     }
   } else if (t.kp == 16) {
     switch (t.words_pad) {

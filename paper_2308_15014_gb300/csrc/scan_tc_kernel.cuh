@@ -88,6 +88,9 @@ constexpr int TC_COLS = 512;  // tensor-memory columns: TC_COLS / N accumulator 
 constexpr int TC_PRODUCER = TC_C / 32;  // warp index of the producer
 constexpr int TC_SLOTS = 8;   // per-query bound slots (stride)
 constexpr uint64_t kTcWaitNs = 1000000000ull;
+// a waiting thread may sleep up to this long per try (it wakes when the
+// phase completes), so spinning warps leave the issue slots to working ones
+constexpr uint32_t kTcSuspendNs = 500;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -109,10 +112,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
     for (int i = 0; i < 64; i++) {
       uint32_t done;
       asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
           " selp.u32 %0, 1, 0, p;\n}\n"
           : "=r"(done)
-          : "r"(a), "r"(parity)
+          : "r"(a), "r"(parity), "r"(kTcSuspendNs)
           : "memory");
       if (done) return true;
     }
@@ -770,7 +773,7 @@ int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem
 }  // namespace
 
 // Launch of the penalty form (scan_tc_pen.cu): N = 128 rows per tile, two
-// stages; kp 12 or 16.
+// stages; kp 10 or 16.
 int tc_launch_pen(const CUtensorMap& map, const TcArgs& a, int metric, int words_pad, int kp,
                   int64_t grid, size_t smem, cudaStream_t s);
 

@@ -11,11 +11,11 @@ int tc_launch_pen(const CUtensorMap& map, const TcArgs& a, int metric, int words
 #define CAPS_PEN(WPV, KPV)                                                                   \
   return metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 128, true>(map, a, grid, smem, s) \
                            : launch_tc<CAPS_IP, WPV, KPV, 128, true>(map, a, grid, smem, s)
-  if (kp == 12) {
+  if (kp == 10) {
     switch (words_pad) {
-      case 1: CAPS_PEN(1, 12);
-      case 2: CAPS_PEN(2, 12);
-      case 4: CAPS_PEN(4, 12);
+      case 1: CAPS_PEN(1, 10);
+      case 2: CAPS_PEN(2, 10);
+      case 4: CAPS_PEN(4, 10);
     }
   } else if (kp == 16) {
     switch (words_pad) {
