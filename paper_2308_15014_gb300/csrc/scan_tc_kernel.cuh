@@ -296,7 +296,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   };
   auto s_blk = [&](int b) { return aux0 + b * astride + (size_t)RA * WP * 4 + RA * 8; };
 
-  __shared__ uint64_t full_bar[S], mma_bar[S], empty_bar[S], taken_bar, meta_bar;
+  __shared__ uint64_t full_bar[S], mma_bar[S], empty_bar[S], taken_bar, meta_bar, afull_bar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_fail;
   // the current and the next item (index: item parity)
@@ -322,6 +322,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     }
     mbar_init(&taken_bar, TC_C / 32);
     mbar_init(&meta_bar, 1);
+    mbar_init(&afull_bar, TC_C / 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -481,8 +482,11 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
 
   if (warp == TC_PRODUCER) prep_meta(0);
   __syncthreads();
-  if (warp != TC_PRODUCER && s_ne[0] >= 0) build_a(0);
-  __syncthreads();
+  if (warp != TC_PRODUCER && s_ne[0] >= 0) {
+    build_a(0);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&afull_bar);  // the producer may issue the item's MMAs
+  }
 
   int g0 = 0;           // tiles this CTA finished before the current item
   int par = 0, n_done = 0;
@@ -538,6 +542,8 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
           bulk_copy(s_xn(b), a.xn + alo, pb, &full_bar[b]);
           tma_hi = g;
           ok = mbar_wait(&full_bar[b], (uint32_t)(u & 1), &s_fail);
+          // the item's first MMA waits for its A operand
+          if (ok && t == 0) ok = mbar_wait(&afull_bar, (uint32_t)(n_done & 1), &s_fail);
           if (ok) {
             tc_fence_after();
             const uint32_t a0 = su32(sA), b0 = su32(sB);
@@ -567,6 +573,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       if (!ok && lane == 0) s_fail = 1;
     } else {
       // ---- epilogue ------------------------------------------------------
+      // (items follow one another without a CTA barrier: the next item's A
+      // operand is built as soon as this item's MMAs are done, while the
+      // producer already streams the next item's tiles)
       const int probe = tid & (TC_M - 1), part = tid / TC_M;
       const bool active = probe < ne;
       const uint64_t my_sel = p_sel[probe];
@@ -702,19 +711,29 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         if (lane == 0) mbar_arrive(&empty_bar[b]);
       }
       flush();
-      // merge the quarter lists of each probe (the B stages are free: every
-      // MMA of the item has completed)
-      uint64_t* parts = reinterpret_cast<uint64_t*>(sB0);
-      const bool fine = s_fail == 0;
-      if (fine && part > 0) {
+      consumers_sync();  // every queue drained: the queue area holds the quarter lists
+      // merge the quarter lists of each probe, as many lists per round as the
+      // queue area holds
+      uint64_t* parts = queue;
+      bool fine = s_fail == 0;
+      constexpr int PER_ROUND = (TC_Q * TC_C) / (KP * TC_M) < TC_PARTS - 1
+                                    ? (TC_Q * TC_C) / (KP * TC_M)
+                                    : TC_PARTS - 1;
+      for (int q0 = 1; q0 < TC_PARTS; q0 += PER_ROUND) {
+        if (fine && part >= q0 && part < q0 + PER_ROUND) {
 #pragma unroll
-        for (int i = 0; i < KP; i++) parts[((size_t)(part - 1) * KP + i) * TC_M + probe] = L[i];
+          for (int i = 0; i < KP; i++)
+            parts[((size_t)(part - q0) * KP + i) * TC_M + probe] = L[i];
+        }
+        consumers_sync();
+        if (fine && part == 0 && active) {
+          for (int q = 0; q < PER_ROUND && q0 + q < TC_PARTS; q++)
+#pragma unroll
+            for (int i = 0; i < KP; i++) net_insert<KP>(L, parts[((size_t)q * KP + i) * TC_M + probe]);
+        }
+        consumers_sync();
       }
-      consumers_sync();
       if (fine && part == 0 && active) {
-        for (int q = 0; q < TC_PARTS - 1; q++)
-#pragma unroll
-          for (int i = 0; i < KP; i++) net_insert<KP>(L, parts[((size_t)q * KP + i) * TC_M + probe]);
         const int e = p_e[par][probe];
         uint64_t* dst = a.part + (int64_t)e * KP;
 #pragma unroll
@@ -728,14 +747,17 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       // the next item's A operand: every MMA of this item has completed (each
       // tile's accumulator was waited for), so A may be overwritten once the
       // producer has the next item's probe data
+      fine = s_fail == 0;
       const bool meta = fine && mbar_wait(&meta_bar, (uint32_t)(n_done & 1), &s_fail);
       if (fine && !meta) s_fail = 1;
-      if (consumers_all(meta) && s_ne[par ^ 1] >= 0) build_a(par ^ 1);
+      if (consumers_all(meta) && s_ne[par ^ 1] >= 0) {
+        build_a(par ^ 1);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&afull_bar);
+      }
     }
     g0 += n_tiles;
     n_done++;
-    fence_async_smem();  // generic stores into the B stages before later copies land there
-    __syncthreads();
     par ^= 1;
   }
 
