@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--paths", default="mlp_bf16,fp32,bf16",
                     help="comma list of search paths (fp32, bf16, mlp_fp32, mlp_bf16); "
                          "the first is the headline")
+    ap.add_argument("--h-sweep", action="store_true",
+                    help="also sweep the AFT height h (k-means + bf16): QPS at recall@10 >= 0.9")
     ap.add_argument("--sparse", action="store_true",
                     help="also measure the label-set workload (2M x 128, 10,000 labels, "
                          "4,096 queries); adds about two minutes")
@@ -273,6 +275,48 @@ def form1_error(w, rng_seed=11, nq=64, nrow=2048):
     exact = ((Q[:, None, :] - X[None, :, :]) ** 2).sum(-1)
     rel = np.abs(approx - exact) / np.maximum(exact, 1e-30)
     return {"pairs": int(rel.size), "max_rel": float(rel.max()), "mean_rel": float(rel.mean())}
+
+
+def h_sweep(args, w, caps, O, torch, samp, gt, g64, cnt):
+    """AFT height ablation (k-means + bf16, the same seed points): for each h
+    the smallest probe count reaching recall@10 >= 0.9 and the batch QPS
+    there (device buffers, CUDA events, L2 flushed)."""
+    Qd = torch.from_numpy(w.Q).cuda()
+    Qbd = torch.from_numpy(w.Qb).cuda()
+    X = torch.from_numpy(w.X).cuda()
+    A = torch.from_numpy(w.A).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ids = torch.empty((w.nq, w.k), dtype=torch.int64, device="cuda")
+    dist = torch.empty((w.nq, w.k), dtype=torch.float32, device="cuda")
+    out = []
+    for h in (0, 1, 3, 7, 15, 31):
+        ix = caps.Index.build(X, A, w.vocab, w.B, h=h, iters=w.iters, init_idx=w.init_idx,
+                              prec=caps.BF16)
+        row = {"h": h, "m_at_0.9": None}
+        for m in M_SWEEP:
+            ix.search(Qd, Qbd, w.k, m, out_ids=ids, out_dist=dist)
+            _, tie, _, _ = O.recall(ids.cpu().numpy()[samp], gt, g64, cnt, w.k, X=w.X,
+                                    Q=w.Q[samp])
+            if tie >= 0.9:
+                for _ in range(3):
+                    ix.search(Qd, Qbd, w.k, m, out_ids=ids, out_dist=dist)
+                evs = []
+                for _ in range(5):
+                    flush.zero_()
+                    e0, e1 = (torch.cuda.Event(enable_timing=True),
+                              torch.cuda.Event(enable_timing=True))
+                    e0.record()
+                    ix.search(Qd, Qbd, w.k, m, out_ids=ids, out_dist=dist)
+                    e1.record()
+                    evs.append((e0, e1))
+                torch.cuda.synchronize()
+                ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
+                row.update({"m_at_0.9": m, "recall_tie": round(tie, 4),
+                            "qps": round(w.nq / (ms / 1e3), 1)})
+                break
+        out.append(row)
+        ix.close()
+    return out
 
 
 def sparse_line(args, caps, O, torch):
@@ -611,6 +655,8 @@ def run_caps(args):
              "returned_dist_vs_fp64": {"pairs": int(rel.size), "max_rel": float(rel.max()),
                                        "mean_rel": float(rel.mean())}}
     sparse = sparse_line(args, caps, O, torch) if args.sparse and world == 1 else None
+    hsw = h_sweep(args, w, caps, O, torch, samp, gt, g64, cnt) if args.h_sweep and world == 1 \
+        else None
 
     if rank != 0:
         return 0
@@ -659,6 +705,8 @@ def run_caps(args):
     }
     if sparse is not None:
         line["label_sets"] = sparse
+    if hsw is not None:
+        line["h_sweep"] = hsw
     print(json.dumps(line, default=_json_default), flush=True)
     for r in res.values():
         r["plan"].close()

@@ -105,3 +105,17 @@ def test_bf16_rejects_unsupported_d():
         caps.Index.build(w.X, w.A, w.vocab, w.B, h=3, iters=1, init_idx=w.init_idx,
                          prec=caps.BF16)
     assert e.value.code == caps.CAPS_EINVAL
+
+
+@pytest.mark.parametrize("vocab", [(1000, 900, 800, 700, 600), (3, 1000, 1000, 1000, 1000, 1000, 5)])
+def test_bf16_wide_attribute_words_equals_oracle(vocab):
+    # 50 or 63 packed attribute bits: two packed words per row, too many
+    # bits for the one-hot code chunk, so the per-pair filter form runs with
+    # WP = 2 (byte data: bit-exact)
+    w = wl(500 + len(vocab), N=6000, nq=120, vocab=vocab)
+    oi, gi = build_pair(w)
+    assert gi.info.attr_words == 2
+    ids, dist = gi.search(w.Q, w.Qb, 10, 6)
+    oids, odist, _, _ = O.search(w.X, O.Attrs.of(w), oi, w.Q, O.Cons.of(w), 10, 6)
+    np.testing.assert_array_equal(ids, oids)
+    np.testing.assert_array_equal(dist, odist)
