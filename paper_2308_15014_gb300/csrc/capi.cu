@@ -1035,9 +1035,23 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
       return rc;
     }
     if (int rc = tm.record(s)) return rc;
-    if (int rc = partition_scores(ix, Qc, n, bt.scores, mlp_hidden, s)) return rc;
-    if (int rc = tm.record(s)) return rc;
-    if (int rc = launch_topm(bt.scores, n, ix->B, m, probe_metric(ix), bt.probe, s)) return rc;
+    const bool mlp = ix->part == CAPS_PART_MLP;
+    const int sK = mlp ? ix->mlp.H : ix->d;
+    if (probe_screen_supported(sK, ix->B, m)) {
+      // exact probe set, screened on the tensor cores (the top-m stage is
+      // part of it, so its stage time reads ~0)
+      if (mlp)
+        if (int rc = ::caps::mlp_hidden(ix->mlp, Qc, n, mlp_hidden, s)) return rc;
+      if (int rc = probe_screened(mlp ? 0 : (ix->metric == CAPS_L2 ? 1 : 2), mlp ? mlp_hidden : Qc,
+                                  n, sK, mlp ? ix->mlp.W2 : ix->C, mlp ? ix->mlp.b2 : nullptr,
+                                  ix->B, m, bt.scores, bt.probe, ix->err, cscr, s))
+        return rc;
+      if (int rc = tm.record(s)) return rc;
+    } else {
+      if (int rc = partition_scores(ix, Qc, n, bt.scores, mlp_hidden, s)) return rc;
+      if (int rc = tm.record(s)) return rc;
+      if (int rc = launch_topm(bt.scores, n, ix->B, m, probe_metric(ix), bt.probe, s)) return rc;
+    }
     if (int rc = tm.record(s)) return rc;
     if (ix->meta.sparse) {
       if (int rc = launch_select_sparse(bt.probe, n, m, ix->h, ix->tags, ix->pos,

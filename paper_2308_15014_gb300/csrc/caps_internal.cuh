@@ -328,6 +328,17 @@ struct MlpNet {
   }
 };
 int mlp_logits(const MlpNet& net, const float* X, int64_t n, float* Hd, float* Z, cudaStream_t s);
+int mlp_hidden(const MlpNet& net, const float* X, int64_t n, float* Hd, cudaStream_t s);
+
+// ---- exact top-m probe screened on the tensor cores (probe_tc.cu) ----------
+// mode 0: logits of hidden rows A [n,K] against W [B,K] + bias (larger
+// better); 1: L2 centroid distances of queries A [n,K] to W = centroids; 2:
+// IP.  Writes the m-partition set of each query to probe [n,m] (order:
+// certain partitions first, by index); Dt [n,B] is scratch.
+bool probe_screen_supported(int K, int B, int m);
+int probe_screened(int mode, const float* A, int64_t n, int K, const float* W, const float* bias,
+                   int B, int m, float* Dt, int32_t* probe, int32_t* err, Scratch& scr,
+                   cudaStream_t s);
 int mlp_assign(const MlpNet& net, const float* X, int64_t n, int32_t* bin, Scratch& scr,
                cudaStream_t s);
 int mlp_loss_grad(const MlpNet& net, const float* X, int64_t n, const float* Y, MlpNet* grad,

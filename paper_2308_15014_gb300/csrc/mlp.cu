@@ -327,6 +327,18 @@ int mlp_logits(const MlpNet& net, const float* X, int64_t n, float* Hd, float* Z
   return CAPS_OK;
 }
 
+// hidden layer Hd [n, H] = relu(W1 X + b1) of rows X [n, d] (rows in chunks)
+int mlp_hidden(const MlpNet& net, const float* X, int64_t n, float* Hd, cudaStream_t s) {
+  const int64_t chunk = 65535LL * GM;
+  for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+    const int rows = (int)std::min(chunk, n - r0);
+    if (int rc = gemm<false, false, 1>(X + r0 * net.d, net.d, net.W1, net.d, Hd + r0 * net.H,
+                                       net.H, rows, net.H, net.d, net.b1, nullptr, 0, s))
+      return rc;
+  }
+  return CAPS_OK;
+}
+
 int mlp_assign(const MlpNet& net, const float* X, int64_t n, int32_t* bin, Scratch& scr,
                cudaStream_t s) {
   if (n == 0) return CAPS_OK;
