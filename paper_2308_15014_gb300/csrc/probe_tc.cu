@@ -244,34 +244,44 @@ k_screen_topm(const float* __restrict__ Dt, int64_t nq, int B, int m, const floa
   const float* dq = Dt + q * B;
   uint64_t* c = cb[wp];
   const unsigned lt = (1u << lane) - 1u;
-  // (1) each lane's four best lower and upper bounds (sorted lists)
-  uint64_t lk[4], uk[4];
+  // (1) each lane's four largest lower and upper bounds (plain floats: only
+  // the values matter here), then sorted as keys across the warp
+  float lv[4], uv[4];
 #pragma unroll
-  for (int i = 0; i < 4; i++) lk[i] = uk[i] = kEmptyKey;
+  for (int i = 0; i < 4; i++) lv[i] = uv[i] = -INFINITY;
   for (int b = lane; b < B; b += 32) {
     float s, e;
     Screen<MODE>::approx(dq[b], an2, an, wn2v[b], bias, b, s, e);
-    uint64_t kl = make_key(-(s - e), (uint32_t)b), ku = make_key(-(s + e), (uint32_t)b);
+    float x = s - e, y = s + e;
+    if (!(x == x)) x = -INFINITY;  // NaN bounds take no part in the estimates
+    if (!(y == y)) y = -INFINITY;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-      const uint64_t x = lk[i] < kl ? lk[i] : kl;
-      kl = lk[i] < kl ? kl : lk[i];
-      lk[i] = x;
-      const uint64_t y = uk[i] < ku ? uk[i] : ku;
-      ku = uk[i] < ku ? ku : uk[i];
-      uk[i] = y;
+      const float hx = fmaxf(lv[i], x);
+      x = fminf(lv[i], x);
+      lv[i] = hx;
+      const float hy = fmaxf(uv[i], y);
+      y = fminf(uv[i], y);
+      uv[i] = hy;
     }
   }
+  uint64_t lk[4], uk[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    lk[i] = make_key(-lv[i], 0u);
+    uk[i] = make_key(-uv[i], 0u);
+  }
   // T: a value at or below the m-th largest lower bound (the m-th best of
-  // the 128 lane keys is no better than the m-th best of all)
+  // the 128 lane values is no better than the m-th best of all)
   warp_sort<4>(lk, lane);
   const int P = m - 1;
   const uint64_t kt = __shfl_sync(0xffffffffu, lk[P & 3], P >> 2);
-  const float T = kt == kEmptyKey ? -INFINITY : -unord_bits((uint32_t)(kt >> 32));
+  const float T = -unord_bits((uint32_t)(kt >> 32));
   // V: the exact m-th largest upper bound (its m-th smallest key); the upper
   // bounds at or above the lane estimate are compacted and sorted
   warp_sort<4>(uk, lane);
   const uint64_t kv = __shfl_sync(0xffffffffu, uk[P & 3], P >> 2);
+  const float Vlo = -unord_bits((uint32_t)(kv >> 32));  // at or below the exact V
   int cnt = 0;
   for (int b0 = 0; b0 < B; b0 += 32) {
     const int b = b0 + lane;
@@ -281,7 +291,7 @@ k_screen_topm(const float* __restrict__ Dt, int64_t nq, int B, int m, const floa
       Screen<MODE>::approx(dq[b], an2, an, wn2v[b], bias, b, s, e);
       ku = make_key(-(s + e), (uint32_t)b);
     }
-    const bool keep = ku <= kv;
+    const bool keep = b < B && -unord_bits((uint32_t)(ku >> 32)) >= Vlo;
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     const int pos = cnt + __popc(bal & lt);
     if (keep && pos < 128) c[pos] = ku;
