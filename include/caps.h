@@ -267,6 +267,23 @@ int caps_probe(const caps_index* index, const float* Q, int64_t nq, int32_t m,
                int32_t* out_probe, void* stream);
 
 /*
+ * caps_probe_set -- the probe set of each query exactly as caps_search_batch
+ * computes it (Alg. 2 "select top m partitions"): out_probe = [nq*m] int32,
+ * the same m partitions as caps_probe's row (same scores, same tie rule),
+ * in an unspecified order within the row.  For m <= 64 (and m <= B, hidden
+ * width or d <= 2048) the scores of all partitions are first bounded by one
+ * split-bf16 tensor-core product (v = hi + lo, hi*hi + hi*lo + lo*hi) with
+ * a per-partition error interval; partitions whose interval lies wholly
+ * above the m-th largest upper bound are in the set, those wholly below the
+ * m-th largest lower bound are not, and only the rest are re-scored with the
+ * fixed-order fp32 chain.  Other m: the same as caps_probe.  Q and
+ * out_probe are host or device pointers; a bounded device wait that expires
+ * is reported by caps_device_status.
+ */
+int caps_probe_set(const caps_index* index, const float* Q, int64_t nq, int32_t m,
+                   int32_t* out_probe, void* stream);
+
+/*
  * caps_select -- Alg. 2 sub-partition selection for given probes:
  * probe = [nq*m] int32 partition ids, out_sel = [nq*m] uint64, bit j-1 set
  * when block j (1..h+1) of that partition is scanned.

@@ -27,9 +27,9 @@ ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS, ARR_MLP, ARR_L
 
 # Every symbol declared in include/caps.h.
 EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "caps_get_info",
-           "caps_export", "caps_assign", "caps_probe", "caps_select", "caps_set_timing",
-           "caps_get_stage_times", "caps_search_batch_noalloc", "caps_device_status",
-           "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign", "caps_plan_create",
+           "caps_export", "caps_assign", "caps_probe", "caps_probe_set", "caps_select",
+           "caps_set_timing", "caps_get_stage_times", "caps_search_batch_noalloc",
+           "caps_device_status", "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign", "caps_plan_create",
            "caps_plan_search", "caps_plan_get_info", "caps_plan_free")
 
 
@@ -99,6 +99,7 @@ def lib(path: Optional[str] = None):
     L.caps_export.argtypes = [P, i32, P, ct.c_size_t, P]
     L.caps_assign.argtypes = [P, i64, i32, P, i32, i32, P, P]
     L.caps_probe.argtypes = [P, P, i64, i32, P, P]
+    L.caps_probe_set.argtypes = [P, P, i64, i32, P, P]
     L.caps_select.argtypes = [P, P, i64, i32, ct.POINTER(caps_attrs), P, P]
     L.caps_search_batch_noalloc.argtypes = [P, P, i64, ct.POINTER(caps_attrs), i32, i32, P, P,
                                             P]
@@ -353,6 +354,15 @@ class Index:
         if out is None:
             out = np.empty((nq, m), dtype=np.int32)
         _check(lib().caps_probe(self._h, _ptr(Q), nq, m, _ptr(out), _stream(stream)))
+        return out
+
+    def probe_set(self, Q, m, out=None, stream=None):
+        """The probe set the batched search uses (row order unspecified)."""
+        Q = _np_or_keep(Q, np.float32)
+        nq = Q.shape[0]
+        if out is None:
+            out = np.empty((nq, m), dtype=np.int32)
+        _check(lib().caps_probe_set(self._h, _ptr(Q), nq, m, _ptr(out), _stream(stream)))
         return out
 
     def select(self, probe, Qb, out=None, stream=None):

@@ -801,6 +801,42 @@ extern "C" int caps_probe(const caps_index* ix, const float* Q, int64_t nq, int3
   return CAPS_OK;
 }
 
+extern "C" int caps_probe_set(const caps_index* ix, const float* Q, int64_t nq, int32_t m,
+                              int32_t* out_probe, void* stream) {
+  if (!ix) return fail(CAPS_EINVAL, "null index");
+  if (nq < 0 || m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
+  const bool mlp = ix->part == CAPS_PART_MLP;
+  const int sK = mlp ? ix->mlp.H : ix->d;
+  if (!probe_screen_supported(sK, ix->B, m)) return caps_probe(ix, Q, nq, m, out_probe, stream);
+  if (nq == 0) return CAPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch scr(s);
+  const float* dQ = nullptr;
+  if (int rc = stage_in(Q, (size_t)nq * ix->d, scr, s, &dQ)) return rc;
+  Out<int32_t> op;
+  if (int rc = op.init(out_probe, (size_t)nq * m, scr)) return rc;
+  const int64_t qc = chunk_rows(ix, nq);
+  float* scores = nullptr;
+  if (int rc = scr.get(&scores, (size_t)qc * ix->B)) return rc;
+  float* hid = nullptr;
+  if (mlp)
+    if (int rc = scr.get(&hid, (size_t)qc * ix->mlp.H)) return rc;
+  for (int64_t c0 = 0; c0 < nq; c0 += qc) {
+    const int64_t n = std::min(qc, nq - c0);
+    const float* Qc = dQ + c0 * ix->d;
+    Scratch cscr(s);
+    if (mlp)
+      if (int rc = ::caps::mlp_hidden(ix->mlp, Qc, n, hid, s)) return rc;
+    if (int rc = probe_screened(mlp ? 0 : (ix->metric == CAPS_L2 ? 1 : 2), mlp ? hid : Qc, n, sK,
+                                mlp ? ix->mlp.W2 : ix->C, mlp ? ix->mlp.b2 : nullptr, ix->B, m,
+                                scores, op.dev + c0 * m, ix->err, cscr, s))
+      return rc;
+  }
+  if (int rc = op.finish(s)) return rc;
+  if (op.host) CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
 extern "C" int caps_select(const caps_index* ix, const int32_t* probe, int64_t nq, int32_t m,
                            const caps_attrs* cons, uint64_t* out_sel, void* stream) {
   if (!ix) return fail(CAPS_EINVAL, "null index");

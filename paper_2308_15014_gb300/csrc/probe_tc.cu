@@ -47,8 +47,10 @@ __global__ void k_split3(const float* __restrict__ X, int64_t rows, int K, int K
   o[2 * Kp + k] = wside ? hi : lo;
 }
 
-// Squared norm of each row (fp32; its rounding is inside eps).
-__global__ void k_rownorm2(const float* __restrict__ X, int64_t rows, int K, float* __restrict__ n2) {
+// Squared norm of each row and, when nr is given, the norm (fp32; the
+// rounding is inside eps).
+__global__ void k_rownorm2(const float* __restrict__ X, int64_t rows, int K, float* __restrict__ n2,
+                           float* __restrict__ nr) {
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= rows) return;
@@ -59,7 +61,10 @@ __global__ void k_rownorm2(const float* __restrict__ X, int64_t rows, int K, flo
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) n2[r] = s;
+  if (lane == 0) {
+    n2[r] = s;
+    if (nr) nr[r] = sqrtf(s);
+  }
 }
 
 // D[M, N] = A[M, Kt] . B[N, Kt]^T (bf16 in, fp32 out): one 128 x 256 tile per
@@ -176,9 +181,8 @@ k_pgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
 template <int MODE>
 struct Screen {
   // approximate score as "larger is better", and its error bound
-  __device__ __forceinline__ static void approx(float dt, float an2, float an, float wn2,
+  __device__ __forceinline__ static void approx(float dt, float an2, float an, float wn2, float wn,
                                                 const float* bias, int b, float& s, float& e) {
-    const float wn = sqrtf(wn2);
     if (MODE == 0) {
       s = dt + bias[b];
       e = kScreenEps * an * wn + 1.0e-6f * fabsf(s);
@@ -203,18 +207,29 @@ struct Screen {
                                                        const float* bias, int b) {
     float acc = 0.f;
     int k = 0;
-    if ((((uintptr_t)w) & 15) == 0) {
-      // the weight row in 16-byte loads, eight in flight; terms still in order
-      for (; k + 32 <= K; k += 32) {
-        float4 x[8];
+    if (((((uintptr_t)w) | ((uintptr_t)a)) & 15) == 0 && K >= 16) {
+      // the weight row in 16-byte loads, the next 16 values in flight while
+      // the current ones are summed; terms still in order
+      float4 x[4], y[4];
 #pragma unroll
-        for (int u = 0; u < 8; u++) x[u] = reinterpret_cast<const float4*>(w + k)[u];
+      for (int u = 0; u < 4; u++) x[u] = reinterpret_cast<const float4*>(w)[u];
+      for (; k + 16 <= K; k += 16) {
+        const bool more = k + 32 <= K;
+        if (more) {
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
-          acc = term(acc, a[k + 4 * u + 0], x[u].x);
-          acc = term(acc, a[k + 4 * u + 1], x[u].y);
-          acc = term(acc, a[k + 4 * u + 2], x[u].z);
-          acc = term(acc, a[k + 4 * u + 3], x[u].w);
+          for (int u = 0; u < 4; u++) y[u] = reinterpret_cast<const float4*>(w + k + 16)[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const float4 av = *reinterpret_cast<const float4*>(a + k + 4 * u);
+          acc = term(acc, av.x, x[u].x);
+          acc = term(acc, av.y, x[u].y);
+          acc = term(acc, av.z, x[u].z);
+          acc = term(acc, av.w, x[u].w);
+        }
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < 4; u++) x[u] = y[u];
         }
       }
     }
@@ -224,16 +239,66 @@ struct Screen {
   }
 };
 
+// Descending bitonic sort of 32*V floats held V per lane (position V*lane+s).
+// No NaN may take part.
+template <int V>
+__device__ __forceinline__ void warp_sort_desc(float (&v)[V], int lane) {
+#pragma unroll
+  for (int size = 2; size <= 32 * V; size <<= 1)
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride < V) {
+#pragma unroll
+        for (int s = 0; s < V; s++) {
+          const int o = s ^ stride;
+          if (o > s) {
+            const bool down = ((V * lane + s) & size) == 0;
+            const float hi = fmaxf(v[s], v[o]), lo = fminf(v[s], v[o]);
+            v[s] = down ? hi : lo;
+            v[o] = down ? lo : hi;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < V; s++) {
+          const int P = V * lane + s;
+          const float o = __shfl_xor_sync(0xffffffffu, v[s], stride / V);
+          const bool down = (P & size) == 0, lower = (P & stride) == 0;
+          v[s] = (lower == down) ? fmaxf(o, v[s]) : fminf(o, v[s]);
+        }
+      }
+    }
+}
+
+// The value at position P of a four-per-lane sorted warp array.
+__device__ __forceinline__ float at_pos4(const float (&v)[4], int P) {
+  const int s = P & 3;
+  const float x = s == 0 ? v[0] : (s == 1 ? v[1] : (s == 2 ? v[2] : v[3]));
+  return __shfl_sync(0xffffffffu, x, P >> 2);
+}
+
+constexpr int kScreenList = 256;  // partitions with ub >= T kept per query
+constexpr int kScreenVList = 128;  // upper bounds >= the estimate of V
+
 // Warp per query: intervals, the certain partitions, exact re-score of the
 // uncertain ones, and the m-partition probe set.  m <= 64.
+//
+// Two passes over the B intervals: the first gives, from each lane's four
+// largest bounds, T (at or below the m-th largest lower bound) and Vlo (at or
+// below the m-th largest upper bound V); the second lists every partition
+// with ub >= T (a superset of the certain and uncertain ones, since Vlo >= T
+// and lb > V >= Vlo) and the upper bounds >= Vlo (all that decide V).  The
+// rest works on the list.  Lists that overflow fall back to full passes.
 template <int MODE>
 __global__ void __launch_bounds__(128)
 k_screen_topm(const float* __restrict__ Dt, int64_t nq, int B, int m, const float* __restrict__ A,
               int K, const float* __restrict__ W, const float* __restrict__ bias,
               const float* __restrict__ an2v, const float* __restrict__ wn2v,
-              int32_t* __restrict__ probe) {
+              const float* __restrict__ wnv, int32_t* __restrict__ probe) {
   extern __shared__ float asm_[];  // [4][K] query features
-  __shared__ uint64_t cb[4][128];
+  __shared__ int l_id[4][kScreenList];
+  __shared__ float l_lb[4][kScreenList], l_ub[4][kScreenList];
+  __shared__ float l_v[4][kScreenVList];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * 4 + wp;
   if (q >= nq) return;
@@ -242,18 +307,20 @@ k_screen_topm(const float* __restrict__ Dt, int64_t nq, int B, int m, const floa
   __syncwarp();
   const float an2 = an2v[q], an = sqrtf(an2);
   const float* dq = Dt + q * B;
-  uint64_t* c = cb[wp];
+  int* lid = l_id[wp];
+  float *llb = l_lb[wp], *lub = l_ub[wp], *lv4 = l_v[wp];
   const unsigned lt = (1u << lane) - 1u;
-  // (1) each lane's four largest lower and upper bounds (plain floats: only
-  // the values matter here), then sorted as keys across the warp
+  const int P = m - 1;
+  // (1) each lane's four largest lower and upper bounds (NaN bounds take no
+  // part), sorted across the warp
   float lv[4], uv[4];
 #pragma unroll
   for (int i = 0; i < 4; i++) lv[i] = uv[i] = -INFINITY;
   for (int b = lane; b < B; b += 32) {
     float s, e;
-    Screen<MODE>::approx(dq[b], an2, an, wn2v[b], bias, b, s, e);
+    Screen<MODE>::approx(dq[b], an2, an, wn2v[b], wnv[b], bias, b, s, e);
     float x = s - e, y = s + e;
-    if (!(x == x)) x = -INFINITY;  // NaN bounds take no part in the estimates
+    if (!(x == x)) x = -INFINITY;
     if (!(y == y)) y = -INFINITY;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -265,83 +332,98 @@ k_screen_topm(const float* __restrict__ Dt, int64_t nq, int B, int m, const floa
       uv[i] = hy;
     }
   }
-  uint64_t lk[4], uk[4];
-#pragma unroll
-  for (int i = 0; i < 4; i++) {
-    lk[i] = make_key(-lv[i], 0u);
-    uk[i] = make_key(-uv[i], 0u);
-  }
-  // T: a value at or below the m-th largest lower bound (the m-th best of
-  // the 128 lane values is no better than the m-th best of all)
-  warp_sort<4>(lk, lane);
-  const int P = m - 1;
-  const uint64_t kt = __shfl_sync(0xffffffffu, lk[P & 3], P >> 2);
-  const float T = -unord_bits((uint32_t)(kt >> 32));
-  // V: the exact m-th largest upper bound (its m-th smallest key); the upper
-  // bounds at or above the lane estimate are compacted and sorted
-  warp_sort<4>(uk, lane);
-  const uint64_t kv = __shfl_sync(0xffffffffu, uk[P & 3], P >> 2);
-  const float Vlo = -unord_bits((uint32_t)(kv >> 32));  // at or below the exact V
-  int cnt = 0;
+  // the m-th best of the 128 lane values is no better than the m-th best of all
+  warp_sort_desc<4>(lv, lane);
+  const float T = at_pos4(lv, P);
+  warp_sort_desc<4>(uv, lane);
+  const float Vlo = at_pos4(uv, P);
+  // (2) the list (ub >= T) and the upper bounds that decide V (ub >= Vlo)
+  int cnt = 0, cv = 0;
   for (int b0 = 0; b0 < B; b0 += 32) {
     const int b = b0 + lane;
-    uint64_t ku = kEmptyKey;
+    float x = 0.f, y = -INFINITY;
     if (b < B) {
       float s, e;
-      Screen<MODE>::approx(dq[b], an2, an, wn2v[b], bias, b, s, e);
-      ku = make_key(-(s + e), (uint32_t)b);
+      Screen<MODE>::approx(dq[b], an2, an, wn2v[b], wnv[b], bias, b, s, e);
+      x = s - e;
+      y = s + e;
     }
-    const bool keep = b < B && -unord_bits((uint32_t)(ku >> 32)) >= Vlo;
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    const int pos = cnt + __popc(bal & lt);
-    if (keep && pos < 128) c[pos] = ku;
-    cnt += __popc(bal);
+    const bool keep = b < B && y >= T, kv = b < B && y >= Vlo;  // false for NaN
+    const unsigned bk = __ballot_sync(0xffffffffu, keep), bv = __ballot_sync(0xffffffffu, kv);
+    const int pos = cnt + __popc(bk & lt), pv = cv + __popc(bv & lt);
+    if (keep && pos < kScreenList) {
+      lid[pos] = b;
+      llb[pos] = x;
+      lub[pos] = y;
+    }
+    if (kv && pv < kScreenVList) lv4[pv] = y;
+    cnt += __popc(bk);
+    cv += __popc(bv);
   }
   __syncwarp();
-  bool have_v = cnt <= 128;
-  float V = INFINITY;  // without the exact V no partition is certain
-  if (have_v) {
-    uint64_t v4[4];
+  // V: the exact m-th largest upper bound; without it no partition is certain
+  float V = INFINITY;
+  if (cv <= kScreenVList) {
+    float v4[4];
 #pragma unroll
-    for (int s2 = 0; s2 < 4; s2++) v4[s2] = (4 * lane + s2 < cnt) ? c[4 * lane + s2] : kEmptyKey;
-    warp_sort<4>(v4, lane);
-    const uint64_t km = __shfl_sync(0xffffffffu, v4[P & 3], P >> 2);
-    V = -unord_bits((uint32_t)(km >> 32));
+    for (int s2 = 0; s2 < 4; s2++) v4[s2] = (4 * lane + s2 < cv) ? lv4[4 * lane + s2] : -INFINITY;
+    warp_sort_desc<4>(v4, lane);
+    V = at_pos4(v4, P);
   }
-  __syncwarp();
-  // (2) certain partitions (lb > V: at most m - 1 upper bounds exceed V) go
-  // straight to the probe list; uncertain ones (ub >= T) are collected
+  // (3) certain partitions (lb > V: at most m - 1 upper bounds exceed V) go
+  // straight to the probe list; uncertain ones (ub >= T) are collected in
+  // place of the list, in partition order
   int ci = 0, nu = 0;
   int32_t* out = probe + q * m;
-  for (int b0 = 0; b0 < B; b0 += 32) {
-    const int b = b0 + lane;
-    bool cert = false, unc = false;
-    if (b < B) {
-      float s, e;
-      Screen<MODE>::approx(dq[b], an2, an, wn2v[b], bias, b, s, e);
-      cert = (s - e) > V;
-      unc = !cert && (s + e) >= T;
+  if (cnt <= kScreenList) {
+    for (int r0 = 0; r0 < cnt; r0 += 32) {
+      const int r = r0 + lane;
+      int b = 0;
+      bool cert = false, unc = false;
+      if (r < cnt) {
+        b = lid[r];
+        cert = llb[r] > V;
+        unc = !cert;  // every listed partition has ub >= T
+      }
+      __syncwarp();
+      const unsigned bc = __ballot_sync(0xffffffffu, cert);
+      if (cert) out[ci + __popc(bc & lt)] = b;
+      ci += __popc(bc);
+      const unsigned bu = __ballot_sync(0xffffffffu, unc);
+      if (unc) lid[nu + __popc(bu & lt)] = b;  // at or before this lane's own slot
+      nu += __popc(bu);
     }
-    const unsigned bc = __ballot_sync(0xffffffffu, cert);
-    if (cert) out[ci + __popc(bc & lt)] = b;
-    ci += __popc(bc);
-    const unsigned bu = __ballot_sync(0xffffffffu, unc);
-    const int pos = nu + __popc(bu & lt);
-    if (unc && pos < 128) c[pos] = (uint64_t)b;
-    nu += __popc(bu);
+  } else {
+    for (int b0 = 0; b0 < B; b0 += 32) {
+      const int b = b0 + lane;
+      bool cert = false, unc = false;
+      if (b < B) {
+        float s, e;
+        Screen<MODE>::approx(dq[b], an2, an, wn2v[b], wnv[b], bias, b, s, e);
+        cert = (s - e) > V;
+        unc = !cert && (s + e) >= T;
+      }
+      const unsigned bc = __ballot_sync(0xffffffffu, cert);
+      if (cert) out[ci + __popc(bc & lt)] = b;
+      ci += __popc(bc);
+      const unsigned bu = __ballot_sync(0xffffffffu, unc);
+      const int pos = nu + __popc(bu & lt);
+      if (unc && pos < kScreenList) lid[pos] = b;
+      nu += __popc(bu);
+    }
   }
   __syncwarp();
   const int need = m - ci;
-  // (3) exact scores of the uncertain partitions; the best `need` complete
+  // (4) exact scores of the uncertain partitions; the best `need` complete
   // the set (ties to the lower partition)
   WarpTopK<2> top;
   top.init();
   uint64_t kth = kEmptyKey;
-  if (nu <= 128) {
+  if (nu <= kScreenList) {
     for (int r0 = 0; r0 < nu; r0 += 32) {
       uint64_t key = kEmptyKey;
       if (r0 + lane < nu) {
-        const int b = (int)c[r0 + lane];
+        const int b = lid[r0 + lane];
         key = Screen<MODE>::exact_key(a, W + (int64_t)b * K, K, bias, b);
       }
       top.offer(key, kth, need, lane);
@@ -353,7 +435,7 @@ k_screen_topm(const float* __restrict__ Dt, int64_t nq, int B, int m, const floa
       uint64_t key = kEmptyKey;
       if (b < B) {
         float s, e;
-        Screen<MODE>::approx(dq[b], an2, an, wn2v[b], bias, b, s, e);
+        Screen<MODE>::approx(dq[b], an2, an, wn2v[b], wnv[b], bias, b, s, e);
         if (!((s - e) > V) && (s + e) >= T) key = Screen<MODE>::exact_key(a, W + (int64_t)b * K, K, bias, b);
       }
       top.offer(key, kth, need, lane);
@@ -372,7 +454,7 @@ k_screen_topm(const float* __restrict__ Dt, int64_t nq, int B, int m, const floa
       uint64_t key = kEmptyKey;
       if (b < B) {
         float s, e;
-        Screen<MODE>::approx(dq[b], an2, an, wn2v[b], bias, b, s, e);
+        Screen<MODE>::approx(dq[b], an2, an, wn2v[b], wnv[b], bias, b, s, e);
         if (!((s - e) > V)) key = Screen<MODE>::exact_key(a, W + (int64_t)b * K, K, bias, b);
         if (key == kEmptyKey && !((s - e) > V)) key = kEmptyKey - 1 - (uint64_t)(B - b);
       }
@@ -417,18 +499,19 @@ int probe_screened(int mode, const float* A, int64_t n, int K, const float* W, c
   if (!probe_screen_supported(K, B, m)) return fail(CAPS_EINVAL, "screened probe: bad sizes");
   const int Kp = (K + 63) / 64 * 64, Kt = 3 * Kp;
   __nv_bfloat16 *Ah = nullptr, *Wh = nullptr;
-  float *an2 = nullptr, *wn2 = nullptr;
+  float *an2 = nullptr, *wn2 = nullptr, *wn = nullptr;
   if (int rc = scr.get(&Ah, (size_t)n * Kt)) return rc;
   if (int rc = scr.get(&Wh, (size_t)B * Kt)) return rc;
   if (int rc = scr.get(&an2, (size_t)n)) return rc;
   if (int rc = scr.get(&wn2, (size_t)B)) return rc;
+  if (int rc = scr.get(&wn, (size_t)B)) return rc;
   k_split3<<<(unsigned)((n * Kp + 255) / 256), 256, 0, s>>>(A, n, K, Kp, 0, Ah);
   CAPS_LAUNCH("k_split3");
   k_split3<<<(unsigned)(((int64_t)B * Kp + 255) / 256), 256, 0, s>>>(W, B, K, Kp, 1, Wh);
   CAPS_LAUNCH("k_split3");
-  k_rownorm2<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, n, K, an2);
+  k_rownorm2<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, n, K, an2, nullptr);
   CAPS_LAUNCH("k_rownorm2");
-  k_rownorm2<<<(unsigned)((B + 7) / 8), 256, 0, s>>>(W, B, K, wn2);
+  k_rownorm2<<<(unsigned)((B + 7) / 8), 256, 0, s>>>(W, B, K, wn2, wn);
   CAPS_LAUNCH("k_rownorm2");
   alignas(64) CUtensorMap mA, mB;
   if (int rc = encode_bf16_map(&mA, Ah, n, Kt)) return rc;
@@ -446,7 +529,7 @@ int probe_screened(int mode, const float* A, int64_t n, int K, const float* W, c
     if (ssm > 48 * 1024)                                                                      \
       CAPS_CUDA(cudaFuncSetAttribute(k_screen_topm<MD>,                                       \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm)); \
-    k_screen_topm<MD><<<g, 128, ssm, s>>>(Dt, n, B, m, A, K, W, bias, an2, wn2, probe);      \
+    k_screen_topm<MD><<<g, 128, ssm, s>>>(Dt, n, B, m, A, K, W, bias, an2, wn2, wn, probe);  \
   } while (0)
   if (mode == 0) CAPS_SCR(0);
   else if (mode == 1) CAPS_SCR(1);
