@@ -41,6 +41,7 @@
 #include <cudaTypedefs.h>
 
 #include "caps_internal.cuh"
+#include <type_traits>
 
 namespace caps {
 
@@ -231,9 +232,10 @@ __host__ __device__ constexpr bool tc_fits(int kc, int WP, int N, bool pen) {
 }
 __host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N, bool pen) {
   // 1024-byte alignment slack + A + B stages + candidate queues + aux stages
-  // (the final merge of the quarter lists reuses the B stages)
+  // (one per accumulator stage; the final merge of the quarter lists reuses
+  // the queues)
   return 1024 + tc_a_bytes(kc) + (size_t)tc_stages(N, pen) * tc_b_bytes(kc, N) +
-         (size_t)TC_Q * TC_C * 8 + (size_t)tc_stages(N, pen) * tc_aux_bytes(WP, N);
+         (size_t)TC_Q * TC_C * 8 + (size_t)(TC_COLS / N) * tc_aux_bytes(WP, N);
 }
 
 template <int KP>
@@ -246,6 +248,35 @@ __device__ __forceinline__ void net_insert(uint64_t (&L)[KP], uint64_t x) {
     x = L[i] < x ? x : L[i];
     L[i] = lo;
   }
+}
+
+// L (ascending) becomes the KP smallest keys of L and the ascending list at
+// other[i * TC_M]: the pairwise minima of L and the reversed other list are
+// those keys as a bitonic sequence (rising, then falling); zero keys in front
+// (below every key) pad it to a power of two, and a bitonic merger sorts it.
+template <int KP>
+__device__ __forceinline__ void net_merge(uint64_t (&L)[KP], const uint64_t* other) {
+  constexpr int P = KP <= 16 ? 16 : 32;
+  static_assert(KP <= P && P <= 32, "list too long");
+  uint64_t c[P];
+#pragma unroll
+  for (int i = 0; i < P - KP; i++) c[i] = 0ull;
+#pragma unroll
+  for (int i = 0; i < KP; i++) {
+    const uint64_t o = other[(size_t)(KP - 1 - i) * TC_M];
+    c[P - KP + i] = L[i] < o ? L[i] : o;
+  }
+#pragma unroll
+  for (int st = P / 2; st > 0; st >>= 1)
+#pragma unroll
+    for (int i = 0; i < P; i++)
+      if ((i & st) == 0) {
+        const uint64_t x = c[i], y = c[i + st];
+        c[i] = x < y ? x : y;
+        c[i + st] = x < y ? y : x;
+      }
+#pragma unroll
+  for (int i = 0; i < KP; i++) L[i] = c[P - KP + i];
 }
 
 // One persistent CTA per SM walks the work items (partition, <= 128 probes)
@@ -271,7 +302,10 @@ __device__ __forceinline__ void net_insert(uint64_t (&L)[KP], uint64_t x) {
 template <int METRIC, int WP, int KP, int N, bool PEN>
 __global__ void __launch_bounds__(TC_T, 1)
 k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
-  constexpr int S = tc_stages(N, PEN);
+  // SB shared-memory stages hold B tiles (free once the tile's MMAs are
+  // done); ST accumulator stages in tensor memory, each with the tile's ids,
+  // norms, attribute words and block ids (free once the epilogue read them)
+  constexpr int SB = tc_stages(N, PEN), ST = TC_COLS / N;
   constexpr int RA = N + 8;
   constexpr int CPT = N / TC_PARTS;  // accumulator columns per epilogue thread and tile
   extern __shared__ unsigned char smem_raw[];
@@ -284,7 +318,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   unsigned char* sA = base;
   unsigned char* sB0 = sA + tc_a_bytes(kc);
   const size_t bstride = tc_b_bytes(kc, N);
-  uint64_t* queue = reinterpret_cast<uint64_t*>(sB0 + S * bstride);
+  uint64_t* queue = reinterpret_cast<uint64_t*>(sB0 + SB * bstride);
   unsigned char* aux0 = reinterpret_cast<unsigned char*>(queue + (size_t)TC_Q * TC_C);
   constexpr size_t astride = tc_aux_bytes(WP, N);
   auto s_attr = [&](int b) { return reinterpret_cast<uint32_t*>(aux0 + b * astride); };
@@ -296,7 +330,8 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   };
   auto s_blk = [&](int b) { return aux0 + b * astride + (size_t)RA * WP * 4 + RA * 8; };
 
-  __shared__ uint64_t full_bar[S], mma_bar[S], empty_bar[S], taken_bar, meta_bar, afull_bar;
+  __shared__ uint64_t full_bar[SB], bfree_bar[SB], aux_bar[ST], mma_bar[ST], empty_bar[ST];
+  __shared__ uint64_t taken_bar, meta_bar, afull_bar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_fail;
   // the current and the next item (index: item parity)
@@ -309,14 +344,18 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   __shared__ float p_qn[TC_M];
   __shared__ float p_cut[TC_M];  // penalty form: scores at or above are masked pairs
   // producer only: tile schedule of its item
-  __shared__ int s_tlo[S], s_tn[S];
+  __shared__ int s_tlo[ST], s_tn[ST];
   __shared__ int run_lo[64], run_hi[64], run_j0[64];
   __shared__ int n_runs;
   __shared__ int32_t boff[65];
 
   if (tid == 0) {
-    for (int i = 0; i < S; i++) {
+    for (int i = 0; i < SB; i++) {
       mbar_init(&full_bar[i], 1);
+      mbar_init(&bfree_bar[i], 1);
+    }
+    for (int i = 0; i < ST; i++) {
+      mbar_init(&aux_bar[i], 1);
       mbar_init(&mma_bar[i], 1);
       mbar_init(&empty_bar[i], TC_C / 32);
     }
@@ -498,23 +537,27 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
 
     if (warp == TC_PRODUCER) {
       // ---- producer ------------------------------------------------------
+      // copies run ahead of the MMAs: before tile t's MMAs the copy of tile
+      // t + SB - 1 is issued, into the B stage of tile t - 1 (free once that
+      // tile's MMAs are done) and the aux stage of tile t + SB - 1 - ST (free
+      // once the epilogue has read it)
       int rr = 0, rlo = n_runs > 0 ? run_lo[0] : 0;
       bool ok = true;
-      for (int t = 0; t < n_tiles; t++) {
-        const int g = g0 + t, b = g % S, u = g / S;
+      int tl = 0;  // next tile of this item to copy
+      auto load = [&](int t) -> bool {  // warp-uniform
+        const int g = g0 + t, sb = g % SB, st = g % ST;
         while (rlo >= run_hi[rr]) {
           rr++;
           rlo = run_lo[rr];
         }
         const int lo = rlo, n = min(N, run_hi[rr] - rlo), j0 = run_j0[rr];
         rlo += n;
-        if (u > 0) ok = mbar_wait(&empty_bar[b], (uint32_t)((u - 1) & 1), &s_fail);
-        if (!__all_sync(0xffffffffu, ok)) {
-          ok = false;
-          break;
-        }
+        bool k = true;
+        if (g >= SB) k = mbar_wait(&bfree_bar[sb], (uint32_t)((g / SB - 1) & 1), &s_fail);
+        if (k && g >= ST) k = mbar_wait(&empty_bar[st], (uint32_t)((g / ST - 1) & 1), &s_fail);
+        if (!__all_sync(0xffffffffu, k)) return false;
         if (!PEN) {
-          uint8_t* blk = s_blk(b);
+          uint8_t* blk = s_blk(st);
           for (int r = lane; r < n; r += 32) {
             int j = j0;
             while (j + 1 < nb && boff[j + 1] <= lo + r) j++;
@@ -522,43 +565,53 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
           }
         }
         if (lane == 0) {
-          s_tlo[b] = lo;
-          s_tn[b] = n;
+          s_tlo[st] = lo;
+          s_tn[st] = n;
         }
         __syncwarp();
         if (lane == 0) {
           const int alo = lo & ~3;
           const int arows = ((lo + n + 3) & ~3) - alo;
           const uint32_t ab = PEN ? 0u : (uint32_t)(arows * WP * 4), pb = (uint32_t)(arows * 4);
-          unsigned char* sB = sB0 + b * bstride;
-          expect_tx(&full_bar[b], (uint32_t)(kc * N * 128) + ab + 2 * pb);
+          unsigned char* sB = sB0 + sb * bstride;
+          expect_tx(&full_bar[sb], (uint32_t)(kc * N * 128));
           for (int c = 0; c < kc; c++)
 #pragma unroll
             for (int hb = 0; hb < N / TC_BOX; hb++)
               tma_2d(sB + (size_t)c * N * 128 + (size_t)hb * TC_BOX * 128, &tmX, 64 * c,
-                     lo + hb * TC_BOX, &full_bar[b]);
-          if (!PEN) bulk_copy(s_attr(b), a.Ap + (int64_t)alo * WP, ab, &full_bar[b]);
-          bulk_copy(s_perm(b), a.perm + alo, pb, &full_bar[b]);
-          bulk_copy(s_xn(b), a.xn + alo, pb, &full_bar[b]);
+                     lo + hb * TC_BOX, &full_bar[sb]);
+          expect_tx(&aux_bar[st], ab + 2 * pb);
+          if (!PEN) bulk_copy(s_attr(st), a.Ap + (int64_t)alo * WP, ab, &aux_bar[st]);
+          bulk_copy(s_perm(st), a.perm + alo, pb, &aux_bar[st]);
+          bulk_copy(s_xn(st), a.xn + alo, pb, &aux_bar[st]);
           tma_hi = g;
-          ok = mbar_wait(&full_bar[b], (uint32_t)(u & 1), &s_fail);
+        }
+        return true;
+      };
+      while (ok && tl < n_tiles && tl < SB - 1) ok = load(tl++);
+      for (int t = 0; ok && t < n_tiles; t++) {
+        if (tl < n_tiles) ok = load(tl++);
+        if (!ok) break;
+        const int g = g0 + t, sb = g % SB, st = g % ST;
+        if (lane == 0) {
+          ok = mbar_wait(&full_bar[sb], (uint32_t)((g / SB) & 1), &s_fail);
           // the item's first MMA waits for its A operand
           if (ok && t == 0) ok = mbar_wait(&afull_bar, (uint32_t)(n_done & 1), &s_fail);
           if (ok) {
             tc_fence_after();
-            const uint32_t a0 = su32(sA), b0 = su32(sB);
+            const uint32_t a0 = su32(sA), b0 = su32(sB0 + sb * bstride);
             for (int ks = 0; ks < kc * 4; ks++) {
               const int c = ks >> 2, kin = ks & 3;
               const uint64_t ad = sdesc(a0 + (uint32_t)(c * TC_M * 128 + kin * 32));
               const uint64_t bd = sdesc(b0 + (uint32_t)(c * N * 128 + kin * 32));
-              mma_bf16(tbase + (uint32_t)(b * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
+              mma_bf16(tbase + (uint32_t)(st * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
             }
-            mma_commit(&mma_bar[b]);
+            mma_commit(&mma_bar[st]);
+            mma_commit(&bfree_bar[sb]);
             mma_hi = g;
           }
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
       }
       // prepare the next item's metadata while the epilogue finishes this
       // one, once the epilogue has taken this item's probe data
@@ -612,8 +665,8 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       const bool warp_live = __any_sync(0xffffffffu, active);
       const int cbeg = part * CPT;
       for (int t = 0; t < n_tiles; t++) {
-        const int g = g0 + t, b = g % S, u = g / S;
-        const bool ok = mbar_wait(&full_bar[b], (uint32_t)(u & 1), &s_fail) &&
+        const int g = g0 + t, b = g % ST, u = g / ST;
+        const bool ok = mbar_wait(&aux_bar[b], (uint32_t)(u & 1), &s_fail) &&
                         mbar_wait(&mma_bar[b], (uint32_t)(u & 1), &s_fail);
         if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform: the loads below are collective
           s_fail = 1;
@@ -644,7 +697,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
             // the MMA already folded the block selection and the attribute
             // filter in: a masked pair scores at least my_cut (the key of an
             // empty list decodes to NaN, which fminf ignores)
-            const float tf = fminf(my_cut, unord_bits((uint32_t)(thr >> 32)));
+            // one bound: sc <= ts (the list's key) and sc < my_cut is sc <= tf
+            const float ts = unord_bits((uint32_t)(thr >> 32));
+            const float tf = ts < my_cut ? ts : __uint_as_float(__float_as_uint(my_cut) - 1u);
             float xw[8];
             if (((lo - alo + c0) & 3) == 0) {
               const float4 x0 = *reinterpret_cast<const float4*>(xnr + c0);
@@ -655,18 +710,22 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
 #pragma unroll
               for (int j = 0; j < 8; j++) xw[j] = xnr[c0 + j];
             }
+            auto pairs = [&](auto whole) {  // whole: all 8 rows inside the tile
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-              const float dot = __uint_as_float(cur[j]);
-              const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xw[j] + my_qn) : -dot;
-              if (j < lim && sc <= tf && sc < my_cut) {
-                const uint64_t key = make_key(sc, (uint32_t)prm[c0 + j]);
-                if (key < thr) {
-                  queue[(size_t)qcnt * TC_C + tid] = key;
-                  qcnt++;
+              for (int j = 0; j < 8; j++) {
+                const float dot = __uint_as_float(cur[j]);
+                const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xw[j] + my_qn) : -dot;
+                if ((decltype(whole)::value || j < lim) && sc <= tf) {
+                  const uint64_t key = make_key(sc, (uint32_t)prm[c0 + j]);
+                  if (key < thr) {
+                    queue[(size_t)qcnt * TC_C + tid] = key;
+                    qcnt++;
+                  }
                 }
               }
-            }
+            };
+            if (lim >= 8) pairs(std::true_type{});
+            else pairs(std::false_type{});
           } else {
             // the 8 rows' block ids and attribute words in few wide loads
             // (the same addresses for every lane: broadcast)
@@ -712,26 +771,37 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       }
       flush();
       consumers_sync();  // every queue drained: the queue area holds the quarter lists
-      // merge the quarter lists of each probe, as many lists per round as the
-      // queue area holds
+      // merge the four quarter lists of each probe: in two levels (parts 1
+      // and 3 hand theirs to parts 0 and 2, then part 2 to part 0) when two
+      // lists per probe fit in the queue area, else one list at a time
       uint64_t* parts = queue;
       bool fine = s_fail == 0;
-      constexpr int PER_ROUND = (TC_Q * TC_C) / (KP * TC_M) < TC_PARTS - 1
-                                    ? (TC_Q * TC_C) / (KP * TC_M)
-                                    : TC_PARTS - 1;
-      for (int q0 = 1; q0 < TC_PARTS; q0 += PER_ROUND) {
-        if (fine && part >= q0 && part < q0 + PER_ROUND) {
+      static_assert(TC_PARTS == 4 && KP * TC_M <= TC_Q * TC_C, "quarter lists");
+      if constexpr (2 * KP * TC_M <= TC_Q * TC_C) {
+        if (fine && (part & 1)) {
 #pragma unroll
-          for (int i = 0; i < KP; i++)
-            parts[((size_t)(part - q0) * KP + i) * TC_M + probe] = L[i];
+          for (int i = 0; i < KP; i++) parts[((size_t)(part >> 1) * KP + i) * TC_M + probe] = L[i];
         }
         consumers_sync();
-        if (fine && part == 0 && active) {
-          for (int q = 0; q < PER_ROUND && q0 + q < TC_PARTS; q++)
+        if (fine && !(part & 1) && active)
+          net_merge<KP>(L, parts + (size_t)(part >> 1) * KP * TC_M + probe);
+        if (fine && part == 2) {  // into the slot only this thread read
 #pragma unroll
-            for (int i = 0; i < KP; i++) net_insert<KP>(L, parts[((size_t)q * KP + i) * TC_M + probe]);
+          for (int i = 0; i < KP; i++) parts[((size_t)KP + i) * TC_M + probe] = L[i];
         }
         consumers_sync();
+        if (fine && part == 0 && active) net_merge<KP>(L, parts + (size_t)KP * TC_M + probe);
+        // (the barrier before the next item's first queue write follows below)
+      } else {
+        for (int src = 1; src < TC_PARTS; src++) {
+          if (fine && part == src) {
+#pragma unroll
+            for (int i = 0; i < KP; i++) parts[(size_t)i * TC_M + probe] = L[i];
+          }
+          consumers_sync();
+          if (fine && part == 0 && active) net_merge<KP>(L, parts + probe);
+          consumers_sync();
+        }
       }
       if (fine && part == 0 && active) {
         const int e = p_e[par][probe];
@@ -766,10 +836,12 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     // flight land (bounded waits), release tensor memory and leave
     if (warp == TC_PRODUCER && lane == 0) {
       atomicExch(a.err, 1);
-      for (int g = max(0, tma_hi - S + 1); g <= tma_hi; g++)
-        mbar_wait(&full_bar[g % S], (uint32_t)((g / S) & 1), nullptr);
-      for (int g = max(0, mma_hi - S + 1); g <= mma_hi; g++)
-        mbar_wait(&mma_bar[g % S], (uint32_t)((g / S) & 1), nullptr);
+      for (int g = max(0, tma_hi - SB + 1); g <= tma_hi; g++)
+        mbar_wait(&full_bar[g % SB], (uint32_t)((g / SB) & 1), nullptr);
+      for (int g = max(0, tma_hi - ST + 1); g <= tma_hi; g++)
+        mbar_wait(&aux_bar[g % ST], (uint32_t)((g / ST) & 1), nullptr);
+      for (int g = max(0, mma_hi - ST + 1); g <= mma_hi; g++)
+        mbar_wait(&mma_bar[g % ST], (uint32_t)((g / ST) & 1), nullptr);
     }
   }
   tc_fence_before();
