@@ -234,7 +234,7 @@ k_scan_blocks(int32_t* __restrict__ data, int64_t n, int32_t* __restrict__ sums)
   __shared__ int tot;
   const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK;
   int carry = 0;
-  for (int it = 0; it < SCAN_ITEMS; it++) {
+  for (int it = 0; it < SCAN_ITEMS && base + (int64_t)it * SCAN_T < n; it++) {  // block-uniform
     const int64_t e = base + (int64_t)it * SCAN_T + threadIdx.x;
     const int v = e < n ? data[e] : 0;
     const int inc = block_incl_scan(v, wsum);

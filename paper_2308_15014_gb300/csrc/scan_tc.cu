@@ -211,6 +211,56 @@ __global__ void k_bin_scatter(const int32_t* __restrict__ probe, int64_t ne,
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < ne) ent[atomicAdd(&cursor[probe[i]], 1)] = (int32_t)i;
 }
+// The same grouping without contended global atomics (B <= kBinShared): G
+// blocks each count their slice of the entries in shared memory; a scan over
+// the blocks gives every (partition, block) its first output position, and
+// each block scatters its slice through shared-memory cursors.
+constexpr int GRP_T = 512, kBinShared = 12288, kBinBlocks = 128;
+__global__ void __launch_bounds__(GRP_T)
+k_bin_hist(const int32_t* __restrict__ probe, int64_t ne, int64_t chunk, int B, int G,
+           int32_t* __restrict__ bin_cnt, int32_t* __restrict__ blk) {
+  extern __shared__ int h[];
+  for (int i = threadIdx.x; i < B; i += GRP_T) h[i] = 0;
+  __syncthreads();
+  const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(ne, beg + chunk);
+  for (int64_t e = beg + threadIdx.x; e < end; e += GRP_T) atomicAdd(&h[probe[e]], 1);
+  __syncthreads();
+  for (int i = threadIdx.x; i < B; i += GRP_T) {
+    const int c = h[i];
+    blk[(int64_t)i * G + blockIdx.x] = c;
+    if (c) atomicAdd(&bin_cnt[i], c);
+  }
+}
+// One warp per partition: blk[b][g] becomes bin_off[b] + the counts of the
+// blocks before g.
+__global__ void k_bin_blockscan(const int32_t* __restrict__ bin_off, int B, int G,
+                                int32_t* __restrict__ blk) {
+  const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (b >= B) return;
+  int carry = bin_off[b];
+  for (int g0 = 0; g0 < G; g0 += 32) {
+    const int g = g0 + lane;
+    const int c = g < G ? blk[(int64_t)b * G + g] : 0;
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (g < G) blk[(int64_t)b * G + g] = carry + inc - c;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+}
+__global__ void __launch_bounds__(GRP_T)
+k_bin_scatter_blk(const int32_t* __restrict__ probe, int64_t ne, int64_t chunk, int B, int G,
+                  const int32_t* __restrict__ blk, int32_t* __restrict__ ent) {
+  extern __shared__ int cur[];
+  for (int i = threadIdx.x; i < B; i += GRP_T) cur[i] = blk[(int64_t)i * G + blockIdx.x];
+  __syncthreads();
+  const int64_t beg = (int64_t)blockIdx.x * chunk, end = min(ne, beg + chunk);
+  for (int64_t e = beg + threadIdx.x; e < end; e += GRP_T) ent[atomicAdd(&cur[probe[e]], 1)] = (int32_t)e;
+}
+
 // Within each partition, order the probe entries by a 12-bit code of their
 // selected-block mask (lowest block, highest block, number of blocks): probes
 // that scan the same blocks end up in the same work item.  One CTA per
@@ -446,19 +496,35 @@ int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B
   if (int rc = scr.get(&cursor, (size_t)B + 1)) return rc;
   // partition histogram, offsets, scatter; then mask order inside each partition
   CAPS_CUDA(cudaMemsetAsync(bin_off, 0, sizeof(int32_t) * ((size_t)B + 1), s));
+  const bool shared_bins = B <= kBinShared;
+  const int G = (int)std::min<int64_t>(kBinBlocks, std::max<int64_t>(1, (ne + 2047) / 2048));
+  const int64_t chunk = (ne + G - 1) / G;
+  const size_t hsm = sizeof(int32_t) * (size_t)B;
+  int32_t* blk = nullptr;
   const unsigned g = (unsigned)((ne + 255) / 256);
-  if (ne > 0) {
+  if (ne > 0 && shared_bins) {
+    if (int rc = scr.get(&blk, (size_t)B * G)) return rc;
+    k_bin_hist<<<(unsigned)G, GRP_T, hsm, s>>>(probe, ne, chunk, B, G, bin_off, blk);
+    CAPS_LAUNCH("k_bin_hist");
+  } else if (ne > 0) {
     k_bin_count<<<g, 256, 0, s>>>(probe, ne, bin_off);
     CAPS_LAUNCH("k_bin_count");
   }
   if (int rc = scan_exclusive_i32(bin_off, (int64_t)B + 1, scr, s)) return rc;
-  CAPS_CUDA(cudaMemcpyAsync(cursor, bin_off, sizeof(int32_t) * ((size_t)B + 1),
-                            cudaMemcpyDeviceToDevice, s));
   if (ne > 0) {
     int32_t* tmp = nullptr;
     if (int rc = scr.get(&tmp, (size_t)ne)) return rc;
-    k_bin_scatter<<<g, 256, 0, s>>>(probe, ne, cursor, tmp);
-    CAPS_LAUNCH("k_bin_scatter");
+    if (shared_bins) {
+      k_bin_blockscan<<<(unsigned)(((int64_t)B * 32 + 255) / 256), 256, 0, s>>>(bin_off, B, G, blk);
+      CAPS_LAUNCH("k_bin_blockscan");
+      k_bin_scatter_blk<<<(unsigned)G, GRP_T, hsm, s>>>(probe, ne, chunk, B, G, blk, tmp);
+      CAPS_LAUNCH("k_bin_scatter_blk");
+    } else {
+      CAPS_CUDA(cudaMemcpyAsync(cursor, bin_off, sizeof(int32_t) * ((size_t)B + 1),
+                                cudaMemcpyDeviceToDevice, s));
+      k_bin_scatter<<<g, 256, 0, s>>>(probe, ne, cursor, tmp);
+      CAPS_LAUNCH("k_bin_scatter");
+    }
     k_bin_group_mask<<<(unsigned)B, 512, 0, s>>>(bin_off, sel, tmp, w->ent);
     CAPS_LAUNCH("k_bin_group_mask");
   }
