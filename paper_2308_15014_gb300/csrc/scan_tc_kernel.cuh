@@ -348,6 +348,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   __shared__ int run_lo[64], run_hi[64], run_j0[64];
   __shared__ int n_runs;
   __shared__ int32_t boff[65];
+  __shared__ uint8_t s_pbit[32];  // penalty form: word * 32 + bit of the g-th encoded bit
 
   if (tid == 0) {
     for (int i = 0; i < SB; i++) {
@@ -364,6 +365,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     mbar_init(&afull_bar, TC_C / 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
+    int gb = 0;
+    for (int w = 0; w < WP; w++)
+      for (uint32_t um = a.pen_mask[w]; um && gb < 32; um &= um - 1) s_pbit[gb++] = (uint8_t)(32 * w + __ffs(um) - 1);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -487,34 +491,40 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       *reinterpret_cast<uint4*>(sA + (size_t)c * TC_M * 128 + t * 128 + ((uu ^ (t & 7)) << 4)) = v;
     }
     if (PEN) {
-      unsigned char* rowp = sA + (size_t)a.kcd * TC_M * 128 + t * 128;
-      *reinterpret_cast<uint4*>(rowp + ((2 * qq) << 4)) = make_uint4(0u, 0u, 0u, 0u);
-      *reinterpret_cast<uint4*>(rowp + ((2 * qq + 1) << 4)) = make_uint4(0u, 0u, 0u, 0u);
-      consumers_sync();  // the chunk is zero before the -P entries go in
-      if (qq == 0 && q >= 0) {
+      // each of the row's four threads computes 16 of the chunk's columns
+      uint16_t negP = 0;
+      uint64_t sel = 0ull;
+      if (q >= 0) {
         const float bound = 4.f * (a.xn_max + p_qn[t]);
         int ex = (int)((__float_as_uint(bound) >> 23) & 0xffu) - 126;  // 2^ex >= bound
         ex = max(0, min(126, ex));
-        const uint16_t negP = (uint16_t)(0x8000u | ((uint32_t)(ex + 127) << 7));
-        auto put = [&](int col) {
-          *reinterpret_cast<uint16_t*>(rowp + (((col >> 3) ^ (t & 7)) << 4) + (col & 7) * 2) = negP;
-        };
-        int gb = 0;
+        negP = (uint16_t)(0x8000u | ((uint32_t)(ex + 127) << 7));
+        sel = p_sel[t];
+      }
+      const int nbit = 2 * a.pen_bits;
+      uint32_t w32[8];
 #pragma unroll
-        for (int w = 0; w < WP; w++) {
-          uint32_t um = a.pen_mask[w];
-          const uint32_t qm = p_qm[t * WP + w], qv = p_qv[t * WP + w];
-          while (um) {
-            const int i = __ffs(um) - 1;
-            um &= um - 1;
-            if ((qm >> i) & 1u) put(2 * gb + 1 - (int)((qv >> i) & 1u));
-            gb++;
+      for (int h = 0; h < 16; h++) {
+        const int c = 16 * qq + h;
+        bool masked = false;
+        if (q >= 0) {
+          if (c < nbit) {  // the column of the bit value the filter rules out
+            const int pb = s_pbit[c >> 1], w = pb >> 5, i = pb & 31;
+            const uint32_t qm = p_qm[t * WP + w], qv = p_qv[t * WP + w];
+            masked = ((qm >> i) & 1u) && (uint32_t)(c & 1) != ((qv >> i) & 1u);
+          } else if (c < nbit + nb) {  // a block the probe does not select
+            masked = !((sel >> (c - nbit)) & 1ull);
           }
         }
-        const uint64_t sel = p_sel[t];
-        for (int j = 0; j < nb; j++)
-          if (!((sel >> j) & 1ull)) put(2 * a.pen_bits + j);
+        const uint32_t v = masked ? (uint32_t)negP : 0u;
+        if (h & 1) w32[h >> 1] |= v << 16;
+        else w32[h >> 1] = v;
       }
+      unsigned char* rowp = sA + (size_t)a.kcd * TC_M * 128 + t * 128;
+      *reinterpret_cast<uint4*>(rowp + (((2 * qq) ^ (t & 7)) << 4)) =
+          make_uint4(w32[0], w32[1], w32[2], w32[3]);
+      *reinterpret_cast<uint4*>(rowp + (((2 * qq + 1) ^ (t & 7)) << 4)) =
+          make_uint4(w32[4], w32[5], w32[6], w32[7]);
     }
     fence_async_smem();  // generic stores of A before the MMAs read it
   };
