@@ -120,7 +120,15 @@ k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ de
     }
   }
   __syncwarp();
-  if (live && T != kEmptyKey && cnt <= 128) {
+  if (live && T != kEmptyKey && cnt <= 64) {  // (kp <= 64: the first kp are enough)
+    uint64_t v[2];
+#pragma unroll
+    for (int s = 0; s < 2; s++) v[s] = (2 * lane + s < cnt) ? cbuf[2 * lane + s] : kEmptyKey;
+    warp_sort<2>(v, lane);
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; s++) cbuf[2 * lane + s] = v[s];
+  } else if (live && T != kEmptyKey && cnt <= 128) {
     uint64_t v[4];
 #pragma unroll
     for (int s = 0; s < 4; s++) v[s] = (4 * lane + s < cnt) ? cbuf[4 * lane + s] : kEmptyKey;

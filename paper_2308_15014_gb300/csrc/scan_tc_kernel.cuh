@@ -16,7 +16,8 @@
 // (TMEM lane p), one per quarter of the tile's rows: for every row the
 // thread keeps the pair only if the probe selected the row's block and the
 // row passes the probe's filter, forms the approximate score (L2:
-// |x|^2 + |q|^2 - 2 q.x in fp32; IP: -q.x) and, if it beats the thread's
+// |x|^2 - 2 q.x in fp32, the query's own |q|^2 left out because keys are only
+// ever compared with keys of the same query; IP: -q.x) and, if it beats the thread's
 // current threshold, appends the key to a small queue in shared memory; when
 // any lane's queue fills, the warp merges every queue into the lanes' sorted
 // KP-key register lists with a fixed compare-exchange network (no divergent
@@ -31,9 +32,9 @@
 // passes has only exact zero products there, so its dot product is the same
 // fp32 value as without the chunk; a pair that fails gets at least -P added.
 // With P = 2^e >= 4 (max_x |x|^2 + |q|^2) every failing pair scores at least
-// 1.49 P (L2) or 0.87 P (IP) while every passing pair scores below 0.51 P or
-// 0.13 P, so the epilogue only compares the score against P (L2) or P/2
-// (IP) and never reads attribute words or block ids.
+// 1.49 P - |q|^2 >= 1.24 P (L2) or 0.87 P (IP) while every passing pair scores
+// below 0.51 P or 0.13 P, so the epilogue only compares the score against P
+// (L2) or P/2 (IP) and never reads attribute words or block ids.
 #pragma once
 
 #include <cuda.h>
@@ -648,7 +649,6 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         my_qm[w] = p_qm[probe * WP + w];
         my_qv[w] = p_qv[probe * WP + w];
       }
-      const float my_qn = p_qn[probe];
       const float my_cut = PEN ? p_cut[probe] : 0.f;
       const int my_q = active ? p_e[par][probe] / a.m : 0;
       __syncwarp();
@@ -724,7 +724,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
 #pragma unroll
               for (int j = 0; j < 8; j++) {
                 const float dot = __uint_as_float(cur[j]);
-                const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xw[j] + my_qn) : -dot;
+                const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xw[j]) : -dot;
                 if ((decltype(whole)::value || j < lim) && sc <= tf) {
                   const uint64_t key = make_key(sc, (uint32_t)prm[c0 + j]);
                   if (key < thr) {
@@ -760,7 +760,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
               if (pass) {
                 const int r = c0 + j;
                 const float dot = __uint_as_float(cur[j]);
-                const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r] + my_qn) : -dot;
+                const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r]) : -dot;
                 const uint64_t key = make_key(sc, (uint32_t)prm[r]);
                 // label sets: the signature test above is necessary; the
                 // exact test runs only for keys that would enter the list
