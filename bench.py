@@ -64,8 +64,9 @@ def parse():
     ap.add_argument("--config", choices=["sift1m", "small"], default="sift1m")
     ap.add_argument("--m", type=int, default=0, help="fixed probe count (0 = sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--paths", default="mlp_bf16,fp32,bf16",
-                    help="comma list of search paths (fp32, bf16, mlp_fp32, mlp_bf16); "
+    ap.add_argument("--paths", default="mlp_bf16,fp32,bf16,fp8",
+                    help="comma list of search paths (fp32, bf16, fp8, mlp_fp32, mlp_bf16, "
+                         "mlp_fp8); "
                          "the first is the headline")
     ap.add_argument("--h-sweep", action="store_true",
                     help="also sweep the AFT height h (k-means + bf16): QPS at recall@10 >= 0.9")
@@ -249,32 +250,56 @@ def traffic_from_profile(kernel=SCAN_KERNEL, src_name=SCAN_SRC, m=None):
     return None
 
 
-def form1_error(w, rng_seed=11, nq=64, nrow=2048):
-    """Relative error of the BF16 tile score against the FP64 distance.
+def e4m3(v):
+    """Round to the nearest e4m3 value (ties to even, saturating at 448): three
+    mantissa bits, exponent bias 7, subnormal spacing 2^-9."""
+    v = np.asarray(v, dtype=np.float64)
+    a = np.abs(v)
+    e = np.minimum(np.floor(np.log2(np.maximum(a, 2.0 ** -6))), 8.0)
+    quantum = 2.0 ** (e - 3)
+    return np.sign(v) * np.minimum(np.round(a / quantum) * quantum, 448.0)
 
-    The tensor-core tile multiplies bf16-rounded vectors and accumulates in
-    fp32; the score is |x|^2 + |q|^2 - 2 q.x with fp32 norms.  Here the bf16
-    rounding is applied to x and q, the products are summed in fp64 (the
-    fp32 accumulation adds at most ~d * 2^-24 relative), and the result is
-    compared with the exact squared distance in fp64 on random (query, row)
-    pairs.  The returned distances themselves are exact fp32 (re-ranked)."""
+
+def form1_error(w, rng_seed=11, nq=64, nrow=2048):
+    """Relative error of the BF16 and the e4m3 tile score against the FP64
+    distance.
+
+    The tensor-core tile multiplies rounded vectors and accumulates in fp32;
+    the score is |x|^2 + |q|^2 - 2 q.x with fp32 norms.  BF16: x and q rounded
+    to bf16.  e4m3: each row (and query) scaled by s = max |x| / 448 (fp32),
+    x / s (fp32) rounded to e4m3, the dot product multiplied back by the two
+    scales.  The products are summed in fp64 here (the fp32 accumulation adds
+    at most ~d * 2^-24 relative) and compared with the exact squared distance
+    in fp64 on random (query, row) pairs.  The returned distances themselves
+    are exact fp32 (re-ranked)."""
     rng = np.random.default_rng(rng_seed)
     qi = rng.choice(w.Q.shape[0], min(nq, w.Q.shape[0]), replace=False)
     ri = rng.choice(w.X.shape[0], min(nrow, w.X.shape[0]), replace=False)
-    X = w.X[ri].astype(np.float64)
-    Q = w.Q[qi].astype(np.float64)
+    X32, Q32 = w.X[ri].astype(np.float32), w.Q[qi].astype(np.float32)
+    X, Q = X32.astype(np.float64), Q32.astype(np.float64)
 
     def bf16(a):
         u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
         u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000  # round to nearest even
         return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
+    def scaled_e4m3(a32):
+        amax = np.abs(a32).max(1)
+        sc = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+        return e4m3((a32 / sc[:, None]).astype(np.float32)), sc.astype(np.float64)
+
     xn = (X * X).sum(1)
     qn = (Q * Q).sum(1)
-    approx = xn[None, :] + qn[:, None] - 2.0 * (bf16(Q) @ bf16(X).T)
     exact = ((Q[:, None, :] - X[None, :, :]) ** 2).sum(-1)
-    rel = np.abs(approx - exact) / np.maximum(exact, 1e-30)
-    return {"pairs": int(rel.size), "max_rel": float(rel.max()), "mean_rel": float(rel.mean())}
+    out = {}
+    x8, xs = scaled_e4m3(X32)
+    q8, qs = scaled_e4m3(Q32)
+    for name, dot in (("bf16", bf16(Q) @ bf16(X).T), ("e4m3", (q8 @ x8.T) * qs[:, None] * xs[None, :])):
+        approx = xn[None, :] + qn[:, None] - 2.0 * dot
+        rel = np.abs(approx - exact) / np.maximum(exact, 1e-30)
+        out[name] = {"pairs": int(rel.size), "max_rel": float(rel.max()),
+                     "mean_rel": float(rel.mean())}
+    return out
 
 
 def h_sweep(args, w, caps, O, torch, samp, gt, g64, cnt):
@@ -575,7 +600,8 @@ def run_caps(args):
     gt, _, g64, cnt = O.bruteforce(w.X, O.Attrs.of(w), w.Q[samp], O.Cons(Qb=w.Qb[samp]), w.k)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     kinds = {"fp32": (caps.FP32, caps.KMEANS), "bf16": (caps.BF16, caps.KMEANS),
-             "mlp_fp32": (caps.FP32, caps.MLP), "mlp_bf16": (caps.BF16, caps.MLP)}
+             "fp8": (caps.FP8, caps.KMEANS), "mlp_fp32": (caps.FP32, caps.MLP),
+             "mlp_bf16": (caps.BF16, caps.MLP), "mlp_fp8": (caps.FP8, caps.MLP)}
     paths = [p for p in args.paths.split(",") if p]
     res = {}
     for pth in paths:
@@ -640,7 +666,7 @@ def run_caps(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_v = world * w.nq / float(np.mean(e2e_t))
 
-    # ---- form 1: bf16 tile scores and returned distances against fp64 -------
+    # ---- form 1: bf16 / e4m3 tile scores and returned distances against fp64 -
     from workloads import make_dense_workload
     wf = make_dense_workload(name="float_mixture", N=20_000, d=w.d, ncomp=100,
                              center=("uniform", 128.0), sigma=16.0, vocab=[20, 50, 100],
@@ -676,7 +702,8 @@ def run_caps(args):
         "metric": METRIC, "value": round(head["value"], 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms"], 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if paths[0].endswith("bf16") else "f32", "data": "synthetic",
+        "dtype": {"bf16": "bf16", "fp8": "e4m3"}.get(paths[0].split("_")[-1], "f32"),
+        "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "d": w.d, "L": int(w.A.shape[1]),
                    "B": w.B, "h": w.h, "kmeans_iters": w.iters, "m": m, "k": w.k,
                    "path": paths[0], "partitioner": "mlp 128-512-1024" if paths[0].startswith("mlp")

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libcaps_gb300.so")
-SOURCES = ["build_kernels.cu", "search_kernels.cu", "scan_bin.cu", "scan_tc.cu", "scan_tc_pen.cu", "probe_tc.cu", "mlp.cu",
+SOURCES = ["build_kernels.cu", "search_kernels.cu", "scan_bin.cu", "scan_tc.cu", "scan_tc_pen.cu", "scan_tc_f8.cu",
+           "probe_tc.cu", "mlp.cu",
            "capi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

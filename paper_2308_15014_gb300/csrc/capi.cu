@@ -380,10 +380,12 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     if (p->mlp_epochs == 0 && !p->mlp_init)
       return fail(CAPS_EINVAL, "an MLP build needs mlp_epochs > 0 or mlp_init");
   }
-  if (p->prec != CAPS_FP32 && p->prec != CAPS_BF16)
-    return fail(CAPS_EINVAL, "precision must be CAPS_FP32 or CAPS_BF16");
+  if (p->prec != CAPS_FP32 && p->prec != CAPS_BF16 && p->prec != CAPS_FP8E4M3)
+    return fail(CAPS_EINVAL, "precision must be CAPS_FP32, CAPS_BF16 or CAPS_FP8E4M3");
   if (p->prec == CAPS_BF16 && (d % 8 != 0 || d < 64 || d > 128))
     return fail(CAPS_EINVAL, "the bf16 form needs d a multiple of 8 in [64, 128]");
+  if (p->prec == CAPS_FP8E4M3 && (d % 16 != 0 || d < 64 || d > 128))
+    return fail(CAPS_EINVAL, "the e4m3 form needs d a multiple of 16 in [64, 128]");
   if (p->rerank_factor < 0 || p->rerank_factor > 16)
     return fail(CAPS_EINVAL, "rerank_factor must be in [0, 16] (0 = 4)");
   keep_pool_warm();
@@ -538,6 +540,40 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     if (int rc = build_mlp(p, dX, dA, N, d, meta, s, ix)) return rc;
     if (int rc = finish()) return rc;
   }
+  if (p->prec == CAPS_FP8E4M3) {
+    // e4m3 form: e4m3 rows (ceil(d/128)*128 bytes) + per-row scales + fp32
+    // squared norms + inverse permutation; the filter is tested per pair
+    ix->pen = 0;
+    ix->pen_bits = 0;
+    const int cols8 = (d + 127) / 128 * 128;
+    uint8_t* xb = nullptr;
+    if (int rc = ix->alloc(&xb, (size_t)N * cols8)) return rc;
+    ix->Xb = xb;
+    if (int rc = ix->alloc(&ix->xn, (size_t)N + 4)) return rc;
+    if (int rc = ix->alloc(&ix->xs, (size_t)N + 4)) return rc;
+    if (int rc = ix->alloc(&ix->iperm, (size_t)N)) return rc;
+    TcIndexPrep tp;
+    tp.Xp = ix->Xp;
+    tp.N = N;
+    tp.d = d;
+    tp.perm = ix->perm;
+    tp.Ap = ix->Ap;
+    tp.words_pad = meta.words_pad;
+    tp.offsets = ix->offsets;
+    tp.B = B;
+    tp.nb = h + 1;
+    tp.pen = 0;
+    tp.pen_bits = 0;
+    for (int w = 0; w < 4; w++) tp.pen_mask[w] = 0u;
+    tp.f8 = 1;
+    tp.xs = ix->xs;
+    tp.Xb = ix->Xb;
+    tp.xn = ix->xn;
+    tp.iperm = ix->iperm;
+    tp.xn_max = &ix->xn_max;
+    tp.tmap = ix->tmap;
+    if (int rc = tc_prepare_index(tp, s)) return rc;
+  }
   if (p->prec == CAPS_BF16) {
     // bf16 form: bf16 rows + fp32 squared norms + inverse permutation
     // penalty form when the one-hot code of the packed attribute bits (two
@@ -571,6 +607,8 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     tp.pen = ix->pen;
     tp.pen_bits = T;
     for (int w = 0; w < 4; w++) tp.pen_mask[w] = um[w];
+    tp.f8 = 0;
+    tp.xs = nullptr;
     tp.Xb = ix->Xb;
     tp.xn = ix->xn;
     tp.iperm = ix->iperm;
@@ -967,7 +1005,9 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
 
 // which forms of the tensor-core scan serve this index and k
 bool tc_explicit_ok(const caps_index* ix, int k) {
-  return ix->prec == CAPS_BF16 && tc_scan_supported(ix->d, k, tc_kp(k), ix->meta.words_pad);
+  const bool f8 = ix->prec == CAPS_FP8E4M3;
+  return (ix->prec == CAPS_BF16 || f8) &&
+         tc_scan_supported(ix->d, k, tc_kp(k), ix->meta.words_pad, f8 ? 1 : 0);
 }
 bool uses_pen(const caps_index* ix, int k) {
   return ix->prec == CAPS_BF16 && k <= 32 && ix->pen &&
@@ -1033,11 +1073,15 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
   uint64_t* part = nullptr;
   if (binmajor || tc)
     if (int rc = scr.get(&part, (size_t)qc * m * kp)) return rc;
-  uint16_t* Qh = nullptr;
+  uint16_t* Qh = nullptr;  // bf16 queries, or e4m3 bytes in the first half
   float* qn = nullptr;
+  float* qs = nullptr;
+  const int f8 = ix->prec == CAPS_FP8E4M3 ? 1 : 0;
   if (tc) {
     if (int rc = scr.get(&Qh, (size_t)qc * ix->d)) return rc;
     if (int rc = scr.get(&qn, (size_t)qc)) return rc;
+    if (f8)
+      if (int rc = scr.get(&qs, (size_t)qc)) return rc;
   }
   const int L = ix->meta.L;
   StageTimer& tm = g_timer;
@@ -1119,7 +1163,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
     a.out_dist = od.dev + c0 * k;
     if (tc) {
       BinWork w;
-      if (int rc = tc_query_prep(Qc, n, ix->d, Qh, qn, s)) return rc;
+      if (int rc = tc_query_prep(Qc, n, ix->d, Qh, qn, f8, qs, s)) return rc;
       if (int rc = tc_group(bt.probe, bt.sel, ix->h, n * m, ix->B, item_cap, &w, cscr, s))
         return rc;
       if (int rc = tm.record(s)) return rc;
@@ -1128,6 +1172,9 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
       t.qmask = bt.qp.qmask;
       t.qval = bt.qp.qval;
       t.Qh = Qh;
+      t.f8 = f8;
+      t.qs = qs;
+      t.xs = ix->xs;
       t.qn = qn;
       t.Ap = ix->Ap;
       t.perm = ix->perm;

@@ -353,7 +353,10 @@ struct TcScanArgs {
   const uint64_t* sel;
   const uint32_t* qmask;
   const uint32_t* qval;
-  const void* Qh;       // [nq*d] bf16 queries
+  const void* Qh;       // [nq*d] bf16 (or e4m3 with f8) queries
+  int f8;               // 1: e4m3 rows and queries with per-row / per-query scales
+  const float* qs;      // f8: [nq] per-query scales
+  const float* xs;      // f8: [N+4] per-row scales
   const float* qn;      // [nq] fp32 squared norms
   const uint32_t* Ap;
   const int32_t* perm;
@@ -374,7 +377,7 @@ struct TcScanArgs {
 };
 int tc_kp(int k);
 int tc_rerank_depth(int k, int factor);
-bool tc_scan_supported(int d, int k, int kp, int words_pad);
+bool tc_scan_supported(int d, int k, int kp, int words_pad, int f8 = 0);
 bool tc_pen_supported(int d, int kp, int words_pad);
 // What the bf16 form of an index is made from, and where it goes.
 struct TcIndexPrep {
@@ -388,6 +391,8 @@ struct TcIndexPrep {
   int B, nb;
   int pen, pen_bits;       // code chunk for the penalty form
   uint32_t pen_mask[4];
+  int f8;                  // 1: e4m3 rows of ceil(d/128)*128 bytes + per-row scales
+  float* xs;               // out (f8): [N] per-row scales
   void* Xb;                // out: [N*cols] bf16 rows, cols = d, or (ceil(d/64)+1)*64 with pen
   float* xn;               // out: [N] squared norms
   int32_t* iperm;          // out: original id -> layout row
@@ -395,7 +400,8 @@ struct TcIndexPrep {
   void* tmap;              // out: CUtensorMap over Xb
 };
 int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s);
-int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, cudaStream_t s);
+int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, int f8, float* qs,
+                  cudaStream_t s);
 // item_cap: most probes per work item (1..128; 0: 128)
 int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, int item_cap,
              BinWork* w, Scratch& scr, cudaStream_t s);
@@ -434,6 +440,7 @@ struct caps_index {
   int64_t n_labels = 0;
   void* Xb = nullptr;
   float* xn = nullptr;
+  float* xs = nullptr;  // e4m3 form: per-row scales [N+4]
   int32_t* iperm = nullptr;
   alignas(128) unsigned char tmap[128] = {};
   // penalty form of the bf16 scan: each bf16 row carries a 64-column one-hot

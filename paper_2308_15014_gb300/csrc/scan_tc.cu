@@ -10,8 +10,61 @@
 
 #include "scan_tc_kernel.cuh"
 
+#include <cuda_fp8.h>
+
 namespace caps {
 namespace {
+
+// ---- e4m3 rows (form 1, per-row scale) --------------------------------------
+// Scale of a row: max |x_j| / 448 (the largest finite e4m3 value), 1 for a
+// zero row; coordinate j is stored as e4m3(x_j / scale), round to nearest
+// even, saturating.
+__device__ __forceinline__ float f8_scale(float amax) { return amax > 0.f ? amax / 448.f : 1.f; }
+__device__ __forceinline__ uint8_t f8_code(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+// one warp per query: e4m3 copy (cols bytes, zero padded), the scale, and
+// the fp32 squared norm over the coordinates in order (one fma each)
+__global__ void k_query_fp8(const float* __restrict__ Q, int64_t nq, int d,
+                            uint8_t* __restrict__ Qh, float* __restrict__ qs,
+                            float* __restrict__ qn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= nq) return;
+  const float* x = Q + q * d;
+  float amax = 0.f;
+  for (int j = lane; j < d; j += 32) amax = fmaxf(amax, fabsf(x[j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  const float sc = f8_scale(amax);
+  for (int j = lane; j < d; j += 32) Qh[q * d + j] = f8_code(x[j] / sc);
+  if (lane == 0) {
+    float acc = 0.f;
+    for (int j = 0; j < d; j++) acc = fmaf(x[j], x[j], acc);
+    qn[q] = acc;
+    qs[q] = sc;
+  }
+}
+// one thread per row: e4m3 row (cols bytes, zero padded), its scale and its
+// fp32 squared norm (coordinates in order, one fma each)
+__global__ void k_rows_fp8(const float* __restrict__ Xp, int64_t N, int d, int cols,
+                           uint8_t* __restrict__ Xb, float* __restrict__ xn,
+                           float* __restrict__ xs) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const float* x = Xp + r * d;
+  float amax = 0.f, acc = 0.f;
+  for (int j = 0; j < d; j++) {
+    amax = fmaxf(amax, fabsf(x[j]));
+    acc = fmaf(x[j], x[j], acc);
+  }
+  const float sc = f8_scale(amax);
+  uint8_t* row = Xb + r * cols;
+  for (int j = 0; j < d; j++) row[j] = f8_code(x[j] / sc);
+  for (int j = d; j < cols; j++) row[j] = 0;
+  xn[r] = acc;
+  xs[r] = sc;
+}
 
 // ---- bf16 query copy and fp32 squared norms -------------------------------
 __global__ void k_query_bf16(const float* __restrict__ Q, int64_t nq, int d,
@@ -429,9 +482,10 @@ int tc_rerank_depth(int k, int factor) {
   return std::min(64, std::max(k, f * k));
 }
 
-bool tc_scan_supported(int d, int k, int kp, int words_pad) {
+bool tc_scan_supported(int d, int k, int kp, int words_pad, int f8) {
   if (d % 8 != 0 || d < 64 || d > 128 || k > 32 || (kp != 10 && kp != 16 && kp != 32))
     return false;
+  if (f8) return d % 16 == 0 && tc_fits((d + 127) / 128, words_pad, 128, false);
   return tc_fits((d + 63) / 64, words_pad, 128, false);
 }
 
@@ -442,6 +496,36 @@ bool tc_pen_supported(int d, int kp, int words_pad) {
 
 int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
   const int64_t N = p.N;
+  if (p.f8) {
+    // e4m3 rows of ceil(d / 128) * 128 bytes, per-row scales and fp32 norms
+    const int cols8 = (p.d + 127) / 128 * 128;
+    k_rows_fp8<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(p.Xp, N, p.d, cols8,
+                                                            static_cast<uint8_t*>(p.Xb), p.xn, p.xs);
+    CAPS_LAUNCH("k_rows_fp8");
+    *p.xn_max = 0.f;
+    k_inverse_perm<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(p.perm, N, p.iperm);
+    CAPS_LAUNCH("k_inverse_perm");
+    // 2-D tensor map: boxes of 128 coordinates (128 bytes) x 128 rows,
+    // 128-byte swizzle
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult qres;
+    CAPS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                               cudaEnableDefault, &qres));
+    if (!fn || qres != cudaDriverEntryPointSuccess)
+      return fail(CAPS_ECUDA, "cuTensorMapEncodeTiled is not available");
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cuuint64_t gdim[2] = {(cuuint64_t)cols8, (cuuint64_t)N};
+    cuuint64_t gstride[1] = {(cuuint64_t)cols8};
+    cuuint32_t box[2] = {128, (cuuint32_t)TC_BOX};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(static_cast<CUtensorMap*>(p.tmap), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, p.Xb,
+                        gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(CAPS_ECUDA, "cuTensorMapEncodeTiled failed (e4m3 rows)");
+    CAPS_CUDA(cudaStreamSynchronize(s));
+    return CAPS_OK;
+  }
   const int kcd = (p.d + 63) / 64;
   const int cols = p.pen ? (kcd + 1) * 64 : p.d;
   unsigned int* xmax = nullptr;
@@ -485,8 +569,14 @@ int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
   return CAPS_OK;
 }
 
-int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, cudaStream_t s) {
+int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, int f8, float* qs,
+                  cudaStream_t s) {
   if (nq == 0) return CAPS_OK;
+  if (f8) {
+    k_query_fp8<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, d, static_cast<uint8_t*>(Qh), qs, qn);
+    CAPS_LAUNCH("k_query_fp8");
+    return CAPS_OK;
+  }
   k_query_bf16<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, d,
                                                         static_cast<__nv_bfloat16*>(Qh), qn);
   CAPS_LAUNCH("k_query_bf16");
@@ -561,7 +651,9 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   a.sel = t.sel;
   a.qmask = t.qmask;
   a.qval = t.qval;
-  a.Qh = static_cast<const __nv_bfloat16*>(t.Qh);
+  a.Qh = t.Qh;
+  a.qs = t.qs;
+  a.xs = t.xs;
   a.qn = t.qn;
   a.Ap = t.Ap;
   a.perm = t.perm;
@@ -570,7 +662,7 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   a.m = t.m;
   a.h = t.h;
   a.d = t.d;
-  a.kcd = (t.d + 63) / 64;
+  a.kcd = t.f8 ? (t.d + 127) / 128 : (t.d + 63) / 64;
   a.kc = a.kcd + (t.pen ? 1 : 0);
   a.kp = t.kp;
   a.pen_bits = t.pen_bits;
@@ -596,6 +688,11 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   }
   if (!tc_fits(a.kc, t.words_pad, 128, false))
     return fail(CAPS_EINVAL, "the per-pair filter form does not fit this index");
+  if (t.f8) {
+    const int N8 = t.tile_n != 128 && tc_fits(a.kc, t.words_pad, 256, false) ? 256 : 128;
+    return tc_launch_f8(map, a, t.metric, t.words_pad, t.kp, N8, g,
+                        tc_smem_bytes(a.kc, t.words_pad, N8, false), s);
+  }
   // 256-row tiles where they fit, else 128
   const int N = t.tile_n != 128 && tc_fits(a.kc, t.words_pad, 256, false) ? 256 : 128;
   const size_t smem = tc_smem_bytes(a.kc, t.words_pad, N, false);

@@ -58,7 +58,9 @@ struct TcArgs {
   const uint64_t* sel;
   const uint32_t* qmask;
   const uint32_t* qval;
-  const __nv_bfloat16* Qh;  // [nq*d]
+  const void* Qh;           // [nq*d] bf16 or e4m3 (F8) query rows
+  const float* qs;          // F8: [nq] per-query scale
+  const float* xs;          // F8: [N+4] per-row scale, layout order
   const float* qn;          // [nq]
   const uint32_t* Ap;
   const int32_t* perm;
@@ -192,6 +194,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, 
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
       "l"(ad), "l"(bd), "r"(id), "r"(acc));
 }
+// Instruction descriptor: e4m3 x e4m3 -> f32 (format code 0 for A and B), A
+// and B K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f8(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f8(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t id,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(id), "r"(acc));
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    su32(bar))
@@ -218,10 +232,10 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&v)[8]) {
 __host__ __device__ constexpr int tc_stages(int N, bool pen) { return pen ? 2 : TC_COLS / N; }
 __host__ __device__ constexpr size_t tc_a_bytes(int kc) { return (size_t)kc * TC_M * 128; }
 __host__ __device__ constexpr size_t tc_b_bytes(int kc, int N) { return (size_t)kc * N * 128; }
-// per stage: attribute words, ids and norms of N + 8 rows (4-row aligned
-// superset of the tile), block id of each row
+// per stage: attribute words, ids, norms and (e4m3 rows) scales of N + 8
+// rows (4-row aligned superset of the tile), block id of each row
 __host__ __device__ constexpr size_t tc_aux_bytes(int WP, int N) {
-  return (((size_t)(N + 8) * WP * 4 + (size_t)(N + 8) * 8 + (size_t)(N + 8)) + 15) & ~(size_t)15;
+  return (((size_t)(N + 8) * WP * 4 + (size_t)(N + 8) * 12 + (size_t)(N + 8)) + 15) & ~(size_t)15;
 }
 // shared memory one CTA may hold (227 KB), and an upper bound of the
 // kernel's static part (barriers, per-probe arrays, the tile schedule)
@@ -300,7 +314,7 @@ __device__ __forceinline__ void net_merge(uint64_t (&L)[KP], const uint64_t* oth
 // every slot holds a key, the largest of them, T, has at least ns * KP >= R
 // keys of distinct lists at or below it, so a later partition of that query
 // drops every key above T: such a key cannot be among the R best.
-template <int METRIC, int WP, int KP, int N, bool PEN>
+template <int METRIC, int WP, int KP, int N, bool PEN, bool F8>
 __global__ void __launch_bounds__(TC_T, 1)
 k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   // SB shared-memory stages hold B tiles (free once the tile's MMAs are
@@ -329,7 +343,11 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   auto s_xn = [&](int b) {
     return reinterpret_cast<float*>(aux0 + b * astride + (size_t)RA * WP * 4 + RA * 4);
   };
-  auto s_blk = [&](int b) { return aux0 + b * astride + (size_t)RA * WP * 4 + RA * 8; };
+  auto s_xs = [&](int b) {
+    return reinterpret_cast<float*>(aux0 + b * astride + (size_t)RA * WP * 4 + RA * 8);
+  };
+  auto s_blk = [&](int b) { return aux0 + b * astride + (size_t)RA * WP * 4 + RA * 12; };
+  static_assert(!(PEN && F8), "the penalty form is bf16 only");
 
   __shared__ uint64_t full_bar[SB], bfree_bar[SB], aux_bar[ST], mma_bar[ST], empty_bar[ST];
   __shared__ uint64_t taken_bar, meta_bar, afull_bar;
@@ -380,7 +398,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
-  const uint32_t idesc = idesc_bf16(TC_M, N);
+  const uint32_t idesc = F8 ? idesc_f8(TC_M, N) : idesc_bf16(TC_M, N);
 
   // ---- producer: take the next item and prepare everything but A ----------
   // (fills s_ne/s_ntiles/s_bin/p_e/p_thr[par], the probe data, the runs)
@@ -482,12 +500,15 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     const int t = tid & (TC_M - 1), qq = tid / TC_M;
     const int ne_n = s_ne[par];
     const int q = t < ne_n ? p_e[par][t] / a.m : -1;
-    const int units = a.kcd * 8, dunits = a.d / 8;
+    // 16-byte units: 8 bf16 or 16 e4m3 coordinates
+    const int rowb = a.d * (F8 ? 1 : 2);
+    const int units = a.kcd * 8, dunits = rowb / 16;
+    const unsigned char* qrow = static_cast<const unsigned char*>(a.Qh) + (int64_t)(q < 0 ? 0 : q) * rowb;
     const int u0 = qq * units / TC_PARTS, u1 = (qq + 1) * units / TC_PARTS;
 #pragma unroll 4
     for (int u = u0; u < u1; u++) {
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (q >= 0 && u < dunits) v = *reinterpret_cast<const uint4*>(a.Qh + (int64_t)q * a.d + 8 * u);
+      if (q >= 0 && u < dunits) v = *reinterpret_cast<const uint4*>(qrow + 16 * u);
       const int c = u >> 3, uu = u & 7;
       *reinterpret_cast<uint4*>(sA + (size_t)c * TC_M * 128 + t * 128 + ((uu ^ (t & 7)) << 4)) = v;
     }
@@ -591,10 +612,11 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
             for (int hb = 0; hb < N / TC_BOX; hb++)
               tma_2d(sB + (size_t)c * N * 128 + (size_t)hb * TC_BOX * 128, &tmX, 64 * c,
                      lo + hb * TC_BOX, &full_bar[sb]);
-          expect_tx(&aux_bar[st], ab + 2 * pb);
+          expect_tx(&aux_bar[st], ab + (F8 ? 3 : 2) * pb);
           if (!PEN) bulk_copy(s_attr(st), a.Ap + (int64_t)alo * WP, ab, &aux_bar[st]);
           bulk_copy(s_perm(st), a.perm + alo, pb, &aux_bar[st]);
           bulk_copy(s_xn(st), a.xn + alo, pb, &aux_bar[st]);
+          if (F8) bulk_copy(s_xs(st), a.xs + alo, pb, &aux_bar[st]);
           tma_hi = g;
         }
         return true;
@@ -615,7 +637,8 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
               const int c = ks >> 2, kin = ks & 3;
               const uint64_t ad = sdesc(a0 + (uint32_t)(c * TC_M * 128 + kin * 32));
               const uint64_t bd = sdesc(b0 + (uint32_t)(c * N * 128 + kin * 32));
-              mma_bf16(tbase + (uint32_t)(st * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
+              if (F8) mma_f8(tbase + (uint32_t)(st * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
+              else mma_bf16(tbase + (uint32_t)(st * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
             }
             mma_commit(&mma_bar[st]);
             mma_commit(&bfree_bar[sb]);
@@ -651,6 +674,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       }
       const float my_cut = PEN ? p_cut[probe] : 0.f;
       const int my_q = active ? p_e[par][probe] / a.m : 0;
+      const float my_qs = F8 && active ? a.qs[my_q] : 1.f;  // e4m3: the query's scale
       __syncwarp();
       if (lane == 0) mbar_arrive(&taken_bar);  // the producer may refill the probe data
       uint64_t* pthr = p_thr[par];
@@ -688,6 +712,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         const uint32_t* attr = s_attr(b) + (lo - alo) * WP;
         const int32_t* prm = s_perm(b) + (lo - alo);
         const float* xnr = s_xn(b) + (lo - alo);
+        const float* xsr = s_xs(b) + (lo - alo);
         const uint8_t* blk = s_blk(b);
         const uint32_t tacc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * N + cbeg);
         const int ncol = warp_live ? min(CPT, n - cbeg) : 0;  // warp-uniform
@@ -759,7 +784,8 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
               for (int w = 0; w < WP; w++) pass = pass && ((aw[j * WP + w] & my_qm[w]) == my_qv[w]);
               if (pass) {
                 const int r = c0 + j;
-                const float dot = __uint_as_float(cur[j]);
+                float dot = __uint_as_float(cur[j]);
+                if (F8) dot *= my_qs * xsr[r];  // the rows' and the query's scales
                 const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xnr[r]) : -dot;
                 const uint64_t key = make_key(sc, (uint32_t)prm[r]);
                 // label sets: the signature test above is necessary; the
@@ -861,9 +887,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(TC_COLS));
 }
 
-template <int METRIC, int WP, int KP, int N, bool PEN>
+template <int METRIC, int WP, int KP, int N, bool PEN, bool F8 = false>
 int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem, cudaStream_t s) {
-  auto kern = k_scan_tc<METRIC, WP, KP, N, PEN>;
+  auto kern = k_scan_tc<METRIC, WP, KP, N, PEN, F8>;
   cudaFuncAttributes fa;
   CAPS_CUDA(cudaFuncGetAttributes(&fa, kern));
   if (smem + fa.sharedSizeBytes > kTcSmemLimit)
@@ -876,6 +902,10 @@ int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem
 
 }  // namespace
 
+// Launch of the e4m3 form (scan_tc_f8.cu): per-pair filter, N = 256 or 128
+// rows per tile; kp 10, 16 or 32.
+int tc_launch_f8(const CUtensorMap& map, const TcArgs& a, int metric, int words_pad, int kp, int N,
+                 int64_t grid, size_t smem, cudaStream_t s);
 // Launch of the penalty form (scan_tc_pen.cu): N = 128 rows per tile, two
 // stages; kp 10 or 16.
 int tc_launch_pen(const CUtensorMap& map, const TcArgs& a, int metric, int words_pad, int kp,

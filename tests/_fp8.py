@@ -1,0 +1,70 @@
+"""Plain model of the FP8 (e4m3) form of the scan, for the GPU tests.
+
+e4m3 (three mantissa bits, exponent bias 7, subnormal spacing 2^-9, largest
+finite value 448, round to nearest even, saturating); each row and query is
+scaled by s = max |x| / 448 in fp32 and stored as e4m3(x / s).  The form's
+approximate score of a passing (probe, row) pair is |x|^2 - 2 s_q s_x (q8 . x8)
+(L2; the query's own norm is common to all its keys) or -s_q s_x (q8 . x8)
+(IP); each probed partition keeps its KP best keys (score, then id), each
+query re-scores its R best keys over the m lists with the oracle's exact
+fp32 distance and keeps the k best (distance, then id).
+"""
+import numpy as np
+
+import oracle as O
+
+
+def e4m3(v):
+    v = np.asarray(v, dtype=np.float64)
+    a = np.abs(v)
+    e = np.minimum(np.floor(np.log2(np.maximum(a, 2.0 ** -6))), 8.0)
+    quantum = 2.0 ** (e - 3)
+    return np.sign(v) * np.minimum(np.round(a / quantum) * quantum, 448.0)
+
+
+def scaled_e4m3(a):
+    a32 = np.asarray(a, dtype=np.float32)
+    amax = np.abs(a32).max(1)
+    s = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    return e4m3((a32 / s[:, None]).astype(np.float32)), s.astype(np.float64)
+
+
+def kp_of(k):
+    return 10 if k <= 10 else (16 if k <= 16 else 32)
+
+
+def rerank_depth(k):
+    return min(64, max(k, 4 * k))
+
+
+def search(w, oi, k, m):
+    """ids [nq, k] of the FP8 form (-1 padded)."""
+    KP, R, nb = kp_of(k), rerank_depth(k), w.h + 1
+    P = O.probe(w.Q, oi.C, m, w.metric)
+    S = O.select(oi.tags, w.h, O.Attrs.of(w), P, O.Cons.of(w))
+    x8, xs = scaled_e4m3(w.X)
+    q8, qs = scaled_e4m3(w.Q)
+    xn = (w.X.astype(np.float64) ** 2).sum(1)
+    out = np.full((w.nq, k), -1, dtype=np.int64)
+    for q in range(w.nq):
+        keys = []
+        for j in range(m):
+            b, sel = int(P[q, j]), int(S[q, j])
+            rows = []
+            for blk in range(nb):
+                if (sel >> blk) & 1:
+                    rows.extend(oi.perm[oi.offsets[b * nb + blk]:oi.offsets[b * nb + blk + 1]].tolist())
+            rows = np.array([r for r in rows if np.all((w.Qb[q] < 0) | (w.A[r] == w.Qb[q]))],
+                            dtype=np.int64)
+            if len(rows) == 0:
+                continue
+            dot = (x8[rows] @ q8[q]) * xs[rows] * qs[q]
+            sc = xn[rows] - 2.0 * dot if w.metric == 0 else -dot
+            top = np.lexsort((rows, sc))[:KP]
+            keys += list(zip(sc[top].tolist(), rows[top].tolist()))
+        keys.sort()
+        sgn = 1.0 if w.metric == 0 else -1.0
+        ex = sorted((sgn * float(O.dist32(w.X[r], w.Q[q], w.metric)), r) for _, r in keys[:R])
+        got = [r for _, r in ex[:k]]
+        out[q, :len(got)] = got
+    return out

@@ -1,0 +1,142 @@
+"""FP8 (e4m3) form of the scan: e4m3 rows and queries with per-row and
+per-query scales (max |x| / 448), fp32 accumulation on the tensor cores, and
+the exact fp32 re-rank of rerank_factor * k candidates, against the CPU
+oracle.
+
+e4m3 keeps three mantissa bits, so the tile scores are approximate even on
+byte-valued data and the candidate lists differ from the exact ones.  The
+reference for the form is a plain model of it (tests/_fp8.py: the oracle's
+probes, selections and exact distances, e4m3 rounding, per-partition KP best
+keys, R best per query re-scored); the GPU's ids must agree with it rank by
+rank except at rare near-ties (its fp32 accumulation against the model's
+fp64).  Exact: every returned distance is the oracle's fp32 distance of that
+id, every returned id passes the query's filter, results are sorted with the
+oracle's tie rule, and every launch shape returns the same bits.  How many of
+the oracle's neighbours the form recovers is a quality figure (floor).
+"""
+import numpy as np
+import pytest
+
+import _fp8
+import oracle as O
+from workloads import make_dense_workload
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2308_15014_gb300 import build
+    build.build()
+
+
+import paper_2308_15014_gb300 as caps  # noqa: E402
+
+
+def wl(seed, N=8000, d=128, B=24, h=9, nq=150, integer=True, metric=0, normalize=False,
+       vocab=(5, 7, 11)):
+    return make_dense_workload(
+        name="fp8", N=N, d=d, ncomp=12, center=("uniform", 128.0) if integer else ("normal", 2.0),
+        sigma=16.0 if integer else 1.0, vocab=list(vocab), zipf_s=1.0, nq=nq, cmin=1, cmax=3,
+        B=B, h=h, iters=5, m=4, k=10, seed=seed, integer=integer, metric=metric,
+        normalize=normalize)
+
+
+def build_pair(w, prec=caps.FP8):
+    oi = O.build(w.X, O.Attrs.of(w), w.B, w.h, w.iters, w.init_idx, w.metric)
+    gi = caps.Index.build(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.A).cuda(), w.vocab,
+                          w.B, h=w.h, iters=w.iters, metric=w.metric, init_idx=w.init_idx,
+                          prec=prec)
+    return oi, gi
+
+
+def check_against_model(w, oi, ids, k, m, min_agree=0.99):
+    want = _fp8.search(w, oi, k, m)
+    agree = float((ids == want).mean())
+    assert agree >= min_agree, agree
+    return agree
+
+
+def check_against_oracle(w, ids, dist, oids, floor):
+    np.testing.assert_array_equal(ids >= 0, oids >= 0)
+    hit = tot = 0
+    for q in range(w.nq):
+        got = ids[q][ids[q] >= 0]
+        assert len(set(got.tolist())) == len(got)
+        want = set(oids[q][oids[q] >= 0].tolist())
+        hit += len(want.intersection(got.tolist()))
+        tot += len(want)
+        for r, i in enumerate(got):
+            # the re-rank returns the exact fp32 distance of every id
+            assert dist[q, r] == np.float32(O.dist32(w.X[i], w.Q[q], w.metric))
+            b = w.Qb[q]
+            assert np.all((b < 0) | (w.A[i] == b))
+        # best first, ties to the lower id
+        key = dist[q][: len(got)] if w.metric == 0 else -dist[q][: len(got)]
+        order = np.lexsort((got, key))
+        np.testing.assert_array_equal(order, np.arange(len(got)))
+    assert hit / tot >= floor, hit / tot
+    return hit / tot
+
+
+@pytest.mark.parametrize("integer,metric", [(True, 0), (False, 0), (False, 1)])
+def test_fp8_rerank_against_oracle(integer, metric):
+    w = wl(700 + 2 * metric + integer, integer=integer, metric=metric, normalize=metric == 1)
+    oi, gi = build_pair(w)
+    ids, dist = gi.search(w.Q, w.Qb, 10, 5)
+    check_against_model(w, oi, ids, 10, 5)
+    oids, odist, _, _ = O.search(w.X, O.Attrs.of(w), oi, w.Q, O.Cons.of(w), 10, 5)
+    # e4m3 on byte data (neighbours a few percent apart) recovers about 74 %
+    check_against_oracle(w, ids, dist, oids, floor=0.7 if integer else 0.93)
+
+
+@pytest.mark.parametrize("k,m", [(1, 3), (16, 8), (32, 6)])
+def test_fp8_list_lengths(k, m):
+    # candidate lists of 10, 16 and 32 keys per probe
+    w = wl(710 + k, d=64, nq=120)
+    oi, gi = build_pair(w)
+    ids, dist = gi.search(w.Q, w.Qb, k, m)
+    check_against_model(w, oi, ids, k, m)
+    oids, odist, _, _ = O.search(w.X, O.Attrs.of(w), oi, w.Q, O.Cons.of(w), k, m)
+    check_against_oracle(w, ids, dist, oids, floor=0.6)
+
+
+def test_fp8_plan_shapes_agree():
+    # the autotuner runs every launch shape of the e4m3 form (256 or 128 rows
+    # per tile x 128 or 64 probes per item) and requires identical bits
+    w = wl(720, N=20_000, nq=700)
+    oi, gi = build_pair(w)
+    Q = torch.from_numpy(w.Q).cuda()
+    Qb = torch.from_numpy(w.Qb).cuda()
+    plan = gi.plan(Q, Qb, 10, 6, autotune=True)
+    assert {(c["tile_n"], c["item_cap"], c["pen"]) for c in plan.info["candidates"]} == {
+        (256, 128, 0), (128, 128, 0), (256, 64, 0), (128, 64, 0)}
+    p_ids, p_dist = plan.search(Q, Qb)
+    d_ids, d_dist = gi.search(Q, Qb, 10, 6)
+    torch.cuda.synchronize()
+    assert torch.equal(p_ids, d_ids) and torch.equal(p_dist, d_dist)
+    check_against_model(w, oi, p_ids.cpu().numpy(), 10, 6)
+    oids, _, _, _ = O.search(w.X, O.Attrs.of(w), oi, w.Q, O.Cons.of(w), 10, 6)
+    check_against_oracle(w, p_ids.cpu().numpy(), p_dist.cpu().numpy(), oids, floor=0.6)
+    plan.close()
+
+
+def test_fp8_all_partitions_against_bruteforce():
+    w = wl(730, N=5000, B=8, nq=100, integer=False)
+    oi, gi = build_pair(w)
+    ids, dist = gi.search(w.Q, w.Qb, 10, w.B)
+    check_against_model(w, oi, ids, 10, w.B)
+    gt, g32, _, _ = O.bruteforce(w.X, O.Attrs.of(w), w.Q, O.Cons.of(w), 10)
+    check_against_oracle(w, ids, dist, gt, floor=0.9)
+
+
+def test_fp8_rejects_unsupported_d():
+    for d in (72, 48):
+        w = wl(740, d=d, N=1000, nq=5)
+        with pytest.raises(caps.CapsError) as e:
+            caps.Index.build(w.X, w.A, w.vocab, w.B, h=3, iters=1, init_idx=w.init_idx,
+                             prec=caps.FP8)
+        assert e.value.code == caps.CAPS_EINVAL
