@@ -1348,7 +1348,10 @@ extern "C" int caps_plan_create(const caps_index* ix, const float* Q, int64_t nq
       int shapes[6][3];
       int n_shapes = 0;
       for (const auto& sh : all)
-        if (sh[2] ? pen_ok : tc_explicit_ok(ix, k)) {
+        if (sh[2] ? pen_ok
+                  : tc_explicit_ok(ix, k) &&
+                        tc_tile_fits(ix->d, ix->meta.words_pad, sh[0],
+                                     ix->prec == CAPS_FP8E4M3 ? 1 : 0)) {
           for (int j = 0; j < 3; j++) shapes[n_shapes][j] = sh[j];
           n_shapes++;
         }

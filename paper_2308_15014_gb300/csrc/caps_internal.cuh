@@ -378,6 +378,8 @@ struct TcScanArgs {
 int tc_kp(int k);
 int tc_rerank_depth(int k, int factor);
 bool tc_scan_supported(int d, int k, int kp, int words_pad, int f8 = 0);
+// whether the per-pair filter form with N-row tiles fits in shared memory
+bool tc_tile_fits(int d, int words_pad, int N, int f8);
 bool tc_pen_supported(int d, int kp, int words_pad);
 // What the bf16 form of an index is made from, and where it goes.
 struct TcIndexPrep {

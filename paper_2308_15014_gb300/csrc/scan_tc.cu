@@ -482,11 +482,16 @@ int tc_rerank_depth(int k, int factor) {
   return std::min(64, std::max(k, f * k));
 }
 
+bool tc_tile_fits(int d, int words_pad, int N, int f8) {
+  const int kc = f8 ? (d + 127) / 128 : (d + 63) / 64;
+  return tc_fits(kc, words_pad, N, false, f8 != 0);
+}
+
 bool tc_scan_supported(int d, int k, int kp, int words_pad, int f8) {
   if (d % 8 != 0 || d < 64 || d > 128 || k > 32 || (kp != 10 && kp != 16 && kp != 32))
     return false;
-  if (f8) return d % 16 == 0 && tc_fits((d + 127) / 128, words_pad, 128, false);
-  return tc_fits((d + 63) / 64, words_pad, 128, false);
+  if (f8 && d % 16 != 0) return false;
+  return tc_tile_fits(d, words_pad, 128, f8) || tc_tile_fits(d, words_pad, 256, f8);
 }
 
 bool tc_pen_supported(int d, int kp, int words_pad) {
@@ -686,16 +691,15 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
     return tc_launch_pen(map, a, t.metric, t.words_pad, t.kp, g,
                          tc_smem_bytes(a.kc, t.words_pad, 128, true), s);
   }
-  if (!tc_fits(a.kc, t.words_pad, 128, false))
+  // 256-row tiles unless 128 were asked for; whichever of the two fits
+  const bool f8 = t.f8 != 0;
+  const bool fit128 = tc_fits(a.kc, t.words_pad, 128, false, f8);
+  const bool fit256 = tc_fits(a.kc, t.words_pad, 256, false, f8);
+  if (!fit128 && !fit256)
     return fail(CAPS_EINVAL, "the per-pair filter form does not fit this index");
-  if (t.f8) {
-    const int N8 = t.tile_n != 128 && tc_fits(a.kc, t.words_pad, 256, false) ? 256 : 128;
-    return tc_launch_f8(map, a, t.metric, t.words_pad, t.kp, N8, g,
-                        tc_smem_bytes(a.kc, t.words_pad, N8, false), s);
-  }
-  // 256-row tiles where they fit, else 128
-  const int N = t.tile_n != 128 && tc_fits(a.kc, t.words_pad, 256, false) ? 256 : 128;
-  const size_t smem = tc_smem_bytes(a.kc, t.words_pad, N, false);
+  const int N = (t.tile_n != 128 && fit256) || !fit128 ? 256 : 128;
+  const size_t smem = tc_smem_bytes(a.kc, t.words_pad, N, false, f8);
+  if (f8) return tc_launch_f8(map, a, t.metric, t.words_pad, t.kp, N, g, smem, s);
 #define CAPS_TC(WPV, KPV)                                                                      \
   if (N == 128)                                                                                \
     return t.metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 128, false>(map, a, g, smem, s)  \

@@ -234,23 +234,26 @@ __host__ __device__ constexpr size_t tc_a_bytes(int kc) { return (size_t)kc * TC
 __host__ __device__ constexpr size_t tc_b_bytes(int kc, int N) { return (size_t)kc * N * 128; }
 // per stage: attribute words, ids, norms and (e4m3 rows) scales of N + 8
 // rows (4-row aligned superset of the tile), block id of each row
-__host__ __device__ constexpr size_t tc_aux_bytes(int WP, int N) {
-  return (((size_t)(N + 8) * WP * 4 + (size_t)(N + 8) * 12 + (size_t)(N + 8)) + 15) & ~(size_t)15;
+__host__ __device__ constexpr size_t tc_aux_bytes(int WP, int N, bool f8 = false) {
+  return (((size_t)(N + 8) * WP * 4 + (size_t)(N + 8) * (f8 ? 12 : 8) + (size_t)(N + 8)) + 15) &
+         ~(size_t)15;
 }
 // shared memory one CTA may hold (227 KB), and an upper bound of the
 // kernel's static part (barriers, per-probe arrays, the tile schedule)
 constexpr size_t kTcSmemLimit = 227 * 1024;
-__host__ __device__ constexpr size_t tc_static_bound(int WP) { return 7168 + 1024 * (size_t)WP; }
-__host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N, bool pen);
-__host__ __device__ constexpr bool tc_fits(int kc, int WP, int N, bool pen) {
-  return tc_smem_bytes(kc, WP, N, pen) + tc_static_bound(WP) <= kTcSmemLimit;
+__host__ __device__ constexpr size_t tc_static_bound(int WP, bool pen) {
+  return 7168 + 1024 * (size_t)WP + (pen ? (size_t)4096 : 0);
 }
-__host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N, bool pen) {
+__host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N, bool pen, bool f8 = false);
+__host__ __device__ constexpr bool tc_fits(int kc, int WP, int N, bool pen, bool f8 = false) {
+  return tc_smem_bytes(kc, WP, N, pen, f8) + tc_static_bound(WP, pen) <= kTcSmemLimit;
+}
+__host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N, bool pen, bool f8) {
   // 1024-byte alignment slack + A + B stages + candidate queues + aux stages
   // (one per accumulator stage; the final merge of the quarter lists reuses
   // the queues)
   return 1024 + tc_a_bytes(kc) + (size_t)tc_stages(N, pen) * tc_b_bytes(kc, N) +
-         (size_t)TC_Q * TC_C * 8 + (size_t)(TC_COLS / N) * tc_aux_bytes(WP, N);
+         (size_t)TC_Q * TC_C * 8 + (size_t)(TC_COLS / N) * tc_aux_bytes(WP, N, f8);
 }
 
 template <int KP>
@@ -335,7 +338,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   const size_t bstride = tc_b_bytes(kc, N);
   uint64_t* queue = reinterpret_cast<uint64_t*>(sB0 + SB * bstride);
   unsigned char* aux0 = reinterpret_cast<unsigned char*>(queue + (size_t)TC_Q * TC_C);
-  constexpr size_t astride = tc_aux_bytes(WP, N);
+  constexpr size_t astride = tc_aux_bytes(WP, N, F8);
   auto s_attr = [&](int b) { return reinterpret_cast<uint32_t*>(aux0 + b * astride); };
   auto s_perm = [&](int b) {
     return reinterpret_cast<int32_t*>(aux0 + b * astride + (size_t)RA * WP * 4);
@@ -346,7 +349,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   auto s_xs = [&](int b) {
     return reinterpret_cast<float*>(aux0 + b * astride + (size_t)RA * WP * 4 + RA * 8);
   };
-  auto s_blk = [&](int b) { return aux0 + b * astride + (size_t)RA * WP * 4 + RA * 12; };
+  auto s_blk = [&](int b) { return aux0 + b * astride + (size_t)RA * WP * 4 + RA * (F8 ? 12 : 8); };
   static_assert(!(PEN && F8), "the penalty form is bf16 only");
 
   __shared__ uint64_t full_bar[SB], bfree_bar[SB], aux_bar[ST], mma_bar[ST], empty_bar[ST];
@@ -356,6 +359,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   // the current and the next item (index: item parity)
   __shared__ int s_ne[2], s_ntiles[2], s_bin[2];
   __shared__ uint64_t p_thr[2][TC_M];
+  // penalty form: each quarter list's ceil(KP/4)-th key (all ones until it
+  // has that many); the per-pair form has no shared memory to spare for it
+  __shared__ uint64_t s_qk[PEN ? TC_PARTS : 1][TC_M];
   __shared__ int32_t p_e[2][TC_M];
   // probe data of the item about to start (read once into registers)
   __shared__ uint64_t p_sel[TC_M];
@@ -383,6 +389,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     mbar_init(&meta_bar, 1);
     mbar_init(&afull_bar, TC_C / 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int i = 0; i < (PEN ? TC_PARTS : 1) * TC_M; i++) (&s_qk[0][0])[i] = kEmptyKey;
     s_fail = 0;
     int gb = 0;
     for (int w = 0; w < WP; w++)
@@ -695,6 +702,23 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         // the four threads of a probe share the smallest of their KP-th keys:
         // a key above it has KP better keys in one quarter list already
         if (thr != kEmptyKey) atomicMin(reinterpret_cast<unsigned long long*>(&pthr[probe]), thr);
+        // and the largest of their ceil(KP/4)-th keys: the four lists (of
+        // distinct rows) hold at least KP keys at or below it.  A slot read
+        // before its quarter's latest flush is larger, so the bound holds
+        if constexpr (PEN) {
+          constexpr int QK = (KP + TC_PARTS - 1) / TC_PARTS - 1;
+          s_qk[part][probe] = L[QK];
+          uint64_t mq = s_qk[0][probe];
+#pragma unroll
+          for (int pp = 1; pp < TC_PARTS; pp++) {
+            const uint64_t v = s_qk[pp][probe];
+            mq = v > mq ? v : mq;
+          }
+          if (mq != kEmptyKey) {
+            atomicMin(reinterpret_cast<unsigned long long*>(&pthr[probe]), mq);
+            if (mq < thr) thr = mq;
+          }
+        }
       };
       const bool warp_live = __any_sync(0xffffffffu, active);
       const int cbeg = part * CPT;
@@ -850,6 +874,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
                         a.qslot + (int64_t)(e / a.m) * TC_SLOTS + s_bin[par] % a.nslot),
                     (unsigned long long)L[KP - 1]);
       }
+      if (PEN) s_qk[part][probe] = kEmptyKey;  // read again only after the barrier below
       // the next item's A operand: every MMA of this item has completed (each
       // tile's accumulator was waited for), so A may be overwritten once the
       // producer has the next item's probe data

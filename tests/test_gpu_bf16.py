@@ -119,3 +119,12 @@ def test_bf16_wide_attribute_words_equals_oracle(vocab):
     oids, odist, _, _ = O.search(w.X, O.Attrs.of(w), oi, w.Q, O.Cons.of(w), 10, 6)
     np.testing.assert_array_equal(ids, oids)
     np.testing.assert_array_equal(dist, odist)
+    # the tensor-core scan serves it (a plan has shapes to tune): with two
+    # attribute words only the 256-row tiles fit in shared memory
+    plan = gi.plan(w.Q, w.Qb, 10, 6, autotune=True)
+    assert {(c["tile_n"], c["item_cap"], c["pen"]) for c in plan.info["candidates"]} == {
+        (256, 128, 0), (256, 64, 0)}
+    p_ids, p_dist = plan.search(w.Q, w.Qb)
+    np.testing.assert_array_equal(p_ids, oids)
+    np.testing.assert_array_equal(p_dist, odist)
+    plan.close()
