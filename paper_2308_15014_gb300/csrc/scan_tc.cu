@@ -204,45 +204,59 @@ k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ de
     for (int s = 0; s < 2; s++) cbuf[2 * lane + s] = cand.v[s];
   }
   __syncwarp();
-  // exact fp32 scores of the kp candidates, one per lane (32 at a time):
-  // 16-byte loads of the candidate's row, eight in flight, and the fma chain
-  // over the coordinates in order
+  // exact fp32 scores of the kp <= 64 candidates, two per lane (lane and
+  // lane + 32): their rows in 16-byte loads, four per candidate in flight,
+  // and their two fma chains interleaved, each over the coordinates in order
   TopKm<KPL_K> top;
   top.init();
   uint64_t kth2 = kEmptyKey;
-  for (int r0 = 0; r0 < kp; r0 += 32) {
-    const int c = r0 + lane;  // this lane's candidate
-    const uint64_t ck = c < kp ? cbuf[c] : kEmptyKey;
-    uint64_t key = kEmptyKey;
-    if (ck != kEmptyKey) {
-      const uint32_t id = (uint32_t)(ck & 0xffffffffu);
-      const float4* xr = reinterpret_cast<const float4*>(Xp + (int64_t)iperm[id] * d);
-      float acc = 0.f;
-      for (int j0 = 0; j0 < d / 4; j0 += 8) {
-        float4 x[8];
+  {
+    uint64_t ck[2];
+    const float4* xr[2];
 #pragma unroll
-        for (int u = 0; u < 8; u++)
-          if (j0 + u < d / 4) x[u] = xr[j0 + u];
+    for (int h = 0; h < 2; h++) {
+      const int c = lane + 32 * h;
+      ck[h] = c < kp ? cbuf[c] : kEmptyKey;
+      xr[h] = reinterpret_cast<const float4*>(Xp);
+      if (ck[h] != kEmptyKey)
+        xr[h] = reinterpret_cast<const float4*>(Xp + (int64_t)iperm[(uint32_t)(ck[h] & 0xffffffffu)] * d);
+    }
+    const bool has0 = ck[0] != kEmptyKey, has1 = ck[1] != kEmptyKey;
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int j0 = 0; j0 < d / 4; j0 += 4) {
+      float4 x0[4], x1[4];
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
-          if (j0 + u < d / 4) {
-            const float* qv = qs + 4 * (j0 + u);
-            const float xv[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+      for (int u = 0; u < 4; u++) {
+        if (has0 && j0 + u < d / 4) x0[u] = xr[0][j0 + u];
+        if (has1 && j0 + u < d / 4) x1[u] = xr[1][j0 + u];
+      }
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-              if (METRIC == CAPS_L2) {
-                const float t = xv[e] - qv[e];
-                acc = fmaf(t, t, acc);
-              } else {
-                acc = fmaf(xv[e], qv[e], acc);
-              }
+      for (int u = 0; u < 4; u++) {
+        if (j0 + u < d / 4) {
+          const float4 q4 = *reinterpret_cast<const float4*>(qs + 4 * (j0 + u));
+          const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+          const float a0[4] = {x0[u].x, x0[u].y, x0[u].z, x0[u].w};
+          const float a1[4] = {x1[u].x, x1[u].y, x1[u].z, x1[u].w};
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            if (METRIC == CAPS_L2) {
+              const float t0 = a0[e] - qv[e], t1 = a1[e] - qv[e];
+              acc0 = fmaf(t0, t0, acc0);
+              acc1 = fmaf(t1, t1, acc1);
+            } else {
+              acc0 = fmaf(a0[e], qv[e], acc0);
+              acc1 = fmaf(a1[e], qv[e], acc1);
             }
           }
         }
       }
-      key = make_key(METRIC == CAPS_L2 ? acc : -acc, id);
     }
-    top.offer(key, kth2, k, lane);
+    const uint64_t k0 = has0 ? make_key(METRIC == CAPS_L2 ? acc0 : -acc0, (uint32_t)(ck[0] & 0xffffffffu))
+                             : kEmptyKey;
+    const uint64_t k1 = has1 ? make_key(METRIC == CAPS_L2 ? acc1 : -acc1, (uint32_t)(ck[1] & 0xffffffffu))
+                             : kEmptyKey;
+    top.offer(k0, kth2, k, lane);
+    top.offer(k1, kth2, k, lane);
   }
 #pragma unroll
   for (int s = 0; s < KPL_K; s++) {
