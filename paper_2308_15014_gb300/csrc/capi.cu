@@ -616,6 +616,19 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     tp.tmap = ix->tmap;
     if (int rc = tc_prepare_index(tp, s)) return rc;
   }
+  {
+    // the weight side of the screened probe, fixed from here on
+    const bool mlp = p->part == CAPS_PART_MLP;
+    const int sK = mlp ? ix->mlp.H : d;
+    if (probe_screen_supported(sK, B, 1)) {
+      uint16_t* wh = nullptr;
+      if (int rc = ix->alloc(&wh, probe_weights_elems(sK, B))) return rc;
+      ix->pw.Wh = wh;
+      if (int rc = ix->alloc(&ix->pw.wn2, (size_t)B)) return rc;
+      if (int rc = ix->alloc(&ix->pw.wn, (size_t)B)) return rc;
+      if (int rc = probe_weights_prepare(mlp ? ix->mlp.W2 : ix->C, B, sK, ix->pw, s)) return rc;
+    }
+  }
   CAPS_CUDA(cudaStreamSynchronize(s));
   return CAPS_OK;
 }
@@ -867,7 +880,7 @@ extern "C" int caps_probe_set(const caps_index* ix, const float* Q, int64_t nq, 
       if (int rc = ::caps::mlp_hidden(ix->mlp, Qc, n, hid, s)) return rc;
     if (int rc = probe_screened(mlp ? 0 : (ix->metric == CAPS_L2 ? 1 : 2), mlp ? hid : Qc, n, sK,
                                 mlp ? ix->mlp.W2 : ix->C, mlp ? ix->mlp.b2 : nullptr, ix->B, m,
-                                scores, op.dev + c0 * m, ix->err, cscr, s))
+                                scores, op.dev + c0 * m, ix->err, cscr, s, &ix->pw))
       return rc;
   }
   if (int rc = op.finish(s)) return rc;
@@ -1124,7 +1137,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
         if (int rc = ::caps::mlp_hidden(ix->mlp, Qc, n, mlp_hidden, s)) return rc;
       if (int rc = probe_screened(mlp ? 0 : (ix->metric == CAPS_L2 ? 1 : 2), mlp ? mlp_hidden : Qc,
                                   n, sK, mlp ? ix->mlp.W2 : ix->C, mlp ? ix->mlp.b2 : nullptr,
-                                  ix->B, m, bt.scores, bt.probe, ix->err, cscr, s))
+                                  ix->B, m, bt.scores, bt.probe, ix->err, cscr, s, &ix->pw))
         return rc;
       if (int rc = tm.record(s)) return rc;
     } else {

@@ -336,9 +336,20 @@ int mlp_hidden(const MlpNet& net, const float* X, int64_t n, float* Hd, cudaStre
 // IP.  Writes the m-partition set of each query to probe [n,m] (order:
 // certain partitions first, by index); Dt [n,B] is scratch.
 bool probe_screen_supported(int K, int B, int m);
+// Weight side of the screened probe (centroids or the MLP's output layer,
+// B rows of K): bf16 [hi | lo | hi] rows of 3 * Kp (Kp = K rounded up to 64)
+// and the rows' squared norms and norms; fixed once the index is built.
+struct ProbeWeights {
+  void* Wh = nullptr;
+  float* wn2 = nullptr;
+  float* wn = nullptr;
+};
+size_t probe_weights_elems(int K, int B);
+int probe_weights_prepare(const float* W, int B, int K, const ProbeWeights& pw, cudaStream_t s);
+// pw: the weight side prepared at build time, or null (prepared here)
 int probe_screened(int mode, const float* A, int64_t n, int K, const float* W, const float* bias,
                    int B, int m, float* Dt, int32_t* probe, int32_t* err, Scratch& scr,
-                   cudaStream_t s);
+                   cudaStream_t s, const ProbeWeights* pw = nullptr);
 int mlp_assign(const MlpNet& net, const float* X, int64_t n, int32_t* bin, Scratch& scr,
                cudaStream_t s);
 int mlp_loss_grad(const MlpNet& net, const float* X, int64_t n, const float* Y, MlpNet* grad,
@@ -443,6 +454,7 @@ struct caps_index {
   void* Xb = nullptr;
   float* xn = nullptr;
   float* xs = nullptr;  // e4m3 form: per-row scales [N+4]
+  caps::ProbeWeights pw;  // weight side of the screened probe (when it applies)
   int32_t* iperm = nullptr;
   alignas(128) unsigned char tmap[128] = {};
   // penalty form of the bf16 scan: each bf16 row carries a 64-column one-hot

@@ -47,6 +47,35 @@ __global__ void k_split3(const float* __restrict__ X, int64_t rows, int K, int K
   o[2 * Kp + k] = wside ? hi : lo;
 }
 
+// Query side in one pass, a warp per row: bf16 [hi | hi | lo] (two
+// coordinates per lane and store) and the row's squared norm (fp32; its
+// rounding is inside eps).
+__global__ void k_split3_rows(const float* __restrict__ X, int64_t rows, int K, int Kp,
+                              __nv_bfloat16* __restrict__ out, float* __restrict__ n2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= rows) return;
+  const float* x = X + r * K;
+  __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + r * 3 * (int64_t)Kp);
+  const int hp = Kp / 2;
+  float acc = 0.f;
+  for (int k2 = lane; k2 < hp; k2 += 32) {
+    const int k = 2 * k2;
+    const float v0 = k < K ? x[k] : 0.f, v1 = k + 1 < K ? x[k + 1] : 0.f;
+    acc = fmaf(v0, v0, acc);
+    acc = fmaf(v1, v1, acc);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(v0, v1);
+    const __nv_bfloat162 lo =
+        __floats2bfloat162_rn(v0 - __low2float(hi), v1 - __high2float(hi));
+    o[k2] = hi;
+    o[hp + k2] = hi;
+    o[2 * hp + k2] = lo;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) n2[r] = acc;
+}
+
 // Squared norm of each row and, when nr is given, the norm (fp32; the
 // rounding is inside eps).
 __global__ void k_rownorm2(const float* __restrict__ X, int64_t rows, int K, float* __restrict__ n2,
@@ -492,27 +521,43 @@ int encode_bf16_map(void* map, const void* ptr, int64_t rows, int64_t cols) {
 
 bool probe_screen_supported(int K, int B, int m) { return m >= 1 && m <= 64 && m <= B && K >= 1 && K <= 2048; }
 
+size_t probe_weights_elems(int K, int B) { return (size_t)B * 3 * (size_t)((K + 63) / 64 * 64); }
+
+int probe_weights_prepare(const float* W, int B, int K, const ProbeWeights& pw, cudaStream_t s) {
+  const int Kp = (K + 63) / 64 * 64;
+  k_split3<<<(unsigned)(((int64_t)B * Kp + 255) / 256), 256, 0, s>>>(
+      W, B, K, Kp, 1, static_cast<__nv_bfloat16*>(pw.Wh));
+  CAPS_LAUNCH("k_split3");
+  k_rownorm2<<<(unsigned)((B + 7) / 8), 256, 0, s>>>(W, B, K, pw.wn2, pw.wn);
+  CAPS_LAUNCH("k_rownorm2");
+  return CAPS_OK;
+}
+
 int probe_screened(int mode, const float* A, int64_t n, int K, const float* W, const float* bias,
                    int B, int m, float* Dt, int32_t* probe, int32_t* err, Scratch& scr,
-                   cudaStream_t s) {
+                   cudaStream_t s, const ProbeWeights* pre) {
   if (n == 0) return CAPS_OK;
   if (!probe_screen_supported(K, B, m)) return fail(CAPS_EINVAL, "screened probe: bad sizes");
   const int Kp = (K + 63) / 64 * 64, Kt = 3 * Kp;
-  __nv_bfloat16 *Ah = nullptr, *Wh = nullptr;
-  float *an2 = nullptr, *wn2 = nullptr, *wn = nullptr;
+  __nv_bfloat16* Ah = nullptr;
+  float* an2 = nullptr;
   if (int rc = scr.get(&Ah, (size_t)n * Kt)) return rc;
-  if (int rc = scr.get(&Wh, (size_t)B * Kt)) return rc;
   if (int rc = scr.get(&an2, (size_t)n)) return rc;
-  if (int rc = scr.get(&wn2, (size_t)B)) return rc;
-  if (int rc = scr.get(&wn, (size_t)B)) return rc;
-  k_split3<<<(unsigned)((n * Kp + 255) / 256), 256, 0, s>>>(A, n, K, Kp, 0, Ah);
-  CAPS_LAUNCH("k_split3");
-  k_split3<<<(unsigned)(((int64_t)B * Kp + 255) / 256), 256, 0, s>>>(W, B, K, Kp, 1, Wh);
-  CAPS_LAUNCH("k_split3");
-  k_rownorm2<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, n, K, an2, nullptr);
-  CAPS_LAUNCH("k_rownorm2");
-  k_rownorm2<<<(unsigned)((B + 7) / 8), 256, 0, s>>>(W, B, K, wn2, wn);
-  CAPS_LAUNCH("k_rownorm2");
+  ProbeWeights pw;
+  if (pre && pre->Wh) {
+    pw = *pre;
+  } else {
+    __nv_bfloat16* wh = nullptr;
+    if (int rc = scr.get(&wh, (size_t)B * Kt)) return rc;
+    pw.Wh = wh;
+    if (int rc = scr.get(&pw.wn2, (size_t)B)) return rc;
+    if (int rc = scr.get(&pw.wn, (size_t)B)) return rc;
+    if (int rc = probe_weights_prepare(W, B, K, pw, s)) return rc;
+  }
+  __nv_bfloat16* Wh = static_cast<__nv_bfloat16*>(pw.Wh);
+  const float *wn2 = pw.wn2, *wn = pw.wn;
+  k_split3_rows<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(A, n, K, Kp, Ah, an2);
+  CAPS_LAUNCH("k_split3_rows");
   alignas(64) CUtensorMap mA, mB;
   if (int rc = encode_bf16_map(&mA, Ah, n, Kt)) return rc;
   if (int rc = encode_bf16_map(&mB, Wh, B, Kt)) return rc;
