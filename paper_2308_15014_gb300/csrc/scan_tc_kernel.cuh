@@ -300,16 +300,20 @@ __device__ __forceinline__ void net_merge(uint64_t (&L)[KP], const uint64_t* oth
 // One persistent CTA per SM walks the work items (partition, <= 128 probes)
 // in the order a global counter hands them out, so partitions of very
 // different sizes balance across the SMs within one launch.  Warp 16 is the
-// producer: for each tile of an item it waits until the epilogue has released
-// the stage, writes the rows' block ids, starts the copies and, once they
-// have landed, issues the MMAs of that tile into the stage's accumulator;
-// after the item's last tile it already takes and prepares the next item
-// (its rows' ranges and the probes' data) while the epilogue finishes the
-// current one.  Warps 0-15 are the epilogue; they meet the producer only
-// through mbarriers (full: copies landed; mma: accumulator written; empty:
-// all 16 warps done with the stage; taken: the probes' data read; meta: the
-// next item's data ready), and at item boundaries, where they have built the
-// next item's A operand.
+// producer.  Its copies run ahead of its MMAs: before tile t's MMAs it starts
+// the copies of tile t + SB - 1 — the rows into the B stage of tile t - 1
+// (free once that tile's MMAs completed) and the rows' ids, norms, attribute
+// words and block ids into the aux stage of that tile's accumulator (free
+// once the epilogue has read it) — then waits for tile t's rows and issues
+// its MMAs into accumulator stage t mod ST.  After the item's last tile it
+// already takes and prepares the next item (its rows' ranges and the probes'
+// data) while the epilogue finishes the current one.  Warps 0-15 are the
+// epilogue; they meet the producer only through mbarriers (full: rows
+// landed; bfree: B stage's MMAs done; aux: ids and norms landed; mma:
+// accumulator written; empty: all 16 warps done with the accumulator and aux
+// stage; taken: the probes' data read; meta: the next item's data ready;
+// afull: the next item's A operand built), and at item boundaries, where
+// they merge the probes' quarter lists and build the next item's A operand.
 //
 // Bound across a query's partitions: the rerank keeps the best R keys of the
 // query's m lists.  Each finished list offers its KP-th key to one of the
