@@ -302,6 +302,24 @@ def form1_error(w, rng_seed=11, nq=64, nrow=2048):
     return out
 
 
+def query_stats(w, rows_scanned, rows_passed):
+    """Selectivity |D_C| / N of the batch's filters (percentiles and a
+    per-decade histogram) and the mean candidates per query of the measured
+    probe count: rows in the selected blocks, and rows passing the filter."""
+    sel = np.asarray(w.selectivity, dtype=np.float64) if w.selectivity is not None else None
+    out = {"rows_selected_per_query": round(float(rows_scanned) / w.nq, 1),
+           "rows_passing_per_query": round(float(rows_passed) / w.nq, 1)}
+    if sel is not None and sel.size:
+        edges = [0.0, 1e-4, 1e-3, 1e-2, 1e-1, 1.0 + 1e-12]
+        hist = np.histogram(sel, bins=edges)[0]
+        out["selectivity"] = {
+            "p0": float(sel.min()), "p50": float(np.median(sel)), "p100": float(sel.max()),
+            "mean": float(sel.mean()),
+            "hist": {"<0.01%": int(hist[0]), "0.01-0.1%": int(hist[1]), "0.1-1%": int(hist[2]),
+                     "1-10%": int(hist[3]), ">=10%": int(hist[4])}}
+    return out
+
+
 def h_sweep(args, w, caps, O, torch, samp, gt, g64, cnt):
     """AFT height ablation (k-means + bf16, the same seed points): for each h
     the smallest probe count reaching recall@10 >= 0.9 and the batch QPS
@@ -729,6 +747,7 @@ def run_caps(args):
         "clocks": head["clocks"],
         "cpu_baseline": cpu,
         "form1_error": form1,
+        "queries": query_stats(w, rows_scanned, rows_passed),
     }
     if sparse is not None:
         line["label_sets"] = sparse
