@@ -443,6 +443,24 @@ def oracle_baseline(w, m, k, budget_s=15.0):
                       f"same seed centroids without Lloyd iterations ({build_s:.1f} s, untimed)"}
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (the slowest rank's time), or x
+    itself on one rank; every rank gets the same result."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, nq, seconds):
+    """Whole-job queries/s: each of the world ranks answered nq queries, the
+    slowest of them in `seconds`."""
+    return world * nq / seconds
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -573,12 +591,8 @@ def measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world, local
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.nq / (ms / 1e3)
+    ms = max_over_ranks(float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs])), world, "cuda")
+    value = job_throughput(world, w.nq, ms / 1e3)
 
     # ---- per-stage device times (events on the launching stream) -----------
     caps.set_timing(True)
@@ -682,7 +696,7 @@ def run_caps(args):
         t0 = time.perf_counter()
         plan.search(Qh, Qbh, out_ids=ids_h, out_dist=dist_h)  # returns after the D2H copies
         e2e_t.append(time.perf_counter() - t0)
-    e2e_v = world * w.nq / float(np.mean(e2e_t))
+    e2e_v = job_throughput(world, w.nq, max_over_ranks(float(np.mean(e2e_t)), world, "cuda"))
 
     # ---- form 1: bf16 / e4m3 tile scores and returned distances against fp64 -
     from workloads import make_dense_workload
