@@ -443,6 +443,9 @@ def oracle_baseline(w, m, k, budget_s=15.0):
                       f"same seed centroids without Lloyd iterations ({build_s:.1f} s, untimed)"}
 
 
+REFERENCE_M = 40
+
+
 def max_over_ranks(x, world, device):
     """The largest value of x over the ranks (the slowest rank's time), or x
     itself on one rank; every rank gets the same result."""
@@ -469,7 +472,9 @@ def run_reference(args):
     from oracle.build import build_oracle
     build_oracle()
     w = load_workload(args.config)
-    m = args.m or 16
+    # the probe count of the headline line on this workload (the smallest m
+    # at which the learned bf16 path reaches recall@10 >= 0.9), unless given
+    m = args.m or REFERENCE_M
     at = O.Attrs.of(w)
     idx = O.build(w.X, at, w.B, w.h, 0, w.init_idx, w.metric)
     cores = O.set_threads(0)
