@@ -936,7 +936,7 @@ int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem
 int tc_launch_f8(const CUtensorMap& map, const TcArgs& a, int metric, int words_pad, int kp, int N,
                  int64_t grid, size_t smem, cudaStream_t s);
 // Launch of the penalty form (scan_tc_pen.cu): N = 128 rows per tile, two
-// stages; kp 10 or 16.
+// B-tile stages and four accumulator stages; kp 10 or 16.
 int tc_launch_pen(const CUtensorMap& map, const TcArgs& a, int metric, int words_pad, int kp,
                   int64_t grid, size_t smem, cudaStream_t s);
 
