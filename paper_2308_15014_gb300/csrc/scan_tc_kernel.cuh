@@ -363,9 +363,10 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   // the current and the next item (index: item parity)
   __shared__ int s_ne[2], s_ntiles[2], s_bin[2];
   __shared__ uint64_t p_thr[2][TC_M];
-  // penalty form: each quarter list's ceil(KP/4)-th key (all ones until it
-  // has that many); the per-pair form has no shared memory to spare for it
-  __shared__ uint64_t s_qk[PEN ? TC_PARTS : 1][TC_M];
+  // penalty form: the score bits of each quarter list's ceil(KP/4)-th and
+  // ceil(KP/4) - 1-th keys (all ones until it has that many); the per-pair
+  // form has no shared memory to spare for them
+  __shared__ uint32_t s_qa[PEN ? TC_PARTS : 1][TC_M], s_qb[PEN ? TC_PARTS : 1][TC_M];
   __shared__ int32_t p_e[2][TC_M];
   // probe data of the item about to start (read once into registers)
   __shared__ uint64_t p_sel[TC_M];
@@ -393,7 +394,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     mbar_init(&meta_bar, 1);
     mbar_init(&afull_bar, TC_C / 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int i = 0; i < (PEN ? TC_PARTS : 1) * TC_M; i++) (&s_qk[0][0])[i] = kEmptyKey;
+    for (int i = 0; i < (PEN ? TC_PARTS : 1) * TC_M; i++) (&s_qa[0][0])[i] = (&s_qb[0][0])[i] = ~0u;
     s_fail = 0;
     int gb = 0;
     for (int w = 0; w < WP; w++)
@@ -706,18 +707,42 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         // the four threads of a probe share the smallest of their KP-th keys:
         // a key above it has KP better keys in one quarter list already
         if (thr != kEmptyKey) atomicMin(reinterpret_cast<unsigned long long*>(&pthr[probe]), thr);
-        // and the largest of their ceil(KP/4)-th keys: the four lists (of
-        // distinct rows) hold at least KP keys at or below it.  A slot read
-        // before its quarter's latest flush is larger, so the bound holds
+        // and a bound from all four lists (of distinct rows): with QB =
+        // ceil(KP/4), the NHI quarters whose QB-th keys are smallest count QB
+        // keys each and the others QB - 1, KP keys in all at or below the
+        // largest of those keys' scores.  A slot read before its quarter's
+        // latest flush is larger, so the bound holds
         if constexpr (PEN) {
-          constexpr int QK = (KP + TC_PARTS - 1) / TC_PARTS - 1;
-          s_qk[part][probe] = L[QK];
-          uint64_t mq = s_qk[0][probe];
+          constexpr int QB = (KP + TC_PARTS - 1) / TC_PARTS;
+          constexpr int NHI = KP - TC_PARTS * (QB - 1);
+          static_assert(QB >= 2 && NHI >= 1 && NHI <= TC_PARTS, "quarter split");
+          s_qa[part][probe] = (uint32_t)(L[QB - 1] >> 32);
+          s_qb[part][probe] = (uint32_t)(L[QB - 2] >> 32);
+          uint32_t qa[TC_PARTS], qb[TC_PARTS];
 #pragma unroll
-          for (int pp = 1; pp < TC_PARTS; pp++) {
-            const uint64_t v = s_qk[pp][probe];
-            mq = v > mq ? v : mq;
+          for (int pp = 0; pp < TC_PARTS; pp++) {
+            qa[pp] = s_qa[pp][probe];
+            qb[pp] = s_qb[pp][probe];
           }
+          // order the quarters by their QB-th key (compare-exchange network)
+          auto cx = [&](int i, int j) {
+            if (qa[j] < qa[i]) {
+              const uint32_t ta = qa[i], tb = qb[i];
+              qa[i] = qa[j];
+              qb[i] = qb[j];
+              qa[j] = ta;
+              qb[j] = tb;
+            }
+          };
+          cx(0, 1);
+          cx(2, 3);
+          cx(0, 2);
+          cx(1, 3);
+          cx(1, 2);
+          uint32_t bs = qa[NHI - 1];
+#pragma unroll
+          for (int pp = NHI; pp < TC_PARTS; pp++) bs = qb[pp] > bs ? qb[pp] : bs;
+          const uint64_t mq = ((uint64_t)bs << 32) | 0xffffffffull;
           if (mq != kEmptyKey) {
             atomicMin(reinterpret_cast<unsigned long long*>(&pthr[probe]), mq);
             if (mq < thr) thr = mq;
@@ -878,7 +903,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
                         a.qslot + (int64_t)(e / a.m) * TC_SLOTS + s_bin[par] % a.nslot),
                     (unsigned long long)L[KP - 1]);
       }
-      if (PEN) s_qk[part][probe] = kEmptyKey;  // read again only after the barrier below
+      if (PEN) s_qa[part][probe] = s_qb[part][probe] = ~0u;  // read again only after the barrier below
       // the next item's A operand: every MMA of this item has completed (each
       // tile's accumulator was waited for), so A may be overwritten once the
       // producer has the next item's probe data
