@@ -108,9 +108,10 @@ typedef struct {
  *   prec         CAPS_FP32: every distance in fp32.
  *                CAPS_BF16: the index also keeps a bf16 copy of the rows;
  *                searches score all selected rows with bf16 tensor-core
- *                tiles (fp32 accumulation, L2 as |x|^2 + |q|^2 - 2 q.x) and
- *                re-score the best rerank_factor * k candidates of each query
- *                exactly in fp32 before keeping k.  Needs d % 8 == 0 and
+ *                tiles (fp32 accumulation; L2 candidates ranked by
+ *                |x|^2 - 2 q.x, the query's own |q|^2 being common to all its
+ *                keys) and re-score the best rerank_factor * k candidates of
+ *                each query exactly in fp32 before keeping k.  Needs d % 8 == 0 and
  *                64 <= d <= 128; searches with k > 32 (or a candidate list beyond
  *                64) use the fp32 scan instead.
  *                CAPS_FP8E4M3: as CAPS_BF16 with e4m3 rows and queries, each
