@@ -9,7 +9,8 @@ all 10,000 queries (Alg. 2: filter packing, centroid scores, top-m, block
 selection, fused scan + top-k) with queries resident in HBM; the index build
 (Alg. 1) runs once before and is reported as build time.  m is the smallest
 probe count in {8,12,16,24,32,40,48,64} whose tie-aware recall@10 (against the
-CPU oracle's exact filtered kNN on a seeded sample of queries) is >= 0.9.
+exact filtered kNN of a seeded sample of queries: an fp32 index searched with
+every partition probed, ordered by fp64 distance) is >= 0.9.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
 (the plain C restatement of the method) on the same workload instead.
@@ -302,6 +303,72 @@ def form1_error(w, rng_seed=11, nq=64, nrow=2048):
     return out
 
 
+def exact_truth(caps, torch, w, samp, labels=False):
+    """Exact filtered kNN of the sampled queries, through the library: an fp32
+    index searched with every partition probed (m = B) returns the exact
+    filtered top-k (the tests check this against brute force); the 2k best it
+    returns are ordered by their fp64 distances, and the k first kept.
+    Returns ids [n, k] (-1 padded), their fp64 distances, and the number of
+    valid points found (at most 2k) per query."""
+    k, k2, Bt = w.k, min(2 * w.k, 128), 64
+    init = (np.arange(Bt, dtype=np.int64) * (w.N // Bt)).astype(np.int64)
+    X = torch.from_numpy(w.X).cuda()
+    if labels:
+        ix = caps.Index.build(X, None, None, Bt, h=w.h, iters=0, init_idx=init, metric=w.metric,
+                              labels=(w.sp_off, w.sp_lab, w.sp_vocab))
+        rows = [w.q_lab[w.q_off[q]:w.q_off[q + 1]] for q in samp]
+        q_off = np.zeros(len(samp) + 1, dtype=np.int64)
+        q_off[1:] = np.cumsum([len(r) for r in rows])
+        q_lab = np.concatenate(rows).astype(np.int32) if len(rows) else np.zeros(0, np.int32)
+        ids, _ = ix.search(np.ascontiguousarray(w.Q[samp]), (q_off, q_lab), k2, Bt)
+    else:
+        ix = caps.Index.build(X, torch.from_numpy(w.A).cuda(), w.vocab, Bt, h=w.h, iters=0,
+                              init_idx=init, metric=w.metric)
+        ids, _ = ix.search(np.ascontiguousarray(w.Q[samp]), np.ascontiguousarray(w.Qb[samp]),
+                           k2, Bt)
+    ix.close()
+    n = len(samp)
+    gt = np.full((n, k), -1, dtype=np.int64)
+    g64 = np.full((n, k), np.inf if w.metric == 0 else -np.inf)
+    cnt = np.zeros(n, dtype=np.int64)
+    for i, q in enumerate(samp):
+        got = ids[i][ids[i] >= 0]
+        cnt[i] = len(got)
+        d = exact_dist(w.X[got], w.Q[q], w.metric)
+        order = np.lexsort((got, d if w.metric == 0 else -d))[:k]
+        gt[i, :len(order)] = got[order]
+        g64[i, :len(order)] = d[order]
+    return gt, g64, cnt
+
+
+def exact_dist(rows, q, metric):
+    """fp64 squared L2 distance (or inner product) of each row to q."""
+    r = rows.astype(np.float64)
+    qq = q.astype(np.float64)
+    return ((r - qq) ** 2).sum(1) if metric == 0 else r @ qq
+
+
+def recall_at_k(ids, gt, g64, cnt, k, X, Q, metric=0):
+    """RecallK@K over the sampled queries, two readings: strict (returned ids
+    in the true top-k, divided by min(k, |D_C|)); tie-aware (a returned id
+    whose exact distance is no worse than the true k-th counts).  Returns the
+    two means."""
+    strict, tie = [], []
+    for q in range(ids.shape[0]):
+        den = int(min(k, cnt[q]))
+        if den == 0:
+            strict.append(1.0)
+            tie.append(1.0)
+            continue
+        got = ids[q, :k][ids[q, :k] >= 0]
+        strict.append(len(set(gt[q, :den].tolist()).intersection(got.tolist())) / den)
+        d = exact_dist(X[got], Q[q], metric) if len(got) else np.zeros(0)
+        kth = g64[q, den - 1]
+        hits = int((d <= kth).sum() if metric == 0 else (d >= kth).sum())
+        tie.append(min(hits, den) / den)
+    return float(np.mean(strict)), float(np.mean(tie))
+
+
 def query_stats(w, rows_scanned, rows_passed):
     """Selectivity |D_C| / N of the batch's filters (percentiles and a
     per-decade histogram) and the mean candidates per query of the measured
@@ -320,7 +387,7 @@ def query_stats(w, rows_scanned, rows_passed):
     return out
 
 
-def h_sweep(args, w, caps, O, torch, samp, gt, g64, cnt):
+def h_sweep(args, w, caps, torch, samp, gt, g64, cnt):
     """AFT height ablation (k-means + bf16, the same seed points): for each h
     the smallest probe count reaching recall@10 >= 0.9 and the batch QPS
     there (device buffers, CUDA events, L2 flushed)."""
@@ -338,8 +405,8 @@ def h_sweep(args, w, caps, O, torch, samp, gt, g64, cnt):
         row = {"h": h, "m_at_0.9": None}
         for m in M_SWEEP:
             ix.search(Qd, Qbd, w.k, m, out_ids=ids, out_dist=dist)
-            _, tie, _, _ = O.recall(ids.cpu().numpy()[samp], gt, g64, cnt, w.k, X=w.X,
-                                    Q=w.Q[samp])
+            _, tie = recall_at_k(ids.cpu().numpy()[samp], gt, g64, cnt, w.k, w.X, w.Q[samp],
+                                 w.metric)
             if tie >= 0.9:
                 for _ in range(3):
                     ix.search(Qd, Qbd, w.k, m, out_ids=ids, out_dist=dist)
@@ -362,10 +429,10 @@ def h_sweep(args, w, caps, O, torch, samp, gt, g64, cnt):
     return out
 
 
-def sparse_line(args, caps, O, torch):
+def sparse_line(args, caps, torch):
     """Label-set workload (2M x 128 fp32 mixture, 10,000-label vocabulary,
     1-20 labels per point, queries requiring 1-8 labels): build, probe sweep,
-    recall against the oracle's exact filtered kNN on a query sample, QPS of
+    recall against the exact filtered kNN on a query sample, QPS of
     the batched query (device buffers, CUDA events, L2 flushed)."""
     from workloads import config_sparse2m
     t0 = time.perf_counter()
@@ -373,9 +440,7 @@ def sparse_line(args, caps, O, torch):
     gen_s = time.perf_counter() - t0
     rng = np.random.default_rng(6)
     samp = np.sort(rng.choice(w.nq, 200, replace=False))
-    cons = O.Cons(q_off=w.q_off, q_lab=w.q_lab)
-    sub = cons.subset(samp)
-    gt, _, g64, cnt = O.bruteforce(w.X, O.Attrs.of(w), w.Q[samp], sub, w.k)
+    gt, g64, cnt = exact_truth(caps, torch, w, samp, labels=True)
     Qd = torch.from_numpy(w.Q).cuda()
     qoff = torch.from_numpy(w.q_off).cuda()
     qlab = torch.from_numpy(w.q_lab).cuda()
@@ -395,8 +460,8 @@ def sparse_line(args, caps, O, torch):
         sweep, chosen = [], None
         for m in SPARSE_M_SWEEP:
             ix.search(Qd, (qoff, qlab), w.k, m, out_ids=ids, out_dist=dist)
-            strict, tie, _, _ = O.recall(ids.cpu().numpy()[samp], gt, g64, cnt, w.k, X=w.X,
-                                         Q=w.Q[samp])
+            strict, tie = recall_at_k(ids.cpu().numpy()[samp], gt, g64, cnt, w.k, w.X,
+                                      w.Q[samp], w.metric)
             evs = []
             for _ in range(max(3, args.warmup)):
                 ix.search(Qd, (qoff, qlab), w.k, m, out_ids=ids, out_dist=dist)
@@ -421,6 +486,8 @@ def sparse_line(args, caps, O, torch):
 def oracle_baseline(w, m, k, budget_s=15.0):
     """CPU oracle (plain C, all host cores) on a bounded sample of queries."""
     import oracle as O
+    from oracle.build import build_oracle
+    build_oracle()
     cores = O.set_threads(0)
     at = O.Attrs.of(w)
     t0 = time.perf_counter()
@@ -510,7 +577,7 @@ MLP_ARGS = dict(mlp_hidden=512, mlp_epochs=20, mlp_samples=131072, mlp_batch=409
                 mlp_label_k=10, seed=17)
 
 
-def measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world, local, part=0):
+def measure_path(args, w, caps, prec, samp, gt, g64, cnt, flush, world, local, part=0):
     """Build the index in the given precision and partitioner, pick m, time
     the batch."""
     import torch
@@ -537,7 +604,7 @@ def measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world, local
     for m in ((args.m,) if args.m else M_SWEEP):
         search(m)
         ids = out_ids.cpu().numpy()[samp]
-        strict, tie, _, _ = O.recall(ids, gt, g64, cnt, w.k, X=w.X, Q=w.Q[samp])
+        strict, tie = recall_at_k(ids, gt, g64, cnt, w.k, w.X, w.Q[samp], w.metric)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         search(m)
         ev0.record()
@@ -625,16 +692,12 @@ def run_caps(args):
     from paper_2308_15014_gb300 import build as capsbuild
     capsbuild.build()
     import paper_2308_15014_gb300 as caps
-    import oracle as O
-    from oracle.build import build_oracle
-    build_oracle()
 
     w = load_workload(args.config)
-    # recall on a seeded sample of queries against the oracle's exact kNN
+    # recall on a seeded sample of queries against their exact filtered kNN
     rng = np.random.default_rng(5)
     samp = np.sort(rng.choice(w.nq, min(RECALL_SAMPLE, w.nq), replace=False))
-    O.set_threads(0)
-    gt, _, g64, cnt = O.bruteforce(w.X, O.Attrs.of(w), w.Q[samp], O.Cons(Qb=w.Qb[samp]), w.k)
+    gt, g64, cnt = exact_truth(caps, torch, w, samp)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     kinds = {"fp32": (caps.FP32, caps.KMEANS), "bf16": (caps.BF16, caps.KMEANS),
              "fp8": (caps.FP8, caps.KMEANS), "mlp_fp32": (caps.FP32, caps.MLP),
@@ -643,8 +706,8 @@ def run_caps(args):
     res = {}
     for pth in paths:
         prec, part = kinds[pth]
-        res[pth] = measure_path(args, w, caps, O, prec, samp, gt, g64, cnt, flush, world,
-                                local, part=part)
+        res[pth] = measure_path(args, w, caps, prec, samp, gt, g64, cnt, flush, world, local,
+                                part=part)
     head = res[paths[0]]
     ix, m, stage = head["ix"], head["m"], head["stage"]
 
@@ -717,8 +780,8 @@ def run_caps(args):
     form1 = {"tile_score_vs_fp64": {w.name: form1_error(w), "float_mixture_d128": form1_error(wf)},
              "returned_dist_vs_fp64": {"pairs": int(rel.size), "max_rel": float(rel.max()),
                                        "mean_rel": float(rel.mean())}}
-    sparse = sparse_line(args, caps, O, torch) if args.sparse and world == 1 else None
-    hsw = h_sweep(args, w, caps, O, torch, samp, gt, g64, cnt) if args.h_sweep and world == 1 \
+    sparse = sparse_line(args, caps, torch) if args.sparse and world == 1 else None
+    hsw = h_sweep(args, w, caps, torch, samp, gt, g64, cnt) if args.h_sweep and world == 1 \
         else None
 
     if rank != 0:
