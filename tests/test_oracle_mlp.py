@@ -95,3 +95,69 @@ def test_training_reduces_loss_and_labels_are_distributions():
     net = _net(np.random.default_rng(5), 8, 16, w.B, scale=0.3)
     _, losses = O.mlp_train(w.X[samples], Y, net, epochs=30, batch=40, lr=1e-2)
     assert losses[-1] < 0.7 * losses[0]
+
+
+def _bias_only_net(d, H, b2, rng):
+    """W1 = 0 and b1 = 0 make every hidden unit relu(0) = 0, so each row's
+    logits are b2 whatever x is and no gradient reaches W1, b1 or W2."""
+    B = len(b2)
+    return O.MLP(np.zeros((H, d)), np.zeros(H), rng.standard_normal((B, H)),
+                 np.asarray(b2, np.float64))
+
+
+def test_train_minibatches_cover_every_row_in_order():
+    """mlp_train's loss list, checked against the closed form of the
+    cross-entropy with constant logits: with lr = 0 nothing moves, so step s
+    reports mean over its rows r of sum_c Y[r,c] (logsumexp(b2) - b2[c]).
+    n = 5, batch = 2: three minibatches per epoch ([0,1], [2,3], [4]), the
+    last one partial; the second epoch follows a given permutation.  A
+    dropped tail batch, a padded one, or minibatches cut from the rows in
+    storage order instead of the epoch's order all change the list."""
+    rng = np.random.default_rng(31)
+    d, H = 3, 4
+    b2 = np.array([0.0, 1.0, 2.5, -1.0])
+    net = _bias_only_net(d, H, b2, rng)
+    n, batch = 5, 2
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = rng.random((n, len(b2))).astype(np.float32)
+    Y /= Y.sum(1, keepdims=True)
+    order = [np.arange(n), np.array([3, 0, 4, 1, 2])]
+    _, losses = O.mlp_train(X, Y, net, epochs=2, batch=batch, lr=0.0, order=order)
+    lse = np.log(np.exp(b2).sum())
+    Y64 = Y.astype(np.float64)
+    row_ce = lse * Y64.sum(1) - Y64 @ b2
+    want = []
+    for e in range(2):
+        for b0 in range(0, n, batch):
+            want.append(row_ce[order[e][b0:b0 + batch]].mean())
+    assert len(losses) == 6
+    np.testing.assert_allclose(losses, want, rtol=1e-12, atol=1e-12)
+
+
+def test_train_adam_step_counter_runs_across_epochs():
+    """Adam with a constant gradient g moves every step by exactly
+    lr * g / (|g| + eps): the bias-corrected moments are g and g^2 only when
+    the step counter t equals the number of steps taken so far.  A softmax
+    saturated far from its one-hot target (b2 = (0, 100, 0), every label on
+    class 0) has d loss / d b2 = p - y = (-1, +1, ~e^-100) on every row of
+    every minibatch, so after T steps b2[0] = T * lr / (1 + eps) and
+    b2[1] = 100 - T * lr / (1 + eps).  n = 5 rows in batches of 2 for 2
+    epochs is T = 6 steps; a counter restarted each epoch would make the
+    fourth step about 1.72 lr, a dropped partial batch would give T = 4."""
+    rng = np.random.default_rng(32)
+    d, H = 2, 3
+    net = _bias_only_net(d, H, [0.0, 100.0, 0.0], rng)
+    n, batch, lr, eps = 5, 2, 0.01, 1e-8
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = np.zeros((n, 3), np.float32)
+    Y[:, 0] = 1.0
+    w, losses = O.mlp_train(X, Y, net, epochs=2, batch=batch, lr=lr)
+    T = 6
+    assert len(losses) == T
+    step = lr / (1.0 + eps)
+    assert abs(w.b2[0] - T * step) < 1e-12
+    assert abs(w.b2[1] - (100.0 - T * step)) < 1e-12
+    assert abs(w.b2[2]) < 1e-12
+    np.testing.assert_array_equal(w.W1, 0.0)
+    np.testing.assert_array_equal(w.b1, 0.0)
+    np.testing.assert_array_equal(w.W2, net.W2)
