@@ -9,8 +9,8 @@ all 10,000 queries (Alg. 2: filter packing, centroid scores, top-m, block
 selection, fused scan + top-k) with queries resident in HBM; the index build
 (Alg. 1) runs once before and is reported as build time.  m is the smallest
 probe count in {8,12,16,24,32,40,48,64} whose tie-aware recall@10 (against the
-exact filtered kNN of a seeded sample of queries: an fp32 index searched with
-every partition probed, ordered by fp64 distance) is >= 0.9.
+exact filtered kNN of a seeded sample of queries, from the CPU oracle's brute
+force ordered by fp64 distance, untimed) is >= 0.9.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
 (the plain C restatement of the method) on the same workload instead.
@@ -303,13 +303,26 @@ def form1_error(w, rng_seed=11, nq=64, nrow=2048):
     return out
 
 
-def exact_truth(caps, torch, w, samp, labels=False):
-    """Exact filtered kNN of the sampled queries, through the library: an fp32
-    index searched with every partition probed (m = B) returns the exact
-    filtered top-k (the tests check this against brute force); the 2k best it
-    returns are ordered by their fp64 distances, and the k first kept.
-    Returns ids [n, k] (-1 padded), their fp64 distances, and the number of
-    valid points found (at most 2k) per query."""
+def oracle_truth(w, samp):
+    """Exact filtered kNN of the sampled queries (Def. 2, appendix
+    "Groundtruth") from the CPU oracle's brute force: every point filtered,
+    the valid ones ordered by fp64 distance (ties to the lower id).  Runs
+    outside every timed region.  Returns ids [n, k] (-1 padded), their fp64
+    distances and |D_C| per query."""
+    import oracle as O
+    from oracle.build import build_oracle
+    build_oracle()
+    O.set_threads(0)
+    cons = O.Cons.of(w).subset(samp)
+    ids, _, d64, cnt = O.bruteforce(w.X, O.Attrs.of(w), np.ascontiguousarray(w.Q[samp]), cons,
+                                    w.k, metric=w.metric, order64=True)
+    return ids, d64, cnt
+
+
+def library_truth(caps, torch, w, samp, labels=False):
+    """The same sample answered by the library with every partition probed
+    (m = B: the exact filtered top-k by construction), its 2k best reordered
+    by fp64 distance.  Used only to cross-check oracle_truth."""
     k, k2, Bt = w.k, min(2 * w.k, 128), 64
     init = (np.arange(Bt, dtype=np.int64) * (w.N // Bt)).astype(np.int64)
     X = torch.from_numpy(w.X).cuda()
@@ -328,17 +341,34 @@ def exact_truth(caps, torch, w, samp, labels=False):
                            k2, Bt)
     ix.close()
     n = len(samp)
-    gt = np.full((n, k), -1, dtype=np.int64)
     g64 = np.full((n, k), np.inf if w.metric == 0 else -np.inf)
-    cnt = np.zeros(n, dtype=np.int64)
     for i, q in enumerate(samp):
         got = ids[i][ids[i] >= 0]
-        cnt[i] = len(got)
         d = exact_dist(w.X[got], w.Q[q], w.metric)
         order = np.lexsort((got, d if w.metric == 0 else -d))[:k]
-        gt[i, :len(order)] = got[order]
         g64[i, :len(order)] = d[order]
-    return gt, g64, cnt
+    return g64
+
+
+def exact_truth(caps, torch, w, samp, labels=False):
+    """Ground truth for the recall of the sampled queries: the oracle's brute
+    force, cross-checked against the library's m = B search (the k best fp64
+    distances of the two must agree to 1e-6 relative, position by position;
+    the bench stops if they do not).  Returns (ids, fp64 distances, |D_C|,
+    the cross-check's summary)."""
+    gt, g64, cnt = oracle_truth(w, samp)
+    lib64 = library_truth(caps, torch, w, samp, labels=labels)
+    fin = np.isfinite(g64) | np.isfinite(lib64)
+    both = np.isfinite(g64) & np.isfinite(lib64)
+    tol = 1e-6 * np.maximum(1.0, np.abs(np.where(both, g64, 0.0)))
+    bad = (fin & ~both) | (both & (np.abs(g64 - lib64) > tol))
+    n_bad = int(bad.any(1).sum())
+    if n_bad:
+        raise RuntimeError(f"ground truth: the library's exact (m = B) search disagrees with the "
+                           f"oracle's brute force on {n_bad} of {len(samp)} sampled queries")
+    check = {"truth": "oracle brute force (fp64 order)", "queries": int(len(samp)),
+             "library_m_eq_B_agrees": True}
+    return gt, g64, cnt, check
 
 
 def exact_dist(rows, q, metric):
@@ -440,7 +470,7 @@ def sparse_line(args, caps, torch):
     gen_s = time.perf_counter() - t0
     rng = np.random.default_rng(6)
     samp = np.sort(rng.choice(w.nq, 200, replace=False))
-    gt, g64, cnt = exact_truth(caps, torch, w, samp, labels=True)
+    gt, g64, cnt, _ = exact_truth(caps, torch, w, samp, labels=True)
     Qd = torch.from_numpy(w.Q).cuda()
     qoff = torch.from_numpy(w.q_off).cuda()
     qlab = torch.from_numpy(w.q_lab).cuda()
@@ -483,17 +513,50 @@ def sparse_line(args, caps, torch):
     return out
 
 
-def oracle_baseline(w, m, k, budget_s=15.0):
-    """CPU oracle (plain C, all host cores) on a bounded sample of queries."""
+def oracle_index_of(caps, ix, w):
+    """The oracle's own index over the partitions of a built library index:
+    the oracle runs Alg. 1's second level itself (attribute-frequency trees
+    and layout) from the library's f(x_i) (ARR_BIN), and for a learned
+    partitioner also takes the trained network, whose m largest fp32 logits
+    it computes itself per query (Alg. 2 probe).  So the CPU times the same
+    index, probe rule and m as the GPU; only the first-level training
+    (k-means, network) is not redone on the host cores.
+    Returns (oracle index, network or None)."""
+    import oracle as O
+    bins = ix.export(caps.ARR_BIN)
+    net = None
+    if ix.info.part == caps.MLP:
+        H, d, B = ix.info.mlp_hidden, w.d, w.B
+        Wf = ix.export(caps.ARR_MLP)
+        net = O.MLP(Wf[:H * d].reshape(H, d), Wf[H * d:H * d + H],
+                    Wf[H * d + H:H * d + H + B * H].reshape(B, H), Wf[H * d + H + B * H:])
+        oi = O.build(w.X, O.Attrs.of(w), w.B, w.h, 0, w.init_idx, w.metric, bins=bins)
+    else:
+        oi = O.build(w.X, O.Attrs.of(w), w.B, w.h, 0, w.init_idx, w.metric,
+                     C=ix.export(caps.ARR_CENTROIDS))
+    return oi, net
+
+
+def oracle_query(w, at, oi, net, sub, m):
+    """One batch of Alg. 2 on the host cores: the probe (the network's m
+    largest logits, or the m nearest centroids inside the oracle's search),
+    block selection, filtered scan and top-k."""
+    import oracle as O
+    Q = np.ascontiguousarray(w.Q[sub])
+    probe_in = O.probe_logits(Q, net, m) if net is not None else None
+    return O.search(w.X, at, oi, Q, O.Cons(Qb=w.Qb[sub]), w.k, m, probe_in=probe_in)
+
+
+def oracle_baseline(caps, ix, w, m, budget_s=15.0):
+    """CPU oracle (plain C, all host cores) on a bounded sample of queries,
+    over the same partitions as the measured library index."""
     import oracle as O
     from oracle.build import build_oracle
     build_oracle()
     cores = O.set_threads(0)
     at = O.Attrs.of(w)
     t0 = time.perf_counter()
-    # k-means at this size is beyond a CPU budget of seconds: the oracle's
-    # index uses the same seed points as centroids (0 Lloyd iterations)
-    idx = O.build(w.X, at, w.B, w.h, 0, w.init_idx, w.metric)
+    oi, net = oracle_index_of(caps, ix, w)
     build_s = time.perf_counter() - t0
     rng = np.random.default_rng(7)
     order = rng.permutation(w.nq)
@@ -501,13 +564,15 @@ def oracle_baseline(w, m, k, budget_s=15.0):
     while done < w.nq and spent < budget_s:
         sub = order[done:done + n]
         t0 = time.perf_counter()
-        O.search(w.X, at, idx, w.Q[sub], O.Cons(Qb=w.Qb[sub]), k, m)
+        oracle_query(w, at, oi, net, sub, m)
         spent += time.perf_counter() - t0
         done += len(sub)
         n *= 2
+    part = "learned partitioner's logits" if net is not None else "k-means centroids"
     return {"value": done / spent, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {w.nq} queries at m={m}, k={k}; oracle index built from the "
-                      f"same seed centroids without Lloyd iterations ({build_s:.1f} s, untimed)"}
+            "sample": f"{done} of {w.nq} queries at m={m}, k={w.k}; the oracle's index laid out "
+                      f"by the oracle from the measured GPU index's partitions (probe: the "
+                      f"{part}; {build_s:.1f} s, untimed)"}
 
 
 REFERENCE_M = 40
@@ -531,41 +596,74 @@ def job_throughput(world, nq, seconds):
     return world * nq / seconds
 
 
+def headline_config(w, m, path, world):
+    """The `config` object of both arms' JSON lines (the same workload, index,
+    probe count and batch)."""
+    return {"workload": w.name, "N": w.N, "d": w.d, "L": int(w.A.shape[1]), "B": w.B, "h": w.h,
+            "kmeans_iters": w.iters, "m": m, "k": w.k, "path": path,
+            "partitioner": "mlp 128-512-1024" if path.startswith("mlp") else "k-means",
+            "queries_per_step": w.nq, "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def build_index(caps, torch, w, path):
+    """Alg. 1 on the GPU for one of the search paths (precision, partitioner)."""
+    prec, part = {"fp32": (caps.FP32, caps.KMEANS), "bf16": (caps.BF16, caps.KMEANS),
+                  "fp8": (caps.FP8, caps.KMEANS), "mlp_fp32": (caps.FP32, caps.MLP),
+                  "mlp_bf16": (caps.BF16, caps.MLP), "mlp_fp8": (caps.FP8, caps.MLP)}[path]
+    X = torch.from_numpy(w.X).cuda()
+    A = torch.from_numpy(w.A).cuda()
+    extra = MLP_ARGS if part == caps.MLP else {}
+    return caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, metric=w.metric,
+                            init_idx=w.init_idx, prec=prec, part=part, **extra)
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle (plain C restatement of Alg. 2 with
+    OpenMP over queries) times whole 10,000-query batches on the host cores,
+    over the index of the headline path -- its partitions built on the GPU
+    (k-means / network training are untimed set-up), its attribute-frequency
+    trees, layout, probes, selections and scans all the oracle's own."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    import torch
     import oracle as O
     from oracle.build import build_oracle
+    from paper_2308_15014_gb300 import build as capsbuild
     build_oracle()
+    capsbuild.build()
+    import paper_2308_15014_gb300 as caps
+    torch.cuda.set_device(0)
     w = load_workload(args.config)
+    path = [p for p in args.paths.split(",") if p][0]
     # the probe count of the headline line on this workload (the smallest m
     # at which the learned bf16 path reaches recall@10 >= 0.9), unless given
     m = args.m or REFERENCE_M
+    ix = build_index(caps, torch, w, path)
+    torch.cuda.synchronize()
+    oi, net = oracle_index_of(caps, ix, w)
+    ix.close()
     at = O.Attrs.of(w)
-    idx = O.build(w.X, at, w.B, w.h, 0, w.init_idx, w.metric)
     cores = O.set_threads(0)
-    rng = np.random.default_rng(11)
-    per_step = min(w.nq, 2000)
+    allq = np.arange(w.nq)
     for _ in range(args.warmup):
-        sub = rng.choice(w.nq, per_step, replace=False)
-        O.search(w.X, at, idx, w.Q[sub], O.Cons(Qb=w.Qb[sub]), w.k, m)
+        oracle_query(w, at, oi, net, allq, m)
     times = []
     for _ in range(args.steps):
-        sub = rng.choice(w.nq, per_step, replace=False)
         t0 = time.perf_counter()
-        O.search(w.X, at, idx, w.Q[sub], O.Cons(Qb=w.Qb[sub]), w.k, m)
+        oracle_query(w, at, oi, net, allq, m)
         times.append(time.perf_counter() - t0)
-    v = per_step * len(times) / sum(times)
+    v = w.nq * len(times) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "N": w.N, "d": w.d, "B": w.B, "h": w.h, "m": m,
-                       "k": w.k, "queries_per_step": per_step},
+            "config": headline_config(w, m, path, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} random queries per step; oracle index from "
-                                       "the seed centroids (0 Lloyd iterations)"},
+                             "sample": f"all {w.nq} queries per step at m={m}; the oracle's "
+                                       "index laid out by the oracle from the GPU-built "
+                                       "partitions of the same path (untimed set-up)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line, default=_json_default), flush=True)
     return 0
@@ -697,7 +795,7 @@ def run_caps(args):
     # recall on a seeded sample of queries against their exact filtered kNN
     rng = np.random.default_rng(5)
     samp = np.sort(rng.choice(w.nq, min(RECALL_SAMPLE, w.nq), replace=False))
-    gt, g64, cnt = exact_truth(caps, torch, w, samp)
+    gt, g64, cnt, truth_check = exact_truth(caps, torch, w, samp)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     kinds = {"fp32": (caps.FP32, caps.KMEANS), "bf16": (caps.BF16, caps.KMEANS),
              "fp8": (caps.FP8, caps.KMEANS), "mlp_fp32": (caps.FP32, caps.MLP),
@@ -788,7 +886,7 @@ def run_caps(args):
         return 0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = oracle_baseline(w, m, w.k)
+        cpu = oracle_baseline(caps, ix, w, m)
     others = {}
     for pth in paths[1:]:
         r = res[pth]
@@ -804,14 +902,10 @@ def run_caps(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"bf16": "bf16", "fp8": "e4m3"}.get(paths[0].split("_")[-1], "f32"),
         "data": "synthetic",
-        "config": {"workload": w.name, "N": w.N, "d": w.d, "L": int(w.A.shape[1]),
-                   "B": w.B, "h": w.h, "kmeans_iters": w.iters, "m": m, "k": w.k,
-                   "path": paths[0], "partitioner": "mlp 128-512-1024" if paths[0].startswith("mlp")
-                   else "k-means", "queries_per_step": w.nq,
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": headline_config(w, m, paths[0], world),
         "recall_at_10": {"tie_aware": head["rec"]["recall_tie"],
-                         "strict": head["rec"]["recall_strict"], "sample_queries": int(len(samp))},
+                         "strict": head["rec"]["recall_strict"], "sample_queries": int(len(samp)),
+                         "truth": truth_check},
         "sweep": head["sweep"],
         "build_s": round(head["build_s"], 3),
         "stage_ms": {k_: round(v_, 4) for k_, v_ in stage.items()},

@@ -195,7 +195,9 @@ int caps_build(const caps_build_params* params, const float* X, int64_t N,
  * out_ids = [nq*k] int64 original point ids, best first, ties to the lower
  * id, -1 where fewer than k valid points were found; out_dist = [nq*k] fp32
  * (squared L2 or inner product), +inf (L2) / -inf (IP) on padded slots.
- * 1 <= k <= 128, 1 <= m <= B.  nq = 0 is a no-op.
+ * 1 <= k <= 128, 1 <= m <= B; m > 128 also needs B <= 16384 (the top-m
+ * choice then sorts all B scores of a query in shared memory), CAPS_EINVAL
+ * otherwise.  nq = 0 is a no-op.
  */
 int caps_search_batch(const caps_index* index, const float* Q, int64_t nq,
                       const caps_attrs* constraints, int32_t k, int32_t m,
@@ -215,6 +217,21 @@ int caps_device_status(const caps_index* index, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* caps_last_error(void);
+
+/* ---- allocation accounting and failure injection (failure detection) -----
+ * Not part of the method (the paper has no counterpart): hooks to test the
+ * library's handling of an exhausted device.  Every device allocation the
+ * library makes (index arrays, plan buffers, per-call stream-ordered
+ * scratch) goes through one gate.
+ * caps_alloc_count: device allocations made so far by this process
+ *   (successful or not), all threads and devices together.
+ * caps_inject_alloc_failure(n): the n-th device allocation from now (n = 1:
+ *   the next one) fails without reaching the CUDA allocator, exactly as an
+ *   out-of-memory device would: the call that needed it returns CAPS_ENOMEM,
+ *   releases what it had taken and leaves every existing index and plan
+ *   usable.  One failure per arming; n <= 0 disarms. */
+int64_t caps_alloc_count(void);
+void caps_inject_alloc_failure(int64_t n);
 
 /* ---- introspection and single steps (used to check each step alone) ---- */
 
@@ -328,7 +345,8 @@ int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W,
 
 /*
  * caps_search_batch_noalloc -- the same batched query as caps_search_batch
- * (same arguments, same results), for callers that cannot allocate device
+ * (same arguments; on a CAPS_FP32 index the same results), for callers that
+ * cannot allocate device
  * memory: a process whose device memory is reserved up front by another
  * framework, a serving loop that must never wait on the allocator or on the
  * device-wide synchronisation that freeing implies, or an integration that
@@ -341,7 +359,12 @@ int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W,
  * library holds until the process exits.  Batches that need more run in
  * several passes over that array; the call returns CAPS_EINVAL when even one
  * query does not fit (about 4*B + 12*m + 4*L + 33 bytes per query, i.e.
- * B up to about 4 million).
+ * B up to about 4 million) and, as caps_search_batch, for m > 128 with
+ * B > 16384.
+ *   - It always runs the exact fp32 scan over the index's fp32 rows: on a
+ *     CAPS_BF16 or CAPS_FP8E4M3 index it returns what caps_search_batch
+ *     returns on a CAPS_FP32 index with the same partitions, not the
+ *     tensor-core form's results.  Only k-means indexes are served.
  *   - Q, constraints->dense, out_ids and out_dist must be device memory of
  *     the current device (host memory would need a staging allocation):
  *     CAPS_EINVAL otherwise.  The call only enqueues work on `stream`.

@@ -671,19 +671,23 @@ void orc_mlp_assign32(const float* X, int64_t n, int d, int H, int B, const floa
 /* fp32 logits in the same fixed order (queries' partition scores). */
 void orc_mlp_logits32(const float* X, int64_t n, int d, int H, int B, const float* W1,
                       const float* b1, const float* W2, const float* b2, float* Z) {
-  float* h = (float*)malloc(sizeof(float) * (size_t)H);
-  for (int64_t i = 0; i < n; i++) {
-    for (int u = 0; u < H; u++) {
-      float a = 0.0f;
-      for (int j = 0; j < d; j++) a = fmaf(W1[(int64_t)u * d + j], X[i * d + j], a);
-      a = a + b1[u];
-      h[u] = a > 0.0f ? a : 0.0f;
+#pragma omp parallel
+  {
+    float* h = (float*)malloc(sizeof(float) * (size_t)H);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+      for (int u = 0; u < H; u++) {
+        float a = 0.0f;
+        for (int j = 0; j < d; j++) a = fmaf(W1[(int64_t)u * d + j], X[i * d + j], a);
+        a = a + b1[u];
+        h[u] = a > 0.0f ? a : 0.0f;
+      }
+      for (int c = 0; c < B; c++) {
+        float a = 0.0f;
+        for (int u = 0; u < H; u++) a = fmaf(W2[(int64_t)c * H + u], h[u], a);
+        Z[i * B + c] = a + b2[c];
+      }
     }
-    for (int c = 0; c < B; c++) {
-      float a = 0.0f;
-      for (int u = 0; u < H; u++) a = fmaf(W2[(int64_t)c * H + u], h[u], a);
-      Z[i * B + c] = a + b2[c];
-    }
+    free(h);
   }
-  free(h);
 }

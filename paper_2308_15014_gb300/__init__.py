@@ -30,7 +30,8 @@ EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "c
            "caps_export", "caps_assign", "caps_probe", "caps_probe_set", "caps_select",
            "caps_set_timing", "caps_get_stage_times", "caps_search_batch_noalloc",
            "caps_device_status", "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign", "caps_plan_create",
-           "caps_plan_search", "caps_plan_get_info", "caps_plan_free")
+           "caps_plan_search", "caps_plan_get_info", "caps_plan_free", "caps_alloc_count",
+           "caps_inject_alloc_failure")
 
 
 class CapsError(RuntimeError):
@@ -115,6 +116,10 @@ def lib(path: Optional[str] = None):
     L.caps_plan_free.restype = None
     L.caps_set_timing.argtypes = [i32]
     L.caps_get_stage_times.argtypes = [ct.POINTER(caps_stage_times)]
+    L.caps_alloc_count.argtypes = []
+    L.caps_alloc_count.restype = i64
+    L.caps_inject_alloc_failure.argtypes = [i64]
+    L.caps_inject_alloc_failure.restype = None
     _lib = L
     return L
 
@@ -396,7 +401,10 @@ class Index:
 
     def search_noalloc(self, Q, Qb, k, m, out_ids, out_dist, stream=None):
         """caps_search_batch_noalloc: same query, no device allocation.
-        Q, Qb, out_ids and out_dist must be CUDA tensors."""
+        Q (float32 [nq, d]), Qb (int32 [nq, L]), out_ids (int64 [nq, k]) and
+        out_dist (float32 [nq, k]) must be contiguous CUDA tensors on one
+        device; nothing is converted (a conversion would allocate)."""
+        check_noalloc_args(Q, Qb, k, out_ids, out_dist, self.info.d, self.info.L)
         at, keep = _dense_attrs(Qb)
         _check(lib().caps_search_batch_noalloc(self._h, _ptr(Q), Q.shape[0], ct.byref(at), k, m,
                                                _ptr(out_ids), _ptr(out_dist), _stream(stream)))
@@ -411,6 +419,43 @@ class Index:
         _check(lib().caps_plan_create(self._h, _ptr(Q), Q.shape[0], ct.byref(at), k, m,
                                       1 if autotune else 0, _stream(stream), ct.byref(h)))
         return Plan(h, self, k)
+
+
+def check_noalloc_args(Q, Qb, k, out_ids, out_dist, d, L):
+    """Argument checks of Index.search_noalloc, made before any pointer
+    reaches the library: the C call cannot tell a float64 query or a short
+    output from a correct one, and would read or write past its end."""
+    t = _torch()
+    if t is None:
+        raise ValueError("search_noalloc takes CUDA tensors (torch is not available)")
+    want = (("Q", Q, t.float32, d), ("Qb", Qb, t.int32, L), ("out_ids", out_ids, t.int64, k),
+            ("out_dist", out_dist, t.float32, k))
+    nq = Q.shape[0] if isinstance(Q, t.Tensor) and Q.dim() == 2 else None
+    for name, a, dt, cols in want:
+        if not isinstance(a, t.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if a.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {a.dtype}")
+        if a.dim() != 2 or a.shape[1] != cols or (nq is not None and a.shape[0] != nq):
+            raise ValueError(f"{name} must have shape ({nq}, {cols}), got {tuple(a.shape)}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    devs = {a.device for _, a, _, _ in want}
+    if any(dv.type != "cuda" for dv in devs):
+        raise ValueError("Q, Qb, out_ids and out_dist must be CUDA tensors")
+    if len(devs) != 1:
+        raise ValueError("Q, Qb, out_ids and out_dist must be on one device")
+
+
+def alloc_count() -> int:
+    """caps_alloc_count: device allocations the library has made so far."""
+    return int(lib().caps_alloc_count())
+
+
+def inject_alloc_failure(n: int):
+    """caps_inject_alloc_failure: fail the n-th device allocation from now
+    (1 = the next) as an out-of-memory device would; n <= 0 disarms."""
+    lib().caps_inject_alloc_failure(int(n))
 
 
 class Plan:

@@ -2,6 +2,7 @@
 // the order of the kernels for index construction (Alg. 1) and batched query
 // (Alg. 2).  All arithmetic of the method runs in the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -23,6 +24,18 @@ int fail(int code, const std::string& msg) {
 int cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return CAPS_ECUDA;
+}
+
+static std::atomic<long long> g_alloc_calls{0};
+static std::atomic<long long> g_alloc_fail_at{0};  // 0: no failure armed
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t stream, bool async) {
+  *p = nullptr;
+  const long long n = ++g_alloc_calls;
+  long long at = g_alloc_fail_at.load();
+  if (at != 0 && n >= at && g_alloc_fail_at.compare_exchange_strong(at, 0))
+    return cudaErrorMemoryAllocation;
+  return async ? cudaMallocAsync(p, bytes, stream) : cudaMalloc(p, bytes);
 }
 
 namespace {
@@ -211,6 +224,12 @@ int make_meta(const caps_attrs* at, cudaStream_t s, DenseMeta* meta) {
 using namespace caps;
 
 extern "C" const char* caps_last_error(void) { return g_err.c_str(); }
+
+extern "C" int64_t caps_alloc_count(void) { return (int64_t)g_alloc_calls.load(); }
+
+extern "C" void caps_inject_alloc_failure(int64_t n) {
+  g_alloc_fail_at.store(n > 0 ? g_alloc_calls.load() + n : 0);
+}
 
 namespace caps {
 namespace {
@@ -1271,12 +1290,14 @@ struct caps_plan {
 namespace {
 template <class T>
 int plan_alloc(T** p, size_t count) {
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(1, count) * sizeof(T));
+  void* q = nullptr;
+  cudaError_t e = dev_alloc(&q, std::max<size_t>(1, count) * sizeof(T), nullptr, false);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return fail(CAPS_ENOMEM, "cudaMalloc failed for a plan buffer");
+    return fail(CAPS_ENOMEM, "device allocation failed for a plan buffer");
   }
+  *p = static_cast<T*>(q);
   return CAPS_OK;
 }
 
@@ -1514,17 +1535,17 @@ extern "C" int caps_mlp_loss_grad(int32_t d, int32_t H, int32_t B, const float* 
   g.b1 = o2.dev;
   g.W2 = o3.dev;
   g.b2 = o4.dev;
-  double* dl = nullptr;
+  float* dl = nullptr;
   if (int rc = scr.get(&dl, 1)) return rc;
   if (int rc = mlp_loss_grad(net, dX, n, dY, &g, dl, scr, s)) return rc;
   if (int rc = o1.finish(s)) return rc;
   if (int rc = o2.finish(s)) return rc;
   if (int rc = o3.finish(s)) return rc;
   if (int rc = o4.finish(s)) return rc;
-  double lh = 0.0;
-  CAPS_CUDA(cudaMemcpyAsync(&lh, dl, sizeof(double), cudaMemcpyDeviceToHost, s));
+  float lh = 0.f;
+  CAPS_CUDA(cudaMemcpyAsync(&lh, dl, sizeof(float), cudaMemcpyDeviceToHost, s));
   CAPS_CUDA(cudaStreamSynchronize(s));
-  if (loss) *loss = (float)lh;
+  if (loss) *loss = lh;
   return CAPS_OK;
 }
 

@@ -186,6 +186,14 @@ extern thread_local long long g_kernel_launches;
     ++::caps::g_kernel_launches;                                 \
   } while (0)
 
+// ---- device allocation gate ------------------------------------------------
+// Every device allocation of the library goes through dev_alloc: it counts
+// the calls (caps_alloc_count) and fails the n-th one on request
+// (caps_inject_alloc_failure) as if the device were out of memory, without
+// calling the allocator, so the CAPS_ENOMEM paths can be tested on the host.
+// stream == nullptr: cudaMalloc; otherwise cudaMallocAsync on that stream.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t stream, bool async);
+
 // ---- stream-ordered scratch ------------------------------------------------
 // Temporary device buffers for one call, allocated from the stream-ordered
 // pool and released on the same stream.
@@ -203,10 +211,10 @@ struct Scratch {
     if (count == 0) count = 1;
     if (n == 256) return fail(CAPS_ENOMEM, "scratch slots exhausted");
     void* p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), s);
+    cudaError_t e = dev_alloc(&p, count * sizeof(T), s, true);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(CAPS_ENOMEM, "cudaMallocAsync failed for scratch");
+      return fail(CAPS_ENOMEM, "device allocation failed for scratch");
     }
     ptrs[n++] = p;
     *out = (T*)p;
@@ -353,7 +361,7 @@ int probe_screened(int mode, const float* A, int64_t n, int K, const float* W, c
 int mlp_assign(const MlpNet& net, const float* X, int64_t n, int32_t* bin, Scratch& scr,
                cudaStream_t s);
 int mlp_loss_grad(const MlpNet& net, const float* X, int64_t n, const float* Y, MlpNet* grad,
-                  double* loss_dev, Scratch& scr, cudaStream_t s);
+                  float* loss_dev, Scratch& scr, cudaStream_t s);
 int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs, int batch,
               float lr, float* losses_host, cudaStream_t s);
 int mlp_gather_rows(const float* X, const int64_t* idx, int64_t n, int d, float* out,
@@ -481,10 +489,10 @@ struct caps_index {
   int alloc(T** p, size_t count) {
     if (count == 0) count = 1;
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    cudaError_t e = caps::dev_alloc(&q, count * sizeof(T), nullptr, false);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return caps::fail(CAPS_ENOMEM, "cudaMalloc failed for an index array");
+      return caps::fail(CAPS_ENOMEM, "device allocation failed for an index array");
     }
     allocs.push_back(q);
     bytes += (int64_t)(count * sizeof(T));

@@ -89,10 +89,11 @@ k_gemm(const float* __restrict__ A, int lda, const float* __restrict__ Bm, int l
   }
 }
 
-// Softmax cross-entropy per row (warp per row): dz and the loss (summed).
+// Softmax cross-entropy per row (warp per row): dz and the row's share of
+// the mean loss (summed over the rows afterwards in a fixed fp32 order).
 __global__ void k_softmax_xent(const float* __restrict__ Z, const float* __restrict__ Y, int n,
                                int B, float inv_n, float* __restrict__ dZ,
-                               double* __restrict__ loss) {
+                               float* __restrict__ row_loss) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
@@ -121,7 +122,7 @@ __global__ void k_softmax_xent(const float* __restrict__ Z, const float* __restr
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  if (lane == 0) atomicAdd(loss, (double)l * (double)inv_n);
+  if (lane == 0) row_loss[i] = l * inv_n;
 }
 
 // Column sums (bias gradients) in a fixed order: chunks of CS_ROWS rows, in
@@ -358,18 +359,20 @@ int mlp_assign(const MlpNet& net, const float* X, int64_t n, int32_t* bin, Scrat
 }
 
 int mlp_loss_grad(const MlpNet& net, const float* X, int64_t n, const float* Y, MlpNet* grad,
-                  double* loss_dev, Scratch& scr, cudaStream_t s) {
+                  float* loss_dev, Scratch& scr, cudaStream_t s) {
   if (n < 1 || n > INT_MAX) return fail(CAPS_EINVAL, "mlp: batch size out of range");
   const int d = net.d, H = net.H, B = net.B, nn = (int)n;
-  float *Hd = nullptr, *Z = nullptr, *dZ = nullptr, *dH = nullptr;
+  float *Hd = nullptr, *Z = nullptr, *dZ = nullptr, *dH = nullptr, *rl = nullptr;
+  if (int rc = scr.get(&rl, (size_t)n)) return rc;
   if (int rc = scr.get(&Hd, (size_t)n * H)) return rc;
   if (int rc = scr.get(&Z, (size_t)n * B)) return rc;
   if (int rc = scr.get(&dZ, (size_t)n * B)) return rc;
   if (int rc = scr.get(&dH, (size_t)n * H)) return rc;
   if (int rc = mlp_logits(net, X, n, Hd, Z, s)) return rc;
-  CAPS_CUDA(cudaMemsetAsync(loss_dev, 0, sizeof(double), s));
-  k_softmax_xent<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(Z, Y, nn, B, 1.f / (float)n, dZ, loss_dev);
+  k_softmax_xent<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(Z, Y, nn, B, 1.f / (float)n, dZ, rl);
   CAPS_LAUNCH("k_softmax_xent");
+  // the mean loss: the rows' shares summed in a fixed order (one column)
+  if (int rc = colsum(rl, nn, 1, loss_dev, scr, s)) return rc;
   // gW2 [B,H] = dZ^T [B,n] . Hd [n,H];  gb2 = column sums of dZ
   if (int rc = gemm<true, true, 0>(dZ, B, Hd, H, grad->W2, H, B, H, nn, nullptr, nullptr, 0, s))
     return rc;
@@ -408,7 +411,7 @@ int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs
   const int64_t total = P1 + net.H + P2 + net.B;
   Scratch scr(s);
   float *g = nullptr, *mo = nullptr, *ve = nullptr;
-  double* loss = nullptr;
+  float* loss = nullptr;
   if (int rc = scr.get(&g, (size_t)total)) return rc;
   if (int rc = scr.get(&mo, (size_t)total)) return rc;
   if (int rc = scr.get(&ve, (size_t)total)) return rc;
@@ -431,10 +434,9 @@ int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs
       t++;
       if (int rc = mlp_adam(w, g, mo, ve, total, lr, t, s)) return rc;
       if (losses_host) {
-        double lh = 0.0;
-        CAPS_CUDA(cudaMemcpyAsync(&lh, loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CAPS_CUDA(cudaMemcpyAsync(&losses_host[t - 1], loss, sizeof(float),
+                                  cudaMemcpyDeviceToHost, s));
         CAPS_CUDA(cudaStreamSynchronize(s));
-        losses_host[t - 1] = (float)lh;
       }
     }
   }

@@ -548,7 +548,14 @@ int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
   const int kcd = (p.d + 63) / 64;
   const int cols = p.pen ? (kcd + 1) * 64 : p.d;
   unsigned int* xmax = nullptr;
-  CAPS_CUDA(cudaMallocAsync(&xmax, sizeof(unsigned int), s));
+  {
+    void* q = nullptr;
+    if (dev_alloc(&q, sizeof(unsigned int), s, true) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CAPS_ENOMEM, "device allocation failed for the norm maximum");
+    }
+    xmax = static_cast<unsigned int*>(q);
+  }
   CAPS_CUDA(cudaMemsetAsync(xmax, 0, sizeof(unsigned int), s));
   const uint4 pm = make_uint4(p.pen_mask[0], p.pen_mask[1], p.pen_mask[2], p.pen_mask[3]);
   k_rows_bf16<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(

@@ -15,7 +15,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        for m in re.finditer(r"^\s*(?:int|void|const char\*)\s+(caps_\w+)\s*\(", src, re.M):
+        for m in re.finditer(r"^\s*(?:int|int64_t|void|const char\*)\s+(caps_\w+)\s*\(", src, re.M):
             names.add(m.group(1))
     return names
 

@@ -32,9 +32,9 @@ def caps():
     return c
 
 
-def _workload(B, nq):
+def _workload(B, nq, d=32):
     from workloads import make_dense_workload
-    return make_dense_workload(name="noalloc", N=30_000, d=32, ncomp=40, center=("normal", 2.0),
+    return make_dense_workload(name="noalloc", N=30_000, d=d, ncomp=40, center=("normal", 2.0),
                                sigma=1.0, vocab=[6, 10, 20], zipf_s=1.0, nq=nq, cmin=1, cmax=3,
                                B=B, h=7, iters=4, m=8, k=10, seed=123)
 
@@ -48,14 +48,42 @@ def test_noalloc_matches_search_batch_on_two_calls(caps, B, nq, k, m):
     Q = torch.from_numpy(w.Q).cuda()
     Qb = torch.from_numpy(w.Qb).cuda()
     ref_ids, ref_dist = ix.search(Q, Qb, k, m)
-    for _ in range(2):
+    for call in range(2):
         ids = torch.full((nq, k), -7, dtype=torch.int64, device="cuda")
         dist = torch.full((nq, k), -7.0, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        n0 = caps.alloc_count()
         ix.search_noalloc(Q, Qb, k, m, ids, dist)
         torch.cuda.synchronize()
+        # the property the entry point exists for: no device allocation
+        assert caps.alloc_count() == n0, f"call {call} allocated device memory"
         assert_search_equal(ids.cpu().numpy(), dist.cpu().numpy(), ref_ids.cpu().numpy(),
                             ref_dist.cpu().numpy(), X=w.X, Q=w.Q, A=w.A, Qb=w.Qb)
     ix.close()
+
+
+def test_noalloc_on_a_bf16_index_runs_the_exact_fp32_scan(caps):
+    # a BF16 index keeps its fp32 rows; the no-allocation call scans those,
+    # so it answers like caps_search_batch on an fp32 index of the same
+    # partitions (k-means does not depend on the scan precision)
+    nq, k, m = 400, 10, 6
+    w = _workload(32, nq, d=64)
+    X, A = torch.from_numpy(w.X).cuda(), torch.from_numpy(w.A).cuda()
+    ix16 = caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, init_idx=w.init_idx,
+                            prec=caps.BF16)
+    ix32 = caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, init_idx=w.init_idx)
+    Q = torch.from_numpy(w.Q).cuda()
+    Qb = torch.from_numpy(w.Qb).cuda()
+    ref_ids, ref_dist = ix32.search(Q, Qb, k, m)
+    for _ in range(2):
+        ids = torch.full((nq, k), -7, dtype=torch.int64, device="cuda")
+        dist = torch.full((nq, k), -7.0, dtype=torch.float32, device="cuda")
+        ix16.search_noalloc(Q, Qb, k, m, ids, dist)
+        torch.cuda.synchronize()
+        assert_search_equal(ids.cpu().numpy(), dist.cpu().numpy(), ref_ids.cpu().numpy(),
+                            ref_dist.cpu().numpy(), X=w.X, Q=w.Q, A=w.A, Qb=w.Qb)
+    ix16.close()
+    ix32.close()
 
 
 def test_noalloc_rejects_host_buffers(caps):
@@ -63,7 +91,14 @@ def test_noalloc_rejects_host_buffers(caps):
     ix = caps.Index.build(w.X, w.A, w.vocab, w.B, h=w.h, iters=2, init_idx=w.init_idx)
     ids = torch.empty((10, 5), dtype=torch.int64, device="cuda")
     dist = torch.empty((10, 5), dtype=torch.float32, device="cuda")
-    with pytest.raises(caps.CapsError) as e:
+    with pytest.raises(ValueError, match="CUDA"):
         ix.search_noalloc(torch.from_numpy(w.Q), torch.from_numpy(w.Qb), 5, 2, ids, dist)
-    assert e.value.code == caps.CAPS_EINVAL
+    # the library refuses host memory on its own as well (the C ABI's check)
+    from paper_2308_15014_gb300 import lib, _dense_attrs, _ptr
+    import ctypes as ct
+    Qh = np.ascontiguousarray(w.Q[:10])
+    at, keep = _dense_attrs(torch.from_numpy(w.Qb[:10]).cuda())
+    rc = lib().caps_search_batch_noalloc(ix._h, _ptr(Qh), 10, ct.byref(at), 5, 2, _ptr(ids),
+                                         _ptr(dist), None)
+    assert rc == caps.CAPS_EINVAL
     ix.close()
