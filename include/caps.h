@@ -209,10 +209,12 @@ void caps_free(caps_index* index);
 
 /* caps_device_status -- synchronise `stream` and report whether a bounded
  * device-side wait expired in an earlier search on this index (the kernel
- * then stops, sets a flag and returns instead of waiting forever; its
- * results are not valid).  Returns CAPS_ETIMEOUT once per such event (and
- * clears the flag), CAPS_OK otherwise.  caps_search_batch calls it itself
- * whenever it synchronises for host outputs. */
+ * then stops, sets a flag and returns instead of waiting forever; that
+ * search returns padding only: ids -1, distances +inf / -inf).  Returns
+ * CAPS_ETIMEOUT once per such event (and clears the flag), CAPS_OK
+ * otherwise; until it has been reported, tensor-core searches on the index
+ * also return padding.  caps_search_batch calls it itself whenever it
+ * synchronises for host outputs. */
 int caps_device_status(const caps_index* index, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -232,6 +234,18 @@ const char* caps_last_error(void);
  *   usable.  One failure per arming; n <= 0 disarms. */
 int64_t caps_alloc_count(void);
 void caps_inject_alloc_failure(int64_t n);
+
+/* caps_test_scan_stall -- test hook of the bounded device waits (failure
+ * detection; the paper has no counterpart).  item >= 0: every tensor-core
+ * scan launched afterwards by this process (caps_search_batch on a
+ * CAPS_BF16 or CAPS_FP8E4M3 index, and plans created afterwards) issues no
+ * copy and no MMA for its work item number `item` (items are handed out in
+ * order from 0), so the kernel's wait for that item's first tile cannot
+ * complete; every bounded wait then gives up after wait_ns nanoseconds
+ * (0: the default 1 s), the kernel stops with nothing in flight, and
+ * caps_device_status reports CAPS_ETIMEOUT.  item < 0 restores normal
+ * operation and the default limit.  Nothing faults, traps or hangs. */
+void caps_test_scan_stall(int64_t item, uint64_t wait_ns);
 
 /* ---- introspection and single steps (used to check each step alone) ---- */
 

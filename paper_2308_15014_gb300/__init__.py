@@ -31,7 +31,7 @@ EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "c
            "caps_set_timing", "caps_get_stage_times", "caps_search_batch_noalloc",
            "caps_device_status", "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign", "caps_plan_create",
            "caps_plan_search", "caps_plan_get_info", "caps_plan_free", "caps_alloc_count",
-           "caps_inject_alloc_failure")
+           "caps_inject_alloc_failure", "caps_test_scan_stall")
 
 
 class CapsError(RuntimeError):
@@ -120,6 +120,8 @@ def lib(path: Optional[str] = None):
     L.caps_alloc_count.restype = i64
     L.caps_inject_alloc_failure.argtypes = [i64]
     L.caps_inject_alloc_failure.restype = None
+    L.caps_test_scan_stall.argtypes = [i64, ct.c_uint64]
+    L.caps_test_scan_stall.restype = None
     _lib = L
     return L
 
@@ -456,6 +458,13 @@ def inject_alloc_failure(n: int):
     """caps_inject_alloc_failure: fail the n-th device allocation from now
     (1 = the next) as an out-of-memory device would; n <= 0 disarms."""
     lib().caps_inject_alloc_failure(int(n))
+
+
+def scan_stall_hook(item: int, wait_ns: int = 0):
+    """caps_test_scan_stall: later tensor-core scans withhold every copy and
+    MMA of work item `item` and give up each bounded wait after wait_ns
+    (item < 0: normal operation)."""
+    lib().caps_test_scan_stall(int(item), int(wait_ns))
 
 
 class Plan:

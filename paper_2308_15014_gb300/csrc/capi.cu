@@ -231,6 +231,10 @@ extern "C" void caps_inject_alloc_failure(int64_t n) {
   g_alloc_fail_at.store(n > 0 ? g_alloc_calls.load() + n : 0);
 }
 
+extern "C" void caps_test_scan_stall(int64_t item, uint64_t wait_ns) {
+  tc_set_stall((long long)item, (unsigned long long)wait_ns);
+}
+
 namespace caps {
 namespace {
 // Label of training point s: normalised histogram of the partitions of its
@@ -585,6 +589,7 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     tp.pen_bits = 0;
     for (int w = 0; w < 4; w++) tp.pen_mask[w] = 0u;
     tp.f8 = 1;
+    tp.metric = p->metric;
     tp.xs = ix->xs;
     tp.Xb = ix->Xb;
     tp.xn = ix->xn;
@@ -596,7 +601,8 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   if (p->prec == CAPS_BF16) {
     // bf16 form: bf16 rows + fp32 squared norms + inverse permutation
     // penalty form when the one-hot code of the packed attribute bits (two
-    // columns per bit) and of the blocks fits one 64-column chunk
+    // columns per bit) and, for L2, the three parts of -|x|^2/2 fit one
+    // 64-column chunk
     int T = 0;
     uint32_t um[4] = {};
     for (int f = 0; f < meta.L; f++) {
@@ -604,7 +610,7 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
       T += meta.bits[f];
     }
     // (label sets need the exact subset test per key: never the penalty form)
-    ix->pen = !meta.sparse && 2 * T + (h + 1) <= 64 ? 1 : 0;
+    ix->pen = !meta.sparse && tc_pen_columns(T, p->metric) <= 64 ? 1 : 0;
     ix->pen_bits = T;
     for (int w = 0; w < 4; w++) ix->pen_mask[w] = um[w];
     const int cols = ix->pen ? ((d + 63) / 64 + 1) * 64 : d;
@@ -627,6 +633,7 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     tp.pen_bits = T;
     for (int w = 0; w < 4; w++) tp.pen_mask[w] = um[w];
     tp.f8 = 0;
+    tp.metric = p->metric;
     tp.xs = nullptr;
     tp.Xb = ix->Xb;
     tp.xn = ix->xn;
@@ -1196,6 +1203,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
     if (tc) {
       BinWork w;
       if (int rc = tc_query_prep(Qc, n, ix->d, Qh, qn, f8, qs, s)) return rc;
+      const int rerank = tc_rerank_depth(k, ix->rerank_factor);
       if (int rc = tc_group(bt.probe, bt.sel, ix->h, n * m, ix->B, item_cap, &w, cscr, s))
         return rc;
       if (int rc = tm.record(s)) return rc;
@@ -1217,7 +1225,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
       t.h = ix->h;
       t.d = ix->d;
       t.kp = kp;
-      t.rerank = tc_rerank_depth(k, ix->rerank_factor);
+      t.rerank = rerank;
       t.tile_n = tile_n;
       t.pen = use_pen ? 1 : 0;
       t.pen_bits = ix->pen_bits;
@@ -1232,6 +1240,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
       t.metric = ix->metric;
       t.part = part;
       t.err = ix->err;
+      t.n_rows = ix->N;
       if (int rc = tc_scan(t, w, s)) return rc;
       if (int rc = tm.record(s)) return rc;
       if (int rc = tc_merge_rerank(t, bt.qp.dead, n, k, Qc, ix->Xp, ix->iperm, a.out_ids,

@@ -393,6 +393,7 @@ struct TcScanArgs {
   SparseRef sp;         // sparse label sets: exact check before a key is queued
   uint64_t* part;       // [nq*m*kp]
   int32_t* err;
+  int64_t n_rows = 0;   // rows of the index (ids are below it)
 };
 int tc_kp(int k);
 int tc_rerank_depth(int k, int factor);
@@ -400,6 +401,13 @@ bool tc_scan_supported(int d, int k, int kp, int words_pad, int f8 = 0);
 // whether the per-pair filter form with N-row tiles fits in shared memory
 bool tc_tile_fits(int d, int words_pad, int N, int f8);
 bool tc_pen_supported(int d, int kp, int words_pad);
+// columns of the penalty form's code chunk: two per encoded attribute bit,
+// and for L2 three for the row's -|x|^2/2 (the chunk holds 64)
+int tc_pen_columns(int pen_bits, int metric);
+// test hook of the bounded waits: later scans withhold every copy and MMA of
+// work item `item` and wait at most wait_ns at each bounded wait (item < 0:
+// normal operation, default limit)
+void tc_set_stall(long long item, unsigned long long wait_ns);
 // What the bf16 form of an index is made from, and where it goes.
 struct TcIndexPrep {
   const float* Xp;         // [N*d] rows in layout order
@@ -412,6 +420,7 @@ struct TcIndexPrep {
   int B, nb;
   int pen, pen_bits;       // code chunk for the penalty form
   uint32_t pen_mask[4];
+  int metric;              // CAPS_L2: the code chunk also carries -|x|^2/2
   int f8;                  // 1: e4m3 rows of ceil(d/128)*128 bytes + per-row scales
   float* xs;               // out (f8): [N] per-row scales
   void* Xb;                // out: [N*cols] bf16 rows, cols = d, or (ceil(d/64)+1)*64 with pen

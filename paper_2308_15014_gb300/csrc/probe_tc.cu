@@ -105,7 +105,7 @@ k_pgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
         int N, int Kt, float* __restrict__ D, int32_t* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
-      reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+      smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   __shared__ uint64_t full[PG_S], freeb[PG_S], done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_fail;
@@ -149,7 +149,7 @@ k_pgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
     for (int c = 0; c < nk && ok; c++) {
       const int s = c % PG_S;
       const uint32_t u = (uint32_t)(c / PG_S);
-      ok = mbar_wait(&full[s], u & 1, &s_fail);
+      ok = mbar_wait(&full[s], u & 1, &s_fail, kTcWaitNs);
       if (!ok) break;
       waited = c + 1;
       tc_fence_after();
@@ -160,7 +160,7 @@ k_pgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
                  (c > 0 || ks > 0) ? 1u : 0u);
       mma_commit(&freeb[s]);
       if (c + PG_S < nk) {
-        ok = mbar_wait(&freeb[s], u & 1, &s_fail);  // the stage is free again
+        ok = mbar_wait(&freeb[s], u & 1, &s_fail, kTcWaitNs);  // the stage is free again
         if (ok) issue(c + PG_S);
       }
     }
@@ -168,11 +168,11 @@ k_pgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
       s_fail = 1;
       atomicExch(err, 1);
       for (int c = waited; c < issued; c++)  // let the copies in flight land
-        mbar_wait(&full[c % PG_S], (uint32_t)((c / PG_S) & 1), nullptr);
+        mbar_wait(&full[c % PG_S], (uint32_t)((c / PG_S) & 1), nullptr, kTcWaitNs);
     }
     mma_commit(&done);  // arrives once every MMA issued so far has completed
   }
-  const bool ok = mbar_wait(&done, 0u, nullptr) && s_fail == 0;
+  const bool ok = mbar_wait(&done, 0u, nullptr, kTcWaitNs) && s_fail == 0;
   tc_fence_after();
   if (__all_sync(0xffffffffu, ok)) {
     const int row = m0 + 32 * warp + lane;
@@ -494,6 +494,30 @@ k_screen_topm(const float* __restrict__ Dt, int64_t nq, int B, int m, const floa
   for (int s2 = 0; s2 < 2; s2++) {
     const int Pp = 2 * lane + s2;
     if (Pp < need) out[ci + Pp] = (int32_t)(top.v[s2] & 0xffffffffu);
+  }
+  // (5) the set in the order of the approximate scores, best first (ties to
+  // the lower partition): only the order inside the row changes, so that the
+  // scan can take every query's nearest partitions first
+  __syncwarp();
+  uint64_t ord[2];
+#pragma unroll
+  for (int s2 = 0; s2 < 2; s2++) {
+    const int Pp = 2 * lane + s2;
+    ord[s2] = kEmptyKey;
+    if (Pp < m) {
+      const int b = out[Pp];
+      float sc, e;
+      Screen<MODE>::approx(dq[b], an2, an, wn2v[b], wnv[b], bias, b, sc, e);
+      if (!(sc == sc)) sc = -INFINITY;
+      ord[s2] = make_key(-sc, (uint32_t)b);
+    }
+  }
+  warp_sort<2>(ord, lane);
+  __syncwarp();
+#pragma unroll
+  for (int s2 = 0; s2 < 2; s2++) {
+    const int Pp = 2 * lane + s2;
+    if (Pp < m) out[Pp] = (int32_t)(ord[s2] & 0xffffffffu);
   }
 }
 

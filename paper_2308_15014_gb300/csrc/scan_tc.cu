@@ -5,6 +5,7 @@
 // re-rank of the best rerank_factor * k candidates (coordinates in order,
 // one fma each) before the final top-k.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstring>
 
@@ -129,7 +130,10 @@ struct TopKm {
 };
 
 // Merge each query's m lists of kp keys, re-score the kp best exactly in
-// fp32 (coordinates in order, one fma each) and keep the k best.  The scan's
+// fp32 (coordinates in order, one fma each) and keep the k best.  When the
+// scan stopped on an expired bounded wait (*err set) its lists are not all
+// written: every query then gets padding only (the call reports the
+// timeout), and no key is read.  The scan's
 // per-query bound T (the largest of the query's bound slots, once all are
 // set) has at least kp keys of the lists at or below it, so only those keys
 // compete: they are compacted and sorted in the warp (up to 128), else the
@@ -139,13 +143,20 @@ __global__ void __launch_bounds__(128)
 k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ dead, int64_t nq,
                int m, int lp, int kp, int k, const uint64_t* __restrict__ qslot, int nslot,
                const float* __restrict__ Q, int d, const float* __restrict__ Xp,
-               const int32_t* __restrict__ iperm, int64_t* __restrict__ out_ids,
-               float* __restrict__ out_dist) {
+               const int32_t* __restrict__ iperm, int64_t n_rows, int64_t* __restrict__ out_ids,
+               float* __restrict__ out_dist, const int32_t* __restrict__ err) {
   // [4][d] queries, [4][128] candidate keys
   extern __shared__ float qsm[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * 4 + wp;
   if (q >= nq) return;
+  if (err != nullptr && *reinterpret_cast<const volatile int32_t*>(err) != 0) {
+    for (int i = lane; i < k; i += 32) {
+      out_ids[q * k + i] = -1;
+      out_dist[q * k + i] = METRIC == CAPS_L2 ? INFINITY : -INFINITY;
+    }
+    return;
+  }
   float* qs = qsm + (size_t)wp * d;
   uint64_t* cbuf = reinterpret_cast<uint64_t*>(qsm + 4 * (size_t)d) + (size_t)wp * 128;
   for (int j = lane; j < d; j += 32) qs[j] = Q[q * d + j];
@@ -217,6 +228,9 @@ k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ de
     for (int h = 0; h < 2; h++) {
       const int c = lane + 32 * h;
       ck[h] = c < kp ? cbuf[c] : kEmptyKey;
+      // (an id outside the rows can only come from a list the scan did not
+      // finish; it is dropped, never dereferenced)
+      if (ck[h] != kEmptyKey && (int64_t)(uint32_t)(ck[h] & 0xffffffffu) >= n_rows) ck[h] = kEmptyKey;
       xr[h] = reinterpret_cast<const float4*>(Xp);
       if (ck[h] != kEmptyKey)
         xr[h] = reinterpret_cast<const float4*>(Xp + (int64_t)iperm[(uint32_t)(ck[h] & 0xffffffffu)] * d);
@@ -420,14 +434,14 @@ __global__ void k_tc_items_fill(const int32_t* __restrict__ bin_off,
 
 // ---- build-side helpers ----------------------------------------------------
 // bf16 copy of each row in `cols` columns (vector, zero padding, and in the
-// penalty form the 64-column one-hot code of the row's packed attribute bits
-// and of its block), its fp32 squared norm (coordinates in order, one fma
-// each) and the largest squared norm
+// penalty form the 64-column code chunk: a one-hot code of the row's packed
+// attribute bits, two columns per bit, then for L2 the row's -|x|^2/2 as
+// three bf16 parts that sum to it exactly), its fp32 squared norm
+// (coordinates in order, one fma each) and the largest squared norm
 __global__ void k_rows_bf16(const float* __restrict__ Xp, int64_t N, int d, int cols, int kcd,
                             const uint32_t* __restrict__ Ap, int WP, int pen, int pen_bits,
-                            uint4 pen_mask, const int32_t* __restrict__ offsets, int n_blocks,
-                            int nb, __nv_bfloat16* __restrict__ Xb, float* __restrict__ xn,
-                            unsigned int* __restrict__ xn_max_bits) {
+                            uint4 pen_mask, int pen_norm, __nv_bfloat16* __restrict__ Xb,
+                            float* __restrict__ xn, unsigned int* __restrict__ xn_max_bits) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   __nv_bfloat16* row = Xb + r * cols;
@@ -455,14 +469,19 @@ __global__ void k_rows_bf16(const float* __restrict__ Xp, int64_t N, int d, int 
       gb++;
     }
   }
-  // block of row r: the last offset <= r (offsets[n_blocks] = N)
-  int lo = 0, hi = n_blocks;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (offsets[mid] <= r) lo = mid;
-    else hi = mid;
+  if (pen_norm) {
+    // v = -|x|^2/2 = h1 + h2 + h3 exactly: h1 = bf16(v) leaves v - h1 with
+    // at most 16 significant bits (exact in fp32), h2 = bf16(v - h1) leaves at
+    // most 8, which bf16 holds exactly
+    const float v = -0.5f * acc;
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h1);
+    const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(h2);
+    code[2 * pen_bits + 0] = h1;
+    code[2 * pen_bits + 1] = h2;
+    code[2 * pen_bits + 2] = __float2bfloat16_rn(r2);
   }
-  code[2 * pen_bits + lo % nb] = one;
 }
 __global__ void k_inverse_perm(const int32_t* __restrict__ perm, int64_t N,
                                int32_t* __restrict__ iperm) {
@@ -513,6 +532,23 @@ bool tc_pen_supported(int d, int kp, int words_pad) {
   return tc_fits((d + 63) / 64 + 1, words_pad, 128, true);
 }
 
+int tc_pen_columns(int pen_bits, int metric) { return 2 * pen_bits + (metric == CAPS_L2 ? 3 : 0); }
+
+namespace {
+std::atomic<long long> g_tc_withhold{-1};
+std::atomic<unsigned long long> g_tc_wait_ns{kTcWaitNs};
+}  // namespace
+
+void tc_set_stall(long long item, unsigned long long wait_ns) {
+  if (item < 0) {
+    g_tc_withhold.store(-1);
+    g_tc_wait_ns.store(kTcWaitNs);
+  } else {
+    g_tc_withhold.store(item);
+    g_tc_wait_ns.store(wait_ns > 0 ? wait_ns : kTcWaitNs);
+  }
+}
+
 int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
   const int64_t N = p.N;
   if (p.f8) {
@@ -559,8 +595,8 @@ int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
   CAPS_CUDA(cudaMemsetAsync(xmax, 0, sizeof(unsigned int), s));
   const uint4 pm = make_uint4(p.pen_mask[0], p.pen_mask[1], p.pen_mask[2], p.pen_mask[3]);
   k_rows_bf16<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
-      p.Xp, N, p.d, cols, kcd, p.Ap, p.words_pad, p.pen, p.pen_bits, pm, p.offsets,
-      p.B * p.nb, p.nb, static_cast<__nv_bfloat16*>(p.Xb), p.xn, xmax);
+      p.Xp, N, p.d, cols, kcd, p.Ap, p.words_pad, p.pen, p.pen_bits, pm,
+      p.pen && p.metric == CAPS_L2 ? 1 : 0, static_cast<__nv_bfloat16*>(p.Xb), p.xn, xmax);
   cudaError_t le = cudaGetLastError();
   unsigned int xmax_h = 0;
   if (le == cudaSuccess) le = cudaMemcpyAsync(&xmax_h, xmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
@@ -702,6 +738,13 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   }
   a.part = t.part;
   a.err = t.err;
+  a.pen_ks = t.pen ? (tc_pen_columns(t.pen_bits, t.metric) + 15) / 16 : 0;
+  a.pen_norm = t.pen && t.metric == CAPS_L2 ? 1 : 0;
+  a.wait_ns = g_tc_wait_ns.load();
+  {
+    const long long w = g_tc_withhold.load();
+    a.withhold = w >= 0 && w < INT_MAX ? (int)w : -1;
+  }
   const CUtensorMap& map = *static_cast<const CUtensorMap*>(t.tmap);
   // persistent: one CTA per SM (the shared memory admits no second), never
   // more CTAs than work items
@@ -765,8 +808,8 @@ int tc_merge_rerank(const TcScanArgs& t, const uint8_t* dead, int64_t nq, int k,
     CAPS_CUDA(cudaFuncSetAttribute(k_merge_rerank<MET, 1>,                                      \
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
     k_merge_rerank<MET, 1><<<grid, 128, smem, s>>>(t.part, dead, nq, t.m, t.kp, depth, k,       \
-                                                   t.qslot, nslot, Q, t.d, Xp, iperm, out_ids,  \
-                                                   out_dist);                                   \
+                                                   t.qslot, nslot, Q, t.d, Xp, iperm, t.n_rows, \
+                                                   out_ids, out_dist, t.err);                   \
   } while (0)
   if (t.metric == CAPS_L2) CAPS_MR(CAPS_L2);
   else CAPS_MR(CAPS_IP);

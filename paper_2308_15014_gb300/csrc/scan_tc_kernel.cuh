@@ -24,17 +24,23 @@
 // insertion).  Each partition so contributes its KP best keys per probe
 // (KP >= k).
 //
-// Penalty form (PEN): every bf16 row carries one extra 64-column chunk, a
+// Penalty form (PEN): every bf16 row carries one extra 64-column chunk: a
 // one-hot code of its attribute bits (two columns per packed bit: "bit is
-// 0", "bit is 1") and of its block within the partition.  The A operand's
+// 0", "bit is 1") and, for L2, -|x|^2/2 split exactly into three bf16 parts
+// (h1 = bf16(v), h2 = bf16(v - h1), h3 = v - h1 - h2).  The A operand's
 // matching chunk holds -P in the columns of the bit values a probe's filter
-// rules out and of the blocks it did not select, 0 elsewhere.  A pair that
-// passes has only exact zero products there, so its dot product is the same
-// fp32 value as without the chunk; a pair that fails gets at least -P added.
-// With P = 2^e >= 4 (max_x |x|^2 + |q|^2) every failing pair scores at least
-// 1.49 P - |q|^2 >= 1.24 P (L2) or 0.87 P (IP) while every passing pair scores
-// below 0.51 P or 0.13 P, so the epilogue only compares the score against P
-// (L2) or P/2 (IP) and never reads attribute words or block ids.
+// rules out, 1 in the three norm columns, 0 elsewhere, so the accumulator of
+// a pair is acc = q.x - |x|^2/2 - (P for every ruled-out bit the row has).
+// A pair that passes has only exact zero products in the code columns, so
+// its acc is the same fp32 value as without them; the approximate score is
+// -2 acc = |x|^2 - 2 q.x (L2) or -acc = -q.x (IP), an exact scaling.  With
+// P = 2^e >= 4 (max_x |x|^2 + |q|^2) a passing pair has acc >= -P/4 and a
+// failing one acc <= -7P/8, so acc >= -P/2 is the whole filter.  The block
+// selection needs no columns: Alg. 2's selection never leaves out a row that
+// passes the filter, so a row of an unselected block never passes it.  The
+// epilogue so reads one fp32 value per pair and compares it with one floor
+// per probe (the list's bound turned into accumulator units, or the cut);
+// only the rare pairs above the floor become keys.
 #pragma once
 
 #include <cuda.h>
@@ -78,20 +84,25 @@ struct TcArgs {
   SparseRef sp;          // label sets: exact check before a key is queued
   uint64_t* part;        // [nq*m*kp]
   int32_t* err;
+  int pen_ks;            // penalty form: 16-column MMA steps of the code chunk (used columns)
+  int pen_norm;          // penalty form, L2: the chunk carries -|x|^2/2 after the bit columns
+  uint64_t wait_ns;      // limit of every bounded wait (ns)
+  int withhold;          // test hook: the producer issues no copy or MMA for this item (-1: none)
 };
 
 namespace {
 
 constexpr int TC_M = 128;     // probes per work item (MMA M, TMEM lanes)
 constexpr int TC_C = 512;     // epilogue threads: four per probe (one per quarter tile)
-constexpr int TC_T = TC_C + 32;  // + one producer warp (copies and MMAs)
+constexpr int TC_T = TC_C + 64;  // + a producer warp (copies and MMAs) and a prep warp
 constexpr int TC_PARTS = TC_C / TC_M;
 constexpr int TC_Q = 12;      // per-thread candidate queue (merged when > 4 wait)
 constexpr int TC_BOX = 128;   // rows per 2-D copy (the tensor map's box)
 constexpr int TC_COLS = 512;  // tensor-memory columns: TC_COLS / N accumulator stages
 constexpr int TC_PRODUCER = TC_C / 32;  // warp index of the producer
+constexpr int TC_PREP = TC_PRODUCER + 1;  // warp index of the prep warp (next item's data)
 constexpr int TC_SLOTS = 8;   // per-query bound slots (stride)
-constexpr uint64_t kTcWaitNs = 1000000000ull;
+constexpr uint64_t kTcWaitNs = 1000000000ull;  // default limit of a bounded wait
 // a waiting thread may sleep up to this long per try (it wakes when the
 // phase completes), so spinning warps leave the issue slots to working ones
 constexpr uint32_t kTcSuspendNs = 500;
@@ -108,8 +119,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
 }
 // Bounded wait for the completion of the barrier phase with the given parity.
-// Gives up after kTcWaitNs, or early once *fail is set (fail may be null).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* fail) {
+// Gives up after `limit` ns, or early once *fail is set (fail may be null).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* fail,
+                                          uint64_t limit) {
   const uint32_t a = su32(bar);
   const uint64_t t0 = gtimer();
   while (true) {
@@ -124,7 +136,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
       if (done) return true;
     }
     if (fail != nullptr && *fail) return false;
-    if (gtimer() - t0 > kTcWaitNs) return false;
+    if (gtimer() - t0 > limit) return false;
   }
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -220,6 +232,30 @@ __device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&v)[8])
         "=r"(v[7])
       : "r"(taddr));
 }
+// 16 accumulator columns of this warp's 32 lanes (issue only, as above).
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait16(uint32_t (&v)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+                 "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]),
+                 "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
+}
+// max of three floats in one instruction (a NaN operand is ignored)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
 // Completes the outstanding loads; v is tied in so that no use of it moves above.
 __device__ __forceinline__ void tmem_wait(uint32_t (&v)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
@@ -258,14 +294,17 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N, bool p
 
 template <int KP>
 __device__ __forceinline__ void net_insert(uint64_t (&L)[KP], uint64_t x) {
-  // sorted ascending; x moves down until it finds its place, the largest
-  // key falls off the end (an empty key changes nothing)
+  // sorted ascending; x goes to the first position whose key is not below
+  // it, the keys from there on move down by one and the largest falls off
+  // the end (an empty key changes nothing).  Every position is decided from
+  // its own and its predecessor's key alone, so the KP compares and selects
+  // are independent of one another (no chain through the list).
+  bool lt[KP];
 #pragma unroll
-  for (int i = 0; i < KP; i++) {
-    const uint64_t lo = L[i] < x ? L[i] : x;
-    x = L[i] < x ? x : L[i];
-    L[i] = lo;
-  }
+  for (int i = 0; i < KP; i++) lt[i] = L[i] < x;
+#pragma unroll
+  for (int i = KP - 1; i > 0; i--) L[i] = lt[i] ? L[i] : (lt[i - 1] ? x : L[i - 1]);
+  L[0] = lt[0] ? L[0] : x;
 }
 
 // L (ascending) becomes the KP smallest keys of L and the ascending list at
@@ -317,10 +356,11 @@ __device__ __forceinline__ void net_merge(uint64_t (&L)[KP], const uint64_t* oth
 //
 // Bound across a query's partitions: the rerank keeps the best R keys of the
 // query's m lists.  Each finished list offers its KP-th key to one of the
-// query's ns = ceil(R / KP) slots (slot = partition mod ns, atomic min).  Once
-// every slot holds a key, the largest of them, T, has at least ns * KP >= R
-// keys of distinct lists at or below it, so a later partition of that query
-// drops every key above T: such a key cannot be among the R best.
+// query's ns = ceil(R / KP) slots (slot = the probe's rank mod ns, atomic
+// min).  Once every slot holds a key, the largest of them, T, has at least
+// ns * KP >= R keys of distinct lists at or below it, so a later partition
+// of that query drops every key above T: such a key cannot be among the R
+// best.
 template <int METRIC, int WP, int KP, int N, bool PEN, bool F8>
 __global__ void __launch_bounds__(TC_T, 1)
 k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
@@ -335,8 +375,10 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   const int kc = a.kc, nb = a.h + 1;
   const int n_items = *a.n_items;
 
-  unsigned char* base =
-      reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // 1024-byte alignment by pointer arithmetic on the shared array itself, so
+  // that every pointer derived from it stays a shared-memory pointer (shared
+  // loads and stores, not generic ones)
+  unsigned char* base = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = base;
   unsigned char* sB0 = sA + tc_a_bytes(kc);
   const size_t bstride = tc_b_bytes(kc, N);
@@ -357,11 +399,11 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   static_assert(!(PEN && F8), "the penalty form is bf16 only");
 
   __shared__ uint64_t full_bar[SB], bfree_bar[SB], aux_bar[ST], mma_bar[ST], empty_bar[ST];
-  __shared__ uint64_t taken_bar, meta_bar, afull_bar;
+  __shared__ uint64_t taken_bar, meta_bar[2], afull_bar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_fail;
   // the current and the next item (index: item parity)
-  __shared__ int s_ne[2], s_ntiles[2], s_bin[2];
+  __shared__ int s_ne[2], s_ntiles[2], s_bin[2], s_item[2];
   __shared__ uint64_t p_thr[2][TC_M];
   // penalty form: the score bits of each quarter list's ceil(KP/4)-th and
   // ceil(KP/4) - 1-th keys (all ones until it has that many); the per-pair
@@ -375,9 +417,10 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   __shared__ float p_cut[TC_M];  // penalty form: scores at or above are masked pairs
   // producer only: tile schedule of its item
   __shared__ int s_tlo[ST], s_tn[ST];
-  __shared__ int run_lo[64], run_hi[64], run_j0[64];
-  __shared__ int n_runs;
-  __shared__ int32_t boff[65];
+  // the tile schedule (runs of selected blocks) of the current and the next item
+  __shared__ int run_lo[2][64], run_hi[2][64], run_j0[2][64];
+  __shared__ int n_runs[2];
+  __shared__ int32_t boff[2][65];
   __shared__ uint8_t s_pbit[32];  // penalty form: word * 32 + bit of the g-th encoded bit
 
   if (tid == 0) {
@@ -391,7 +434,8 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       mbar_init(&empty_bar[i], TC_C / 32);
     }
     mbar_init(&taken_bar, TC_C / 32);
-    mbar_init(&meta_bar, 1);
+    mbar_init(&meta_bar[0], 1);
+    mbar_init(&meta_bar[1], 1);
     mbar_init(&afull_bar, TC_C / 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int i = 0; i < (PEN ? TC_PARTS : 1) * TC_M; i++) (&s_qa[0][0])[i] = (&s_qb[0][0])[i] = ~0u;
@@ -414,18 +458,21 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
 
   // ---- producer: take the next item and prepare everything but A ----------
   // (fills s_ne/s_ntiles/s_bin/p_e/p_thr[par], the probe data, the runs)
-  TcItem pit;  // producer: the item it prepared last
   auto prep_meta = [&](int par) -> bool {
     int id = 0;
     if (lane == 0) id = atomicAdd(a.next_item, 1);
     id = __shfl_sync(0xffffffffu, id, 0);
     if (id >= n_items) {
-      if (lane == 0) s_ne[par] = -1;
+      if (lane == 0) {
+        s_ne[par] = -1;
+        s_item[par] = -1;
+      }
       return false;
     }
-    pit = a.items[id];
+    const TcItem pit = a.items[id];
     const int32_t* off = a.offsets + (int64_t)pit.b * nb;
-    for (int j = lane; j <= nb; j += 32) boff[j] = off[j];
+    int32_t* bo = boff[par];
+    for (int j = lane; j <= nb; j += 32) bo[j] = off[j];
     uint64_t U = 0ull;
 #pragma unroll
     for (int i = 0; i < TC_M / 32; i++) {
@@ -463,12 +510,14 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         p_qm[t * WP + w] = qm[w];
         p_qv[t * WP + w] = qv[w];
       }
-      float cut = 0.f;
+      // penalty form: P = 2^ex >= 4 (max |x|^2 + |q|^2); a pair passes the
+      // filter iff its accumulator is >= -P/2 (the cut; +inf: no probe)
+      float cut = INFINITY;
       if (PEN && t < pit.ne) {
         const float bound = 4.f * (a.xn_max + qn);
         int ex = (int)((__float_as_uint(bound) >> 23) & 0xffu) - 126;  // 2^ex >= bound
         ex = max(0, min(126, ex));
-        cut = __uint_as_float((uint32_t)(METRIC == CAPS_L2 ? ex + 127 : ex + 126) << 23);
+        cut = __uint_as_float(0x80000000u | ((uint32_t)(ex + 126) << 23));
       }
       p_cut[t] = cut;
     }
@@ -485,19 +534,20 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         }
         int j2 = j;
         while (j2 + 1 < nb && ((U >> (j2 + 1)) & 1ull)) j2++;
-        if (boff[j2 + 1] > boff[j]) {
-          run_lo[nr] = boff[j];
-          run_hi[nr] = boff[j2 + 1];
-          run_j0[nr] = j;
-          nt += (boff[j2 + 1] - boff[j] + N - 1) / N;
+        if (bo[j2 + 1] > bo[j]) {
+          run_lo[par][nr] = bo[j];
+          run_hi[par][nr] = bo[j2 + 1];
+          run_j0[par][nr] = j;
+          nt += (bo[j2 + 1] - bo[j] + N - 1) / N;
           nr++;
         }
         j = j2 + 1;
       }
-      n_runs = nr;
+      n_runs[par] = nr;
       s_ntiles[par] = nt;
       s_ne[par] = pit.ne;
       s_bin[par] = pit.b;
+      s_item[par] = id;
     }
     __syncwarp();
     return true;
@@ -506,8 +556,8 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   // row t = probe t's query, bf16, zero-padded to kcd*64 coordinates, 16-byte
   // unit u of chunk c stored at unit u ^ (t%8); four threads per row, one per
   // quarter of the units.  In the penalty form one more chunk: -P in the
-  // column of every attribute bit value the probe's filter rules out and of
-  // every block it does not select, 0 elsewhere.
+  // column of every attribute bit value the probe's filter rules out, 1 in
+  // the three columns of the rows' -|x|^2/2 parts (L2), 0 elsewhere.
   auto build_a = [&](int par) {
     const int t = tid & (TC_M - 1), qq = tid / TC_M;
     const int ne_n = s_ne[par];
@@ -527,30 +577,28 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     if (PEN) {
       // each of the row's four threads computes 16 of the chunk's columns
       uint16_t negP = 0;
-      uint64_t sel = 0ull;
       if (q >= 0) {
         const float bound = 4.f * (a.xn_max + p_qn[t]);
         int ex = (int)((__float_as_uint(bound) >> 23) & 0xffu) - 126;  // 2^ex >= bound
         ex = max(0, min(126, ex));
         negP = (uint16_t)(0x8000u | ((uint32_t)(ex + 127) << 7));
-        sel = p_sel[t];
       }
       const int nbit = 2 * a.pen_bits;
+      const int nnorm = a.pen_norm ? 3 : 0;
       uint32_t w32[8];
 #pragma unroll
       for (int h = 0; h < 16; h++) {
         const int c = 16 * qq + h;
-        bool masked = false;
+        uint32_t v = 0u;
         if (q >= 0) {
           if (c < nbit) {  // the column of the bit value the filter rules out
             const int pb = s_pbit[c >> 1], w = pb >> 5, i = pb & 31;
             const uint32_t qm = p_qm[t * WP + w], qv = p_qv[t * WP + w];
-            masked = ((qm >> i) & 1u) && (uint32_t)(c & 1) != ((qv >> i) & 1u);
-          } else if (c < nbit + nb) {  // a block the probe does not select
-            masked = !((sel >> (c - nbit)) & 1ull);
+            if (((qm >> i) & 1u) && (uint32_t)(c & 1) != ((qv >> i) & 1u)) v = (uint32_t)negP;
+          } else if (c < nbit + nnorm) {  // times the row's -|x|^2/2 parts
+            v = 0x3F80u;                  // bf16 1.0
           }
         }
-        const uint32_t v = masked ? (uint32_t)negP : 0u;
         if (h & 1) w32[h >> 1] |= v << 16;
         else w32[h >> 1] = v;
       }
@@ -563,18 +611,46 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
     fence_async_smem();  // generic stores of A before the MMAs read it
   };
 
-  if (warp == TC_PRODUCER) prep_meta(0);
+  if (warp == TC_PREP) prep_meta(0);
   __syncthreads();
-  if (warp != TC_PRODUCER && s_ne[0] >= 0) {
+  if (warp < TC_PRODUCER && s_ne[0] >= 0) {
     build_a(0);
     __syncwarp();
     if (lane == 0) mbar_arrive(&afull_bar);  // the producer may issue the item's MMAs
+  }
+  // ---- prep warp: item i + 1's data while item i runs ---------------------
+  // Once the epilogue has taken item i's probe data (which also means the
+  // producer is done with item i - 1's tile schedule), the next item's
+  // metadata, probe data and tile schedule go into the other buffer, and
+  // meta_bar[i % 2] completes.  Two barriers: the producer waits for item
+  // i's data only at item i's start, by which time item i + 1's data may
+  // already be complete too.
+  if (warp == TC_PREP) {
+    for (int i = 0; s_ne[i & 1] >= 0; i++) {
+      bool ok = s_fail == 0 && mbar_wait(&taken_bar, (uint32_t)(i & 1), &s_fail, a.wait_ns);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) s_fail = 1;
+        break;
+      }
+      prep_meta((i & 1) ^ 1);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&meta_bar[i & 1]);  // item i + 1's data is ready
+    }
   }
 
   int g0 = 0;           // tiles this CTA finished before the current item
   int par = 0, n_done = 0;
   int tma_hi = -1, mma_hi = -1;  // producer: last tile whose copies / MMAs were issued
-  while (true) {
+  while (warp <= TC_PRODUCER) {
+    if (warp == TC_PRODUCER && n_done > 0) {  // this item's data, from the prep warp
+      const int j = n_done - 1;
+      const bool ok = s_fail == 0 &&
+                      mbar_wait(&meta_bar[j & 1], (uint32_t)((j >> 1) & 1), &s_fail, a.wait_ns);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) s_fail = 1;
+        break;
+      }
+    }
     const int ne = s_ne[par];
     if (ne < 0 || s_fail) break;
     const int n_tiles = s_ntiles[par];
@@ -585,26 +661,31 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       // t + SB - 1 is issued, into the B stage of tile t - 1 (free once that
       // tile's MMAs are done) and the aux stage of tile t + SB - 1 - ST (free
       // once the epilogue has read it)
-      int rr = 0, rlo = n_runs > 0 ? run_lo[0] : 0;
+      const int* rl = run_lo[par];
+      const int* rh = run_hi[par];
+      const int* rj = run_j0[par];
+      const int32_t* bo = boff[par];
+      int rr = 0, rlo = n_runs[par] > 0 ? rl[0] : 0;
       bool ok = true;
       int tl = 0;  // next tile of this item to copy
       auto load = [&](int t) -> bool {  // warp-uniform
         const int g = g0 + t, sb = g % SB, st = g % ST;
-        while (rlo >= run_hi[rr]) {
+        while (rlo >= rh[rr]) {
           rr++;
-          rlo = run_lo[rr];
+          rlo = rl[rr];
         }
-        const int lo = rlo, n = min(N, run_hi[rr] - rlo), j0 = run_j0[rr];
+        const int lo = rlo, n = min(N, rh[rr] - rlo), j0 = rj[rr];
         rlo += n;
         bool k = true;
-        if (g >= SB) k = mbar_wait(&bfree_bar[sb], (uint32_t)((g / SB - 1) & 1), &s_fail);
-        if (k && g >= ST) k = mbar_wait(&empty_bar[st], (uint32_t)((g / ST - 1) & 1), &s_fail);
+        if (g >= SB) k = mbar_wait(&bfree_bar[sb], (uint32_t)((g / SB - 1) & 1), &s_fail, a.wait_ns);
+        if (k && g >= ST)
+          k = mbar_wait(&empty_bar[st], (uint32_t)((g / ST - 1) & 1), &s_fail, a.wait_ns);
         if (!__all_sync(0xffffffffu, k)) return false;
         if (!PEN) {
           uint8_t* blk = s_blk(st);
           for (int r = lane; r < n; r += 32) {
             int j = j0;
-            while (j + 1 < nb && boff[j + 1] <= lo + r) j++;
+            while (j + 1 < nb && bo[j + 1] <= lo + r) j++;
             blk[r] = (uint8_t)j;
           }
         }
@@ -624,28 +705,36 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
             for (int hb = 0; hb < N / TC_BOX; hb++)
               tma_2d(sB + (size_t)c * N * 128 + (size_t)hb * TC_BOX * 128, &tmX, 64 * c,
                      lo + hb * TC_BOX, &full_bar[sb]);
-          expect_tx(&aux_bar[st], ab + (F8 ? 3 : 2) * pb);
+          // ids (and, per-pair form, attribute words and norms; e4m3 scales):
+          // the penalty form needs only the ids
+          expect_tx(&aux_bar[st], ab + (PEN ? 1 : (F8 ? 3 : 2)) * pb);
           if (!PEN) bulk_copy(s_attr(st), a.Ap + (int64_t)alo * WP, ab, &aux_bar[st]);
           bulk_copy(s_perm(st), a.perm + alo, pb, &aux_bar[st]);
-          bulk_copy(s_xn(st), a.xn + alo, pb, &aux_bar[st]);
+          if (!PEN) bulk_copy(s_xn(st), a.xn + alo, pb, &aux_bar[st]);
           if (F8) bulk_copy(s_xs(st), a.xs + alo, pb, &aux_bar[st]);
           tma_hi = g;
         }
         return true;
       };
-      while (ok && tl < n_tiles && tl < SB - 1) ok = load(tl++);
-      for (int t = 0; ok && t < n_tiles; t++) {
-        if (tl < n_tiles) ok = load(tl++);
+      // test hook: a withheld item gets no copy and no MMA, so the epilogue's
+      // bounded wait for its first tile expires with nothing left in flight
+      const int n_issue = s_item[par] == a.withhold ? 0 : n_tiles;
+      // MMA steps per tile: four per vector chunk, and the used part of the
+      // penalty chunk
+      const int ksteps = PEN ? (kc - 1) * 4 + a.pen_ks : kc * 4;
+      while (ok && tl < n_issue && tl < SB - 1) ok = load(tl++);
+      for (int t = 0; ok && t < n_issue; t++) {
+        if (tl < n_issue) ok = load(tl++);
         if (!ok) break;
         const int g = g0 + t, sb = g % SB, st = g % ST;
         if (lane == 0) {
-          ok = mbar_wait(&full_bar[sb], (uint32_t)((g / SB) & 1), &s_fail);
+          ok = mbar_wait(&full_bar[sb], (uint32_t)((g / SB) & 1), &s_fail, a.wait_ns);
           // the item's first MMA waits for its A operand
-          if (ok && t == 0) ok = mbar_wait(&afull_bar, (uint32_t)(n_done & 1), &s_fail);
+          if (ok && t == 0) ok = mbar_wait(&afull_bar, (uint32_t)(n_done & 1), &s_fail, a.wait_ns);
           if (ok) {
             tc_fence_after();
             const uint32_t a0 = su32(sA), b0 = su32(sB0 + sb * bstride);
-            for (int ks = 0; ks < kc * 4; ks++) {
+            for (int ks = 0; ks < ksteps; ks++) {
               const int c = ks >> 2, kin = ks & 3;
               const uint64_t ad = sdesc(a0 + (uint32_t)(c * TC_M * 128 + kin * 32));
               const uint64_t bd = sdesc(b0 + (uint32_t)(c * N * 128 + kin * 32));
@@ -658,16 +747,6 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
           }
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
-      }
-      // prepare the next item's metadata while the epilogue finishes this
-      // one, once the epilogue has taken this item's probe data
-      if (ok) {
-        ok = mbar_wait(&taken_bar, (uint32_t)(n_done & 1), &s_fail);
-        ok = __all_sync(0xffffffffu, ok);
-      }
-      if (ok) {
-        prep_meta(par ^ 1);
-        if (lane == 0) mbar_arrive(&meta_bar);  // the epilogue may build the next A operand
       }
       if (!ok && lane == 0) s_fail = 1;
     } else {
@@ -695,11 +774,16 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       for (int i = 0; i < KP; i++) L[i] = kEmptyKey;
       uint64_t thr = kEmptyKey;
       int qcnt = 0;
-      auto flush = [&]() {  // warp-uniform call: as many rounds as the fullest queue
+      // Merge every queue into its lanes' lists (warp-uniform call: as many
+      // rounds as the fullest queue; the next round's key is loaded while the
+      // current one is inserted).
+      auto flush = [&]() {
         const int mx = __reduce_max_sync(0xffffffffu, (unsigned)qcnt);
+        uint64_t nx = qcnt > 0 ? queue[tid] : kEmptyKey;
 #pragma unroll 1
         for (int i = 0; i < mx; i++) {
-          const uint64_t x = i < qcnt ? queue[(size_t)i * TC_C + tid] : kEmptyKey;
+          const uint64_t x = nx;
+          nx = i + 1 < qcnt ? queue[(size_t)(i + 1) * TC_C + tid] : kEmptyKey;
           net_insert<KP>(L, x);
         }
         qcnt = 0;
@@ -751,15 +835,42 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       };
       const bool warp_live = __any_sync(0xffffffffu, active);
       const int cbeg = part * CPT;
+      // The next item's A operand, built as soon as every MMA of this item
+      // has completed (right after the wait for the last tile's accumulator;
+      // at once for an item without tiles), so that its MMAs run while this
+      // item's last tile and list merge are still in the epilogue.
+      auto next_a = [&]() {
+        const bool ok = s_fail == 0 && mbar_wait(&meta_bar[n_done & 1], (uint32_t)((n_done >> 1) & 1),
+                                                 &s_fail, a.wait_ns);
+        if (!__all_sync(0xffffffffu, ok)) {
+          s_fail = 1;
+          return;
+        }
+        if (s_ne[par ^ 1] >= 0) {
+          build_a(par ^ 1);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&afull_bar);  // the producer may issue the item's MMAs
+        }
+      };
+      // penalty form: the smallest accumulator value that can still enter
+      // this thread's list (the list's bound in accumulator units, never
+      // below the filter cut; +inf for a lane without a probe)
+      auto floor_of = [&](uint64_t tk) -> float {
+        if (tk == kEmptyKey) return my_cut;
+        const float ts = unord_bits((uint32_t)(tk >> 32));
+        return fmaxf(METRIC == CAPS_L2 ? -0.5f * ts : -ts, my_cut);
+      };
+      if (n_tiles == 0) next_a();
       for (int t = 0; t < n_tiles; t++) {
         const int g = g0 + t, b = g % ST, u = g / ST;
-        const bool ok = mbar_wait(&aux_bar[b], (uint32_t)(u & 1), &s_fail) &&
-                        mbar_wait(&mma_bar[b], (uint32_t)(u & 1), &s_fail);
+        const bool ok = mbar_wait(&aux_bar[b], (uint32_t)(u & 1), &s_fail, a.wait_ns) &&
+                        mbar_wait(&mma_bar[b], (uint32_t)(u & 1), &s_fail, a.wait_ns);
         if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform: the loads below are collective
           s_fail = 1;
           break;
         }
         tc_fence_after();
+        if (t == n_tiles - 1) next_a();  // every MMA of the item has completed
         const int lo = s_tlo[b], n = s_tn[b];
         const int alo = lo & ~3;
         const uint32_t* attr = s_attr(b) + (lo - alo) * WP;
@@ -769,7 +880,69 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         const uint8_t* blk = s_blk(b);
         const uint32_t tacc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * N + cbeg);
         const int ncol = warp_live ? min(CPT, n - cbeg) : 0;  // warp-uniform
-        const int ngr = ncol > 0 ? (ncol + 7) >> 3 : 0;
+        if constexpr (PEN) {
+          // the thread's 32 accumulators in two loads of 16; the largest of
+          // each 8 against the floor; only lanes with a value at or above it
+          // turn pairs into keys
+          static_assert(CPT == 32, "the penalty form uses 128-row tiles");
+          float fl;
+#pragma unroll 1
+          for (int h16 = 0; h16 < 2 && 16 * h16 < ncol; h16++) {  // warp-uniform bounds
+            // the probe's shared bound, fresh for every 16 columns
+            {
+              const uint64_t st = pthr[probe];
+              if (st < thr) thr = st;
+            }
+            fl = floor_of(thr);
+            uint32_t v[16];
+            tmem_ld16_issue(tacc + (uint32_t)(16 * h16), v);
+            tmem_wait16(v);
+            const int c0 = cbeg + 16 * h16, lim = ncol - 16 * h16;
+            if (lim < 16) {  // rows past the end of the tile's run
+#pragma unroll
+              for (int j = 0; j < 16; j++)
+                if (j >= lim) v[j] = 0xff800000u;  // -inf
+            }
+            const float mx = fmax3(fmax3(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2])),
+                                   fmax3(__uint_as_float(v[3]), __uint_as_float(v[4]), __uint_as_float(v[5])),
+                                   fmax3(__uint_as_float(v[6]), __uint_as_float(v[7]), __uint_as_float(v[8])));
+            const float my = fmax3(fmax3(__uint_as_float(v[9]), __uint_as_float(v[10]), __uint_as_float(v[11])),
+                                   fmax3(__uint_as_float(v[12]), __uint_as_float(v[13]), __uint_as_float(v[14])),
+                                   __uint_as_float(v[15]));
+            if (__any_sync(0xffffffffu, fmaxf(mx, my) >= fl)) {
+#pragma unroll
+              for (int hh = 0; hh < 2; hh++) {
+                // the lane's hot columns of this half as a bit mask; a half no
+                // lane needs is skipped by the whole warp.  Keys of a hot half
+                // are built for all 8 columns at once (the columns' ids are
+                // broadcast loads) and stored only where the lane's bit is
+                // set, at positions from a prefix count: no column waits for
+                // another.
+                uint32_t hm = 0u;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                  hm |= (__uint_as_float(v[8 * hh + j]) >= fl ? 1u : 0u) << j;
+                if (__any_sync(0xffffffffu, hm != 0u)) {
+#pragma unroll
+                  for (int j = 0; j < 8; j++) {
+                    const float acc = __uint_as_float(v[8 * hh + j]);
+                    const uint64_t key = make_key(METRIC == CAPS_L2 ? -2.f * acc : -acc,
+                                                  (uint32_t)prm[c0 + 8 * hh + j]);
+                    if ((hm >> j) & 1u)
+                      queue[(size_t)(qcnt + __popc(hm & ((1u << j) - 1u))) * TC_C + tid] = key;
+                  }
+                  qcnt += __popc(hm);
+                  // at most 8 more keys per lane before the next check
+                  if (__any_sync(0xffffffffu, qcnt > TC_Q - 8)) {
+                    flush();
+                    fl = floor_of(thr);
+                  }
+                }
+              }
+            }
+          }
+        }
+        const int ngr = (!PEN && ncol > 0) ? (ncol + 7) >> 3 : 0;
 #pragma unroll 1
         for (int gi = 0; gi < ngr; gi++) {
           uint32_t cur[8];
@@ -781,40 +954,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
             if (st < thr) thr = st;
           }
           const int lim = n - c0;  // rows of this group inside the tile
-          if (PEN) {
-            // the MMA already folded the block selection and the attribute
-            // filter in: a masked pair scores at least my_cut (the key of an
-            // empty list decodes to NaN, which fminf ignores)
-            // one bound: sc <= ts (the list's key) and sc < my_cut is sc <= tf
-            const float ts = unord_bits((uint32_t)(thr >> 32));
-            const float tf = ts < my_cut ? ts : __uint_as_float(__float_as_uint(my_cut) - 1u);
-            float xw[8];
-            if (((lo - alo + c0) & 3) == 0) {
-              const float4 x0 = *reinterpret_cast<const float4*>(xnr + c0);
-              const float4 x1 = *reinterpret_cast<const float4*>(xnr + c0 + 4);
-              xw[0] = x0.x; xw[1] = x0.y; xw[2] = x0.z; xw[3] = x0.w;
-              xw[4] = x1.x; xw[5] = x1.y; xw[6] = x1.z; xw[7] = x1.w;
-            } else {
-#pragma unroll
-              for (int j = 0; j < 8; j++) xw[j] = xnr[c0 + j];
-            }
-            auto pairs = [&](auto whole) {  // whole: all 8 rows inside the tile
-#pragma unroll
-              for (int j = 0; j < 8; j++) {
-                const float dot = __uint_as_float(cur[j]);
-                const float sc = METRIC == CAPS_L2 ? fmaf(-2.f, dot, xw[j]) : -dot;
-                if ((decltype(whole)::value || j < lim) && sc <= tf) {
-                  const uint64_t key = make_key(sc, (uint32_t)prm[c0 + j]);
-                  if (key < thr) {
-                    queue[(size_t)qcnt * TC_C + tid] = key;
-                    qcnt++;
-                  }
-                }
-              }
-            };
-            if (lim >= 8) pairs(std::true_type{});
-            else pairs(std::false_type{});
-          } else {
+          {
             // the 8 rows' block ids and attribute words in few wide loads
             // (the same addresses for every lane: broadcast)
             const uint2 bw = *reinterpret_cast<const uint2*>(blk + c0);
@@ -897,41 +1037,39 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         uint64_t* dst = a.part + (int64_t)e * KP;
 #pragma unroll
         for (int i = 0; i < KP; i++) dst[i] = L[i];
-        // offer the list's KP-th key to the query's bound
+        // offer the list's KP-th key to the query's bound (slot = the probe's
+        // rank mod the slot count: distinct lists per slot)
         if (L[KP - 1] != kEmptyKey)
           atomicMin(reinterpret_cast<unsigned long long*>(
-                        a.qslot + (int64_t)(e / a.m) * TC_SLOTS + s_bin[par] % a.nslot),
+                        a.qslot + (int64_t)(e / a.m) * TC_SLOTS + (e % a.m) % a.nslot),
                     (unsigned long long)L[KP - 1]);
       }
       if (PEN) s_qa[part][probe] = s_qb[part][probe] = ~0u;  // read again only after the barrier below
-      // the next item's A operand: every MMA of this item has completed (each
-      // tile's accumulator was waited for), so A may be overwritten once the
-      // producer has the next item's probe data
-      fine = s_fail == 0;
-      const bool meta = fine && mbar_wait(&meta_bar, (uint32_t)(n_done & 1), &s_fail);
-      if (fine && !meta) s_fail = 1;
-      if (consumers_all(meta) && s_ne[par ^ 1] >= 0) {
-        build_a(par ^ 1);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&afull_bar);
-      }
+      // (the next item's A operand was built at its last tile) every thread
+      // is done with this item's lists and quarter bounds before any starts
+      // the next item's queue writes and flushes
+      consumers_sync();
     }
     g0 += n_tiles;
     n_done++;
     par ^= 1;
   }
 
+  // every thread is out of the item loop before the failure flag is read:
+  // a producer that ran out of items may leave the loop before a wait of
+  // the epilogue expires
+  __syncthreads();
   if (s_fail) {
     // a copy or an MMA did not complete in time: flag it, let what is in
     // flight land (bounded waits), release tensor memory and leave
     if (warp == TC_PRODUCER && lane == 0) {
       atomicExch(a.err, 1);
       for (int g = max(0, tma_hi - SB + 1); g <= tma_hi; g++)
-        mbar_wait(&full_bar[g % SB], (uint32_t)((g / SB) & 1), nullptr);
+        mbar_wait(&full_bar[g % SB], (uint32_t)((g / SB) & 1), nullptr, a.wait_ns);
       for (int g = max(0, tma_hi - ST + 1); g <= tma_hi; g++)
-        mbar_wait(&aux_bar[g % ST], (uint32_t)((g / ST) & 1), nullptr);
+        mbar_wait(&aux_bar[g % ST], (uint32_t)((g / ST) & 1), nullptr, a.wait_ns);
       for (int g = max(0, mma_hi - ST + 1); g <= mma_hi; g++)
-        mbar_wait(&mma_bar[g % ST], (uint32_t)((g / ST) & 1), nullptr);
+        mbar_wait(&mma_bar[g % ST], (uint32_t)((g / ST) & 1), nullptr, a.wait_ns);
     }
   }
   tc_fence_before();

@@ -103,3 +103,42 @@ def test_alloc_count_moves_with_allocations():
     ix = _build(w, 0)
     assert caps.alloc_count() > n0
     ix.close()
+
+
+@pytest.mark.parametrize("pen_bits_fit", [True, False])
+def test_scan_bounded_wait_expires_then_exact(pen_bits_fit):
+    """A wait that nothing completes: the tensor-core scan's producer is told
+    (test hook) to issue no copy and no MMA for work item 0, so the
+    epilogue's bounded wait for that item's first tile runs out (2 ms here);
+    the kernel stops with nothing in flight and the search reports
+    CAPS_ETIMEOUT.  The next search on the same index answers exactly.
+    Queries without constraints select every block, so item 0 has tiles.
+    pen_bits_fit False: 7 fields of vocab 100 (49 packed bits) leave no room
+    for the penalty chunk, so the per-pair filter form of the scan runs."""
+    vocab = [4, 8, 16] if pen_bits_fit else [100] * 7
+    w = make_dense_workload(name="stall", N=6000, d=64, ncomp=10, center=("uniform", 128.0),
+                            sigma=16.0, vocab=vocab, zipf_s=1.0, nq=200, cmin=1, cmax=3,
+                            B=16, h=7, iters=3, m=4, k=10, seed=405, integer=True)
+    ix = _build(w, caps.BF16)
+    Q = torch.from_numpy(w.Q).cuda()
+    free = np.full_like(w.Qb, -1)
+    Qb = torch.from_numpy(free).cuda()
+    oi = O.build(w.X, O.Attrs.of(w), w.B, w.h, 0, w.init_idx, C=ix.export(caps.ARR_CENTROIDS))
+    oids, odist, _, _ = O.search(w.X, O.Attrs.of(w), oi, w.Q, O.Cons(Qb=free), w.k, w.m)
+    ids = torch.empty((w.nq, w.k), dtype=torch.int64, device="cuda")
+    dist = torch.empty((w.nq, w.k), dtype=torch.float32, device="cuda")
+    caps.scan_stall_hook(0, 2_000_000)
+    try:
+        ix.search(Q, Qb, w.k, w.m, out_ids=ids, out_dist=dist)  # device outputs: enqueued only
+        with pytest.raises(caps.CapsError) as e:
+            ix.status()
+        assert e.value.code == caps.CAPS_ETIMEOUT
+    finally:
+        caps.scan_stall_hook(-1)
+    ix.status()  # reported once, then clear
+    for _ in range(2):
+        ix.search(Q, Qb, w.k, w.m, out_ids=ids, out_dist=dist)
+        ix.status()
+        np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+        np.testing.assert_array_equal(dist.cpu().numpy(), odist)
+    ix.close()
