@@ -15,6 +15,7 @@ Function map (paper passage -> function):
   Alg. 2 top-m probe ................ probe
   Alg. 2 sub-partition selection .... select
   Alg. 2 full query ................. search
+  Sec. 5.3 OR constraints ........... OrCons, select_or, search_or
   Def. 2 / appendix ground truth .... bruteforce
   appendix RecallK@K ................ recall
   Sec. 5.2 learned partitioner ...... mlp_forward64, mlp_loss_grad, adam,
@@ -59,6 +60,9 @@ def lib():
                                     P, i32, P, P, P, i64, P, P, P, i32, i32, P, P, P, P, P]
         _lib.orc_bruteforce.argtypes = [P, i64, i32, i32, P, P, P, P, ct.c_int32, P, i64,
                                         P, P, P, i32, i32, i32, P, P, P, P]
+        _lib.orc_select_or.argtypes = [P, i32, i32, P, P, i64, i32, P, P, P]
+        _lib.orc_search_or.argtypes = [P, i64, i32, i32, P, P, P, i32, i32, P, i32, P, P, P, i64,
+                                       P, P, i32, i32, P, P, P]
         _lib.orc_set_threads.argtypes = [i32]
         _lib.orc_set_threads.restype = i32
         _lib.orc_mlp_forward64.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P, P]
@@ -294,6 +298,61 @@ def search(X, attrs: Attrs, index: Index, Q, cons: Cons, k, m, probe_in=None):
                      *cons.args(), k, m, _p(ids), _p(dist), _p(n_scan), _p(n_match),
                      _p(_c(probe_in, np.int32)))
     return ids, dist, n_scan, n_match
+
+
+# ---- Sec. 5.3: disjunctive constraints ---------------------------------------
+
+@dataclasses.dataclass
+class OrCons:
+    """Per-(query, field) allowed values: field f of query q allows
+    ``vals[voff[q*L+f]:voff[q*L+f+1]]``; an empty list leaves it free."""
+    voff: np.ndarray
+    vals: np.ndarray
+
+    def __post_init__(self):
+        self.voff = _c(self.voff, np.int64)
+        self.vals = _c(self.vals, np.int32)
+
+    @staticmethod
+    def of_lists(lists):
+        """lists[q][f] = list of allowed values (empty = free)."""
+        L = len(lists[0]) if len(lists) else 0
+        voff = [0]
+        vals = []
+        for row in lists:
+            assert len(row) == L
+            for f in range(L):
+                vals.extend(int(v) for v in row[f])
+                voff.append(len(vals))
+        return OrCons(np.asarray(voff, np.int64), np.asarray(vals, np.int32))
+
+
+def select_or(tags, h, attrs: Attrs, probe_bins, oc: OrCons) -> np.ndarray:
+    """Blocks scanned per (query, probed partition) under OR constraints: the
+    union of Alg. 2's selections over the cross product of the lists."""
+    tags = _c(tags, np.int32)
+    probe_bins = _c(probe_bins, np.int32)
+    nq, m = probe_bins.shape
+    out = np.empty((nq, m), dtype=np.uint64)
+    lib().orc_select_or(_p(tags), h, attrs.L, _p(attrs.vocab), _p(probe_bins), nq, m,
+                        _p(oc.voff), _p(oc.vals), _p(out))
+    return out
+
+
+def search_or(X, attrs: Attrs, index: Index, Q, oc: OrCons, k, m, probe_in=None):
+    """Alg. 2 with OR constraints (dense attributes): ids [nq,k], fp32
+    distances [nq,k]."""
+    X = _c(X, np.float32)
+    Q = _c(Q, np.float32)
+    nq = Q.shape[0]
+    ids = np.empty((nq, k), dtype=np.int64)
+    dist = np.empty((nq, k), dtype=np.float32)
+    lib().orc_search_or(_p(X), X.shape[0], X.shape[1], attrs.L, _p(attrs.A), _p(attrs.vocab),
+                        _p(_c(index.C, np.float32)), index.B, index.metric,
+                        _p(_c(index.tags, np.int32)), index.h, _p(_c(index.perm, np.int32)),
+                        _p(_c(index.offsets, np.int32)), _p(Q), nq, _p(oc.voff), _p(oc.vals), k,
+                        m, _p(ids), _p(dist), _p(_c(probe_in, np.int32)))
+    return ids, dist
 
 
 def bruteforce(X, attrs: Attrs, Q, cons: Cons, k, metric=L2, order64=True):

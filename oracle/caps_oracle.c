@@ -498,6 +498,115 @@ void orc_search(const float* X, int64_t N, int d, int L, const int32_t* A,
   }
 }
 
+/* ---- disjunctive (OR) constraints (Sec. 5.3: several constraints map to
+ * several sub-partitions) ---------------------------------------------------
+ * Field f of query q allows the values vals[voff[q*L+f] .. voff[q*L+f+1]);
+ * an empty list leaves the field unconstrained.  The filter holds when every
+ * constrained field's value is in its list.  In a probed partition the
+ * blocks scanned are the union, over every single-valued query of the cross
+ * product of the lists, of the blocks Alg. 2 selects for it.  Dense
+ * attributes only. */
+static int filter_or(const int32_t* arow, int L, const int64_t* voff, const int32_t* vals,
+                     int64_t q) {
+  for (int f = 0; f < L; f++) {
+    const int64_t b = voff[q * L + f], e = voff[q * L + f + 1];
+    if (b == e) continue;
+    int hit = 0;
+    for (int64_t u = b; u < e; u++)
+      if (vals[u] >= 0 && vals[u] == arow[f]) hit = 1;
+    if (!hit) return 0;
+  }
+  return 1;
+}
+
+/* Union of Alg. 2's block selections over the cross product of the lists:
+ * a mixed-radix count over the constrained fields walks every single-valued
+ * query once. */
+static uint64_t select_blocks_or(const attrs_t* a, const int32_t* tags, int h, int32_t b_bin,
+                                 int L, const int64_t* voff, const int32_t* vals, int64_t q) {
+  int32_t b[64];
+  int64_t pos[64];
+  for (int f = 0; f < L; f++) {
+    pos[f] = voff[q * L + f];
+    b[f] = pos[f] < voff[q * L + f + 1] ? vals[pos[f]] : -1;
+  }
+  uint64_t sel = 0;
+  for (;;) {
+    sel |= select_blocks(a, tags, h, b_bin, b, NULL, 0);
+    int f = 0;
+    for (; f < L; f++) {
+      const int64_t e = voff[q * L + f + 1];
+      if (voff[q * L + f] == e) continue;
+      if (++pos[f] < e) {
+        b[f] = vals[pos[f]];
+        break;
+      }
+      pos[f] = voff[q * L + f];
+      b[f] = vals[pos[f]];
+    }
+    if (f == L) break;
+  }
+  return sel;
+}
+
+void orc_select_or(const int32_t* tags, int h, int L, const int32_t* vocab,
+                   const int32_t* probe, int64_t nq, int m, const int64_t* voff,
+                   const int32_t* vals, uint64_t* sel) {
+  attrs_t a = mk_attrs(L, vocab /* non-NULL marks dense */, vocab, NULL, NULL, 0);
+  for (int64_t q = 0; q < nq; q++)
+    for (int r = 0; r < m; r++)
+      sel[q * m + r] = select_blocks_or(&a, tags, h, probe[q * m + r], L, voff, vals, q);
+}
+
+/* Alg. 2 with disjunctive constraints: probe (the m nearest centroids, or
+ * probe_in), the union block selection above, the OR filter, distances and
+ * the exact top-k (ties to the lower id). */
+void orc_search_or(const float* X, int64_t N, int d, int L, const int32_t* A,
+                   const int32_t* vocab, const float* C, int B, int metric,
+                   const int32_t* tags, int h, const int32_t* perm, const int32_t* offsets,
+                   const float* Q, int64_t nq, const int64_t* voff, const int32_t* vals, int k,
+                   int m, int64_t* out_ids, float* out_dist, const int32_t* probe_in) {
+  attrs_t a = mk_attrs(L, A, vocab, NULL, NULL, 0);
+  (void)N;
+#pragma omp parallel
+  {
+    int32_t* probe = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+    int64_t cap = 1024;
+    cand_t* cand = (cand_t*)malloc(sizeof(cand_t) * (size_t)cap);
+    g_metric_cmp = metric;
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nq; q++) {
+      if (probe_in) memcpy(probe, probe_in + q * m, sizeof(int32_t) * (size_t)m);
+      else orc_probe(Q + q * d, 1, d, C, B, metric, m, probe);
+      int64_t nc = 0;
+      for (int r = 0; r < m; r++) {
+        const int32_t bn = probe[r];
+        const uint64_t sel = select_blocks_or(&a, tags, h, bn, L, voff, vals, q);
+        for (int j = 1; j <= h + 1; j++) {
+          if (!((sel >> (j - 1)) & 1)) continue;
+          const int64_t s = (int64_t)bn * (h + 1) + (j - 1);
+          for (int64_t row = offsets[s]; row < offsets[s + 1]; row++) {
+            const int64_t i = perm[row];
+            if (!filter_or(A + i * L, L, voff, vals, q)) continue;
+            if (nc == cap) {
+              cap *= 2;
+              cand = (cand_t*)realloc(cand, sizeof(cand_t) * (size_t)cap);
+            }
+            cand[nc].s32 = orc_dist32(X + i * d, Q + q * d, d, metric);
+            cand[nc].s = cand[nc].s32;
+            cand[nc].s64 = orc_dist64(X + i * d, Q + q * d, d, metric);
+            cand[nc].i = i;
+            nc++;
+          }
+        }
+      }
+      emit_topk(cand, nc, k, metric, out_ids + q * k, out_dist ? out_dist + q * k : NULL, NULL);
+    }
+    free(cand);
+    free(probe);
+  }
+}
+
 /* Exact filtered kNN (Def. 2; ground truth): filter every point, rank by the
  * fp64 distance (order64 = 1) or by the canonical fp32 one (order64 = 0). */
 void orc_bruteforce(const float* X, int64_t N, int d, int L, const int32_t* A,
