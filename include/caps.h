@@ -355,6 +355,38 @@ int caps_mlp_train(int32_t d, int32_t H, int32_t B, float* W, const float* X,
 int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W,
                     const float* X, int64_t n, int32_t* out_bin, void* stream);
 
+/* ---- disjunctive (OR) constraints (Sec. 5.3) ------------------------------- */
+
+/*
+ * Per-(query, field) lists of allowed values: field f of query i allows
+ * values[offsets[i*L+f] .. offsets[i*L+f+1]) (int32 >= 0; a value outside
+ * [0, vocab[f]) matches no point); an empty list leaves the field
+ * unconstrained.  offsets = [nq*L+1] int64, offsets[0] = 0, non-decreasing.
+ */
+typedef struct {
+  int32_t L;
+  const int64_t* offsets;
+  const int32_t* values;
+} caps_or_constraints;
+
+/*
+ * caps_search_batch_or -- Alg. 2 with disjunctive constraints.  The paper
+ * maps several constraints to several sub-partitions (Sec. 5.3); here a
+ * point passes when every constrained field's value is in its list, and in
+ * each of the m probed partitions the blocks scanned are the union of the
+ * blocks Alg. 2 selects for every single-valued query of the cross product
+ * of the lists.  The library expands each query into those single-valued
+ * queries (at most 256 per query, CAPS_EINVAL beyond), answers them as one
+ * batch of caps_search_batch, and keeps each query's k best results by
+ * (distance, id); the single-valued queries' valid sets are disjoint, so
+ * this is the k best of the union.  Arguments as in caps_search_batch
+ * (dense attribute indexes only); the value lists are read on the host, so
+ * the call synchronises `stream` and returns with the outputs complete.
+ */
+int caps_search_batch_or(const caps_index* index, const float* Q, int64_t nq,
+                         const caps_or_constraints* constraints, int32_t k, int32_t m,
+                         int64_t* out_ids, float* out_dist, void* stream);
+
 /* ---- batched query without device allocation ------------------------------ */
 
 /*

@@ -12,6 +12,7 @@ Function map (paper passage -> function):
   Alg. 1 first level (k-means) ...... kmeans, assign, centroid_update
   Alg. 1 second level (AFT) ......... aft
   contiguous sub-partition layout ... layout
+  dynamic insertion (Table 1) ....... block_of, insert
   Alg. 2 top-m probe ................ probe
   Alg. 2 sub-partition selection .... select
   Alg. 2 full query ................. search
@@ -60,6 +61,7 @@ def lib():
                                     P, i32, P, P, P, i64, P, P, P, i32, i32, P, P, P, P, P]
         _lib.orc_bruteforce.argtypes = [P, i64, i32, i32, P, P, P, P, ct.c_int32, P, i64,
                                         P, P, P, i32, i32, i32, P, P, P, P]
+        _lib.orc_block_of.argtypes = [P, i32, i32, P, P, P, P, ct.c_int32, P, i64, P]
         _lib.orc_select_or.argtypes = [P, i32, i32, P, P, i64, i32, P, P, P]
         _lib.orc_search_or.argtypes = [P, i64, i32, i32, P, P, P, i32, i32, P, i32, P, P, P, i64,
                                        P, P, i32, i32, P, P, P]
@@ -214,6 +216,37 @@ def aft(bin, B, h, attrs: Attrs):
     key = np.zeros(N, dtype=np.uint8)
     lib().orc_aft(_p(bin), N, B, h, *attrs.args(), _p(tags), _p(key))
     return tags, key
+
+
+def block_of(tags, h, attrs: Attrs, bins):
+    """Block (1..h+1) of each point of `attrs` in its partition bins[i] under
+    the fixed tags: the first block whose tag it carries, else h+1 (the
+    insertion rule; for the built points it is the tree's own key)."""
+    tags = _c(tags, np.int32)
+    bins = _c(bins, np.int32)
+    key = np.empty(len(bins), np.uint8)
+    lib().orc_block_of(_p(tags), h, *attrs.args(), _p(bins), len(bins), _p(key))
+    return key
+
+
+def insert(index: Index, X_all, attrs_all: Attrs, n_new, metric=L2, bins_new=None) -> Index:
+    """The index after inserting the last n_new points of X_all / attrs_all:
+    their partitions f(x) (nearest centroid, or the given bins_new from a
+    learned f), their blocks under the unchanged tags, and the layout by
+    (partition, block, id) of all points.  Centroids and tags stay."""
+    X_all = _c(X_all, np.float32)
+    N = X_all.shape[0]
+    n0 = N - n_new
+    if bins_new is None:
+        bins_new = assign(X_all[n0:], index.C, metric)
+    bin_all = np.concatenate([np.asarray(index.bin, np.int32), np.asarray(bins_new, np.int32)])
+    sub = Attrs(A=attrs_all.A[n0:], vocab=attrs_all.vocab) if attrs_all.A is not None else None
+    assert sub is not None, "insertion serves dense attributes"
+    key_new = block_of(index.tags, index.h, sub, bins_new)
+    key_all = np.concatenate([np.asarray(index.key, np.uint8), key_new])
+    perm, offsets = layout(bin_all, key_all, index.B, index.h)
+    return Index(C=index.C, bin=bin_all, tags=index.tags, key=key_all, perm=perm,
+                 offsets=offsets, B=index.B, h=index.h, metric=index.metric)
 
 
 def layout(bin, key, B, h):

@@ -498,6 +498,29 @@ void orc_search(const float* X, int64_t N, int d, int L, const int32_t* A,
   }
 }
 
+/* ---- dynamic insertion (Table 1 claims it; the mechanism is not given) ----
+ * A new point x goes to partition f(x) and, inside it, to the first block j
+ * (1..h) whose tag t_j it carries, else to the remainder block h+1: the block
+ * the attribute-frequency peel of Alg. 1 gives a point, with the partition's
+ * tags kept as they are.  key[i] = that block for point i of bins[i]. */
+void orc_block_of(const int32_t* tags, int h, int L, const int32_t* A, const int32_t* vocab,
+                  const int64_t* sp_off, const int32_t* sp_lab, int32_t sp_vocab,
+                  const int32_t* bins, int64_t n, uint8_t* key) {
+  attrs_t a = mk_attrs(L, A, vocab, sp_off, sp_lab, sp_vocab);
+  for (int64_t i = 0; i < n; i++) {
+    const int32_t* t = tags + (int64_t)bins[i] * h;
+    int j = 1;
+    for (; j <= h; j++) {
+      if (t[j - 1] < 0) {
+        j = h + 1;
+        break;
+      }
+      if (carries(&a, i, t[j - 1])) break;
+    }
+    key[i] = (uint8_t)j;
+  }
+}
+
 /* ---- disjunctive (OR) constraints (Sec. 5.3: several constraints map to
  * several sub-partitions) ---------------------------------------------------
  * Field f of query q allows the values vals[voff[q*L+f] .. voff[q*L+f+1]);

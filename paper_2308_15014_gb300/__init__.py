@@ -31,7 +31,7 @@ EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "c
            "caps_set_timing", "caps_get_stage_times", "caps_search_batch_noalloc",
            "caps_device_status", "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign", "caps_plan_create",
            "caps_plan_search", "caps_plan_get_info", "caps_plan_free", "caps_alloc_count",
-           "caps_inject_alloc_failure", "caps_test_scan_stall")
+           "caps_inject_alloc_failure", "caps_test_scan_stall", "caps_search_batch_or")
 
 
 class CapsError(RuntimeError):
@@ -43,6 +43,10 @@ class CapsError(RuntimeError):
 class caps_attrs(ct.Structure):
     _fields_ = [("L", ct.c_int32), ("dense", ct.c_void_p), ("vocab", ct.c_void_p),
                 ("sp_offsets", ct.c_void_p), ("sp_labels", ct.c_void_p), ("sp_vocab", ct.c_int32)]
+
+
+class caps_or_constraints(ct.Structure):
+    _fields_ = [("L", ct.c_int32), ("offsets", ct.c_void_p), ("values", ct.c_void_p)]
 
 
 class caps_build_params(ct.Structure):
@@ -120,6 +124,8 @@ def lib(path: Optional[str] = None):
     L.caps_alloc_count.restype = i64
     L.caps_inject_alloc_failure.argtypes = [i64]
     L.caps_inject_alloc_failure.restype = None
+    L.caps_search_batch_or.argtypes = [P, P, i64, ct.POINTER(caps_or_constraints), i32, i32, P,
+                                       P, P]
     L.caps_test_scan_stall.argtypes = [i64, ct.c_uint64]
     L.caps_test_scan_stall.restype = None
     _lib = L
@@ -399,6 +405,38 @@ class Index:
                 out_dist = np.empty((nq, k), dtype=np.float32)
         _check(lib().caps_search_batch(self._h, _ptr(Q), nq, ct.byref(at), k, m, _ptr(out_ids),
                                        _ptr(out_dist), _stream(stream)))
+        return out_ids, out_dist
+
+    def search_or(self, Q, lists, k, m, out_ids=None, out_dist=None, stream=None):
+        """caps_search_batch_or: Alg. 2 with per-field value lists (Sec. 5.3).
+        lists: (offsets int64 [nq*L+1], values int32), or a list over queries
+        of lists over fields of allowed values (empty = unconstrained).
+        Returns (ids [nq,k] int64, dist [nq,k] fp32), where the inputs live
+        unless the outputs are given."""
+        Q = _np_or_keep(Q, np.float32)
+        nq = Q.shape[0]
+        if isinstance(lists, (list, tuple)) and not (len(lists) == 2 and hasattr(lists[0], "dtype")):
+            off, vals = [0], []
+            for row in lists:
+                for f in row:
+                    vals.extend(int(v) for v in f)
+                    off.append(len(vals))
+            lists = (np.asarray(off, np.int64), np.asarray(vals, np.int32))
+        off, vals = lists
+        off = _np_or_keep(off, np.int64)
+        vals = _np_or_keep(vals, np.int32)
+        oc = caps_or_constraints(self.info.L, _ptr(off) if len(off) else None,
+                                 _ptr(vals) if len(vals) else None)
+        t = _torch()
+        if out_ids is None:
+            if t is not None and isinstance(Q, t.Tensor) and Q.is_cuda:
+                out_ids = t.empty((nq, k), dtype=t.int64, device=Q.device)
+                out_dist = t.empty((nq, k), dtype=t.float32, device=Q.device)
+            else:
+                out_ids = np.empty((nq, k), dtype=np.int64)
+                out_dist = np.empty((nq, k), dtype=np.float32)
+        _check(lib().caps_search_batch_or(self._h, _ptr(Q), nq, ct.byref(oc), k, m,
+                                          _ptr(out_ids), _ptr(out_dist), _stream(stream)))
         return out_ids, out_dist
 
     def search_noalloc(self, Q, Qb, k, m, out_ids, out_dist, stream=None):

@@ -1607,3 +1607,97 @@ extern "C" int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W, 
   if (ob.host) CAPS_CUDA(cudaStreamSynchronize(s));
   return CAPS_OK;
 }
+
+// ---- disjunctive (OR) constraints (Sec. 5.3) -------------------------------
+extern "C" int caps_search_batch_or(const caps_index* ix, const float* Q, int64_t nq,
+                                    const caps_or_constraints* oc, int32_t k, int32_t m,
+                                    int64_t* out_ids, float* out_dist, void* stream) {
+  if (!ix || !oc) return fail(CAPS_EINVAL, "null argument");
+  if (nq < 0) return fail(CAPS_EINVAL, "nq < 0");
+  if (k < 1 || k > kMaxK) return fail(CAPS_EINVAL, "k must be in [1, 128]");
+  if (m < 1 || m > ix->B) return fail(CAPS_EINVAL, "m must be in [1, B]");
+  if (ix->meta.sparse) return fail(CAPS_EINVAL, "OR constraints need dense attributes");
+  const int L = ix->meta.L;
+  if (oc->L != L) return fail(CAPS_EINVAL, "constraints must have the index's L fields");
+  if (nq == 0) return CAPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the value lists on the host, expanded into single-valued sub-queries
+  std::vector<int64_t> voff;
+  if (int rc = to_host(oc->offsets, (size_t)(nq * L + 1), &voff, s)) return rc;
+  if (voff[0] != 0) return fail(CAPS_EINVAL, "offsets[0] must be 0");
+  for (size_t i = 1; i < voff.size(); i++)
+    if (voff[i] < voff[i - 1]) return fail(CAPS_EINVAL, "offsets must not decrease");
+  std::vector<int32_t> vals;
+  if (int rc = to_host(oc->values, (size_t)voff.back(), &vals, s)) return rc;
+  for (int32_t v : vals)
+    if (v < 0) return fail(CAPS_EINVAL, "OR values must be >= 0");
+  std::vector<int32_t> sub_cons;
+  std::vector<int64_t> sub_q, soff((size_t)nq + 1, 0);
+  std::vector<int64_t> pos((size_t)L);
+  std::vector<int32_t> b((size_t)L);
+  for (int64_t q = 0; q < nq; q++) {
+    int64_t combos = 1;
+    for (int f = 0; f < L; f++) {
+      const int64_t n = voff[q * L + f + 1] - voff[q * L + f];
+      combos *= n > 0 ? n : 1;
+      if (combos > kMaxOrCombos)
+        return fail(CAPS_EINVAL, "an OR query expands into more than 256 single-valued queries");
+    }
+    for (int f = 0; f < L; f++) {
+      pos[f] = voff[q * L + f];
+      b[f] = pos[f] < voff[q * L + f + 1] ? vals[pos[f]] : -1;
+    }
+    for (;;) {  // mixed-radix walk over the constrained fields' lists
+      sub_cons.insert(sub_cons.end(), b.begin(), b.end());
+      sub_q.push_back(q);
+      int f = 0;
+      for (; f < L; f++) {
+        const int64_t e = voff[q * L + f + 1];
+        if (voff[q * L + f] == e) continue;
+        if (++pos[f] < e) {
+          b[f] = vals[pos[f]];
+          break;
+        }
+        pos[f] = voff[q * L + f];
+        b[f] = vals[pos[f]];
+      }
+      if (f == L) break;
+    }
+    soff[q + 1] = (int64_t)sub_q.size();
+  }
+  const int64_t n_sub = (int64_t)sub_q.size();
+  Scratch scr(s);
+  const float* dQ = nullptr;
+  if (int rc = stage_in(Q, (size_t)nq * ix->d, scr, s, &dQ)) return rc;
+  int64_t *d_subq = nullptr, *d_soff = nullptr, *d_ids = nullptr;
+  int32_t* d_cons = nullptr;
+  float *d_Qs = nullptr, *d_dist = nullptr;
+  if (int rc = scr.get(&d_subq, (size_t)n_sub)) return rc;
+  if (int rc = scr.get(&d_soff, (size_t)nq + 1)) return rc;
+  if (int rc = scr.get(&d_cons, (size_t)n_sub * L)) return rc;
+  if (int rc = scr.get(&d_Qs, (size_t)n_sub * ix->d)) return rc;
+  if (int rc = scr.get(&d_ids, (size_t)n_sub * k)) return rc;
+  if (int rc = scr.get(&d_dist, (size_t)n_sub * k)) return rc;
+  CAPS_CUDA(cudaMemcpyAsync(d_subq, sub_q.data(), sizeof(int64_t) * (size_t)n_sub,
+                            cudaMemcpyHostToDevice, s));
+  CAPS_CUDA(cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * soff.size(),
+                            cudaMemcpyHostToDevice, s));
+  CAPS_CUDA(cudaMemcpyAsync(d_cons, sub_cons.data(), sizeof(int32_t) * sub_cons.size(),
+                            cudaMemcpyHostToDevice, s));
+  if (int rc = launch_gather_rows(dQ, d_subq, n_sub, ix->d, d_Qs, s)) return rc;
+  caps_attrs at{};
+  at.L = L;
+  at.dense = d_cons;
+  SearchOpts o;
+  o.cached = true;
+  if (int rc = search_impl(ix, d_Qs, n_sub, &at, k, m, d_ids, d_dist, s, o)) return rc;
+  Out<int64_t> oi;
+  Out<float> od;
+  if (int rc = oi.init(out_ids, (size_t)nq * k, scr)) return rc;
+  if (int rc = od.init(out_dist, (size_t)nq * k, scr)) return rc;
+  if (int rc = launch_or_merge(d_ids, d_dist, d_soff, nq, k, ix->metric, oi.dev, od.dev, s)) return rc;
+  if (int rc = oi.finish(s)) return rc;
+  if (int rc = od.finish(s)) return rc;
+  CAPS_CUDA(cudaStreamSynchronize(s));  // the host copies above outlive the call
+  return caps_device_status(ix, s);
+}

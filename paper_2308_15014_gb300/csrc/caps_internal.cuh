@@ -225,6 +225,11 @@ struct Scratch {
 // ---- build-side launchers (build_kernels.cu) ------------------------------
 int launch_gather_rows(const float* X, const int64_t* idx, int64_t n, int d,
                        float* out, cudaStream_t s);
+// disjunctive constraints: per query, the best k of its sub-queries' results
+// (sub-query rows soff[q] .. soff[q+1], k results each)
+int launch_or_merge(const int64_t* sids, const float* sdist, const int64_t* soff, int64_t nq,
+                    int k, int metric, int64_t* out_ids, float* out_dist, cudaStream_t s);
+constexpr int kMaxOrCombos = 256;  // single-valued sub-queries per OR query
 int launch_assign(const float* X, int64_t N, int d, const float* C, int B,
                   int metric, int32_t* bin, cudaStream_t s);
 int launch_scores(const float* Q, int64_t nq, int d, const float* C, int B,

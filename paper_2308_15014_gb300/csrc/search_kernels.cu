@@ -587,4 +587,58 @@ int launch_scan_topk(const ScanArgs& a, cudaStream_t s) {
                              : launch_scan_w<CAPS_IP>(a, (unsigned)grid, smem, s);
 }
 
+
+// ---- disjunctive constraints: best k of each query's sub-query results -----
+// Warp per query: the k results of each of its single-valued sub-queries
+// (rows soff[q] .. soff[q+1] of sids/sdist, -1 ids skipped) offered to a
+// warp top-k by (distance, id); the sub-queries' valid sets are disjoint, so
+// no id repeats.
+template <int KPL>
+__global__ void __launch_bounds__(128)
+k_or_merge(const int64_t* __restrict__ sids, const float* __restrict__ sdist,
+           const int64_t* __restrict__ soff, int64_t nq, int k, int metric,
+           int64_t* __restrict__ out_ids, float* __restrict__ out_dist) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (q >= nq) return;
+  WarpTopK<KPL> top;
+  top.init();
+  uint64_t kth = kEmptyKey;
+  const int64_t b = soff[q] * k, e = soff[q + 1] * k;
+  for (int64_t i0 = b; i0 < e; i0 += 32) {
+    const int64_t i = i0 + lane;
+    uint64_t key = kEmptyKey;
+    if (i < e && sids[i] >= 0)
+      key = make_key(metric == CAPS_L2 ? sdist[i] : -sdist[i], (uint32_t)sids[i]);
+    top.offer(key, kth, k, lane);
+  }
+#pragma unroll
+  for (int s = 0; s < KPL; s++) {
+    const int P = lane * KPL + s;
+    if (P < k) {
+      const uint64_t key = top.v[s];
+      int64_t id = -1;
+      float dist = metric == CAPS_L2 ? INFINITY : -INFINITY;
+      if (key != kEmptyKey) {
+        id = (int64_t)(uint32_t)(key & 0xffffffffu);
+        const float sc = unord_bits((uint32_t)(key >> 32));
+        dist = metric == CAPS_L2 ? sc : -sc;
+      }
+      out_ids[q * k + P] = id;
+      out_dist[q * k + P] = dist;
+    }
+  }
+}
+
+int launch_or_merge(const int64_t* sids, const float* sdist, const int64_t* soff, int64_t nq,
+                    int k, int metric, int64_t* out_ids, float* out_dist, cudaStream_t s) {
+  if (nq == 0) return CAPS_OK;
+  const unsigned g = (unsigned)((nq + 3) / 4);
+  if (k <= 32) k_or_merge<1><<<g, 128, 0, s>>>(sids, sdist, soff, nq, k, metric, out_ids, out_dist);
+  else if (k <= 64) k_or_merge<2><<<g, 128, 0, s>>>(sids, sdist, soff, nq, k, metric, out_ids, out_dist);
+  else k_or_merge<4><<<g, 128, 0, s>>>(sids, sdist, soff, nq, k, metric, out_ids, out_dist);
+  CAPS_LAUNCH("k_or_merge");
+  return CAPS_OK;
+}
+
 }  // namespace caps
