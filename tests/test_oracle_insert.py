@@ -60,3 +60,22 @@ def test_grown_index_probing_everything_is_exact_filtered_knn():
     # the new points sit where the block rule puts them
     new = np.arange(n0, w.N)
     np.testing.assert_array_equal(oi.key[new], O.block_of(oi.tags, w.h, O.Attrs(A=w.A[new], vocab=w.vocab), oi.bin[new]))
+
+
+def test_block_rule_hand_worked_tree_that_ends_early():
+    """Two fields, vocab 3 and 4 (codes 0-2 and 3-6); h = 3.  Partition 0's
+    peel used codes 1 and 5 and ran out of points (third tag -1); partition
+    1's used 6, 0, 2.  Block = first tag the point carries, else h + 1 = 4,
+    never the block of a -1 tag."""
+    tags = np.array([[1, 5, -1], [6, 0, 2]], np.int32)
+    A = np.array([[1, 3],   # codes 1, 3: carries t1 = 1 -> block 1
+                  [0, 2],   # codes 0, 5: carries t2 = 5 -> block 2
+                  [1, 2],   # codes 1, 5: carries both -> the first, block 1
+                  [0, 0],   # codes 0, 3: neither tag -> remainder 4
+                  [2, 1],   # partition 1, codes 2, 4: carries t3 = 2 -> block 3
+                  [0, 1],   # partition 1, codes 0, 4: carries t2 = 0 -> block 2
+                  [1, 1]],  # partition 1, codes 1, 4: none -> remainder 4
+                 np.int32)
+    bins = np.array([0, 0, 0, 0, 1, 1, 1], np.int32)
+    at = O.Attrs(A=A, vocab=np.array([3, 4], np.int32))
+    np.testing.assert_array_equal(O.block_of(tags, 3, at, bins), [1, 2, 1, 4, 3, 2, 4])
