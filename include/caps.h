@@ -355,6 +355,28 @@ int caps_mlp_train(int32_t d, int32_t H, int32_t B, float* W, const float* X,
 int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W,
                     const float* X, int64_t n, int32_t* out_bin, void* stream);
 
+/* ---- dynamic insertion ------------------------------------------------------ */
+
+/*
+ * caps_insert -- add n points to a built index (the paper lists dynamic
+ * insertion among CAPS's properties, Table 1, without giving a mechanism;
+ * this is the library's reading).  Point i of X [n*d] / attrs (dense, the
+ * index's L fields) gets the original id N + i, where N is the index's size
+ * before the call.  Its partition is f(x) -- the nearest centroid, or the
+ * learned partitioner's argmax -- and inside it the first block whose
+ * attribute-frequency tag it carries, else the remainder block h+1: the
+ * block the peel of Alg. 1 gives a point, with the partition's tags, the
+ * centroids and the network kept as they are.  The index is then laid out
+ * again by (partition, block, id), so searches see every point exactly as an
+ * index built with those partitions and tags would hold it.  Cost: one pass
+ * over the whole index (the layout is rebuilt), so insert in batches.
+ * The call synchronises `stream`.  Query plans made before it refuse to run
+ * afterwards (CAPS_EINVAL): make new ones.  Label-set (sparse) indexes:
+ * CAPS_EINVAL.  Errors leave the index as it was.
+ */
+int caps_insert(caps_index* index, const float* X, int64_t n, const caps_attrs* attrs,
+                void* stream);
+
 /* ---- disjunctive (OR) constraints (Sec. 5.3) ------------------------------- */
 
 /*

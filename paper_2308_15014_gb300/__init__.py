@@ -31,7 +31,8 @@ EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "c
            "caps_set_timing", "caps_get_stage_times", "caps_search_batch_noalloc",
            "caps_device_status", "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign", "caps_plan_create",
            "caps_plan_search", "caps_plan_get_info", "caps_plan_free", "caps_alloc_count",
-           "caps_inject_alloc_failure", "caps_test_scan_stall", "caps_search_batch_or")
+           "caps_inject_alloc_failure", "caps_test_scan_stall", "caps_search_batch_or",
+           "caps_insert")
 
 
 class CapsError(RuntimeError):
@@ -126,6 +127,7 @@ def lib(path: Optional[str] = None):
     L.caps_inject_alloc_failure.restype = None
     L.caps_search_batch_or.argtypes = [P, P, i64, ct.POINTER(caps_or_constraints), i32, i32, P,
                                        P, P]
+    L.caps_insert.argtypes = [P, P, i64, ct.POINTER(caps_attrs), P]
     L.caps_test_scan_stall.argtypes = [i64, ct.c_uint64]
     L.caps_test_scan_stall.restype = None
     _lib = L
@@ -406,6 +408,16 @@ class Index:
         _check(lib().caps_search_batch(self._h, _ptr(Q), nq, ct.byref(at), k, m, _ptr(out_ids),
                                        _ptr(out_dist), _stream(stream)))
         return out_ids, out_dist
+
+    def insert(self, X, A, stream=None):
+        """caps_insert: add the rows X [n, d] with dense attributes A [n, L];
+        they get the ids N .. N+n-1.  Plans made before refuse to run."""
+        X = _np_or_keep(X, np.float32)
+        at, keep = _dense_attrs(A)
+        _check(lib().caps_insert(self._h, _ptr(X), X.shape[0], ct.byref(at), _stream(stream)))
+        inf = caps_index_info()
+        _check(lib().caps_get_info(self._h, ct.byref(inf)))
+        self.info = inf
 
     def search_or(self, Q, lists, k, m, out_ids=None, out_dist=None, stream=None):
         """caps_search_batch_or: Alg. 2 with per-field value lists (Sec. 5.3).

@@ -621,6 +621,70 @@ int launch_layout(const float* X, const int32_t* A, const int32_t* perm, int64_t
   return CAPS_OK;
 }
 
+namespace {
+// ---- dynamic insertion: the built points back in id order, the new ones'
+// blocks ----------------------------------------------------------------------
+// X[perm[r]] = Xp[r]: the rows of the layout back at their original ids
+__global__ void k_unlayout_rows(const float* __restrict__ Xp, const int32_t* __restrict__ perm,
+                                int64_t N, int d, float* __restrict__ X) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * d) return;
+  const int64_t r = t / d, c = t % d;
+  X[(int64_t)perm[r] * d + c] = Xp[t];
+}
+// A[perm[r]][f] = field f's bits of the packed row Ap[r]
+__global__ void k_unpack_attrs(const uint32_t* __restrict__ Ap, const int32_t* __restrict__ perm,
+                               int64_t N, DenseMeta meta, int32_t* __restrict__ A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const int64_t i = perm[r];
+  for (int f = 0; f < meta.L; f++) {
+    const uint32_t w = Ap[r * meta.words_pad + meta.word[f]];
+    const uint32_t mask = meta.bits[f] >= 32 ? 0xffffffffu : ((1u << meta.bits[f]) - 1u);
+    A[i * meta.L + f] = (int32_t)((w >> meta.shift[f]) & mask);
+  }
+}
+// key[i] = the first block j of partition bin[i] whose tag point i carries,
+// else h + 1 (the block the attribute-frequency peel would give it under the
+// partition's tags; a tag of -1 ends the partition's tree)
+__global__ void k_block_of(const int32_t* __restrict__ A, const int32_t* __restrict__ bin, int64_t n,
+                           const int32_t* __restrict__ tags, int h, DenseMeta meta,
+                           const uint8_t* __restrict__ code_field, uint8_t* __restrict__ key) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t* t = tags + (int64_t)bin[i] * h;
+  int j = 1;
+  for (; j <= h; j++) {
+    const int c = t[j - 1];
+    if (c < 0) {
+      j = h + 1;
+      break;
+    }
+    const int f = code_field[c];
+    if (A[i * meta.L + f] == c - meta.code_off[f]) break;
+  }
+  key[i] = (uint8_t)j;
+}
+}  // namespace
+
+int launch_unlayout(const float* Xp, const uint32_t* Ap, const int32_t* perm, int64_t N, int d,
+                    const DenseMeta& meta, float* X, int32_t* A, cudaStream_t s) {
+  if (N == 0) return CAPS_OK;
+  k_unlayout_rows<<<(unsigned)((N * d + 255) / 256), 256, 0, s>>>(Xp, perm, N, d, X);
+  CAPS_LAUNCH("k_unlayout_rows");
+  k_unpack_attrs<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(Ap, perm, N, meta, A);
+  CAPS_LAUNCH("k_unpack_attrs");
+  return CAPS_OK;
+}
+
+int launch_block_of(const int32_t* A, const int32_t* bin, int64_t n, const int32_t* tags, int h,
+                    const DenseMeta& meta, const uint8_t* code_field, uint8_t* key, cudaStream_t s) {
+  if (n == 0) return CAPS_OK;
+  k_block_of<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, bin, n, tags, h, meta, code_field, key);
+  CAPS_LAUNCH("k_block_of");
+  return CAPS_OK;
+}
+
 int launch_pos_table(const int32_t* tags, int B, int h, int64_t n_codes, uint8_t* pos,
                      cudaStream_t s) {
   const int64_t tot = (int64_t)B * h;

@@ -384,6 +384,55 @@ static int build_mlp(const caps_build_params* p, const float* dX, const int32_t*
   return CAPS_OK;
 }
 
+// The arrays of the bf16 / e4m3 forms for the index's current rows (Xp, Ap,
+// perm, offsets in layout order): bf16 rows (with the penalty chunk when
+// ix->pen) or e4m3 rows and per-row scales, fp32 squared norms, the inverse
+// permutation and the tensor map over the rows.  Nothing for CAPS_FP32.
+static int prepare_precision(caps_index* ix, cudaStream_t s) {
+  if (ix->prec == CAPS_FP32) return CAPS_OK;
+  const int64_t N = ix->N;
+  const int d = ix->d;
+  const bool f8 = ix->prec == CAPS_FP8E4M3;
+  if (f8) {
+    // e4m3 rows (ceil(d/128)*128 bytes) + per-row scales + fp32 squared
+    // norms + inverse permutation; the filter is tested per pair
+    const int cols8 = (d + 127) / 128 * 128;
+    uint8_t* xb = nullptr;
+    if (int rc = ix->alloc(&xb, (size_t)N * cols8)) return rc;
+    ix->Xb = xb;
+    if (int rc = ix->alloc(&ix->xs, (size_t)N + 4)) return rc;
+  } else {
+    const int cols = ix->pen ? ((d + 63) / 64 + 1) * 64 : d;
+    uint16_t* xb = nullptr;
+    if (int rc = ix->alloc(&xb, (size_t)N * cols)) return rc;
+    ix->Xb = xb;
+  }
+  if (int rc = ix->alloc(&ix->xn, (size_t)N + 4)) return rc;
+  if (int rc = ix->alloc(&ix->iperm, (size_t)N)) return rc;
+  TcIndexPrep tp;
+  tp.Xp = ix->Xp;
+  tp.N = N;
+  tp.d = d;
+  tp.perm = ix->perm;
+  tp.Ap = ix->Ap;
+  tp.words_pad = ix->meta.words_pad;
+  tp.offsets = ix->offsets;
+  tp.B = ix->B;
+  tp.nb = ix->h + 1;
+  tp.pen = ix->pen;
+  tp.pen_bits = ix->pen_bits;
+  for (int w = 0; w < 4; w++) tp.pen_mask[w] = ix->pen_mask[w];
+  tp.f8 = f8 ? 1 : 0;
+  tp.metric = ix->metric;
+  tp.xs = ix->xs;
+  tp.Xb = ix->Xb;
+  tp.xn = ix->xn;
+  tp.iperm = ix->iperm;
+  tp.xn_max = &ix->xn_max;
+  tp.tmap = ix->tmap;
+  return tc_prepare_index(tp, s);
+}
+
 static int build_impl(const caps_build_params* p, const float* X, int64_t N, int32_t d,
                       const caps_attrs* attrs, cudaStream_t s, caps_index* ix) {
   if (!p || !X || !attrs) return fail(CAPS_EINVAL, "null argument");
@@ -563,43 +612,7 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     if (int rc = build_mlp(p, dX, dA, N, d, meta, s, ix)) return rc;
     if (int rc = finish()) return rc;
   }
-  if (p->prec == CAPS_FP8E4M3) {
-    // e4m3 form: e4m3 rows (ceil(d/128)*128 bytes) + per-row scales + fp32
-    // squared norms + inverse permutation; the filter is tested per pair
-    ix->pen = 0;
-    ix->pen_bits = 0;
-    const int cols8 = (d + 127) / 128 * 128;
-    uint8_t* xb = nullptr;
-    if (int rc = ix->alloc(&xb, (size_t)N * cols8)) return rc;
-    ix->Xb = xb;
-    if (int rc = ix->alloc(&ix->xn, (size_t)N + 4)) return rc;
-    if (int rc = ix->alloc(&ix->xs, (size_t)N + 4)) return rc;
-    if (int rc = ix->alloc(&ix->iperm, (size_t)N)) return rc;
-    TcIndexPrep tp;
-    tp.Xp = ix->Xp;
-    tp.N = N;
-    tp.d = d;
-    tp.perm = ix->perm;
-    tp.Ap = ix->Ap;
-    tp.words_pad = meta.words_pad;
-    tp.offsets = ix->offsets;
-    tp.B = B;
-    tp.nb = h + 1;
-    tp.pen = 0;
-    tp.pen_bits = 0;
-    for (int w = 0; w < 4; w++) tp.pen_mask[w] = 0u;
-    tp.f8 = 1;
-    tp.metric = p->metric;
-    tp.xs = ix->xs;
-    tp.Xb = ix->Xb;
-    tp.xn = ix->xn;
-    tp.iperm = ix->iperm;
-    tp.xn_max = &ix->xn_max;
-    tp.tmap = ix->tmap;
-    if (int rc = tc_prepare_index(tp, s)) return rc;
-  }
   if (p->prec == CAPS_BF16) {
-    // bf16 form: bf16 rows + fp32 squared norms + inverse permutation
     // penalty form when the one-hot code of the packed attribute bits (two
     // columns per bit) and, for L2, the three parts of -|x|^2/2 fit one
     // 64-column chunk
@@ -613,35 +626,11 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     ix->pen = !meta.sparse && tc_pen_columns(T, p->metric) <= 64 ? 1 : 0;
     ix->pen_bits = T;
     for (int w = 0; w < 4; w++) ix->pen_mask[w] = um[w];
-    const int cols = ix->pen ? ((d + 63) / 64 + 1) * 64 : d;
-    uint16_t* xb = nullptr;
-    if (int rc = ix->alloc(&xb, (size_t)N * cols)) return rc;
-    ix->Xb = xb;
-    if (int rc = ix->alloc(&ix->xn, (size_t)N + 4)) return rc;
-    if (int rc = ix->alloc(&ix->iperm, (size_t)N)) return rc;
-    TcIndexPrep tp;
-    tp.Xp = ix->Xp;
-    tp.N = N;
-    tp.d = d;
-    tp.perm = ix->perm;
-    tp.Ap = ix->Ap;
-    tp.words_pad = meta.words_pad;
-    tp.offsets = ix->offsets;
-    tp.B = B;
-    tp.nb = h + 1;
-    tp.pen = ix->pen;
-    tp.pen_bits = T;
-    for (int w = 0; w < 4; w++) tp.pen_mask[w] = um[w];
-    tp.f8 = 0;
-    tp.metric = p->metric;
-    tp.xs = nullptr;
-    tp.Xb = ix->Xb;
-    tp.xn = ix->xn;
-    tp.iperm = ix->iperm;
-    tp.xn_max = &ix->xn_max;
-    tp.tmap = ix->tmap;
-    if (int rc = tc_prepare_index(tp, s)) return rc;
+  } else {
+    ix->pen = 0;
+    ix->pen_bits = 0;
   }
+  if (int rc = prepare_precision(ix, s)) return rc;
   {
     // the weight side of the screened probe, fixed from here on
     const bool mlp = p->part == CAPS_PART_MLP;
@@ -1276,6 +1265,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
 
 struct caps_plan {
   const caps_index* ix = nullptr;
+  int64_t generation = 0;  // the index's generation when the graph was captured
   int64_t nq = 0;
   int32_t k = 0, m = 0;
   float* Q = nullptr;        // [nq*d]
@@ -1357,6 +1347,7 @@ extern "C" int caps_plan_create(const caps_index* ix, const float* Q, int64_t nq
   cudaStream_t s = (cudaStream_t)stream;
   std::unique_ptr<caps_plan> p(new caps_plan());
   p->ix = ix;
+  p->generation = ix->generation;
   p->nq = nq;
   p->k = k;
   p->m = m;
@@ -1470,6 +1461,8 @@ extern "C" int caps_plan_create(const caps_index* ix, const float* Q, int64_t nq
 extern "C" int caps_plan_search(caps_plan* p, const float* Q, int64_t nq, const caps_attrs* cons,
                                 int64_t* out_ids, float* out_dist, void* stream) {
   if (!p) return fail(CAPS_EINVAL, "null plan");
+  if (p->generation != p->ix->generation)
+    return fail(CAPS_EINVAL, "points were inserted after the plan was made: make a new plan");
   if (nq < 0 || nq > p->nq) return fail(CAPS_EINVAL, "nq must be in [0, plan nq]");
   if (int rc = check_cons(p->ix, cons)) return rc;
   if (nq == 0) return CAPS_OK;
@@ -1700,4 +1693,156 @@ extern "C" int caps_search_batch_or(const caps_index* ix, const float* Q, int64_
   if (int rc = od.finish(s)) return rc;
   CAPS_CUDA(cudaStreamSynchronize(s));  // the host copies above outlive the call
   return caps_device_status(ix, s);
+}
+
+// ---- dynamic insertion (Table 1; the mechanism is this library's reading) ---
+extern "C" int caps_insert(caps_index* ix, const float* X, int64_t n, const caps_attrs* attrs,
+                           void* stream) {
+  if (!ix || !attrs) return fail(CAPS_EINVAL, "null argument");
+  if (n < 0) return fail(CAPS_EINVAL, "n < 0");
+  if (ix->meta.sparse) return fail(CAPS_EINVAL, "insertion serves dense attributes only");
+  const DenseMeta& meta = ix->meta;
+  const int L = meta.L, d = ix->d, B = ix->B, h = ix->h;
+  if (attrs->L != L || (n > 0 && (!attrs->dense || !X)))
+    return fail(CAPS_EINVAL, "attributes must be dense with the index's L fields");
+  if (n == 0) return CAPS_OK;
+  const int64_t N0 = ix->N, N1 = N0 + n;
+  if (N1 >= (int64_t)INT32_MAX) return fail(CAPS_EINVAL, "the index would exceed 2^31-1 points");
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch scr(s);
+  const float* dX = nullptr;
+  const int32_t* dA = nullptr;
+  if (int rc = stage_in(X, (size_t)n * d, scr, s, &dX)) return rc;
+  if (int rc = stage_in(attrs->dense, (size_t)n * L, scr, s, &dA)) return rc;
+  int32_t* bad = nullptr;
+  if (int rc = scr.get(&bad, 1)) return rc;
+  CAPS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
+  if (int rc = launch_check_dense(dA, n, meta, bad, s)) return rc;
+  int32_t bad_h = 0;
+  CAPS_CUDA(cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  if (bad_h) return fail(CAPS_EINVAL, "attribute value outside [0, vocab[f])");
+  // every point in id order: the built ones back from the layout, then the new
+  float* Xall = nullptr;
+  int32_t* Aall = nullptr;
+  if (int rc = scr.get(&Xall, (size_t)N1 * d)) return rc;
+  if (int rc = scr.get(&Aall, (size_t)N1 * L)) return rc;
+  if (int rc = launch_unlayout(ix->Xp, ix->Ap, ix->perm, N0, d, meta, Xall, Aall, s)) return rc;
+  CAPS_CUDA(cudaMemcpyAsync(Xall + N0 * d, dX, sizeof(float) * (size_t)n * d,
+                            cudaMemcpyDeviceToDevice, s));
+  CAPS_CUDA(cudaMemcpyAsync(Aall + N0 * L, dA, sizeof(int32_t) * (size_t)n * L,
+                            cudaMemcpyDeviceToDevice, s));
+  // New arrays for every point; the index keeps its old ones until all of
+  // them (and the bf16 / e4m3 rows) are ready, so a failure leaves it as it
+  // was.
+  struct Arrays {
+    int32_t* bin = nullptr;
+    uint8_t* key = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* offsets = nullptr;
+    float* Xp = nullptr;
+    uint32_t* Ap = nullptr;
+    void* Xb = nullptr;
+    float *xn = nullptr, *xs = nullptr;
+    int32_t* iperm = nullptr;
+  };
+  auto release_all = [&](const Arrays& x) {
+    ix->release(x.bin);
+    ix->release(x.key);
+    ix->release(x.perm);
+    ix->release(x.offsets);
+    ix->release(x.Xp);
+    ix->release(x.Ap);
+    ix->release(x.Xb);
+    ix->release(x.xn);
+    ix->release(x.xs);
+    ix->release(x.iperm);
+  };
+  Arrays nw;
+  auto build_new = [&]() -> int {
+    const int64_t nseg = (int64_t)B * (h + 1);
+    if (int rc = ix->alloc(&nw.bin, (size_t)N1)) return rc;
+    if (int rc = ix->alloc(&nw.key, (size_t)N1)) return rc;
+    if (int rc = ix->alloc(&nw.perm, (size_t)N1 + 4)) return rc;
+    if (int rc = ix->alloc(&nw.offsets, (size_t)nseg + 1)) return rc;
+    if (int rc = ix->alloc(&nw.Xp, (size_t)N1 * d)) return rc;
+    if (int rc = ix->alloc(&nw.Ap, (size_t)(N1 + 4) * meta.words_pad)) return rc;
+    CAPS_CUDA(cudaMemcpyAsync(nw.bin, ix->bin, sizeof(int32_t) * (size_t)N0, cudaMemcpyDeviceToDevice, s));
+    CAPS_CUDA(cudaMemcpyAsync(nw.key, ix->key, (size_t)N0, cudaMemcpyDeviceToDevice, s));
+    // f(x) of the new points (the index's partition function), then their
+    // blocks under the unchanged tags
+    if (ix->part == CAPS_PART_MLP) {
+      if (int rc = mlp_assign(ix->mlp, dX, n, nw.bin + N0, scr, s)) return rc;
+    } else if (int rc = launch_assign(dX, n, d, ix->C, B, ix->metric, nw.bin + N0, s)) {
+      return rc;
+    }
+    if (int rc = launch_block_of(dA, nw.bin + N0, n, ix->tags, h, meta, ix->code_field,
+                                 nw.key + N0, s))
+      return rc;
+    // the stable order by (partition, block, id) of all N1 points
+    int32_t* seg = nullptr;
+    if (int rc = scr.get(&seg, (size_t)N1)) return rc;
+    if (int rc = launch_segment_keys(nw.bin, nw.key, N1, h, seg, s)) return rc;
+    if (int rc = stable_sort_by_key(seg, N1, nseg, nw.perm, nw.offsets, scr, s)) return rc;
+    if (int rc = launch_layout(Xall, Aall, nw.perm, N1, d, meta, nw.Xp, nw.Ap, s)) return rc;
+    CAPS_CUDA(cudaMemsetAsync(nw.perm + N1, 0, sizeof(int32_t) * 4, s));
+    CAPS_CUDA(cudaMemsetAsync(nw.Ap + N1 * meta.words_pad, 0, sizeof(uint32_t) * 4 * meta.words_pad, s));
+    return CAPS_OK;
+  };
+  if (int rc = build_new()) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    release_all(nw);
+    return rc;
+  }
+  // switch to the new arrays and derive the bf16 / e4m3 form from them
+  Arrays old;
+  old.bin = ix->bin;
+  old.key = ix->key;
+  old.perm = ix->perm;
+  old.offsets = ix->offsets;
+  old.Xp = ix->Xp;
+  old.Ap = ix->Ap;
+  old.Xb = ix->Xb;
+  old.xn = ix->xn;
+  old.xs = ix->xs;
+  old.iperm = ix->iperm;
+  const float old_xn_max = ix->xn_max;
+  alignas(128) unsigned char old_tmap[sizeof(ix->tmap)];
+  std::memcpy(old_tmap, ix->tmap, sizeof(ix->tmap));
+  auto set = [&](const Arrays& x, int64_t N) {
+    ix->bin = x.bin;
+    ix->key = x.key;
+    ix->perm = x.perm;
+    ix->offsets = x.offsets;
+    ix->Xp = x.Xp;
+    ix->Ap = x.Ap;
+    ix->Xb = x.Xb;
+    ix->xn = x.xn;
+    ix->xs = x.xs;
+    ix->iperm = x.iperm;
+    ix->N = N;
+  };
+  set(nw, N1);
+  int rc = prepare_precision(ix, s);
+  if (rc == CAPS_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "caps_insert");
+  }
+  nw.Xb = ix->Xb;
+  nw.xn = ix->xn;
+  nw.xs = ix->xs;
+  nw.iperm = ix->iperm;
+  if (rc != CAPS_OK) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    set(old, N0);
+    ix->xn_max = old_xn_max;
+    std::memcpy(ix->tmap, old_tmap, sizeof(ix->tmap));
+    release_all(nw);
+    return rc;
+  }
+  release_all(old);
+  ix->generation++;
+  return CAPS_OK;
 }

@@ -265,6 +265,12 @@ int launch_layout(const float* X, const int32_t* A, const int32_t* perm, int64_t
 int launch_pos_table(const int32_t* tags, int B, int h, int64_t n_codes,
                      uint8_t* pos, cudaStream_t s);
 int launch_code_field(const DenseMeta& meta, uint8_t* code_field, cudaStream_t s);
+// dynamic insertion: the layout's rows and packed attributes back in id
+// order (dense attributes), and the block of each new point
+int launch_unlayout(const float* Xp, const uint32_t* Ap, const int32_t* perm, int64_t N, int d,
+                    const DenseMeta& meta, float* X, int32_t* A, cudaStream_t s);
+int launch_block_of(const int32_t* A, const int32_t* bin, int64_t n, const int32_t* tags, int h,
+                    const DenseMeta& meta, const uint8_t* code_field, uint8_t* key, cudaStream_t s);
 
 // ---- search-side launchers (search_kernels.cu) ----------------------------
 struct QueryPrep {
@@ -497,7 +503,9 @@ struct caps_index {
   mutable std::mutex tune_mu;
   mutable std::map<std::pair<int, int>, Shape> tuned;
   int64_t bytes = 0;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;
+  // bumped by every insertion (the arrays move): plans made before it refuse to run
+  int64_t generation = 0;
 
   template <class T>
   int alloc(T** p, size_t count) {
@@ -508,13 +516,24 @@ struct caps_index {
       cudaGetLastError();
       return caps::fail(CAPS_ENOMEM, "device allocation failed for an index array");
     }
-    allocs.push_back(q);
+    allocs.emplace_back(q, count * sizeof(T));
     bytes += (int64_t)(count * sizeof(T));
     *p = (T*)q;
     return CAPS_OK;
   }
+  // free one array of this index (no-op for null)
+  void release(void* q) {
+    if (!q) return;
+    for (size_t i = 0; i < allocs.size(); i++)
+      if (allocs[i].first == q) {
+        cudaFree(q);
+        bytes -= (int64_t)allocs[i].second;
+        allocs.erase(allocs.begin() + (ptrdiff_t)i);
+        return;
+      }
+  }
   ~caps_index() {
-    for (void* q : allocs) cudaFree(q);
+    for (auto& a : allocs) cudaFree(a.first);
   }
 };
 
