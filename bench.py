@@ -69,11 +69,11 @@ def parse():
                     help="comma list of search paths (fp32, bf16, fp8, mlp_fp32, mlp_bf16, "
                          "mlp_fp8); "
                          "the first is the headline")
-    ap.add_argument("--h-sweep", action="store_true",
-                    help="also sweep the AFT height h (k-means + bf16): QPS at recall@10 >= 0.9")
-    ap.add_argument("--sparse", action="store_true",
-                    help="also measure the label-set workload (2M x 128, 10,000 labels, "
-                         "4,096 queries); adds about two minutes")
+    ap.add_argument("--no-ablations", action="store_true",
+                    help="skip the ablations (k-means + bf16, QPS at recall@10 >= 0.9 for AFT "
+                         "heights h, constrained-field counts and 10 attribute fields)")
+    ap.add_argument("--no-sparse", action="store_true",
+                    help="skip the label-set workload (2M x 128, 10,000 labels, 4,096 queries)")
     return ap.parse_args()
 
 
@@ -303,7 +303,7 @@ def form1_error(w, rng_seed=11, nq=64, nrow=2048):
     return out
 
 
-def oracle_truth(w, samp):
+def oracle_truth(w, samp, k=None):
     """Exact filtered kNN of the sampled queries (Def. 2, appendix
     "Groundtruth") from the CPU oracle's brute force: every point filtered,
     the valid ones ordered by fp64 distance (ties to the lower id).  Runs
@@ -315,7 +315,7 @@ def oracle_truth(w, samp):
     O.set_threads(0)
     cons = O.Cons.of(w).subset(samp)
     ids, _, d64, cnt = O.bruteforce(w.X, O.Attrs.of(w), np.ascontiguousarray(w.Q[samp]), cons,
-                                    w.k, metric=w.metric, order64=True)
+                                    k or w.k, metric=w.metric, order64=True)
     return ids, d64, cnt
 
 
@@ -417,66 +417,119 @@ def query_stats(w, rows_scanned, rows_passed):
     return out
 
 
-def h_sweep(args, w, caps, torch, samp, gt, g64, cnt):
-    """AFT height ablation (k-means + bf16, the same seed points): for each h
-    the smallest probe count reaching recall@10 >= 0.9 and the batch QPS
-    there (device buffers, CUDA events, L2 flushed)."""
-    Qd = torch.from_numpy(w.Q).cuda()
-    Qbd = torch.from_numpy(w.Qb).cuda()
-    X = torch.from_numpy(w.X).cuda()
-    A = torch.from_numpy(w.A).cuda()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    ids = torch.empty((w.nq, w.k), dtype=torch.int64, device="cuda")
-    dist = torch.empty((w.nq, w.k), dtype=torch.float32, device="cuda")
-    out = []
+ABLATION_M_SWEEP = M_SWEEP + (96, 128, 192, 256)
+
+
+def qps_at_recall(caps, torch, ix, w, samp, gt, g64, cnt, flush, m_sweep=ABLATION_M_SWEEP, target=0.9,
+                  reps=5, nq=None, k=None):
+    """Smallest probe count in m_sweep whose tie-aware recall@k on the sample
+    reaches the target, and the batch QPS there (device buffers, CUDA events,
+    L2 flushed before each timed search).  Returns a small dict."""
+    k = k or w.k
+    nq = nq or w.nq
+    Qd = torch.from_numpy(np.ascontiguousarray(w.Q[:nq])).cuda()
+    Qbd = torch.from_numpy(np.ascontiguousarray(w.Qb[:nq])).cuda() if w.Qb is not None else \
+        (torch.from_numpy(w.q_off).cuda(), torch.from_numpy(w.q_lab).cuda())
+    ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    dist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    row = {"m": None}
+    for m in m_sweep:
+        ix.search(Qd, Qbd, k, m, out_ids=ids, out_dist=dist)
+        _, tie = recall_at_k(ids.cpu().numpy()[samp], gt, g64, cnt, k, w.X, w.Q[samp], w.metric)
+        if tie >= target:
+            ms = time_search(torch, lambda: ix.search(Qd, Qbd, k, m, out_ids=ids, out_dist=dist),
+                             flush, reps)
+            row = {"m": m, "recall_tie": round(tie, 4), "qps": round(nq / (ms / 1e3), 1)}
+            break
+        row = {"m": None, "recall_tie_at_max_m": round(tie, 4)}
+    return row
+
+
+def time_search(torch, fn, flush, reps=5, warm=2):
+    """Median device time (ms) of fn(), L2 flushed before each timed call."""
+    for _ in range(warm):
+        fn()
+    evs = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+
+def ablations(args, w, caps, torch, flush):
+    """Sec. 6.1 ablations and the appendix's longer attribute vectors, on
+    k-means + bf16 indexes (the same seed points) of the 1M x 128 data:
+    QPS at recall@10 >= 0.9 for (1) AFT heights h (blocks h+1), (2) queries
+    constraining exactly 3, 2 or 1 of the 3 fields (absence fraction 0,
+    1/3, 2/3), (3) 10 attribute fields instead of 3 (queries constrain 1-3
+    of them).  Ground truth of a 300-query sample from the oracle's brute
+    force for every query set."""
+    from workloads import config_sift1m_fields, with_constraints
+    rng = np.random.default_rng(9)
+    samp = np.sort(rng.choice(w.nq, 300, replace=False))
+
+    def build(wl, h=None):
+        return caps.Index.build(torch.from_numpy(wl.X).cuda(), torch.from_numpy(wl.A).cuda(),
+                                wl.vocab, wl.B, h=wl.h if h is None else h, iters=wl.iters,
+                                init_idx=wl.init_idx, prec=caps.BF16)
+
+    out = {"index": "k-means + bf16", "h": [], "constrained_fields": [], "attribute_fields": []}
+    gt = oracle_truth(w, samp)
     for h in (0, 1, 3, 7, 15, 31):
-        ix = caps.Index.build(X, A, w.vocab, w.B, h=h, iters=w.iters, init_idx=w.init_idx,
-                              prec=caps.BF16)
-        row = {"h": h, "m_at_0.9": None}
-        for m in M_SWEEP:
-            ix.search(Qd, Qbd, w.k, m, out_ids=ids, out_dist=dist)
-            _, tie = recall_at_k(ids.cpu().numpy()[samp], gt, g64, cnt, w.k, w.X, w.Q[samp],
-                                 w.metric)
-            if tie >= 0.9:
-                for _ in range(3):
-                    ix.search(Qd, Qbd, w.k, m, out_ids=ids, out_dist=dist)
-                evs = []
-                for _ in range(5):
-                    flush.zero_()
-                    e0, e1 = (torch.cuda.Event(enable_timing=True),
-                              torch.cuda.Event(enable_timing=True))
-                    e0.record()
-                    ix.search(Qd, Qbd, w.k, m, out_ids=ids, out_dist=dist)
-                    e1.record()
-                    evs.append((e0, e1))
-                torch.cuda.synchronize()
-                ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
-                row.update({"m_at_0.9": m, "recall_tie": round(tie, 4),
-                            "qps": round(w.nq / (ms / 1e3), 1)})
-                break
-        out.append(row)
+        ix = build(w, h)
+        out["h"].append({"h": h, **qps_at_recall(caps, torch, ix, w, samp, *gt, flush)})
         ix.close()
+    ix = build(w)
+    for c in (3, 2, 1):
+        wc = with_constraints(w, c, c, 4000 + c, sel_range=(0.001, 0.30))
+        out["constrained_fields"].append(
+            {"constrained": c, "absence_fraction": round((3 - c) / 3, 3),
+             **qps_at_recall(caps, torch, ix, wc, samp, *oracle_truth(wc, samp), flush)})
+    ix.close()
+    for L in (10,):
+        wl = config_sift1m_fields(L)
+        ix = build(wl)
+        out["attribute_fields"].append(
+            {"L": L, "attr_words": int(ix.info.attr_words),
+             **qps_at_recall(caps, torch, ix, wl, samp, *oracle_truth(wl, samp), flush)})
+        ix.close()
+    out["attribute_fields"].insert(0, {"L": 3, **{k_: v_ for k_, v_ in out["h"][4].items()
+                                                   if k_ != "h"}})
     return out
 
 
-def sparse_line(args, caps, torch):
+def sparse_line(args, caps, torch, flush):
     """Label-set workload (2M x 128 fp32 mixture, 10,000-label vocabulary,
-    1-20 labels per point, queries requiring 1-8 labels): build, probe sweep,
-    recall against the exact filtered kNN on a query sample, QPS of
-    the batched query (device buffers, CUDA events, L2 flushed)."""
+    1-20 labels per point, queries requiring 1-8 labels).  Per index form
+    (fp32, bf16): build time, recall@10 and QPS over a probe sweep, the
+    smallest m reaching recall@10 >= 0.9, and the QPS there for batches of
+    1, 16, 256 and 4,096 queries; for the fp32 index also k = 100 (recall@100
+    >= 0.9).  Recall against the oracle's brute force on a 200-query sample;
+    device buffers, CUDA events, L2 flushed before each timed search."""
     from workloads import config_sparse2m
     t0 = time.perf_counter()
     w = config_sparse2m()
     gen_s = time.perf_counter() - t0
     rng = np.random.default_rng(6)
     samp = np.sort(rng.choice(w.nq, 200, replace=False))
-    gt, g64, cnt, _ = exact_truth(caps, torch, w, samp, labels=True)
+    gt10 = exact_truth(caps, torch, w, samp, labels=True)[:3]
+    gt100 = oracle_truth(w, samp, k=100)
     Qd = torch.from_numpy(w.Q).cuda()
     qoff = torch.from_numpy(w.q_off).cuda()
     qlab = torch.from_numpy(w.q_lab).cuda()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     out = {"workload": w.name, "N": w.N, "d": w.d, "labels": int(w.sp_vocab),
            "queries_per_step": w.nq, "generate_s": round(gen_s, 1), "paths": {}}
+
+    def sub(nq):  # the first nq queries' label lists
+        end = int(w.q_off[nq])
+        return (torch.from_numpy(np.ascontiguousarray(w.q_off[:nq + 1])).cuda(),
+                torch.from_numpy(np.ascontiguousarray(w.q_lab[:end])).cuda())
+
     for name, prec in (("fp32", caps.FP32), ("bf16", caps.BF16)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -485,30 +538,36 @@ def sparse_line(args, caps, torch):
                               labels=(w.sp_off, w.sp_lab, w.sp_vocab))
         torch.cuda.synchronize()
         build_s = time.perf_counter() - t0
-        ids = torch.empty((w.nq, w.k), dtype=torch.int64, device="cuda")
-        dist = torch.empty((w.nq, w.k), dtype=torch.float32, device="cuda")
-        sweep, chosen = [], None
-        for m in SPARSE_M_SWEEP:
-            ix.search(Qd, (qoff, qlab), w.k, m, out_ids=ids, out_dist=dist)
-            strict, tie = recall_at_k(ids.cpu().numpy()[samp], gt, g64, cnt, w.k, w.X,
-                                      w.Q[samp], w.metric)
-            evs = []
-            for _ in range(max(3, args.warmup)):
-                ix.search(Qd, (qoff, qlab), w.k, m, out_ids=ids, out_dist=dist)
-            for _ in range(5):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                ix.search(Qd, (qoff, qlab), w.k, m, out_ids=ids, out_dist=dist)
-                e1.record()
-                evs.append((e0, e1))
-            torch.cuda.synchronize()
-            ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
-            sweep.append({"m": m, "recall_tie": round(tie, 4), "recall_strict": round(strict, 4),
-                          "qps": round(w.nq / (ms / 1e3), 1), "ms": round(ms, 4)})
-            if chosen is None and tie >= 0.9:
-                chosen = m
-        out["paths"][name] = {"build_s": round(build_s, 2), "m_at_0.9": chosen, "sweep": sweep}
+        res = {"build_s": round(build_s, 2)}
+        for k, gt, label in ((10, gt10, "k10"), (100, gt100, "k100")):
+            if k == 100 and name != "fp32":
+                continue  # k > 32 runs the fp32 scan on a bf16 index too
+            ids = torch.empty((w.nq, k), dtype=torch.int64, device="cuda")
+            dist = torch.empty((w.nq, k), dtype=torch.float32, device="cuda")
+            sweep, chosen = [], None
+            for m in SPARSE_M_SWEEP:
+                ix.search(Qd, (qoff, qlab), k, m, out_ids=ids, out_dist=dist)
+                _, tie = recall_at_k(ids.cpu().numpy()[samp], *gt, k, w.X, w.Q[samp], w.metric)
+                ms = time_search(torch, lambda: ix.search(Qd, (qoff, qlab), k, m, out_ids=ids,
+                                                          out_dist=dist), flush)
+                sweep.append({"m": m, "recall_tie": round(tie, 4),
+                              "qps": round(w.nq / (ms / 1e3), 1)})
+                if chosen is None and tie >= 0.9:
+                    chosen = m
+                    break
+            row = {"m_at_0.9": chosen, "sweep": sweep}
+            if chosen is not None and k == 10:
+                bq = {}
+                for nb in (1, 16, 256, 4096):
+                    qc, lc = Qd[:nb], sub(nb)
+                    bi = torch.empty((nb, k), dtype=torch.int64, device="cuda")
+                    bd = torch.empty((nb, k), dtype=torch.float32, device="cuda")
+                    ms = time_search(torch, lambda: ix.search(qc, lc, k, chosen, out_ids=bi,
+                                                              out_dist=bd), flush, reps=7)
+                    bq[str(nb)] = {"qps": round(nb / (ms / 1e3), 1), "ms": round(ms, 4)}
+                row["batches"] = bq
+            res[label] = row
+        out["paths"][name] = res
         ix.close()
     return out
 
@@ -669,6 +728,10 @@ def run_reference(args):
     return 0
 
 
+# the e4m3 form re-scores 16 k candidates per query exactly (its tile scores
+# carry about 1 % error, so the right neighbours rank lower than with bf16)
+FP8_RERANK_FACTOR = 16
+
 # learned partitioner: 128 -> 512 -> 1024 (ReLU), 131,072 training points,
 # 10-NN filtered labels, Adam lr 2e-3, batches of 4096, 20 epochs
 MLP_ARGS = dict(mlp_hidden=512, mlp_epochs=20, mlp_samples=131072, mlp_batch=4096, mlp_lr=2e-3,
@@ -684,7 +747,9 @@ def measure_path(args, w, caps, prec, samp, gt, g64, cnt, flush, world, local, p
     A = torch.from_numpy(w.A).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    extra = MLP_ARGS if part == caps.MLP else {}
+    extra = dict(MLP_ARGS) if part == caps.MLP else {}
+    if prec == caps.FP8:
+        extra["rerank_factor"] = FP8_RERANK_FACTOR
     ix = caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, metric=w.metric,
                           init_idx=w.init_idx, prec=prec, part=part, **extra)
     torch.cuda.synchronize()
@@ -891,9 +956,8 @@ def run_caps(args):
     form1 = {"tile_score_vs_fp64": {w.name: form1_error(w), "float_mixture_d128": form1_error(wf)},
              "returned_dist_vs_fp64": {"pairs": int(rel.size), "max_rel": float(rel.max()),
                                        "mean_rel": float(rel.mean())}}
-    sparse = sparse_line(args, caps, torch) if args.sparse and world == 1 else None
-    hsw = h_sweep(args, w, caps, torch, samp, gt, g64, cnt) if args.h_sweep and world == 1 \
-        else None
+    sparse = sparse_line(args, caps, torch, flush) if not args.no_sparse and world == 1 else None
+    abl = ablations(args, w, caps, torch, flush) if not args.no_ablations and world == 1 else None
 
     if rank != 0:
         return 0
@@ -940,8 +1004,8 @@ def run_caps(args):
     }
     if sparse is not None:
         line["label_sets"] = sparse
-    if hsw is not None:
-        line["h_sweep"] = hsw
+    if abl is not None:
+        line["ablations"] = abl
     print(json.dumps(line, default=_json_default), flush=True)
     for r in res.values():
         r["plan"].close()

@@ -112,16 +112,18 @@ typedef struct {
  *                |x|^2 - 2 q.x, the query's own |q|^2 being common to all its
  *                keys) and re-score the best rerank_factor * k candidates of
  *                each query exactly in fp32 before keeping k.  Needs d % 8 == 0 and
- *                64 <= d <= 128; searches with k > 32 (or a candidate list beyond
- *                64) use the fp32 scan instead.
+ *                64 <= d <= 128; searches with k > 32 use the fp32 scan instead.
  *                CAPS_FP8E4M3: as CAPS_BF16 with e4m3 rows and queries, each
  *                row and query scaled by s = max |x| / 448 (e4m3 value =
  *                x / s rounded to nearest even, saturating); the tile's fp32
  *                dot product is multiplied back by both scales.  The filter
  *                is tested per (probe, row) (no penalty chunk).  Needs
  *                d % 16 == 0 and 64 <= d <= 128.
- *   rerank_factor candidates re-scored per result in the bf16 form
- *                (0 = 4, at most 16).
+ *   rerank_factor candidates re-scored per result in the bf16 and e4m3
+ *                forms (0 = 4, at most 16): min(256, rerank_factor * k)
+ *                candidates per query; each probed partition keeps its best
+ *                10, 16 or 32 keys per probe -- at least k and at least a
+ *                quarter of that depth.
  *   mlp_hidden   hidden units H (0 = 512).
  *   mlp_epochs   passes over the training points (0 = use mlp_init as the
  *                trained network).

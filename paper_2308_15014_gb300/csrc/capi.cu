@@ -1032,14 +1032,17 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
                 const SearchOpts& o);
 
 // which forms of the tensor-core scan serve this index and k
+int kp_of(const caps_index* ix, int k) {
+  return tc_kp(k, tc_rerank_depth(k, ix->rerank_factor));
+}
 bool tc_explicit_ok(const caps_index* ix, int k) {
   const bool f8 = ix->prec == CAPS_FP8E4M3;
   return (ix->prec == CAPS_BF16 || f8) &&
-         tc_scan_supported(ix->d, k, tc_kp(k), ix->meta.words_pad, f8 ? 1 : 0);
+         tc_scan_supported(ix->d, k, kp_of(ix, k), ix->meta.words_pad, f8 ? 1 : 0);
 }
 bool uses_pen(const caps_index* ix, int k) {
   return ix->prec == CAPS_BF16 && k <= 32 && ix->pen &&
-         tc_pen_supported(ix->d, tc_kp(k), ix->meta.words_pad);
+         tc_pen_supported(ix->d, kp_of(ix, k), ix->meta.words_pad);
 }
 bool uses_tc(const caps_index* ix, int k) { return tc_explicit_ok(ix, k) || uses_pen(ix, k); }
 }  // namespace
@@ -1078,7 +1081,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
   if (int rc = oi.init(out_ids, (size_t)nq * k, scr)) return rc;
   if (int rc = od.init(out_dist, (size_t)nq * k, scr)) return rc;
   const bool tc = uses_tc(ix, k);
-  const int kp = tc ? tc_kp(k) : k;
+  const int kp = tc ? kp_of(ix, k) : k;
   int tile_n = o.tile_n, item_cap = o.item_cap, pen = o.pen;
   if (o.cached) {
     std::lock_guard<std::mutex> lock(ix->tune_mu);

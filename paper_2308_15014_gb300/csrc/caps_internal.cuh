@@ -406,7 +406,10 @@ struct TcScanArgs {
   int32_t* err;
   int64_t n_rows = 0;   // rows of the index (ids are below it)
 };
-int tc_kp(int k);
+constexpr int kMaxRerank = 256;  // candidates re-scored exactly per query (form 1)
+// keys each partition keeps per probe: 10, 16 or 32, at least k and at least
+// a quarter of the re-rank depth
+int tc_kp(int k, int depth);
 int tc_rerank_depth(int k, int factor);
 bool tc_scan_supported(int d, int k, int kp, int words_pad, int f8 = 0);
 // whether the per-pair filter form with N-row tiles fits in shared memory

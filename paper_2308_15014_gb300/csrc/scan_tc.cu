@@ -8,6 +8,7 @@
 #include <atomic>
 #include <climits>
 #include <cstring>
+#include <type_traits>
 
 #include "scan_tc_kernel.cuh"
 
@@ -145,7 +146,7 @@ k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ de
                const float* __restrict__ Q, int d, const float* __restrict__ Xp,
                const int32_t* __restrict__ iperm, int64_t n_rows, int64_t* __restrict__ out_ids,
                float* __restrict__ out_dist, const int32_t* __restrict__ err) {
-  // [4][d] queries, [4][128] candidate keys
+  // [4][d] queries, [4][kMaxRerank] candidate keys
   extern __shared__ float qsm[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int64_t q = (int64_t)blockIdx.x * 4 + wp;
@@ -158,7 +159,7 @@ k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ de
     return;
   }
   float* qs = qsm + (size_t)wp * d;
-  uint64_t* cbuf = reinterpret_cast<uint64_t*>(qsm + 4 * (size_t)d) + (size_t)wp * 128;
+  uint64_t* cbuf = reinterpret_cast<uint64_t*>(qsm + 4 * (size_t)d) + (size_t)wp * kMaxRerank;
   for (int j = lane; j < d; j += 32) qs[j] = Q[q * d + j];
   const uint64_t* src = part + q * (int64_t)m * lp;
   const int tot = m * lp;
@@ -179,29 +180,32 @@ k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ de
       const bool keep = key <= T;
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
       const int pos = cnt + __popc(bal & lt);
-      if (keep && pos < 128) cbuf[pos] = key;
+      if (keep && pos < kMaxRerank) cbuf[pos] = key;
       cnt += __popc(bal);
     }
   }
   __syncwarp();
-  if (live && T != kEmptyKey && cnt <= 64) {  // (kp <= 64: the first kp are enough)
-    uint64_t v[2];
+  // the kp best keys, ascending, at the front of cbuf: the compacted keys
+  // sorted in the warp when at most kMaxRerank of them compete, else every
+  // list key offered to a warp top-kp
+  auto sort_front = [&](auto vtag) {
+    constexpr int V = decltype(vtag)::value;
+    uint64_t v[V];
 #pragma unroll
-    for (int s = 0; s < 2; s++) v[s] = (2 * lane + s < cnt) ? cbuf[2 * lane + s] : kEmptyKey;
-    warp_sort<2>(v, lane);
+    for (int s = 0; s < V; s++) v[s] = (V * lane + s < cnt) ? cbuf[V * lane + s] : kEmptyKey;
+    warp_sort<V>(v, lane);
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < 2; s++) cbuf[2 * lane + s] = v[s];
+    for (int s = 0; s < V; s++) cbuf[V * lane + s] = v[s];
+  };
+  if (live && T != kEmptyKey && cnt <= 64) {
+    sort_front(std::integral_constant<int, 2>{});
   } else if (live && T != kEmptyKey && cnt <= 128) {
-    uint64_t v[4];
-#pragma unroll
-    for (int s = 0; s < 4; s++) v[s] = (4 * lane + s < cnt) ? cbuf[4 * lane + s] : kEmptyKey;
-    warp_sort<4>(v, lane);
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < 4; s++) cbuf[4 * lane + s] = v[s];
+    sort_front(std::integral_constant<int, 4>{});
+  } else if (live && T != kEmptyKey && cnt <= kMaxRerank) {
+    sort_front(std::integral_constant<int, kMaxRerank / 32>{});
   } else {
-    TopKm<2> cand;
+    TopKm<kMaxRerank / 32> cand;
     cand.init();
     uint64_t kthv = kEmptyKey;
     if (live) {
@@ -212,21 +216,21 @@ k_merge_rerank(const uint64_t* __restrict__ part, const uint8_t* __restrict__ de
     }
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < 2; s++) cbuf[2 * lane + s] = cand.v[s];
+    for (int s = 0; s < kMaxRerank / 32; s++) cbuf[(kMaxRerank / 32) * lane + s] = cand.v[s];
   }
   __syncwarp();
-  // exact fp32 scores of the kp <= 64 candidates, two per lane (lane and
-  // lane + 32): their rows in 16-byte loads, four per candidate in flight,
+  // exact fp32 scores of the kp candidates, 64 at a time, two per lane (c
+  // and c + 32): their rows in 16-byte loads, four per candidate in flight,
   // and their two fma chains interleaved, each over the coordinates in order
   TopKm<KPL_K> top;
   top.init();
   uint64_t kth2 = kEmptyKey;
-  {
+  for (int c0 = 0; c0 < kp; c0 += 64) {
     uint64_t ck[2];
     const float4* xr[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
-      const int c = lane + 32 * h;
+      const int c = c0 + lane + 32 * h;
       ck[h] = c < kp ? cbuf[c] : kEmptyKey;
       // (an id outside the rows can only come from a list the scan did not
       // finish; it is dropped, never dereferenced)
@@ -509,10 +513,15 @@ int sm_count() {
 
 }  // namespace
 
-int tc_kp(int k) { return k <= 10 ? 10 : (k <= 16 ? 16 : 32); }
+int tc_kp(int k, int depth) {
+  // at least k keys per partition, and at least a quarter of the re-rank
+  // depth so that a deep re-rank is not starved by the per-partition cap
+  const int need = std::max(k, (depth + 3) / 4);
+  return need <= 10 ? 10 : (need <= 16 ? 16 : 32);
+}
 int tc_rerank_depth(int k, int factor) {
   const int f = factor > 0 ? factor : 4;
-  return std::min(64, std::max(k, f * k));
+  return std::min(kMaxRerank, std::max(k, f * k));
 }
 
 bool tc_tile_fits(int d, int words_pad, int N, int f8) {
@@ -801,8 +810,8 @@ int tc_merge_rerank(const TcScanArgs& t, const uint8_t* dead, int64_t nq, int k,
   const int nslot = t.qslot ? std::min(TC_SLOTS, std::max(1, (depth + t.kp - 1) / t.kp)) : 0;
   const unsigned grid = (unsigned)((nq + 3) / 4);
   if (t.d % 4 != 0 || t.d > 128) return fail(CAPS_EINVAL, "re-rank needs d % 4 == 0, d <= 128");
-  if (depth > 64) return fail(CAPS_EINVAL, "re-rank depth above 64");
-  const size_t smem = sizeof(float) * 4 * (size_t)t.d + sizeof(uint64_t) * 4 * 128;
+  if (depth > kMaxRerank) return fail(CAPS_EINVAL, "re-rank depth above 256");
+  const size_t smem = sizeof(float) * 4 * (size_t)t.d + sizeof(uint64_t) * 4 * kMaxRerank;
 #define CAPS_MR(MET)                                                                            \
   do {                                                                                          \
     CAPS_CUDA(cudaFuncSetAttribute(k_merge_rerank<MET, 1>,                                      \

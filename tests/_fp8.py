@@ -29,17 +29,21 @@ def scaled_e4m3(a):
     return e4m3((a32 / s[:, None]).astype(np.float32)), s.astype(np.float64)
 
 
-def kp_of(k):
-    return 10 if k <= 10 else (16 if k <= 16 else 32)
+def rerank_depth(k, factor=4):
+    """candidates re-scored exactly per query: factor * k, at most 256"""
+    return min(256, max(k, factor * k))
 
 
-def rerank_depth(k):
-    return min(64, max(k, 4 * k))
+def kp_of(k, depth):
+    """keys per partition: 10, 16 or 32, at least k and a quarter of the depth"""
+    need = max(k, (depth + 3) // 4)
+    return 10 if need <= 10 else (16 if need <= 16 else 32)
 
 
-def search(w, oi, k, m):
+def search(w, oi, k, m, factor=4):
     """ids [nq, k] of the FP8 form (-1 padded)."""
-    KP, R, nb = kp_of(k), rerank_depth(k), w.h + 1
+    R = rerank_depth(k, factor)
+    KP, nb = kp_of(k, R), w.h + 1
     P = O.probe(w.Q, oi.C, m, w.metric)
     S = O.select(oi.tags, w.h, O.Attrs.of(w), P, O.Cons.of(w))
     x8, xs = scaled_e4m3(w.X)

@@ -140,3 +140,22 @@ def test_fp8_rejects_unsupported_d():
             caps.Index.build(w.X, w.A, w.vocab, w.B, h=3, iters=1, init_idx=w.init_idx,
                              prec=caps.FP8)
         assert e.value.code == caps.CAPS_EINVAL
+
+
+@pytest.mark.parametrize("factor,k,m", [(16, 10, 5), (8, 16, 6), (16, 10, 12)])
+def test_fp8_deep_rerank_against_model(factor, k, m):
+    # rerank_factor * k candidates re-scored exactly (up to 256): 160 or 128
+    # here, with 32 keys per partition; the model takes the same rule
+    w = wl(750 + factor + k + m, nq=120)
+    oi = O.build(w.X, O.Attrs.of(w), w.B, w.h, w.iters, w.init_idx, w.metric)
+    gi = caps.Index.build(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.A).cuda(), w.vocab,
+                          w.B, h=w.h, iters=w.iters, metric=w.metric, init_idx=w.init_idx,
+                          prec=caps.FP8, rerank_factor=factor)
+    ids, dist = gi.search(w.Q, w.Qb, k, m)
+    want = _fp8.search(w, oi, k, m, factor=factor)
+    assert float((ids == want).mean()) >= 0.99
+    oids, _, _, _ = O.search(w.X, O.Attrs.of(w), oi, w.Q, O.Cons.of(w), k, m)
+    # a deeper exact re-rank recovers more of the exact neighbours than the
+    # default depth's 0.7 floor on byte data
+    check_against_oracle(w, ids, dist, oids, floor=0.85)
+    gi.close()

@@ -12,7 +12,9 @@ from .synth import (  # noqa: F401
     make_sparse_workload,
     config_small,
     config_sift1m_like,
+    config_sift1m_fields,
     config_learned4m,
+    with_constraints,
     config_sparse2m,
     zipf_probs,
 )

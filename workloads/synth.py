@@ -179,6 +179,19 @@ def make_dense_workload(
         recipe=recipe)
 
 
+def with_constraints(w: Workload, cmin: int, cmax: int, seed: int, sel_range=None,
+                     name: str = "") -> Workload:
+    """The same vectors, attributes and query vectors with new query
+    constraints: each copies cmin..cmax fields from a random data point
+    (cmin = cmax fixes the absence fraction (L - c) / L, Sec. 6.1),
+    rejection-sampled into sel_range when given."""
+    rq = np.random.default_rng(seed)
+    Qb, sel = _dense_constraints(rq, w.A, w.vocab, w.nq, cmin, cmax, sel_range)
+    return dataclasses.replace(w, Qb=Qb, selectivity=sel, name=name or w.name,
+                               recipe=w.recipe + f"; constraints re-drawn: {cmin}-{cmax} copied "
+                                                 f"fields (seed {seed})")
+
+
 def _sparse_labels(rng, N, V, zipf_s, nmax, exponent):
     """1..nmax labels per point, count law P(n) ~ n^-exponent, labels drawn
     without replacement from a bounded Zipf law over V labels."""
@@ -279,6 +292,23 @@ def config_sift1m_like(seed: int = 1002, **over) -> Workload:
     return make_dense_workload(**kw)
 
 
+def config_sift1m_fields(L: int, seed: int = 1002, **over) -> Workload:
+    """The 1M x 128 byte-valued vectors of config_sift1m_like with L
+    attribute fields (vocab 20/50/100 repeating, Zipf s=1.0); queries copy
+    1-3 fields from a random point, selectivity in [0.1%, 30%], so longer
+    attribute vectors leave more fields free (the paper's appendix varies the
+    attribute length L)."""
+    vocab = [(20, 50, 100)[f % 3] for f in range(L)]
+    kw = dict(name=f"sift1m_like_1M_d128_L{L}", N=1_000_000, d=128, ncomp=1000,
+              center=("uniform", 128.0), sigma=16.0, vocab=vocab, zipf_s=1.0,
+              nq=10_000, cmin=1, cmax=min(3, L), B=1024, h=15, iters=20, m=32, k=10, seed=seed,
+              sel_range=(0.001, 0.30), integer=True,
+              recipe=f"as sift1m_like with {L} fields vocab 20/50/100 repeating, 1-3 copied "
+                     "constraints, selectivity in [0.1%,30%]")
+    kw.update(over)
+    return make_dense_workload(**kw)
+
+
 def config_learned4m(seed: int = 1004, **over) -> Workload:
     """4,000,000 x 96 unit-norm vectors (4000 components, centers N(0, I),
     sigma 0.3 before normalisation), inner product, 5 fields vocab
@@ -311,6 +341,7 @@ def config_sparse2m(seed: int = 1005, **over) -> Workload:
 CONFIGS = {
     "small": config_small,
     "sift1m": config_sift1m_like,
+    "sift1m_fields": config_sift1m_fields,
     "learned4m": config_learned4m,
     "sparse2m": config_sparse2m,
 }
