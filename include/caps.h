@@ -140,6 +140,19 @@ typedef struct {
  *                W2 [B*H] | b2 [B] (row-major, output index first); else
  *                U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and zero biases
  *                from SplitMix64(seed + 2).
+ *   mlp_rounds   training rounds (0 = 1).  BLISS's iterative scheme (Sec.
+ *                5.2): after each round every point is assigned anew (see
+ *                mlp_balance_r); before the next round each training point's
+ *                label is recomputed from its same filtered neighbours'
+ *                new partitions, and training continues from the current
+ *                weights (fresh Adam moments).
+ *   mlp_balance_r  0: a point's partition is the argmax of its logits.
+ *                R >= 1 (at most 64 and B, B <= 25600): BLISS's balanced
+ *                assignment -- in id order, each point goes to the
+ *                least-loaded of its R largest logits (ties to the earlier
+ *                of them), loads counted from zero; insertions into such an
+ *                index use the same rule starting from the current
+ *                partition sizes.
  *   init_idx     optional [B] int64: k-means seed point ids (distinct).
  *   centroids    optional [B*d] fp32: fixed first-level centroids; k-means is
  *                skipped and f(x) = best centroid (Alg. 1 first loop).
@@ -160,6 +173,7 @@ typedef struct {
   const int64_t* mlp_sample_idx;
   const int32_t* mlp_sample_cons;
   const float* mlp_init;
+  int32_t mlp_rounds, mlp_balance_r;
 } caps_build_params;
 
 /*
@@ -260,6 +274,9 @@ typedef struct {
   int32_t part;          /* caps_partitioner of the index */
   int32_t mlp_hidden;    /* H of the learned partitioner (0 for k-means) */
   int64_t n_labels;      /* training points of the learned partitioner */
+  int64_t n_label_bins;  /* N when the learned partitioner was built (the
+                            length of CAPS_ARR_LABEL_BINS) */
+  int32_t mlp_balance_r; /* R of the balanced assignment, 0 = argmax */
 } caps_index_info;
 
 int caps_get_info(const caps_index* index, caps_index_info* out);
@@ -283,7 +300,10 @@ enum {
   CAPS_ARR_PERM = 4,
   CAPS_ARR_OFFSETS = 5,
   CAPS_ARR_MLP = 6,     /* [H*d + H + B*H + B] fp32 W1|b1|W2|b2 (MLP index) */
-  CAPS_ARR_LABELS = 7   /* [S*B] fp32 training labels (MLP index) */
+  CAPS_ARR_LABELS = 7,  /* [S*B] fp32 labels of the last training round (MLP index) */
+  CAPS_ARR_LABEL_BINS = 8 /* [N] int32 the partition of every point those labels
+                             were made from (k-means, or the previous round's
+                             assignment) (MLP index) */
 };
 int caps_export(const caps_index* index, int32_t which, void* dst,
                 size_t bytes, void* stream);
@@ -356,6 +376,15 @@ int caps_mlp_train(int32_t d, int32_t H, int32_t B, float* W, const float* X,
  * bias added last, ReLU on the hidden layer. */
 int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W,
                     const float* X, int64_t n, int32_t* out_bin, void* stream);
+
+/* The balanced assignment of BLISS's rounds (Sec. 5.2): each row's R largest
+ * logits (same fp32 logits and tie rule as caps_mlp_assign), then in row
+ * order the least-loaded of them (ties to the earlier), loads starting at
+ * load0 ([B] int64, host or device; NULL = zeros).  1 <= R <= min(64, B),
+ * B <= 25600. */
+int caps_mlp_balance(int32_t d, int32_t H, int32_t B, const float* W, const float* X,
+                     int64_t n, int32_t R, const int64_t* load0, int32_t* out_bin,
+                     void* stream);
 
 /* ---- dynamic insertion ------------------------------------------------------ */
 

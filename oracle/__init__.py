@@ -21,7 +21,7 @@ Function map (paper passage -> function):
   appendix RecallK@K ................ recall
   Sec. 5.2 learned partitioner ...... mlp_forward64, mlp_loss_grad, adam,
                                       mlp_assign32, mlp_logits32, mlp_labels,
-                                      mlp_train, probe_logits
+                                      mlp_train, probe_logits, balanced_assign
 """
 from __future__ import annotations
 
@@ -74,6 +74,7 @@ def lib():
                                   ct.c_double, i32]
         _lib.orc_mlp_assign32.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P]
         _lib.orc_mlp_logits32.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P]
+        _lib.orc_balanced_assign.argtypes = [P, i64, i32, i32, P, P]
     return _lib
 
 
@@ -512,6 +513,18 @@ def probe_logits(Q, net: MLP, m):
     for q in range(Z.shape[0]):
         out[q] = np.lexsort((idx, -Z[q].astype(np.float64)))[:m]
     return out
+
+
+def balanced_assign(top, B, load0=None):
+    """Greedy balanced assignment (BLISS-style rounds): top [n, R] each
+    point's R best partitions, best first; in id order every point goes to
+    its least-loaded candidate (ties to the earlier one).  load0: loads
+    before the first point (default zeros)."""
+    top = _c(top, np.int32)
+    n, R = top.shape
+    bins = np.empty(n, np.int32)
+    lib().orc_balanced_assign(_p(top), n, R, B, _p(_c(load0, np.int64)), _p(bins))
+    return bins
 
 
 def mlp_labels(X, attrs: Attrs, bins, samples, sample_cons, B, k=10, metric=L2):

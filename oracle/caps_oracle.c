@@ -768,6 +768,28 @@ void orc_adam(double* w, const double* g, double* m, double* v, int64_t n, doubl
   }
 }
 
+/* Balanced assignment of the learned partitioner's rounds (BLISS-style, Sec.
+ * 5.2 "iterative learning scheme"): top[i*R .. i*R+R) lists point i's R best
+ * partitions by fp32 logit, best first (ties to the lower partition).
+ * Points are taken in id order; each goes to the candidate with the least
+ * load so far (ties to the earlier candidate) and adds one to its load.
+ * load0 (optional, [B]) gives the loads before the first point. */
+void orc_balanced_assign(const int32_t* top, int64_t n, int R, int B, const int64_t* load0,
+                         int32_t* bins) {
+  int64_t* load = (int64_t*)calloc((size_t)B, sizeof(int64_t));
+  if (load0) memcpy(load, load0, sizeof(int64_t) * (size_t)B);
+  for (int64_t i = 0; i < n; i++) {
+    int32_t best = top[i * R];
+    for (int r = 1; r < R; r++) {
+      const int32_t c = top[i * R + r];
+      if (load[c] < load[best]) best = c;
+    }
+    bins[i] = best;
+    load[best]++;
+  }
+  free(load);
+}
+
 /* fp32 forward in a fixed order (bias, then coordinates in order with one
  * fma each; ReLU), used to take the argmax decision the GPU takes. */
 void orc_mlp_assign32(const float* X, int64_t n, int d, int H, int B, const float* W1,

@@ -23,7 +23,8 @@ CAPS_OK, CAPS_EINVAL, CAPS_ENOMEM, CAPS_ECUDA, CAPS_ETIMEOUT = 0, 1, 2, 3, 4
 L2, IP = 0, 1
 FP32, BF16, FP8 = 0, 1, 2
 KMEANS, MLP = 0, 1
-ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS, ARR_MLP, ARR_LABELS = range(8)
+(ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS, ARR_MLP, ARR_LABELS,
+ ARR_LABEL_BINS) = range(9)
 
 # Every symbol declared in include/caps.h.
 EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "caps_get_info",
@@ -32,7 +33,7 @@ EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "c
            "caps_device_status", "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign", "caps_plan_create",
            "caps_plan_search", "caps_plan_get_info", "caps_plan_free", "caps_alloc_count",
            "caps_inject_alloc_failure", "caps_test_scan_stall", "caps_search_batch_or",
-           "caps_insert")
+           "caps_insert", "caps_mlp_balance")
 
 
 class CapsError(RuntimeError):
@@ -57,7 +58,8 @@ class caps_build_params(ct.Structure):
                 ("mlp_epochs", ct.c_int32), ("init_idx", ct.c_void_p), ("centroids", ct.c_void_p),
                 ("mlp_samples", ct.c_int32), ("mlp_batch", ct.c_int32), ("mlp_lr", ct.c_float),
                 ("mlp_label_k", ct.c_int32), ("mlp_sample_idx", ct.c_void_p),
-                ("mlp_sample_cons", ct.c_void_p), ("mlp_init", ct.c_void_p)]
+                ("mlp_sample_cons", ct.c_void_p), ("mlp_init", ct.c_void_p),
+                ("mlp_rounds", ct.c_int32), ("mlp_balance_r", ct.c_int32)]
 
 
 class caps_stage_times(ct.Structure):
@@ -70,7 +72,8 @@ class caps_index_info(ct.Structure):
     _fields_ = [("N", ct.c_int64), ("d", ct.c_int32), ("B", ct.c_int32), ("h", ct.c_int32),
                 ("L", ct.c_int32), ("metric", ct.c_int32), ("n_codes", ct.c_int64),
                 ("attr_words", ct.c_int32), ("device_bytes", ct.c_int64), ("part", ct.c_int32),
-                ("mlp_hidden", ct.c_int32), ("n_labels", ct.c_int64)]
+                ("mlp_hidden", ct.c_int32), ("n_labels", ct.c_int64),
+                ("n_label_bins", ct.c_int64), ("mlp_balance_r", ct.c_int32)]
 
 
 class caps_plan_info(ct.Structure):
@@ -113,6 +116,7 @@ def lib(path: Optional[str] = None):
     L.caps_mlp_loss_grad.argtypes = [i32, i32, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]
     L.caps_mlp_train.argtypes = [i32, i32, i32, P, P, i64, P, i32, i32, ct.c_float, P, P]
     L.caps_mlp_assign.argtypes = [i32, i32, i32, P, P, i64, P, P]
+    L.caps_mlp_balance.argtypes = [i32, i32, i32, P, P, i64, i32, P, P, P]
     L.caps_plan_create.argtypes = [P, P, i64, ct.POINTER(caps_attrs), i32, i32, i32, P,
                                    ct.POINTER(P)]
     L.caps_plan_search.argtypes = [P, P, i64, ct.POINTER(caps_attrs), P, P, P]
@@ -281,6 +285,20 @@ def mlp_assign(W, d, H, B, X, stream=None):
     return out
 
 
+def mlp_balance(W, d, H, B, X, R, load0=None, stream=None):
+    """caps_mlp_balance: the balanced assignment over each row's R largest
+    logits, loads starting at load0 (zeros when None)."""
+    W = np.ascontiguousarray(W, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    if load0 is not None:
+        load0 = np.ascontiguousarray(load0, np.int64)
+    out = np.empty(X.shape[0], np.int32)
+    _check(lib().caps_mlp_balance(d, H, B, _ptr(W), _ptr(X), X.shape[0], R,
+                                  _ptr(load0) if load0 is not None else None, _ptr(out),
+                                  _stream(stream)))
+    return out
+
+
 class Index:
     """A CAPS index living in GPU memory (caps_build / caps_free)."""
 
@@ -294,7 +312,8 @@ class Index:
     def build(cls, X, A, vocab, B, h=15, iters=20, metric=L2, init_idx=None, centroids=None,
               seed=0, prec=FP32, rerank_factor=0, part=KMEANS, mlp_hidden=0, mlp_epochs=0,
               mlp_samples=0, mlp_batch=0, mlp_lr=0.0, mlp_label_k=0, mlp_sample_idx=None,
-              mlp_sample_cons=None, mlp_init=None, labels=None, stream=None) -> "Index":
+              mlp_sample_cons=None, mlp_init=None, mlp_rounds=0, mlp_balance_r=0, labels=None,
+              stream=None) -> "Index":
         """labels = (sp_off, sp_lab, sp_vocab): label-set attributes instead of
         the dense A / vocab."""
         X = _np_or_keep(X, np.float32)
@@ -309,6 +328,7 @@ class Index:
         p.mlp_hidden, p.mlp_epochs, p.mlp_samples, p.mlp_batch = (mlp_hidden, mlp_epochs,
                                                                   mlp_samples, mlp_batch)
         p.mlp_lr, p.mlp_label_k = mlp_lr, mlp_label_k
+        p.mlp_rounds, p.mlp_balance_r = mlp_rounds, mlp_balance_r
         if mlp_sample_idx is not None:
             mlp_sample_idx = _np_or_keep(mlp_sample_idx, np.int64)
             p.mlp_sample_idx = _ptr(mlp_sample_idx)
@@ -353,6 +373,7 @@ class Index:
         Hm = i.mlp_hidden
         shapes[ARR_MLP] = ((Hm * i.d + Hm + i.B * Hm + i.B,), np.float32)
         shapes[ARR_LABELS] = ((i.n_labels, i.B), np.float32)
+        shapes[ARR_LABEL_BINS] = ((i.n_label_bins,), np.int32)
         shape, dt = shapes[which]
         out = np.empty(shape, dtype=dt)
         _check(lib().caps_export(self._h, which, _ptr(out) if out.size else 1, out.nbytes,

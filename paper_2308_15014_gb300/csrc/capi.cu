@@ -273,6 +273,12 @@ __global__ void k_mlp_cons(const int32_t* __restrict__ A, int L, const int64_t* 
   const int64_t r = t / L, f = t % L;
   cons[t] = keep[t] ? A[samples[r] * L + f] : -1;
 }
+// Points per partition from the (partition, block) offsets.
+__global__ void k_part_loads(const int32_t* __restrict__ offsets, int B, int h,
+                             int64_t* __restrict__ load) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) load[b] = (int64_t)offsets[(int64_t)(b + 1) * (h + 1)] - offsets[(int64_t)b * (h + 1)];
+}
 double u01(uint64_t* st) { return (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0); }
 }  // namespace
 }  // namespace caps
@@ -374,11 +380,34 @@ static int build_mlp(const caps_build_params* p, const float* dX, const int32_t*
     CAPS_CUDA(cudaMemcpyAsync(wbase, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, s));
     CAPS_CUDA(cudaStreamSynchronize(s));
   }
-  if (p->mlp_epochs > 0)
-    if (int rc = mlp_train(ix->mlp, Xs, S, ix->labels, p->mlp_epochs, batch, lr, nullptr, s))
+  // the partitions the first labels were made from: the k-means ones
+  if (int rc = ix->alloc(&ix->label_bins, (size_t)N)) return rc;
+  ix->n_label_bins = N;
+  CAPS_CUDA(cudaMemcpyAsync(ix->label_bins, ix->bin, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+  // rounds (BLISS's iterative scheme): train, assign every point (argmax, or
+  // the balanced assignment over its R largest logits), and before the next
+  // round relabel the training points from their neighbours' new partitions
+  const int rounds = std::max(1, p->mlp_rounds);
+  ix->balance_r = p->mlp_balance_r;
+  for (int r = 0; r < rounds; r++) {
+    if (p->mlp_epochs > 0)
+      if (int rc = mlp_train(ix->mlp, Xs, S, ix->labels, p->mlp_epochs, batch, lr, nullptr, s))
+        return rc;
+    if (ix->balance_r > 0) {
+      if (int rc = mlp_balanced_assign(ix->mlp, dX, N, ix->balance_r, nullptr, ix->bin, scr, s))
+        return rc;
+    } else if (int rc = mlp_assign(ix->mlp, dX, N, ix->bin, scr, s)) {
       return rc;
-  // f(x) = argmax logits for every point
-  if (int rc = mlp_assign(ix->mlp, dX, N, ix->bin, scr, s)) return rc;
+    }
+    if (r + 1 < rounds) {
+      CAPS_CUDA(cudaMemcpyAsync(ix->label_bins, ix->bin, sizeof(int32_t) * N,
+                                cudaMemcpyDeviceToDevice, s));
+      CAPS_CUDA(cudaMemsetAsync(ix->labels, 0, sizeof(float) * S * B, s));
+      k_mlp_labels<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(nid, kq, dS, S, lk, ix->bin, B,
+                                                               ix->labels);
+      CAPS_LAUNCH("k_mlp_labels");
+    }
+  }
   ix->part = CAPS_PART_MLP;
   CAPS_CUDA(cudaStreamSynchronize(s));
   return CAPS_OK;
@@ -451,6 +480,10 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
       return fail(CAPS_EINVAL, "bad MLP parameters");
     if (p->mlp_epochs == 0 && !p->mlp_init)
       return fail(CAPS_EINVAL, "an MLP build needs mlp_epochs > 0 or mlp_init");
+    if (p->mlp_rounds < 0 || p->mlp_rounds > 64) return fail(CAPS_EINVAL, "mlp_rounds must be in [0, 64]");
+    if (p->mlp_balance_r < 0 || p->mlp_balance_r > 64 || p->mlp_balance_r > p->B ||
+        (p->mlp_balance_r > 0 && p->B > 25600))
+      return fail(CAPS_EINVAL, "mlp_balance_r must be in [0, min(64, B)] (B <= 25600 to balance)");
   }
   if (p->prec != CAPS_FP32 && p->prec != CAPS_BF16 && p->prec != CAPS_FP8E4M3)
     return fail(CAPS_EINVAL, "precision must be CAPS_FP32, CAPS_BF16 or CAPS_FP8E4M3");
@@ -685,6 +718,8 @@ extern "C" int caps_get_info(const caps_index* ix, caps_index_info* out) {
   out->part = ix->part;
   out->mlp_hidden = ix->part == CAPS_PART_MLP ? ix->mlp.H : 0;
   out->n_labels = ix->n_labels;
+  out->n_label_bins = ix->n_label_bins;
+  out->mlp_balance_r = ix->balance_r;
   return CAPS_OK;
 }
 
@@ -712,6 +747,11 @@ extern "C" int caps_export(const caps_index* ix, int32_t which, void* dst, size_
       if (ix->part != CAPS_PART_MLP) return fail(CAPS_EINVAL, "not an MLP index");
       src = ix->labels;
       want = sizeof(float) * (size_t)ix->n_labels * ix->B;
+      break;
+    case CAPS_ARR_LABEL_BINS:
+      if (ix->part != CAPS_PART_MLP) return fail(CAPS_EINVAL, "not an MLP index");
+      src = ix->label_bins;
+      want = sizeof(int32_t) * (size_t)ix->n_label_bins;
       break;
     default: return fail(CAPS_EINVAL, "unknown array id");
   }
@@ -1604,6 +1644,36 @@ extern "C" int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W, 
   return CAPS_OK;
 }
 
+extern "C" int caps_mlp_balance(int32_t d, int32_t H, int32_t B, const float* W, const float* X,
+                                int64_t n, int32_t R, const int64_t* load0, int32_t* out_bin,
+                                void* stream) {
+  if (int rc = mlp_dims_ok(d, H, B)) return rc;
+  if (n < 0) return fail(CAPS_EINVAL, "n < 0");
+  if (R < 1 || R > 64 || R > B) return fail(CAPS_EINVAL, "R must be in [1, min(64, B)]");
+  if (B > 25600) return fail(CAPS_EINVAL, "balanced assignment needs B <= 25600");
+  if (n == 0) return CAPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  keep_pool_warm();
+  Scratch scr(s);
+  MlpNet net;
+  net.d = d;
+  net.H = H;
+  net.B = B;
+  const float *dW, *dX;
+  const int64_t* dL = nullptr;
+  if (int rc = stage_in(W, (size_t)net.size(), scr, s, &dW)) return rc;
+  if (int rc = stage_in(X, (size_t)n * d, scr, s, &dX)) return rc;
+  if (load0)
+    if (int rc = stage_in(load0, (size_t)B, scr, s, &dL)) return rc;
+  net.bind(const_cast<float*>(dW));
+  Out<int32_t> ob;
+  if (int rc = ob.init(out_bin, (size_t)n, scr)) return rc;
+  if (int rc = mlp_balanced_assign(net, dX, n, R, dL, ob.dev, scr, s)) return rc;
+  if (int rc = ob.finish(s)) return rc;
+  if (ob.host) CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
 // ---- disjunctive (OR) constraints (Sec. 5.3) -------------------------------
 extern "C" int caps_search_batch_or(const caps_index* ix, const float* Q, int64_t nq,
                                     const caps_or_constraints* oc, int32_t k, int32_t m,
@@ -1774,7 +1844,15 @@ extern "C" int caps_insert(caps_index* ix, const float* X, int64_t n, const caps
     CAPS_CUDA(cudaMemcpyAsync(nw.key, ix->key, (size_t)N0, cudaMemcpyDeviceToDevice, s));
     // f(x) of the new points (the index's partition function), then their
     // blocks under the unchanged tags
-    if (ix->part == CAPS_PART_MLP) {
+    if (ix->part == CAPS_PART_MLP && ix->balance_r > 0) {
+      // the balanced rule, loads starting from the current partition sizes
+      int64_t* load = nullptr;
+      if (int rc = scr.get(&load, (size_t)B)) return rc;
+      k_part_loads<<<(B + 127) / 128, 128, 0, s>>>(ix->offsets, B, h, load);
+      CAPS_LAUNCH("k_part_loads");
+      if (int rc = mlp_balanced_assign(ix->mlp, dX, n, ix->balance_r, load, nw.bin + N0, scr, s))
+        return rc;
+    } else if (ix->part == CAPS_PART_MLP) {
       if (int rc = mlp_assign(ix->mlp, dX, n, nw.bin + N0, scr, s)) return rc;
     } else if (int rc = launch_assign(dX, n, d, ix->C, B, ix->metric, nw.bin + N0, s)) {
       return rc;

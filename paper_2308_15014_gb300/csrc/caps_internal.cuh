@@ -347,6 +347,12 @@ struct MlpNet {
   }
 };
 int mlp_logits(const MlpNet& net, const float* X, int64_t n, float* Hd, float* Z, cudaStream_t s);
+// Balanced assignment of n points (BLISS-style rounds): each point's R
+// largest logits (ties to the lower partition), then in id order the
+// least-loaded of them (ties to the earlier); loads start at load0 ([B]
+// int64 device, or null for zeros).
+int mlp_balanced_assign(const MlpNet& net, const float* X, int64_t n, int R, const int64_t* load0,
+                        int32_t* bin, Scratch& scr, cudaStream_t s);
 int mlp_hidden(const MlpNet& net, const float* X, int64_t n, float* Hd, cudaStream_t s);
 
 // ---- exact top-m probe screened on the tensor cores (probe_tc.cu) ----------
@@ -482,6 +488,9 @@ struct caps_index {
   caps::MlpNet mlp;
   float* labels = nullptr;
   int64_t n_labels = 0;
+  int32_t* label_bins = nullptr;  // [n_label_bins] the partitions the last labels were made from
+  int64_t n_label_bins = 0;       // N at build time
+  int balance_r = 0;              // > 0: BLISS's balanced assignment over R logits
   void* Xb = nullptr;
   float* xn = nullptr;
   float* xs = nullptr;  // e4m3 form: per-row scales [N+4]

@@ -443,4 +443,62 @@ int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs
   return CAPS_OK;
 }
 
+
+namespace {
+// Greedy balanced assignment (one thread, in id order): point i goes to the
+// least-loaded of its R candidates top[i*R..] (best first, ties to the
+// earlier), loads in shared memory starting at load0 (or zero).
+__global__ void __launch_bounds__(32)
+k_balanced_assign(const int32_t* __restrict__ top, int64_t n, int R, int B,
+                  const int64_t* __restrict__ load0, int32_t* __restrict__ bins) {
+  extern __shared__ long long load[];
+  for (int b = threadIdx.x; b < B; b += 32) load[b] = load0 ? load0[b] : 0;
+  __syncwarp();
+  if (threadIdx.x != 0) return;
+  for (int64_t i = 0; i < n; i++) {
+    const int32_t* t = top + i * R;
+    int32_t best = t[0];
+    long long lb = load[best];
+    for (int r = 1; r < R; r++) {
+      const int32_t c = t[r];
+      const long long lc = load[c];
+      if (lc < lb) {
+        best = c;
+        lb = lc;
+      }
+    }
+    bins[i] = best;
+    load[best] = lb + 1;
+  }
+}
+}  // namespace
+
+int mlp_balanced_assign(const MlpNet& net, const float* X, int64_t n, int R, const int64_t* load0,
+                        int32_t* bin, Scratch& scr, cudaStream_t s) {
+  if (n == 0) return CAPS_OK;
+  if (R < 1 || R > 64 || R > net.B) return fail(CAPS_EINVAL, "balance R must be in [1, min(64, B)]");
+  if ((size_t)net.B * sizeof(long long) > 200 * 1024)
+    return fail(CAPS_EINVAL, "balanced assignment needs B <= 25600");
+  // each point's R largest logits (ties to the lower partition), in passes
+  const int64_t per = std::max<int64_t>(1, ((int64_t)1 << 26) / (net.H + net.B));
+  const int64_t pass = std::min(n, per);
+  float *Hd = nullptr, *Z = nullptr;
+  int32_t* top = nullptr;
+  if (int rc = scr.get(&Hd, (size_t)pass * net.H)) return rc;
+  if (int rc = scr.get(&Z, (size_t)pass * net.B)) return rc;
+  if (int rc = scr.get(&top, (size_t)n * R)) return rc;
+  for (int64_t r0 = 0; r0 < n; r0 += pass) {
+    const int64_t rows = std::min(pass, n - r0);
+    if (int rc = mlp_logits(net, X + r0 * net.d, rows, Hd, Z, s)) return rc;
+    if (int rc = launch_topm(Z, rows, net.B, R, CAPS_IP, top + r0 * R, s)) return rc;
+  }
+  const size_t smem = sizeof(long long) * (size_t)net.B;
+  if (smem > 48 * 1024)
+    CAPS_CUDA(cudaFuncSetAttribute(k_balanced_assign, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  k_balanced_assign<<<1, 32, smem, s>>>(top, n, R, net.B, load0, bin);
+  CAPS_LAUNCH("k_balanced_assign");
+  return CAPS_OK;
+}
+
 }  // namespace caps

@@ -133,3 +133,119 @@ def test_learned_partitioner_trains_and_reports_gain():
     # 0.962, m=4 0.956 -> 0.975)
     assert all(rm >= rk for _, rk, rm in rows)
     assert rows[0][2] - rows[0][1] >= 0.1
+
+
+def _net_of(W, d, H, B):
+    return O.MLP(W[:H * d].reshape(H, d), W[H * d:H * d + H],
+                 W[H * d + H:H * d + H + B * H].reshape(B, H), W[H * d + H + B * H:])
+
+
+@pytest.mark.parametrize("R,with_load", [(1, False), (3, False), (5, True), (17, False)])
+def test_balanced_assign_bit_exact_given_weights(R, with_load):
+    # the same fp32 logits and tie rule as the argmax, then the greedy rule
+    rng = np.random.default_rng(40 + R)
+    d, H, B = 24, 40, 17
+    net = rand_net(rng, d, H, B, scale=1.0)
+    X = rng.standard_normal((4000, d)).astype(np.float32)
+    W = caps.mlp_flat(net.W1, net.b1, net.W2, net.b2)
+    load0 = rng.integers(0, 300, B).astype(np.int64) if with_load else None
+    got = caps.mlp_balance(W, d, H, B, X, R, load0=load0)
+    want = O.balanced_assign(O.probe_logits(X, net, R), B, load0=load0)
+    np.testing.assert_array_equal(got, want)
+    if R == 1:
+        np.testing.assert_array_equal(got, O.mlp_assign32(X, net))
+    if R == B:
+        load = np.bincount(got, minlength=B)
+        assert load.max() - load.min() <= 1
+
+
+def test_balanced_rounds_given_weights_equal_oracle():
+    # no training: every round assigns with the given weights, so the label
+    # partitions of the last round and the final partitions are both the
+    # balanced assignment, and the index is the oracle's on those partitions
+    w = _wl(41)
+    rng = np.random.default_rng(41)
+    H, R = 32, 3
+    net = rand_net(rng, w.d, H, w.B, scale=0.02)
+    W = caps.mlp_flat(net.W1, net.b1, net.W2, net.b2)
+    S = 300
+    samp = rng.choice(w.N, S, replace=False)
+    cons = np.where(rng.random((S, 3)) < 0.5, w.A[samp], -1).astype(np.int32)
+    gi = caps.Index.build(w.X, w.A, w.vocab, w.B, h=w.h, iters=w.iters, init_idx=w.init_idx,
+                          part=caps.MLP, mlp_hidden=H, mlp_epochs=0, mlp_init=W, mlp_samples=S,
+                          mlp_sample_idx=samp, mlp_sample_cons=cons, mlp_rounds=3,
+                          mlp_balance_r=R)
+    assert gi.info.mlp_balance_r == R and gi.info.n_label_bins == w.N
+    bins = O.balanced_assign(O.probe_logits(w.X, net, R), w.B)
+    np.testing.assert_array_equal(gi.export(caps.ARR_BIN), bins)
+    np.testing.assert_array_equal(gi.export(caps.ARR_LABEL_BINS), bins)
+    Y = O.mlp_labels(w.X, O.Attrs.of(w), bins, samp, cons, w.B, k=10)
+    np.testing.assert_allclose(gi.export(caps.ARR_LABELS), Y, rtol=1e-6, atol=1e-7)
+    oi = O.build(w.X, O.Attrs.of(w), w.B, w.h, 0, w.init_idx, bins=bins)
+    np.testing.assert_array_equal(gi.export(caps.ARR_TAGS), oi.tags)
+    np.testing.assert_array_equal(gi.export(caps.ARR_PERM), oi.perm)
+    np.testing.assert_array_equal(gi.export(caps.ARR_OFFSETS), oi.offsets)
+    P = O.probe_logits(w.Q, net, 4)
+    ids, dist = gi.search(w.Q, w.Qb, 10, 4)
+    oids, odist, _, _ = O.search(w.X, O.Attrs.of(w), oi, w.Q, O.Cons.of(w), 10, 4, probe_in=P)
+    assert_search_equal(ids, dist, oids, odist, exact=True)
+    gi.close()
+
+
+def test_trained_rounds_relabel_and_balance():
+    # trained over two rounds: the exported labels are the oracle's labels
+    # under the exported label partitions (the first round's assignment, not
+    # k-means), the final partitions are the balanced assignment under the
+    # final weights, and balancing shrinks the largest partition against the
+    # argmax of the same kind of network
+    # (byte-valued rows: the neighbour lists behind the labels are exact)
+    w = _wl(42, N=20_000, d=32, B=24, nq=50)
+    X = torch.from_numpy(w.X).cuda()
+    A = torch.from_numpy(w.A).cuda()
+    H, S, R = 64, 3000, 4
+    rng = np.random.default_rng(42)
+    samp = rng.choice(w.N, S, replace=False)
+    cons = np.where(rng.random((S, 3)) < 0.5, w.A[samp], -1).astype(np.int32)
+    kw = dict(h=w.h, iters=w.iters, init_idx=w.init_idx, part=caps.MLP,
+              mlp_hidden=H, mlp_epochs=10, mlp_samples=S, mlp_batch=500, mlp_lr=1e-3, seed=7,
+              mlp_sample_idx=samp, mlp_sample_cons=cons)
+    bal = caps.Index.build(X, A, w.vocab, w.B, mlp_rounds=2, mlp_balance_r=R, **kw)
+    arg = caps.Index.build(X, A, w.vocab, w.B, **kw)
+    net = _net_of(bal.export(caps.ARR_MLP), w.d, H, w.B)
+    bins = bal.export(caps.ARR_BIN)
+    np.testing.assert_array_equal(bins, O.balanced_assign(O.probe_logits(w.X, net, R), w.B))
+    lbins = bal.export(caps.ARR_LABEL_BINS)
+    C, kbins = O.kmeans(w.X, w.B, w.iters, w.init_idx)
+    assert (lbins != kbins).any()
+    Y = O.mlp_labels(w.X, O.Attrs.of(w), lbins, samp, cons, w.B, k=10)
+    np.testing.assert_allclose(bal.export(caps.ARR_LABELS), Y, rtol=1e-6, atol=1e-7)
+    top_bal = np.bincount(bins, minlength=w.B).max()
+    top_arg = np.bincount(arg.export(caps.ARR_BIN), minlength=w.B).max()
+    print(f"\nlargest partition: argmax {top_arg}, balanced R={R} {top_bal} (mean {w.N // w.B})")
+    assert top_bal < top_arg
+    bal.close()
+    arg.close()
+
+
+def test_insert_into_balanced_index_continues_the_loads():
+    w = _wl(43)
+    rng = np.random.default_rng(43)
+    H, R, n0 = 32, 3, 4500
+    net = rand_net(rng, w.d, H, w.B, scale=0.02)
+    W = caps.mlp_flat(net.W1, net.b1, net.W2, net.b2)
+    init = (np.arange(w.B) * (n0 // w.B)).astype(np.int64)
+    gi = caps.Index.build(w.X[:n0], w.A[:n0], w.vocab, w.B, h=w.h, iters=w.iters, init_idx=init,
+                          part=caps.MLP, mlp_hidden=H, mlp_epochs=0, mlp_init=W, mlp_samples=200,
+                          mlp_balance_r=R)
+    b0 = O.balanced_assign(O.probe_logits(w.X[:n0], net, R), w.B)
+    np.testing.assert_array_equal(gi.export(caps.ARR_BIN), b0)
+    oi = O.build(w.X[:n0], O.Attrs(A=w.A[:n0], vocab=w.vocab), w.B, w.h, 0, init, bins=b0)
+    gi.insert(w.X[n0:], w.A[n0:])
+    bn = O.balanced_assign(O.probe_logits(w.X[n0:], net, R), w.B,
+                           load0=np.bincount(b0, minlength=w.B))
+    oi = O.insert(oi, w.X, O.Attrs.of(w), w.N - n0, bins_new=bn)
+    for which, a in ((caps.ARR_BIN, oi.bin), (caps.ARR_TAGS, oi.tags), (caps.ARR_KEY, oi.key),
+                     (caps.ARR_PERM, oi.perm), (caps.ARR_OFFSETS, oi.offsets)):
+        np.testing.assert_array_equal(gi.export(which), a)
+    assert gi.info.n_label_bins == n0
+    gi.close()

@@ -161,3 +161,38 @@ def test_train_adam_step_counter_runs_across_epochs():
     np.testing.assert_array_equal(w.W1, 0.0)
     np.testing.assert_array_equal(w.b1, 0.0)
     np.testing.assert_array_equal(w.W2, net.W2)
+
+
+def test_balanced_assign_hand_worked():
+    """Three partitions, candidates best first; loads start at zero.
+    p0 (2,0): both empty, the first -> 2 (loads 0,0,1); p1 (2,1): 1 has less
+    -> 1 (0,1,1); p2 (2,1): tie at 1 -> the first, 2 (0,1,2); p3 (0,2): 0
+    -> 0 (1,1,2); p4 (2,0,1): 0 and 1 tie at 1, 0 comes first among them ->
+    0 (2,1,2); p5 (1,2,0): 1 (2,2,2)."""
+    top = [[2, 0, -1], [2, 1, -1], [2, 1, -1], [0, 2, -1], [2, 0, 1], [1, 2, 0]]
+    # rows of R = 3 (the -1 entries are never chosen: rows 0-3 list 2 real
+    # candidates and a third equal to their first)
+    top = np.array([[r[0], r[1], r[2] if r[2] >= 0 else r[0]] for r in top], np.int32)
+    np.testing.assert_array_equal(O.balanced_assign(top, 3), [2, 1, 2, 0, 0, 1])
+    # with loads already in place: partition 2 full, partition 1 next
+    np.testing.assert_array_equal(O.balanced_assign(top[:2], 3, load0=[5, 0, 9]), [0, 1])
+
+
+def test_balanced_assign_special_cases():
+    rng = np.random.default_rng(33)
+    n, B = 997, 13
+    scores = rng.standard_normal((n, B))
+    top = np.argsort(-scores, axis=1, kind="stable").astype(np.int32)
+    # R = 1: the best partition of every point
+    np.testing.assert_array_equal(O.balanced_assign(top[:, :1], B), top[:, 0])
+    # R = B: every partition is a candidate, so the loads end within one
+    bins = O.balanced_assign(top, B)
+    load = np.bincount(bins, minlength=B)
+    assert load.max() - load.min() <= 1
+    # every point lands in one of its candidates, and a larger R never
+    # leaves a larger largest load on this input
+    for R in (2, 4):
+        b = O.balanced_assign(top[:, :R], B)
+        assert all(b[i] in top[i, :R] for i in range(n))
+    assert np.bincount(O.balanced_assign(top[:, :4], B), minlength=B).max() <= \
+        np.bincount(top[:, 0], minlength=B).max()
