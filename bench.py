@@ -74,6 +74,9 @@ def parse():
                          "heights h, constrained-field counts and 10 attribute fields)")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the label-set workload (2M x 128, 10,000 labels, 4,096 queries)")
+    ap.add_argument("--no-learned4m", action="store_true",
+                    help="skip the learned-partitioner workload (4M x 96 inner product, 5 fields, "
+                         "MLP 96 -> 512 -> 1024): k-means vs learned at equal recall, build times")
     return ap.parse_args()
 
 
@@ -572,6 +575,75 @@ def sparse_line(args, caps, torch, flush):
     return out
 
 
+LEARNED4M_M_SWEEP = (1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128)
+
+
+def learned4m_line(args, caps, torch, flush):
+    """The learned-partitioner workload (4M x 96 unit vectors, inner product,
+    5 fields, B = 1024): k-means against the MLP 96 -> 512 -> 1024 trained on
+    filtered-neighbour labels (one round with argmax, and two BLISS rounds
+    with the balanced assignment over 8 logits), all bf16 indexes; per
+    index its build time, the largest partition, the recall@10 / QPS sweep
+    over m and the QPS at recall@10 >= 0.9 (the comparison at equal recall),
+    plus the build's own judge (k-means fallback).  Recall against the
+    oracle's brute force on a 200-query sample."""
+    from workloads import config_learned4m
+    t0 = time.perf_counter()
+    w = config_learned4m()
+    gen_s = time.perf_counter() - t0
+    rng = np.random.default_rng(8)
+    samp = np.sort(rng.choice(w.nq, 200, replace=False))
+    t0 = time.perf_counter()
+    gt = oracle_truth(w, samp)
+    truth_s = time.perf_counter() - t0
+    X = torch.from_numpy(w.X).cuda()
+    A = torch.from_numpy(w.A).cuda()
+    Qd = torch.from_numpy(w.Q).cuda()
+    Qbd = torch.from_numpy(w.Qb).cuda()
+    ids = torch.empty((w.nq, w.k), dtype=torch.int64, device="cuda")
+    dist = torch.empty((w.nq, w.k), dtype=torch.float32, device="cuda")
+    mlp = dict(part=caps.MLP, mlp_hidden=512, mlp_epochs=20, mlp_samples=131072,
+               mlp_batch=4096, mlp_lr=2e-3, mlp_label_k=10, seed=17, mlp_judge_queries=1000,
+               mlp_judge_m=8)
+    variants = (("kmeans", {}), ("learned", mlp),
+                ("learned_balanced", dict(mlp, mlp_rounds=2, mlp_balance_r=8)))
+    out = {"workload": w.name, "N": w.N, "d": w.d, "B": w.B, "metric": "ip",
+           "queries_per_step": w.nq, "generate_s": round(gen_s, 1),
+           "truth_s": round(truth_s, 1), "mlp": "96 -> 512 -> 1024, 131,072 training points, "
+           "20 epochs, 10-NN filtered labels", "paths": {}}
+    for name, extra in variants:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, metric=w.metric,
+                              init_idx=w.init_idx, prec=caps.BF16, **extra)
+        torch.cuda.synchronize()
+        res = {"build_s": round(time.perf_counter() - t0, 2),
+               "largest_partition": int(np.bincount(ix.export(caps.ARR_BIN),
+                                                    minlength=w.B).max()),
+               "mean_partition": w.N // w.B}
+        if extra:
+            i = ix.info
+            res["judge"] = {"queries": 1000, "m": 8,
+                            "recall_kmeans": round(float(i.judge_recall_kmeans), 4),
+                            "recall_learned": round(float(i.judge_recall_mlp), 4),
+                            "kept": "learned" if i.part == caps.MLP else "kmeans"}
+        sweep, chosen = [], None
+        for m in LEARNED4M_M_SWEEP:
+            ix.search(Qd, Qbd, w.k, m, out_ids=ids, out_dist=dist)
+            _, tie = recall_at_k(ids.cpu().numpy()[samp], *gt, w.k, w.X, w.Q[samp], w.metric)
+            ms = time_search(torch, lambda: ix.search(Qd, Qbd, w.k, m, out_ids=ids,
+                                                      out_dist=dist), flush)
+            sweep.append({"m": m, "recall_tie": round(tie, 4), "qps": round(w.nq / (ms / 1e3), 1)})
+            if tie >= 0.9:
+                chosen = sweep[-1]
+                break
+        res["sweep"] = sweep
+        res["at_0.9"] = chosen
+        out["paths"][name] = res
+        ix.close()
+    return out
+
+
 def oracle_index_of(caps, ix, w):
     """The oracle's own index over the partitions of a built library index:
     the oracle runs Alg. 1's second level itself (attribute-frequency trees
@@ -958,6 +1030,8 @@ def run_caps(args):
                                        "mean_rel": float(rel.mean())}}
     sparse = sparse_line(args, caps, torch, flush) if not args.no_sparse and world == 1 else None
     abl = ablations(args, w, caps, torch, flush) if not args.no_ablations and world == 1 else None
+    l4m = learned4m_line(args, caps, torch, flush) if not args.no_learned4m and world == 1 \
+        else None
 
     if rank != 0:
         return 0
@@ -1006,6 +1080,8 @@ def run_caps(args):
         line["label_sets"] = sparse
     if abl is not None:
         line["ablations"] = abl
+    if l4m is not None:
+        line["learned_4m"] = l4m
     print(json.dumps(line, default=_json_default), flush=True)
     for r in res.values():
         r["plan"].close()

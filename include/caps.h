@@ -153,6 +153,16 @@ typedef struct {
  *                of them), loads counted from zero; insertions into such an
  *                index use the same rule starting from the current
  *                partition sizes.
+ *   mlp_judge_queries, mlp_judge_m  k-means as the fallback, exact recall
+ *                as the judge (0 queries = always keep the learned
+ *                partitioner): that many data points (SplitMix64(seed + 5),
+ *                each filtered on its own attributes, each field kept with
+ *                probability 1/2, at least one) are searched with k = 10
+ *                and m = mlp_judge_m on the k-means index and on the learned
+ *                one (fp32 scan); the point itself is left out of its
+ *                results and of its exact filtered neighbours.  The learned
+ *                partitioner is kept unless k-means reaches a higher
+ *                recall@10; both recalls are reported by caps_get_info.
  *   init_idx     optional [B] int64: k-means seed point ids (distinct).
  *   centroids    optional [B*d] fp32: fixed first-level centroids; k-means is
  *                skipped and f(x) = best centroid (Alg. 1 first loop).
@@ -174,6 +184,7 @@ typedef struct {
   const int32_t* mlp_sample_cons;
   const float* mlp_init;
   int32_t mlp_rounds, mlp_balance_r;
+  int32_t mlp_judge_queries, mlp_judge_m;
 } caps_build_params;
 
 /*
@@ -277,6 +288,8 @@ typedef struct {
   int64_t n_label_bins;  /* N when the learned partitioner was built (the
                             length of CAPS_ARR_LABEL_BINS) */
   int32_t mlp_balance_r; /* R of the balanced assignment, 0 = argmax */
+  float judge_recall_kmeans, judge_recall_mlp; /* recall@10 of the build's
+                            judge (mlp_judge_queries), -1 when not judged */
 } caps_index_info;
 
 int caps_get_info(const caps_index* index, caps_index_info* out);

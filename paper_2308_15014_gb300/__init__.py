@@ -59,7 +59,8 @@ class caps_build_params(ct.Structure):
                 ("mlp_samples", ct.c_int32), ("mlp_batch", ct.c_int32), ("mlp_lr", ct.c_float),
                 ("mlp_label_k", ct.c_int32), ("mlp_sample_idx", ct.c_void_p),
                 ("mlp_sample_cons", ct.c_void_p), ("mlp_init", ct.c_void_p),
-                ("mlp_rounds", ct.c_int32), ("mlp_balance_r", ct.c_int32)]
+                ("mlp_rounds", ct.c_int32), ("mlp_balance_r", ct.c_int32),
+                ("mlp_judge_queries", ct.c_int32), ("mlp_judge_m", ct.c_int32)]
 
 
 class caps_stage_times(ct.Structure):
@@ -73,7 +74,8 @@ class caps_index_info(ct.Structure):
                 ("L", ct.c_int32), ("metric", ct.c_int32), ("n_codes", ct.c_int64),
                 ("attr_words", ct.c_int32), ("device_bytes", ct.c_int64), ("part", ct.c_int32),
                 ("mlp_hidden", ct.c_int32), ("n_labels", ct.c_int64),
-                ("n_label_bins", ct.c_int64), ("mlp_balance_r", ct.c_int32)]
+                ("n_label_bins", ct.c_int64), ("mlp_balance_r", ct.c_int32),
+                ("judge_recall_kmeans", ct.c_float), ("judge_recall_mlp", ct.c_float)]
 
 
 class caps_plan_info(ct.Structure):
@@ -312,8 +314,8 @@ class Index:
     def build(cls, X, A, vocab, B, h=15, iters=20, metric=L2, init_idx=None, centroids=None,
               seed=0, prec=FP32, rerank_factor=0, part=KMEANS, mlp_hidden=0, mlp_epochs=0,
               mlp_samples=0, mlp_batch=0, mlp_lr=0.0, mlp_label_k=0, mlp_sample_idx=None,
-              mlp_sample_cons=None, mlp_init=None, mlp_rounds=0, mlp_balance_r=0, labels=None,
-              stream=None) -> "Index":
+              mlp_sample_cons=None, mlp_init=None, mlp_rounds=0, mlp_balance_r=0,
+              mlp_judge_queries=0, mlp_judge_m=0, labels=None, stream=None) -> "Index":
         """labels = (sp_off, sp_lab, sp_vocab): label-set attributes instead of
         the dense A / vocab."""
         X = _np_or_keep(X, np.float32)
@@ -329,6 +331,7 @@ class Index:
                                                                   mlp_samples, mlp_batch)
         p.mlp_lr, p.mlp_label_k = mlp_lr, mlp_label_k
         p.mlp_rounds, p.mlp_balance_r = mlp_rounds, mlp_balance_r
+        p.mlp_judge_queries, p.mlp_judge_m = mlp_judge_queries, mlp_judge_m
         if mlp_sample_idx is not None:
             mlp_sample_idx = _np_or_keep(mlp_sample_idx, np.int64)
             p.mlp_sample_idx = _ptr(mlp_sample_idx)

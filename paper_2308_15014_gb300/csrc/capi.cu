@@ -283,6 +283,116 @@ double u01(uint64_t* st) { return (double)(splitmix64(st) >> 11) * (1.0 / 900719
 }  // namespace
 }  // namespace caps
 
+// Filters of S data points on their own attributes: each field kept with
+// probability 1/2 (SplitMix64(seed), row by row), at least one per point.
+static int draw_cons(const int32_t* dA, int L, const int64_t* dS, int64_t S, uint64_t seed,
+                     Scratch& scr, cudaStream_t s, int32_t** out) {
+  std::vector<uint8_t> keep((size_t)S * L, 0);
+  uint64_t st = seed;
+  for (int64_t r = 0; r < S; r++) {
+    int any = 0;
+    for (int f = 0; f < L; f++) {
+      keep[r * L + f] = u01(&st) < 0.5 ? 1 : 0;
+      any |= keep[r * L + f];
+    }
+    if (!any) keep[r * L + (int)(splitmix64(&st) % (uint64_t)L)] = 1;
+  }
+  uint8_t* dkeep = nullptr;
+  if (int rc = scr.get(&dkeep, (size_t)S * L)) return rc;
+  if (int rc = scr.get(out, (size_t)S * L)) return rc;
+  CAPS_CUDA(cudaMemcpyAsync(dkeep, keep.data(), keep.size(), cudaMemcpyHostToDevice, s));
+  k_mlp_cons<<<(unsigned)((S * L + 255) / 256), 256, 0, s>>>(dA, L, dS, dkeep, S, *out);
+  CAPS_LAUNCH("k_mlp_cons");
+  CAPS_CUDA(cudaStreamSynchronize(s));  // `keep` leaves scope
+  return CAPS_OK;
+}
+
+// The build's judge between k-means and the learned partitioner: held-out
+// data points as queries, filtered on their own attributes, recall@10 of the
+// m-probe search against their exact filtered neighbours (themselves left
+// out).
+namespace {
+constexpr int kJudgeK = 10;
+struct Judge {
+  int64_t J = 0;
+  std::vector<int64_t> qid;    // query point ids
+  const float* Q = nullptr;    // [J*d]
+  const int32_t* cons = nullptr;
+  std::vector<int64_t> exact;  // [J*(kJudgeK+1)]
+};
+}  // namespace
+
+static int judge_prepare(const caps_build_params* p, const float* dX, const int32_t* dA, int64_t N,
+                         int d, int L, Scratch& scr, cudaStream_t s, Judge* jg) {
+  jg->J = std::min<int64_t>(p->mlp_judge_queries, N);
+  jg->qid = floyd_sample(N, jg->J, p->seed + 5);
+  int64_t* dq = nullptr;
+  if (int rc = scr.get(&dq, (size_t)jg->J)) return rc;
+  CAPS_CUDA(cudaMemcpyAsync(dq, jg->qid.data(), sizeof(int64_t) * jg->J, cudaMemcpyHostToDevice, s));
+  float* Q = nullptr;
+  if (int rc = scr.get(&Q, (size_t)jg->J * d)) return rc;
+  if (int rc = mlp_gather_rows(dX, dq, jg->J, d, Q, s)) return rc;
+  int32_t* cons = nullptr;
+  if (int rc = draw_cons(dA, L, dq, jg->J, p->seed + 6, scr, s, &cons)) return rc;
+  jg->Q = Q;
+  jg->cons = cons;
+  return CAPS_OK;
+}
+
+// ids of the judge queries' k+1 best at m probes (fp32 scan)
+static int judge_search(caps_index* ix, const Judge& jg, int m, cudaStream_t s,
+                        std::vector<int64_t>* out) {
+  const int kq = kJudgeK + 1;
+  Scratch scr(s);
+  int64_t* ids = nullptr;
+  float* dist = nullptr;
+  if (int rc = scr.get(&ids, (size_t)jg.J * kq)) return rc;
+  if (int rc = scr.get(&dist, (size_t)jg.J * kq)) return rc;
+  caps_attrs ca;
+  ca.L = ix->meta.L;
+  ca.dense = jg.cons;
+  ca.vocab = nullptr;
+  ca.sp_offsets = nullptr;
+  ca.sp_labels = nullptr;
+  ca.sp_vocab = 0;
+  const int keep_prec = ix->prec;
+  ix->prec = CAPS_FP32;
+  const int rc_s = caps_search_batch(ix, jg.Q, jg.J, &ca, kq, m, ids, dist, s);
+  ix->prec = keep_prec;
+  if (rc_s) return rc_s;
+  out->resize((size_t)jg.J * kq);
+  CAPS_CUDA(cudaMemcpyAsync(out->data(), ids, sizeof(int64_t) * out->size(), cudaMemcpyDeviceToHost, s));
+  CAPS_CUDA(cudaStreamSynchronize(s));
+  return CAPS_OK;
+}
+
+// mean over the queries with a neighbour of |found ∩ exact| / |exact|, both
+// the first 10 valid ids other than the query point itself
+static float judge_recall(const Judge& jg, const std::vector<int64_t>& got) {
+  const int kq = kJudgeK + 1;
+  double sum = 0.0;
+  int64_t cnt = 0;
+  for (int64_t j = 0; j < jg.J; j++) {
+    auto first = [&](const std::vector<int64_t>& v, std::vector<int64_t>* o) {
+      o->clear();
+      for (int t = 0; t < kq && (int)o->size() < kJudgeK; t++) {
+        const int64_t i = v[j * kq + t];
+        if (i >= 0 && i != jg.qid[j]) o->push_back(i);
+      }
+    };
+    std::vector<int64_t> g, f;
+    first(jg.exact, &g);
+    first(got, &f);
+    if (g.empty()) continue;
+    int hit = 0;
+    for (int64_t i : f)
+      for (int64_t e : g) hit += i == e;
+    sum += (double)hit / (double)g.size();
+    cnt++;
+  }
+  return cnt ? (float)(sum / (double)cnt) : 1.f;
+}
+
 // Learned partitioner (Sec. 5.2): labels from exact filtered neighbours over
 // the k-means index, Adam training, f(x) = argmax logits into ix->bin.
 static int build_mlp(const caps_build_params* p, const float* dX, const int32_t* dA, int64_t N,
@@ -309,27 +419,11 @@ static int build_mlp(const caps_build_params* p, const float* dX, const int32_t*
   CAPS_CUDA(cudaMemcpyAsync(dS, samp.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, s));
   // label filters
   const int32_t* dCons = nullptr;
-  int32_t* cons_buf = nullptr;
   if (p->mlp_sample_cons) {
     if (int rc = stage_in(p->mlp_sample_cons, (size_t)S * L, scr, s, &dCons)) return rc;
   } else {
-    std::vector<uint8_t> keep((size_t)S * L, 0);
-    uint64_t st = p->seed + 3;
-    for (int64_t r = 0; r < S; r++) {
-      int any = 0;
-      for (int f = 0; f < L; f++) {
-        keep[r * L + f] = u01(&st) < 0.5 ? 1 : 0;
-        any |= keep[r * L + f];
-      }
-      if (!any) keep[r * L + (int)(splitmix64(&st) % (uint64_t)L)] = 1;
-    }
-    uint8_t* dkeep = nullptr;
-    if (int rc = scr.get(&dkeep, (size_t)S * L)) return rc;
-    if (int rc = scr.get(&cons_buf, (size_t)S * L)) return rc;
-    CAPS_CUDA(cudaMemcpyAsync(dkeep, keep.data(), keep.size(), cudaMemcpyHostToDevice, s));
-    k_mlp_cons<<<(unsigned)((S * L + 255) / 256), 256, 0, s>>>(dA, L, dS, dkeep, S, cons_buf);
-    CAPS_LAUNCH("k_mlp_cons");
-    CAPS_CUDA(cudaStreamSynchronize(s));  // `keep` leaves scope
+    int32_t* cons_buf = nullptr;
+    if (int rc = draw_cons(dA, L, dS, S, p->seed + 3, scr, s, &cons_buf)) return rc;
     dCons = cons_buf;
   }
   // exact filtered neighbours of the training points (m = B, fp32 scan)
@@ -484,6 +578,9 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     if (p->mlp_balance_r < 0 || p->mlp_balance_r > 64 || p->mlp_balance_r > p->B ||
         (p->mlp_balance_r > 0 && p->B > 25600))
       return fail(CAPS_EINVAL, "mlp_balance_r must be in [0, min(64, B)] (B <= 25600 to balance)");
+    if (p->mlp_judge_queries < 0 ||
+        (p->mlp_judge_queries > 0 && (p->mlp_judge_m < 1 || p->mlp_judge_m > p->B)))
+      return fail(CAPS_EINVAL, "mlp_judge_queries >= 0, and mlp_judge_m in [1, B] when judging");
   }
   if (p->prec != CAPS_FP32 && p->prec != CAPS_BF16 && p->prec != CAPS_FP8E4M3)
     return fail(CAPS_EINVAL, "precision must be CAPS_FP32, CAPS_BF16 or CAPS_FP8E4M3");
@@ -642,8 +739,30 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   };
   if (int rc = finish()) return rc;
   if (p->part == CAPS_PART_MLP) {
+    // k-means as the fallback, exact recall as the judge
+    Judge jg;
+    std::vector<int64_t> got;
+    int32_t* kbins = nullptr;
+    const bool judge = p->mlp_judge_queries > 0;
+    if (judge) {
+      if (int rc = judge_prepare(p, dX, dA, N, d, L, scr, s, &jg)) return rc;
+      if (int rc = judge_search(ix, jg, B, s, &jg.exact)) return rc;
+      if (int rc = judge_search(ix, jg, p->mlp_judge_m, s, &got)) return rc;
+      ix->judge_recall[0] = judge_recall(jg, got);
+      if (int rc = scr.get(&kbins, (size_t)N)) return rc;
+      CAPS_CUDA(cudaMemcpyAsync(kbins, ix->bin, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+    }
     if (int rc = build_mlp(p, dX, dA, N, d, meta, s, ix)) return rc;
     if (int rc = finish()) return rc;
+    if (judge) {
+      if (int rc = judge_search(ix, jg, p->mlp_judge_m, s, &got)) return rc;
+      ix->judge_recall[1] = judge_recall(jg, got);
+      if (ix->judge_recall[0] > ix->judge_recall[1]) {
+        CAPS_CUDA(cudaMemcpyAsync(ix->bin, kbins, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+        ix->part = CAPS_PART_KMEANS;
+        if (int rc = finish()) return rc;
+      }
+    }
   }
   if (p->prec == CAPS_BF16) {
     // penalty form when the one-hot code of the packed attribute bits (two
@@ -666,7 +785,7 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   if (int rc = prepare_precision(ix, s)) return rc;
   {
     // the weight side of the screened probe, fixed from here on
-    const bool mlp = p->part == CAPS_PART_MLP;
+    const bool mlp = ix->part == CAPS_PART_MLP;
     const int sK = mlp ? ix->mlp.H : d;
     if (probe_screen_supported(sK, B, 1)) {
       uint16_t* wh = nullptr;
@@ -720,6 +839,8 @@ extern "C" int caps_get_info(const caps_index* ix, caps_index_info* out) {
   out->n_labels = ix->n_labels;
   out->n_label_bins = ix->n_label_bins;
   out->mlp_balance_r = ix->balance_r;
+  out->judge_recall_kmeans = ix->judge_recall[0];
+  out->judge_recall_mlp = ix->judge_recall[1];
   return CAPS_OK;
 }
 

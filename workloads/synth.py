@@ -312,13 +312,17 @@ def config_sift1m_fields(L: int, seed: int = 1002, **over) -> Workload:
 def config_learned4m(seed: int = 1004, **over) -> Workload:
     """4,000,000 x 96 unit-norm vectors (4000 components, centers N(0, I),
     sigma 0.3 before normalisation), inner product, 5 fields vocab
-    10/30/100/300/1000 Zipf s=1.1, B=1024, 10,000 queries with 1-5 constraints."""
+    10/30/100/300/1000 Zipf s=1.1, B=1024, 10,000 queries with 1-5 constraints
+    copied from a random point, rejection-sampled into selectivity [0.1%, 30%]
+    as in the 1M x 128 workload (without it, half of the queries match fewer
+    than 100 points and their neighbours lie in arbitrary partitions)."""
     kw = dict(name="learned_4M_d96_ip", N=4_000_000, d=96, ncomp=4000,
               center=("normal", 1.0), sigma=0.3, vocab=[10, 30, 100, 300, 1000],
               zipf_s=1.1, nq=10_000, cmin=1, cmax=5, B=1024, h=15, iters=20, m=32,
-              k=10, seed=seed, normalize=True, metric=1,
+              k=10, seed=seed, normalize=True, metric=1, sel_range=(0.001, 0.30),
               recipe="mixture 4000 comps, centers N(0,I), sigma 0.3, L2-normalised; "
-                     "Zipf(1.1) fields 10/30/100/300/1000; 1-5 copied constraints")
+                     "Zipf(1.1) fields 10/30/100/300/1000; 1-5 copied constraints, "
+                     "selectivity in [0.1%,30%]")
     kw.update(over)
     return make_dense_workload(**kw)
 
