@@ -70,6 +70,10 @@ def lib():
         _lib.orc_mlp_forward64.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P, P]
         _lib.orc_mlp_loss_grad.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P, P, P, P, P]
         _lib.orc_mlp_loss_grad.restype = ct.c_double
+        _lib.orc_mlp_loss_grad_bf16.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P, P, P, P, P]
+        _lib.orc_mlp_loss_grad_bf16.restype = ct.c_double
+        _lib.orc_bf16.argtypes = [ct.c_double]
+        _lib.orc_bf16.restype = ct.c_double
         _lib.orc_adam.argtypes = [P, P, P, P, i64, ct.c_double, ct.c_double, ct.c_double,
                                   ct.c_double, i32]
         _lib.orc_mlp_assign32.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P]
@@ -465,16 +469,24 @@ def mlp_forward64(X, net: MLP):
     return Z, Hd
 
 
-def mlp_loss_grad(X, Y, net: MLP):
-    """Mean softmax cross-entropy and its fp64 gradients (gW1, gb1, gW2, gb2)."""
+def round_bf16(v):
+    """Nearest bf16 value (ties to even) of each element, as fp64."""
+    f = np.vectorize(lib().orc_bf16, otypes=[np.float64])
+    return f(np.asarray(v, np.float64))
+
+
+def mlp_loss_grad(X, Y, net: MLP, bf16=False):
+    """Mean softmax cross-entropy and its fp64 gradients (gW1, gb1, gW2, gb2).
+    bf16: the step with bf16 weights and activations -- every operand of a
+    matrix product rounded to bf16, products summed exactly."""
     X = _c(X, np.float32)
     Y = _c(Y, np.float32)
     d, H, B = net.dims
     n64 = net.astype(np.float64)
     g = MLP(np.empty((H, d)), np.empty(H), np.empty((B, H)), np.empty(B))
-    loss = lib().orc_mlp_loss_grad(_p(X), X.shape[0], d, H, B, _p(n64.W1), _p(n64.b1),
-                                   _p(n64.W2), _p(n64.b2), _p(Y), _p(g.W1), _p(g.b1), _p(g.W2),
-                                   _p(g.b2))
+    fn = lib().orc_mlp_loss_grad_bf16 if bf16 else lib().orc_mlp_loss_grad
+    loss = fn(_p(X), X.shape[0], d, H, B, _p(n64.W1), _p(n64.b1), _p(n64.W2), _p(n64.b2), _p(Y),
+              _p(g.W1), _p(g.b1), _p(g.W2), _p(g.b2))
     return loss, g
 
 
@@ -548,12 +560,15 @@ def mlp_labels(X, attrs: Attrs, bins, samples, sample_cons, B, k=10, metric=L2):
     return Y
 
 
-def mlp_train(X, Y, net: MLP, epochs, batch, lr, order=None):
+def mlp_train(X, Y, net: MLP, epochs, batch, lr, order=None, bf16=False):
     """Adam on the mean cross-entropy, fp64, minibatches in the given order
-    (default: sample order); returns the trained net and the loss per step."""
+    (default: sample order); returns the trained net and the loss per step.
+    bf16: each step's gradients from the bf16 step (mlp_loss_grad), the
+    fp64 weights being the masters."""
     X = _c(X, np.float32)
     Y = _c(Y, np.float32)
-    w = net.astype(np.float64)
+    # a copy: the caller's net is not updated in place
+    w = MLP(*(np.array(a, dtype=np.float64, copy=True) for a in (net.W1, net.b1, net.W2, net.b2)))
     params = [w.W1, w.b1, w.W2, w.b2]
     ms = [np.zeros_like(a) for a in params]
     vs = [np.zeros_like(a) for a in params]
@@ -563,7 +578,7 @@ def mlp_train(X, Y, net: MLP, epochs, batch, lr, order=None):
         idx = np.arange(n) if order is None else np.asarray(order[e])
         for b0 in range(0, n, batch):
             sel = idx[b0:b0 + batch]
-            loss, g = mlp_loss_grad(X[sel], Y[sel], w)
+            loss, g = mlp_loss_grad(X[sel], Y[sel], w, bf16=bf16)
             t += 1
             for a, ga, ma, va in zip(params, [g.W1, g.b1, g.W2, g.b2], ms, vs):
                 adam(a, np.ascontiguousarray(ga), ma, va, lr, t)

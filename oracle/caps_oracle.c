@@ -757,6 +757,99 @@ double orc_mlp_loss_grad(const float* X, int64_t n, int d, int H, int B,
   return loss / (double)n;
 }
 
+/* Nearest bf16 value of v (8 significant bits, ties to the even one): with
+ * v = m 2^e, 1/2 <= |m| < 1, the result is rint(m 2^8) 2^(e-8).  Finite
+ * values inside the bf16 normal range only. */
+double orc_bf16(double v) {
+  if (v == 0.0 || !isfinite(v)) return v;
+  int e;
+  const double m = frexp(v, &e);
+  return ldexp(nearbyint(ldexp(m, 8)), e - 8);
+}
+
+/* The training step with bf16 weights and activations (the learned
+ * partitioner's "BF16 weights with FP32 master weights" form): the same mean
+ * softmax cross-entropy, with every operand of a matrix product rounded to
+ * bf16 first -- x and W1 in W1 x, the hidden activations h and W2 in W2 h,
+ * dz and h in the W2 gradient, dz and W2 in the back-propagated dh, dh and x
+ * in the W1 gradient -- each product then summed exactly (fp64 here).  Biases,
+ * the ReLU mask, the softmax and the bias gradients (sums of the unrounded dz
+ * and dh) stay at full precision.  The masters (W1, b1, W2, b2) are what the
+ * optimizer updates. */
+double orc_mlp_loss_grad_bf16(const float* X, int64_t n, int d, int H, int B,
+                              const double* W1, const double* b1, const double* W2,
+                              const double* b2, const float* Y, double* gW1, double* gb1,
+                              double* gW2, double* gb2) {
+  double* w1 = (double*)malloc(sizeof(double) * (size_t)H * d);
+  double* w2 = (double*)malloc(sizeof(double) * (size_t)B * H);
+  double* x = (double*)malloc(sizeof(double) * (size_t)d);
+  double* h = (double*)malloc(sizeof(double) * (size_t)H);   /* relu(W1 x + b1) */
+  double* hr = (double*)malloc(sizeof(double) * (size_t)H);  /* bf16(h) */
+  double* z = (double*)malloc(sizeof(double) * (size_t)B);
+  double* dz = (double*)malloc(sizeof(double) * (size_t)B);
+  double* dzr = (double*)malloc(sizeof(double) * (size_t)B);
+  double* dh = (double*)malloc(sizeof(double) * (size_t)H);
+  for (int64_t i = 0; i < (int64_t)H * d; i++) w1[i] = orc_bf16(W1[i]);
+  for (int64_t i = 0; i < (int64_t)B * H; i++) w2[i] = orc_bf16(W2[i]);
+  memset(gW1, 0, sizeof(double) * (size_t)H * d);
+  memset(gb1, 0, sizeof(double) * (size_t)H);
+  memset(gW2, 0, sizeof(double) * (size_t)B * H);
+  memset(gb2, 0, sizeof(double) * (size_t)B);
+  double loss = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    for (int j = 0; j < d; j++) x[j] = orc_bf16((double)X[i * d + j]);
+    for (int u = 0; u < H; u++) {
+      double a = 0.0;
+      for (int j = 0; j < d; j++) a += w1[(int64_t)u * d + j] * x[j];
+      a += b1[u];
+      h[u] = a > 0.0 ? a : 0.0;
+      hr[u] = orc_bf16(h[u]);
+    }
+    for (int c = 0; c < B; c++) {
+      double a = 0.0;
+      for (int u = 0; u < H; u++) a += w2[(int64_t)c * H + u] * hr[u];
+      z[c] = a + b2[c];
+    }
+    double mx = z[0];
+    for (int c = 1; c < B; c++) mx = z[c] > mx ? z[c] : mx;
+    double se = 0.0;
+    for (int c = 0; c < B; c++) se += exp(z[c] - mx);
+    const double lse = mx + log(se);
+    double ysum = 0.0;
+    for (int c = 0; c < B; c++) ysum += (double)Y[i * B + c];
+    for (int c = 0; c < B; c++) {
+      const double p = exp(z[c] - lse);
+      loss -= (double)Y[i * B + c] * (z[c] - lse);
+      dz[c] = (p * ysum - (double)Y[i * B + c]) / (double)n;
+      dzr[c] = orc_bf16(dz[c]);
+    }
+    for (int c = 0; c < B; c++) {
+      gb2[c] += dz[c];
+      for (int u = 0; u < H; u++) gW2[(int64_t)c * H + u] += dzr[c] * hr[u];
+    }
+    for (int u = 0; u < H; u++) {
+      double a = 0.0;
+      for (int c = 0; c < B; c++) a += dzr[c] * w2[(int64_t)c * H + u];
+      dh[u] = h[u] > 0.0 ? a : 0.0;
+    }
+    for (int u = 0; u < H; u++) {
+      gb1[u] += dh[u];
+      const double r = orc_bf16(dh[u]);
+      for (int j = 0; j < d; j++) gW1[(int64_t)u * d + j] += r * x[j];
+    }
+  }
+  free(w1);
+  free(w2);
+  free(x);
+  free(h);
+  free(hr);
+  free(z);
+  free(dz);
+  free(dzr);
+  free(dh);
+  return loss / (double)n;
+}
+
 /* Adam (Kingma & Ba 2015) with bias correction; t counts from 1. */
 void orc_adam(double* w, const double* g, double* m, double* v, int64_t n, double lr,
               double beta1, double beta2, double eps, int t) {

@@ -196,3 +196,182 @@ def test_balanced_assign_special_cases():
         assert all(b[i] in top[i, :R] for i in range(n))
     assert np.bincount(O.balanced_assign(top[:, :4], B), minlength=B).max() <= \
         np.bincount(top[:, 0], minlength=B).max()
+
+
+def _bf16_by_bits(v32):
+    """fp32 -> bf16 by the bit pattern: add 0x7fff plus the lowest kept bit
+    to the 32-bit word and clear the low 16 bits (round to nearest, ties to
+    even), an independent way to the same rounding."""
+    u = np.asarray(v32, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_rounding_matches_the_bit_rule():
+    rng = np.random.default_rng(50)
+    v = (rng.standard_normal(4000) * np.exp2(rng.integers(-20, 20, 4000))).astype(np.float32)
+    # exact halfway cases between neighbouring bf16 values: ties go to even
+    half = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 3 * (1 + 2.0 ** -8),
+                     1 + 2.0 ** -8 + 2.0 ** -20], np.float32)
+    v = np.concatenate([v, half, np.float32([0.0, 1.0, -2.5, 65504.0])])
+    np.testing.assert_array_equal(O.round_bf16(v), _bf16_by_bits(v))
+    assert O.round_bf16([1 + 2.0 ** -8])[0] == 1.0
+    assert O.round_bf16([1 + 3 * 2.0 ** -8])[0] == 1 + 2.0 ** -6
+
+
+def _dyadic_net(rng, d, H, B):
+    """Weights on a coarse dyadic grid: every product and sum of the forward
+    pass below is exact in bf16 and fp64 alike."""
+    q = lambda shape, s: (rng.integers(-4, 5, shape) * s).astype(np.float64)
+    return O.MLP(q((H, d), 0.125), q(H, 0.125), q((B, H), 0.0625), q(B, 0.25))
+
+
+def test_bf16_step_equals_fp64_forward_when_operands_are_representable():
+    # x in {-2..2}/2, weights on 1/8 and 1/16 grids: h and z are exact, so the
+    # loss and the bias gradient of the output layer (unrounded dz) are the
+    # fp64 step's, bit for bit; the other gradients use bf16(dz) and differ
+    rng = np.random.default_rng(51)
+    d, H, B, n = 5, 6, 7, 9
+    net = _dyadic_net(rng, d, H, B)
+    X = (rng.integers(-2, 3, (n, d)) * 0.5).astype(np.float32)
+    Y = np.eye(B, dtype=np.float32)[rng.integers(0, B, n)]
+    l64, g64 = O.mlp_loss_grad(X, Y, net)
+    l16, g16 = O.mlp_loss_grad(X, Y, net, bf16=True)
+    assert l16 == l64
+    np.testing.assert_array_equal(g16.b2, g64.b2)
+
+
+def test_bf16_step_exact_when_dz_is_representable():
+    # W2 = 0, b2 = 0 and B = 4: p = 1/4 for every row, one-hot labels and
+    # n = 2 give dz in {1/8, -3/8} (exact in bf16); h is exact (dyadic x and
+    # W1), so gW2 = dz^T h equals the fp64 step's, and dh = W2^T dz = 0
+    rng = np.random.default_rng(52)
+    d, H, B, n = 3, 5, 4, 2
+    net = _dyadic_net(rng, d, H, B)
+    net.W2[:] = 0.0
+    net.b2[:] = 0.0
+    X = (rng.integers(-2, 3, (n, d)) * 0.5).astype(np.float32)
+    Y = np.eye(B, dtype=np.float32)[[1, 3]]
+    l64, g64 = O.mlp_loss_grad(X, Y, net)
+    l16, g16 = O.mlp_loss_grad(X, Y, net, bf16=True)
+    assert l16 == l64 == np.log(4.0)
+    np.testing.assert_array_equal(g16.W2, g64.W2)
+    assert np.abs(g64.W2).max() > 0
+    np.testing.assert_array_equal(g16.W1, 0.0)
+    np.testing.assert_array_equal(g16.b1, 0.0)
+
+
+def test_bf16_step_within_the_rounding_error_of_fp64():
+    # every product operand carries a relative error of at most 2^-9, and a
+    # gradient entry goes through at most four such roundings on each path
+    # (x, W1 -> h -> bf16(h); z -> dz -> bf16(dz); W2; bf16(dh)): about 1 %
+    # first-order per term; in norm over a whole gradient the bf16 step stays
+    # within 3 % of the fp64 one, while a transposed operand, a wrong sign or
+    # a dropped term lands at O(100 %)
+    rng = np.random.default_rng(53)
+    d, H, B, n = 16, 24, 11, 64
+    net = _net(rng, d, H, B, scale=0.5)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = rng.random((n, B)).astype(np.float32)
+    Y /= Y.sum(1, keepdims=True)
+    l64, g64 = O.mlp_loss_grad(X, Y, net)
+    l16, g16 = O.mlp_loss_grad(X, Y, net, bf16=True)
+    assert abs(l16 - l64) <= 0.01 * abs(l64)
+    for name in ("W1", "b1", "W2", "b2"):
+        a, b = getattr(g16, name), getattr(g64, name)
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert 0.0 < rel < 0.03, (name, rel)
+
+
+def test_bf16_training_on_a_bias_only_net_is_the_fp64_training():
+    # W1 = 0, b1 = 0: every hidden unit is relu(0) = 0, so bf16(h) = 0, the
+    # W2 gradient and dh vanish and only the unrounded bias gradient moves;
+    # the bf16 training's trajectory is then the fp64 one exactly
+    rng = np.random.default_rng(54)
+    d, H = 3, 4
+    net = _bias_only_net(d, H, [0.0, 1.0, 2.5, -1.0], rng)
+    X = rng.standard_normal((5, d)).astype(np.float32)
+    Y = rng.random((5, 4)).astype(np.float32)
+    Y /= Y.sum(1, keepdims=True)
+    w64, l64 = O.mlp_train(X, Y, net, epochs=2, batch=2, lr=0.05)
+    w16, l16 = O.mlp_train(X, Y, net, epochs=2, batch=2, lr=0.05, bf16=True)
+    assert l16 == l64
+    for a, b in ((w16.W1, w64.W1), (w16.b1, w64.b1), (w16.W2, w64.W2), (w16.b2, w64.b2)):
+        np.testing.assert_array_equal(a, b)
+    assert np.abs(w64.b2 - net.b2).max() > 0.05
+
+
+def test_bf16_step_rounds_the_backward_operands():
+    # one row, W1 = 0 and b1 = e_u: h = e_u exactly, so z = bf16(W2)[:, u] + b2
+    # (the loss is the fp64 loss of the net with W2 rounded), the W2 gradient's
+    # column u is bf16(dz) while the b2 gradient is dz itself, and with a
+    # one-hot x = e_j the W1 gradient's column j is bf16(dh) while the b1
+    # gradient is dh itself
+    rng = np.random.default_rng(55)
+    d, H, B, u, j = 4, 6, 9, 2, 1
+    net = O.MLP(np.zeros((H, d)), np.zeros(H), rng.standard_normal((B, H)), rng.standard_normal(B))
+    net.b1[u] = 1.0
+    X = np.zeros((1, d), np.float32)
+    X[0, j] = 1.0
+    Y = rng.random((1, B)).astype(np.float32)
+    Y /= Y.sum()
+    l16, g16 = O.mlp_loss_grad(X, Y, net, bf16=True)
+    rounded = O.MLP(net.W1, net.b1, O.round_bf16(net.W2), net.b2)
+    l64, _ = O.mlp_loss_grad(X, Y, rounded)
+    assert l16 == l64
+    assert (O.round_bf16(g16.b2) != g16.b2).any()  # dz unrounded in the bias gradient
+    np.testing.assert_array_equal(g16.W2[:, u], O.round_bf16(g16.b2))
+    np.testing.assert_array_equal(np.delete(g16.W2, u, axis=1), 0.0)
+    assert O.round_bf16(g16.b1)[u] != g16.b1[u]
+    np.testing.assert_array_equal(g16.W1[:, j], O.round_bf16(g16.b1))
+    np.testing.assert_array_equal(np.delete(g16.W1, j, axis=1), 0.0)
+    np.testing.assert_array_equal(np.delete(g16.b1, u), 0.0)
+
+
+def test_bf16_step_rounds_the_inputs_and_activations():
+    # one row x in [1, 2), W1 = I, b1 = 2^-12 (below half a bf16 step of 1):
+    # h = bf16(x) + 2^-12 and bf16(h) = bf16(x).  With W2, b2 on a dyadic
+    # grid the bf16 step's loss is the fp64 loss of the rounded row with
+    # b1 = 0 (not that of the row itself); the W2 gradient is
+    # bf16(dz) bf16(x)^T and the W1 gradient bf16(dh) bf16(x)^T, with dz and
+    # dh the (unrounded) bias gradients
+    rng = np.random.default_rng(56)
+    d = H = 6
+    B = 5
+    net = _dyadic_net(rng, d, H, B)
+    net.W1[:] = np.eye(H)
+    net.b1[:] = 2.0 ** -12
+    X = (1.0 + rng.random((1, d))).astype(np.float32)
+    Xr = O.round_bf16(X)
+    assert (Xr != X).all()
+    Y = np.eye(B, dtype=np.float32)[[3]]
+    l16, g16 = O.mlp_loss_grad(X, Y, net, bf16=True)
+    plain = O.MLP(net.W1, np.zeros(H), net.W2, net.b2)
+    lr_, _ = O.mlp_loss_grad(Xr.astype(np.float32), Y, plain)
+    lx, _ = O.mlp_loss_grad(X, Y, plain)
+    assert l16 == lr_ and l16 != lx
+    np.testing.assert_array_equal(g16.W2, np.outer(O.round_bf16(g16.b2), Xr[0]))
+    np.testing.assert_array_equal(g16.W1, np.outer(O.round_bf16(g16.b1), Xr[0]))
+
+
+def test_bf16_step_only_sees_the_rounded_rows_and_weights():
+    # rounding is idempotent: the bf16 step of a net and rows equals, bit for
+    # bit, the bf16 step of the same net with W1 and W2 rounded beforehand
+    # and of the rounded rows -- and differs from the fp64 step.  A product
+    # operand left unrounded makes the two disagree.
+    rng = np.random.default_rng(57)
+    d, H, B, n = 6, 9, 7, 12
+    net = _net(rng, d, H, B, scale=0.7)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = rng.random((n, B)).astype(np.float32)
+    Y /= Y.sum(1, keepdims=True)
+    l16, g16 = O.mlp_loss_grad(X, Y, net, bf16=True)
+    pre = O.MLP(O.round_bf16(net.W1), net.b1, O.round_bf16(net.W2), net.b2)
+    lp, gp = O.mlp_loss_grad(O.round_bf16(X).astype(np.float32), Y, pre, bf16=True)
+    assert l16 == lp
+    for name in ("W1", "b1", "W2", "b2"):
+        np.testing.assert_array_equal(getattr(g16, name), getattr(gp, name))
+    for name in ("W1", "W2"):  # the pre-rounding did change the weights
+        assert (getattr(pre, name) != getattr(net, name)).any()
+    l64, _ = O.mlp_loss_grad(X, Y, net)
+    assert l16 != l64
