@@ -153,6 +153,9 @@ typedef struct {
  *                of them), loads counted from zero; insertions into such an
  *                index use the same rule starting from the current
  *                partition sizes.
+ *   mlp_bf16     1: train with bf16 weights and activations on the tensor
+ *                cores, fp32 master weights (caps_mlp_train_bf16); 0: the
+ *                fp32 step.  Assignment and probing use the fp32 weights.
  *   mlp_judge_queries, mlp_judge_m  k-means as the fallback, exact recall
  *                as the judge (0 queries = always keep the learned
  *                partitioner): that many data points (SplitMix64(seed + 5),
@@ -185,6 +188,7 @@ typedef struct {
   const float* mlp_init;
   int32_t mlp_rounds, mlp_balance_r;
   int32_t mlp_judge_queries, mlp_judge_m;
+  int32_t mlp_bf16;
 } caps_build_params;
 
 /*
@@ -383,6 +387,23 @@ int caps_mlp_loss_grad(int32_t d, int32_t H, int32_t B, const float* W1,
 int caps_mlp_train(int32_t d, int32_t H, int32_t B, float* W, const float* X,
                    int64_t n, const float* Y, int32_t epochs, int32_t batch,
                    float lr, float* losses, void* stream);
+
+/* The same step and training with bf16 weights and activations and fp32
+ * master weights (the weights the optimizer updates): every matrix product
+ * runs on the tensor cores with bf16 operands and fp32 accumulation --
+ * H = relu(bf16(X) bf16(W1)^T + b1), Z = bf16(H) bf16(W2)^T + b2,
+ * gW2 = bf16(dZ)^T bf16(H), dH = bf16(dZ) bf16(W2) where H > 0,
+ * gW1 = bf16(dH)^T bf16(X) -- while the biases, the softmax and the bias
+ * gradients (fp32 column sums of dZ and dH) stay fp32.  CAPS_ETIMEOUT if a
+ * bounded device wait expired. */
+int caps_mlp_loss_grad_bf16(int32_t d, int32_t H, int32_t B, const float* W1,
+                            const float* b1, const float* W2, const float* b2,
+                            const float* X, int64_t n, const float* Y, float* gW1,
+                            float* gb1, float* gW2, float* gb2, float* loss,
+                            void* stream);
+int caps_mlp_train_bf16(int32_t d, int32_t H, int32_t B, float* W, const float* X,
+                        int64_t n, const float* Y, int32_t epochs, int32_t batch,
+                        float lr, float* losses, void* stream);
 
 /* f(x) = argmax of the logits (ties to the lower partition) for n rows;
  * every logit accumulates its products in index order with one fma each,

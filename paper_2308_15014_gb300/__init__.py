@@ -33,7 +33,7 @@ EXPORTS = ("caps_build", "caps_search_batch", "caps_free", "caps_last_error", "c
            "caps_device_status", "caps_mlp_loss_grad", "caps_mlp_train", "caps_mlp_assign", "caps_plan_create",
            "caps_plan_search", "caps_plan_get_info", "caps_plan_free", "caps_alloc_count",
            "caps_inject_alloc_failure", "caps_test_scan_stall", "caps_search_batch_or",
-           "caps_insert", "caps_mlp_balance")
+           "caps_insert", "caps_mlp_balance", "caps_mlp_loss_grad_bf16", "caps_mlp_train_bf16")
 
 
 class CapsError(RuntimeError):
@@ -60,7 +60,8 @@ class caps_build_params(ct.Structure):
                 ("mlp_label_k", ct.c_int32), ("mlp_sample_idx", ct.c_void_p),
                 ("mlp_sample_cons", ct.c_void_p), ("mlp_init", ct.c_void_p),
                 ("mlp_rounds", ct.c_int32), ("mlp_balance_r", ct.c_int32),
-                ("mlp_judge_queries", ct.c_int32), ("mlp_judge_m", ct.c_int32)]
+                ("mlp_judge_queries", ct.c_int32), ("mlp_judge_m", ct.c_int32),
+                ("mlp_bf16", ct.c_int32)]
 
 
 class caps_stage_times(ct.Structure):
@@ -117,6 +118,8 @@ def lib(path: Optional[str] = None):
     L.caps_device_status.argtypes = [P, P]
     L.caps_mlp_loss_grad.argtypes = [i32, i32, i32, P, P, P, P, P, i64, P, P, P, P, P, P, P]
     L.caps_mlp_train.argtypes = [i32, i32, i32, P, P, i64, P, i32, i32, ct.c_float, P, P]
+    L.caps_mlp_loss_grad_bf16.argtypes = L.caps_mlp_loss_grad.argtypes
+    L.caps_mlp_train_bf16.argtypes = L.caps_mlp_train.argtypes
     L.caps_mlp_assign.argtypes = [i32, i32, i32, P, P, i64, P, P]
     L.caps_mlp_balance.argtypes = [i32, i32, i32, P, P, i64, i32, P, P, P]
     L.caps_plan_create.argtypes = [P, P, i64, ct.POINTER(caps_attrs), i32, i32, i32, P,
@@ -251,8 +254,9 @@ def mlp_flat(W1, b1, W2, b2):
                                                 np.ravel(b2)]).astype(np.float32))
 
 
-def mlp_loss_grad(W1, b1, W2, b2, X, Y, stream=None):
-    """caps_mlp_loss_grad: loss and fp32 gradients (gW1, gb1, gW2, gb2)."""
+def mlp_loss_grad(W1, b1, W2, b2, X, Y, stream=None, bf16=False):
+    """caps_mlp_loss_grad (bf16: caps_mlp_loss_grad_bf16): loss and fp32
+    gradients (gW1, gb1, gW2, gb2)."""
     W1, b1, W2, b2 = (np.ascontiguousarray(a, np.float32) for a in (W1, b1, W2, b2))
     X = np.ascontiguousarray(X, np.float32)
     Y = np.ascontiguousarray(Y, np.float32)
@@ -260,21 +264,23 @@ def mlp_loss_grad(W1, b1, W2, b2, X, Y, stream=None):
     B = W2.shape[0]
     g = [np.empty_like(a) for a in (W1, b1, W2, b2)]
     loss = ct.c_float()
-    _check(lib().caps_mlp_loss_grad(d, H, B, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2), _ptr(X),
-                                    X.shape[0], _ptr(Y), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]),
-                                    _ptr(g[3]), ct.byref(loss), _stream(stream)))
+    fn = lib().caps_mlp_loss_grad_bf16 if bf16 else lib().caps_mlp_loss_grad
+    _check(fn(d, H, B, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2), _ptr(X), X.shape[0], _ptr(Y),
+              _ptr(g[0]), _ptr(g[1]), _ptr(g[2]), _ptr(g[3]), ct.byref(loss), _stream(stream)))
     return float(loss.value), g
 
 
-def mlp_train(W, d, H, B, X, Y, epochs, batch, lr, stream=None):
-    """caps_mlp_train on a flat W1|b1|W2|b2 copy; returns (W, losses)."""
+def mlp_train(W, d, H, B, X, Y, epochs, batch, lr, stream=None, bf16=False):
+    """caps_mlp_train (bf16: caps_mlp_train_bf16) on a flat W1|b1|W2|b2 copy;
+    returns (W, losses)."""
     W = np.array(W, np.float32, copy=True)
     X = np.ascontiguousarray(X, np.float32)
     Y = np.ascontiguousarray(Y, np.float32)
     steps = epochs * ((X.shape[0] + batch - 1) // batch)
     losses = np.zeros(max(1, steps), np.float32)
-    _check(lib().caps_mlp_train(d, H, B, _ptr(W), _ptr(X), X.shape[0], _ptr(Y), epochs, batch,
-                                lr, _ptr(losses), _stream(stream)))
+    fn = lib().caps_mlp_train_bf16 if bf16 else lib().caps_mlp_train
+    _check(fn(d, H, B, _ptr(W), _ptr(X), X.shape[0], _ptr(Y), epochs, batch, lr, _ptr(losses),
+              _stream(stream)))
     return W, losses[:steps]
 
 
@@ -315,7 +321,8 @@ class Index:
               seed=0, prec=FP32, rerank_factor=0, part=KMEANS, mlp_hidden=0, mlp_epochs=0,
               mlp_samples=0, mlp_batch=0, mlp_lr=0.0, mlp_label_k=0, mlp_sample_idx=None,
               mlp_sample_cons=None, mlp_init=None, mlp_rounds=0, mlp_balance_r=0,
-              mlp_judge_queries=0, mlp_judge_m=0, labels=None, stream=None) -> "Index":
+              mlp_judge_queries=0, mlp_judge_m=0, mlp_bf16=0, labels=None,
+              stream=None) -> "Index":
         """labels = (sp_off, sp_lab, sp_vocab): label-set attributes instead of
         the dense A / vocab."""
         X = _np_or_keep(X, np.float32)
@@ -332,6 +339,7 @@ class Index:
         p.mlp_lr, p.mlp_label_k = mlp_lr, mlp_label_k
         p.mlp_rounds, p.mlp_balance_r = mlp_rounds, mlp_balance_r
         p.mlp_judge_queries, p.mlp_judge_m = mlp_judge_queries, mlp_judge_m
+        p.mlp_bf16 = mlp_bf16
         if mlp_sample_idx is not None:
             mlp_sample_idx = _np_or_keep(mlp_sample_idx, np.int64)
             p.mlp_sample_idx = _ptr(mlp_sample_idx)

@@ -485,7 +485,8 @@ static int build_mlp(const caps_build_params* p, const float* dX, const int32_t*
   ix->balance_r = p->mlp_balance_r;
   for (int r = 0; r < rounds; r++) {
     if (p->mlp_epochs > 0)
-      if (int rc = mlp_train(ix->mlp, Xs, S, ix->labels, p->mlp_epochs, batch, lr, nullptr, s))
+      if (int rc = mlp_train(ix->mlp, Xs, S, ix->labels, p->mlp_epochs, batch, lr, nullptr, s,
+                             p->mlp_bf16 != 0))
         return rc;
     if (ix->balance_r > 0) {
       if (int rc = mlp_balanced_assign(ix->mlp, dX, N, ix->balance_r, nullptr, ix->bin, scr, s))
@@ -1664,10 +1665,10 @@ static int mlp_dims_ok(int32_t d, int32_t H, int32_t B) {
   return CAPS_OK;
 }
 
-extern "C" int caps_mlp_loss_grad(int32_t d, int32_t H, int32_t B, const float* W1,
-                                  const float* b1, const float* W2, const float* b2,
-                                  const float* X, int64_t n, const float* Y, float* gW1,
-                                  float* gb1, float* gW2, float* gb2, float* loss, void* stream) {
+static int mlp_loss_grad_entry(int32_t d, int32_t H, int32_t B, const float* W1, const float* b1,
+                               const float* W2, const float* b2, const float* X, int64_t n,
+                               const float* Y, float* gW1, float* gb1, float* gW2, float* gb2,
+                               float* loss, void* stream, bool bf16) {
   if (int rc = mlp_dims_ok(d, H, B)) return rc;
   if (n < 1) return fail(CAPS_EINVAL, "n must be >= 1");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1703,7 +1704,18 @@ extern "C" int caps_mlp_loss_grad(int32_t d, int32_t H, int32_t B, const float* 
   g.b2 = o4.dev;
   float* dl = nullptr;
   if (int rc = scr.get(&dl, 1)) return rc;
-  if (int rc = mlp_loss_grad(net, dX, n, dY, &g, dl, scr, s)) return rc;
+  int32_t* err = nullptr;
+  if (bf16) {
+    if (int rc = scr.get(&err, 1)) return rc;
+    CAPS_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    if (int rc = mlp_loss_grad_bf16(net, dX, nullptr, n, dY, &g, dl, err, scr, s)) return rc;
+    int32_t he = 0;
+    CAPS_CUDA(cudaMemcpyAsync(&he, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CAPS_CUDA(cudaStreamSynchronize(s));
+    if (he) return fail(CAPS_ETIMEOUT, "a bounded device wait expired in the bf16 step");
+  } else if (int rc = mlp_loss_grad(net, dX, n, dY, &g, dl, scr, s)) {
+    return rc;
+  }
   if (int rc = o1.finish(s)) return rc;
   if (int rc = o2.finish(s)) return rc;
   if (int rc = o3.finish(s)) return rc;
@@ -1715,9 +1727,26 @@ extern "C" int caps_mlp_loss_grad(int32_t d, int32_t H, int32_t B, const float* 
   return CAPS_OK;
 }
 
-extern "C" int caps_mlp_train(int32_t d, int32_t H, int32_t B, float* W, const float* X,
-                              int64_t n, const float* Y, int32_t epochs, int32_t batch, float lr,
-                              float* losses, void* stream) {
+extern "C" int caps_mlp_loss_grad(int32_t d, int32_t H, int32_t B, const float* W1,
+                                  const float* b1, const float* W2, const float* b2,
+                                  const float* X, int64_t n, const float* Y, float* gW1,
+                                  float* gb1, float* gW2, float* gb2, float* loss, void* stream) {
+  return mlp_loss_grad_entry(d, H, B, W1, b1, W2, b2, X, n, Y, gW1, gb1, gW2, gb2, loss, stream,
+                             false);
+}
+
+extern "C" int caps_mlp_loss_grad_bf16(int32_t d, int32_t H, int32_t B, const float* W1,
+                                       const float* b1, const float* W2, const float* b2,
+                                       const float* X, int64_t n, const float* Y, float* gW1,
+                                       float* gb1, float* gW2, float* gb2, float* loss,
+                                       void* stream) {
+  return mlp_loss_grad_entry(d, H, B, W1, b1, W2, b2, X, n, Y, gW1, gb1, gW2, gb2, loss, stream,
+                             true);
+}
+
+static int mlp_train_entry(int32_t d, int32_t H, int32_t B, float* W, const float* X, int64_t n,
+                           const float* Y, int32_t epochs, int32_t batch, float lr, float* losses,
+                           void* stream, bool bf16) {
   if (int rc = mlp_dims_ok(d, H, B)) return rc;
   if (n < 1 || epochs < 0 || batch < 1 || !(lr > 0.f)) return fail(CAPS_EINVAL, "bad training arguments");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1735,10 +1764,22 @@ extern "C" int caps_mlp_train(int32_t d, int32_t H, int32_t B, float* W, const f
   const float *dX, *dY;
   if (int rc = stage_in(X, (size_t)n * d, scr, s, &dX)) return rc;
   if (int rc = stage_in(Y, (size_t)n * B, scr, s, &dY)) return rc;
-  if (int rc = mlp_train(net, dX, n, dY, epochs, batch, lr, losses, s)) return rc;
+  if (int rc = mlp_train(net, dX, n, dY, epochs, batch, lr, losses, s, bf16)) return rc;
   if (int rc = ow.finish(s)) return rc;
   CAPS_CUDA(cudaStreamSynchronize(s));
   return CAPS_OK;
+}
+
+extern "C" int caps_mlp_train(int32_t d, int32_t H, int32_t B, float* W, const float* X,
+                              int64_t n, const float* Y, int32_t epochs, int32_t batch, float lr,
+                              float* losses, void* stream) {
+  return mlp_train_entry(d, H, B, W, X, n, Y, epochs, batch, lr, losses, stream, false);
+}
+
+extern "C" int caps_mlp_train_bf16(int32_t d, int32_t H, int32_t B, float* W, const float* X,
+                                   int64_t n, const float* Y, int32_t epochs, int32_t batch,
+                                   float lr, float* losses, void* stream) {
+  return mlp_train_entry(d, H, B, W, X, n, Y, epochs, batch, lr, losses, stream, true);
 }
 
 extern "C" int caps_mlp_assign(int32_t d, int32_t H, int32_t B, const float* W, const float* X,

@@ -379,8 +379,18 @@ int mlp_assign(const MlpNet& net, const float* X, int64_t n, int32_t* bin, Scrat
                cudaStream_t s);
 int mlp_loss_grad(const MlpNet& net, const float* X, int64_t n, const float* Y, MlpNet* grad,
                   float* loss_dev, Scratch& scr, cudaStream_t s);
+// The training step with bf16 weights and activations on the tensor cores
+// (fp32 masters in net): Xb optional bf16 rows [n, ceil(d/64)*64] of X.
+int mlp_loss_grad_bf16(const MlpNet& net, const float* X, const void* Xb, int64_t n,
+                       const float* Y, MlpNet* grad, float* loss_dev, int32_t* err, Scratch& scr,
+                       cudaStream_t s);
 int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs, int batch,
-              float lr, float* losses_host, cudaStream_t s);
+              float lr, float* losses_host, cudaStream_t s, bool bf16 = false);
+// D[M, N] (fp32, row stride N) = A[M, Kt] . B[N, Kt]^T, bf16 operands in rows
+// of Kt elements (Kt a multiple of 64, 16-byte aligned bases); tcgen05 tiles
+// of 128 x 256; a bounded wait that expires sets *err.
+int bf16_gemm_nt(const void* A, int64_t M, const void* Bm, int N, int Kt, float* D, int32_t* err,
+                 cudaStream_t s);
 int mlp_gather_rows(const float* X, const int64_t* idx, int64_t n, int d, float* out,
                     cudaStream_t s);
 

@@ -11,6 +11,8 @@
 #include <climits>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "caps_internal.cuh"
 
 namespace caps {
@@ -311,6 +313,72 @@ int colsum(const float* D, int n, int ncol, float* out, Scratch& scr, cudaStream
   return CAPS_OK;
 }
 
+// ---- the bf16 training step ----
+// bf16 copy of fp32 [rows, cols]: out [rows, ldo], columns past cols zero
+__global__ void k_to_bf16(const float* __restrict__ src, int64_t rows, int cols, int ldo,
+                          __nv_bfloat16* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * ldo) return;
+  const int64_t r = t / ldo;
+  const int c = (int)(t % ldo);
+  out[t] = __float2bfloat16_rn(c < cols ? src[r * cols + c] : 0.f);
+}
+// bf16 transpose of fp32 [rows, cols]: out [cols, ldo], out[c][r] = src[r][c],
+// columns r >= rows zero; 32 x 32 tiles through shared memory
+__global__ void __launch_bounds__(256)
+k_to_bf16_t(const float* __restrict__ src, int64_t rows, int cols, int64_t ldo,
+            __nv_bfloat16* __restrict__ out) {
+  __shared__ float t[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+#pragma unroll
+  for (int k = 0; k < 32; k += 8) {
+    const int64_t r = r0 + ty + k;
+    const int c = c0 + tx;
+    t[ty + k][tx] = (r < rows && c < cols) ? src[r * cols + c] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 32; k += 8) {
+    const int c = c0 + ty + k;
+    const int64_t r = r0 + tx;
+    if (c < cols && r < ldo) out[(int64_t)c * ldo + r] = __float2bfloat16_rn(t[tx][ty + k]);
+  }
+}
+// P [n, H] <- relu(P + b) (EPI 1) or P + b (EPI 2), in place
+template <int EPI>
+__global__ void k_bias_rows(float* __restrict__ P, int64_t n, int H, const float* __restrict__ b) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * H) return;
+  float v = P[t] + b[t % H];
+  if (EPI == 1) v = v > 0.f ? v : 0.f;
+  P[t] = v;
+}
+// D <- D where the hidden unit was on (Hd > 0), else 0
+__global__ void k_relu_mask(float* __restrict__ D, const float* __restrict__ Hd, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) D[t] = Hd[t] > 0.f ? D[t] : 0.f;
+}
+
+int to_bf16(const float* src, int64_t rows, int cols, int ldo, __nv_bfloat16* out, cudaStream_t s) {
+  const int64_t tot = rows * ldo;
+  if (tot == 0) return CAPS_OK;
+  k_to_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, rows, cols, ldo, out);
+  CAPS_LAUNCH("k_to_bf16");
+  return CAPS_OK;
+}
+int to_bf16_t(const float* src, int64_t rows, int cols, int64_t ldo, __nv_bfloat16* out,
+              cudaStream_t s) {
+  if (cols == 0 || ldo == 0) return CAPS_OK;
+  const dim3 g((unsigned)((ldo + 31) / 32), (unsigned)((cols + 31) / 32));
+  if (g.y > 65535) return fail(CAPS_EINVAL, "transpose: too many columns");
+  k_to_bf16_t<<<g, 256, 0, s>>>(src, rows, cols, ldo, out);
+  CAPS_LAUNCH("k_to_bf16_t");
+  return CAPS_OK;
+}
+inline int pad64(int64_t v) { return (int)((v + 63) / 64 * 64); }
+
 }  // namespace
 
 // logits Z [n, B] of rows X [n, d]; Hd [n, H] scratch.  Rows in chunks.
@@ -386,6 +454,73 @@ int mlp_loss_grad(const MlpNet& net, const float* X, int64_t n, const float* Y, 
   return CAPS_OK;
 }
 
+// Every product on the tensor cores with bf16 operands and fp32
+// accumulation: H = relu(X W1^T + b1), Z = bf16(H) W2^T + b2, dZ from the
+// softmax, gW2 = bf16(dZ)^T bf16(H), dH = (bf16(dZ) W2) where H > 0,
+// gW1 = bf16(dH)^T bf16(X); the bias gradients are fp32 column sums of dZ
+// and dH.  Operands are padded with zeros to multiples of 64 along the
+// contracted index.
+int mlp_loss_grad_bf16(const MlpNet& net, const float* X, const void* Xb_in, int64_t n,
+                       const float* Y, MlpNet* grad, float* loss_dev, int32_t* err, Scratch& scr,
+                       cudaStream_t s) {
+  if (n < 1 || n > INT_MAX) return fail(CAPS_EINVAL, "mlp: batch size out of range");
+  using bf = __nv_bfloat16;
+  const int d = net.d, H = net.H, B = net.B, nn = (int)n;
+  const int dp = pad64(d), Hp = pad64(H), Bp = pad64(B), np_ = pad64(n);
+  bf *W1b, *W2b, *W2bT, *Hb, *HbT, *dZb, *dZbT, *dHbT, *XbT;
+  float *Hd, *Z, *dZ, *dH, *rl;
+  if (int rc = scr.get(&W1b, (size_t)H * dp)) return rc;
+  if (int rc = scr.get(&W2b, (size_t)B * Hp)) return rc;
+  if (int rc = scr.get(&W2bT, (size_t)H * Bp)) return rc;
+  if (int rc = scr.get(&Hb, (size_t)n * Hp)) return rc;
+  if (int rc = scr.get(&HbT, (size_t)H * np_)) return rc;
+  if (int rc = scr.get(&dZb, (size_t)n * Bp)) return rc;
+  if (int rc = scr.get(&dZbT, (size_t)B * np_)) return rc;
+  if (int rc = scr.get(&dHbT, (size_t)H * np_)) return rc;
+  if (int rc = scr.get(&XbT, (size_t)d * np_)) return rc;
+  if (int rc = scr.get(&Hd, (size_t)n * H)) return rc;
+  if (int rc = scr.get(&Z, (size_t)n * B)) return rc;
+  if (int rc = scr.get(&dZ, (size_t)n * B)) return rc;
+  if (int rc = scr.get(&dH, (size_t)n * H)) return rc;
+  if (int rc = scr.get(&rl, (size_t)n)) return rc;
+  const bf* Xb = static_cast<const bf*>(Xb_in);
+  if (!Xb) {
+    bf* xb = nullptr;
+    if (int rc = scr.get(&xb, (size_t)n * dp)) return rc;
+    if (int rc = to_bf16(X, n, d, dp, xb, s)) return rc;
+    Xb = xb;
+  }
+  // bf16 copies of the master weights, and of the rows transposed
+  if (int rc = to_bf16(net.W1, H, d, dp, W1b, s)) return rc;
+  if (int rc = to_bf16(net.W2, B, H, Hp, W2b, s)) return rc;
+  if (int rc = to_bf16_t(net.W2, B, H, Bp, W2bT, s)) return rc;
+  if (int rc = to_bf16_t(X, n, d, np_, XbT, s)) return rc;
+  // forward
+  if (int rc = bf16_gemm_nt(Xb, n, W1b, H, dp, Hd, err, s)) return rc;
+  k_bias_rows<1><<<(unsigned)((n * H + 255) / 256), 256, 0, s>>>(Hd, n, H, net.b1);
+  CAPS_LAUNCH("k_bias_rows");
+  if (int rc = to_bf16(Hd, n, H, Hp, Hb, s)) return rc;
+  if (int rc = to_bf16_t(Hd, n, H, np_, HbT, s)) return rc;
+  if (int rc = bf16_gemm_nt(Hb, n, W2b, B, Hp, Z, err, s)) return rc;
+  k_bias_rows<2><<<(unsigned)((n * B + 255) / 256), 256, 0, s>>>(Z, n, B, net.b2);
+  CAPS_LAUNCH("k_bias_rows");
+  k_softmax_xent<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(Z, Y, nn, B, 1.f / (float)n, dZ, rl);
+  CAPS_LAUNCH("k_softmax_xent");
+  if (int rc = colsum(rl, nn, 1, loss_dev, scr, s)) return rc;
+  // backward
+  if (int rc = to_bf16(dZ, n, B, Bp, dZb, s)) return rc;
+  if (int rc = to_bf16_t(dZ, n, B, np_, dZbT, s)) return rc;
+  if (int rc = bf16_gemm_nt(dZbT, B, HbT, H, np_, grad->W2, err, s)) return rc;
+  if (int rc = colsum(dZ, nn, B, grad->b2, scr, s)) return rc;
+  if (int rc = bf16_gemm_nt(dZb, n, W2bT, H, Bp, dH, err, s)) return rc;
+  k_relu_mask<<<(unsigned)((n * H + 255) / 256), 256, 0, s>>>(dH, Hd, n * H);
+  CAPS_LAUNCH("k_relu_mask");
+  if (int rc = to_bf16_t(dH, n, H, np_, dHbT, s)) return rc;
+  if (int rc = bf16_gemm_nt(dHbT, H, XbT, d, np_, grad->W1, err, s)) return rc;
+  if (int rc = colsum(dH, nn, H, grad->b1, scr, s)) return rc;
+  return CAPS_OK;
+}
+
 int mlp_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr, int t,
              cudaStream_t s) {
   const double b1 = 0.9, b2 = 0.999;
@@ -406,7 +541,7 @@ int mlp_gather_rows(const float* X, const int64_t* idx, int64_t n, int d, float*
 
 // Minibatches of `batch` samples in sample order, the same every epoch.
 int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs, int batch,
-              float lr, float* losses_host, cudaStream_t s) {
+              float lr, float* losses_host, cudaStream_t s, bool bf16) {
   const int64_t P1 = (int64_t)net.H * net.d, P2 = (int64_t)net.B * net.H;
   const int64_t total = P1 + net.H + P2 + net.B;
   Scratch scr(s);
@@ -416,6 +551,16 @@ int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs
   if (int rc = scr.get(&mo, (size_t)total)) return rc;
   if (int rc = scr.get(&ve, (size_t)total)) return rc;
   if (int rc = scr.get(&loss, 1)) return rc;
+  // bf16 form: the rows' bf16 copy once, a flag for the tensor-core waits
+  __nv_bfloat16* Xb = nullptr;
+  int32_t* err = nullptr;
+  const int dp = pad64(net.d);
+  if (bf16) {
+    if (int rc = scr.get(&Xb, (size_t)n * dp)) return rc;
+    if (int rc = to_bf16(X, n, net.d, dp, Xb, s)) return rc;
+    if (int rc = scr.get(&err, 1)) return rc;
+    CAPS_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+  }
   CAPS_CUDA(cudaMemsetAsync(mo, 0, sizeof(float) * total, s));
   CAPS_CUDA(cudaMemsetAsync(ve, 0, sizeof(float) * total, s));
   MlpNet gr = net;
@@ -429,8 +574,14 @@ int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs
     for (int64_t b0 = 0; b0 < n; b0 += batch) {
       const int64_t nb = std::min<int64_t>(batch, n - b0);
       Scratch step(s);
-      if (int rc = mlp_loss_grad(net, X + b0 * net.d, nb, Y + b0 * net.B, &gr, loss, step, s))
+      if (bf16) {
+        if (int rc = mlp_loss_grad_bf16(net, X + b0 * net.d, Xb + b0 * dp, nb, Y + b0 * net.B,
+                                        &gr, loss, err, step, s))
+          return rc;
+      } else if (int rc = mlp_loss_grad(net, X + b0 * net.d, nb, Y + b0 * net.B, &gr, loss, step,
+                                        s)) {
         return rc;
+      }
       t++;
       if (int rc = mlp_adam(w, g, mo, ve, total, lr, t, s)) return rc;
       if (losses_host) {
@@ -439,6 +590,12 @@ int mlp_train(MlpNet& net, const float* X, int64_t n, const float* Y, int epochs
         CAPS_CUDA(cudaStreamSynchronize(s));
       }
     }
+  }
+  if (bf16) {
+    int32_t he = 0;
+    CAPS_CUDA(cudaMemcpyAsync(&he, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CAPS_CUDA(cudaStreamSynchronize(s));
+    if (he) return fail(CAPS_ETIMEOUT, "a bounded device wait expired in the bf16 training");
   }
   return CAPS_OK;
 }

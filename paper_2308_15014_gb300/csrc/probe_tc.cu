@@ -543,6 +543,23 @@ int encode_bf16_map(void* map, const void* ptr, int64_t rows, int64_t cols) {
 
 }  // namespace
 
+int bf16_gemm_nt(const void* A, int64_t M, const void* Bm, int N, int Kt, float* D, int32_t* err,
+                 cudaStream_t s) {
+  if (M == 0 || N == 0) return CAPS_OK;
+  if (M < 0 || N < 0 || Kt < 64 || Kt % 64 != 0 || ((uintptr_t)A & 15) || ((uintptr_t)Bm & 15))
+    return fail(CAPS_EINVAL, "bf16 gemm: bad sizes or alignment");
+  alignas(64) CUtensorMap mA, mB;
+  if (int rc = encode_bf16_map(&mA, A, M, Kt)) return rc;
+  if (int rc = encode_bf16_map(&mB, Bm, N, Kt)) return rc;
+  const size_t smem = pg_smem_bytes();
+  CAPS_CUDA(cudaFuncSetAttribute(k_pgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const dim3 grid((unsigned)((N + PG_N - 1) / PG_N), (unsigned)((M + PG_M - 1) / PG_M));
+  if (grid.y > 65535) return fail(CAPS_EINVAL, "bf16 gemm: too many rows in one call");
+  k_pgemm<<<grid, PG_T, smem, s>>>(mA, mB, (int)M, N, Kt, D, err);
+  CAPS_LAUNCH("k_pgemm");
+  return CAPS_OK;
+}
+
 bool probe_screen_supported(int K, int B, int m) { return m >= 1 && m <= 64 && m <= B && K >= 1 && K <= 2048; }
 
 size_t probe_weights_elems(int K, int B) { return (size_t)B * 3 * (size_t)((K + 63) / 64 * 64); }

@@ -294,3 +294,68 @@ def test_judge_keeps_the_trained_network_and_falls_back_to_kmeans():
     np.testing.assert_array_equal(a[1], b[1])
     for ix in (km, ml, ex, fb):
         ix.close()
+
+
+def test_bf16_step_matches_the_bf16_oracle():
+    # tensor-core products of bf16 operands with fp32 accumulation against
+    # the oracle's bf16 step (same operand rounding, exact sums).  Two
+    # effects separate them: fp32 accumulation (about K 2^-24 relative) and
+    # an intermediate (h, dz, dh) computed in fp32 that lies within its fp32
+    # error of a bf16 rounding boundary and rounds to the neighbouring bf16
+    # value -- one term off by 2^-8 of itself, at most about 4e-3 of the
+    # largest gradient entry.  Against the fp64 step (no rounding) the gap is
+    # many times larger.
+    rng = np.random.default_rng(60)
+    d, H, B, n = 21, 70, 33, 130   # ragged against the 64-wide padding and 128-row tiles
+    net = rand_net(rng, d, H, B)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = rng.random((n, B)).astype(np.float32)
+    Y /= Y.sum(1, keepdims=True)
+    loss, g = caps.mlp_loss_grad(net.W1, net.b1, net.W2, net.b2, X, Y, bf16=True)
+    oloss, og = O.mlp_loss_grad(X, Y, net, bf16=True)
+    _, o64 = O.mlp_loss_grad(X, Y, net)
+    assert abs(loss - oloss) <= 1e-5 * abs(oloss)
+    for a, name in zip(g, ("W1", "b1", "W2", "b2")):
+        b, c = getattr(og, name), getattr(o64, name)
+        np.testing.assert_allclose(a, b, rtol=1e-3, atol=5e-3 * np.abs(b).max(), err_msg=name)
+        near = np.linalg.norm(a - b)
+        assert near <= 1e-3 * np.linalg.norm(b), (name, near / np.linalg.norm(b))
+        if name in ("W1", "W2"):
+            assert near < 0.1 * np.linalg.norm(a - c), name
+
+
+def test_bf16_training_follows_the_bf16_oracle():
+    rng = np.random.default_rng(61)
+    d, H, B, n = 12, 24, 9, 96
+    net = rand_net(rng, d, H, B)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = rng.random((n, B)).astype(np.float32)
+    Y /= Y.sum(1, keepdims=True)
+    W0 = caps.mlp_flat(net.W1, net.b1, net.W2, net.b2)
+    Wg, lg = caps.mlp_train(W0, d, H, B, X, Y, epochs=3, batch=32, lr=1e-2, bf16=True)
+    on, lo = O.mlp_train(X, Y, net, epochs=3, batch=32, lr=1e-2, bf16=True)
+    np.testing.assert_allclose(lg, lo, rtol=2e-3)
+    Wo = caps.mlp_flat(on.W1, on.b1, on.W2, on.b2)
+    # Adam's normalised steps turn a gradient entry's sign near zero into a
+    # full step either way: compare the trajectories in norm, against how far
+    # the weights moved
+    assert np.linalg.norm(Wg - Wo) <= 0.05 * np.linalg.norm(Wo - W0)
+    assert lg[-1] < lg[0]
+
+
+def test_bf16_trained_partitioner_gains_over_kmeans():
+    w = _wl(21, N=20_000, d=32, B=24, nq=300, metric=1, normalize=True, integer=False)
+    X = torch.from_numpy(w.X).cuda()
+    A = torch.from_numpy(w.A).cuda()
+    km = caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, metric=1,
+                          init_idx=w.init_idx)
+    ml = caps.Index.build(X, A, w.vocab, w.B, h=w.h, iters=w.iters, metric=1,
+                          init_idx=w.init_idx, part=caps.MLP, mlp_hidden=64, mlp_epochs=20,
+                          mlp_samples=4000, mlp_batch=500, mlp_lr=3e-3, seed=7, mlp_bf16=1)
+    gt, _, g64, cnt = O.bruteforce(w.X, O.Attrs.of(w), w.Q, O.Cons.of(w), 10, metric=1)
+    rk = O.recall(km.search(w.Q, w.Qb, 10, 1)[0], gt, g64, cnt, 10, X=w.X, Q=w.Q, metric=1)[1]
+    rm = O.recall(ml.search(w.Q, w.Qb, 10, 1)[0], gt, g64, cnt, 10, X=w.X, Q=w.Q, metric=1)[1]
+    print(f"\nrecall@10 at m=1: k-means {rk:.3f}, learned (bf16 training) {rm:.3f}")
+    assert rm - rk >= 0.1
+    km.close()
+    ml.close()
