@@ -32,7 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = ("filtered QPS at recall@10>=0.9 (learned partitioner + BF16 tensor-core path; "
-          "plain FP32 k-means path alongside)")
+          "plain FP32 k-means paths alongside: fp32 on the tensor cores as split bf16 terms, "
+          "and the SIMT fp32 scan)")
 UNIT = "queries/s"
 M_SWEEP = (8, 12, 16, 24, 32, 40, 48, 64)
 SPARSE_M_SWEEP = (8, 16, 32, 64, 128, 256)
@@ -65,10 +66,9 @@ def parse():
     ap.add_argument("--config", choices=["sift1m", "small"], default="sift1m")
     ap.add_argument("--m", type=int, default=0, help="fixed probe count (0 = sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--paths", default="mlp_bf16,fp32,bf16,fp8",
-                    help="comma list of search paths (fp32, bf16, fp8, mlp_fp32, mlp_bf16, "
-                         "mlp_fp8); "
-                         "the first is the headline")
+    ap.add_argument("--paths", default="mlp_bf16,fp32_split,fp32,bf16,fp8",
+                    help="comma list of search paths (fp32, fp32_split, bf16, fp8, mlp_fp32, "
+                         "mlp_fp32_split, mlp_bf16, mlp_fp8); the first is the headline")
     ap.add_argument("--no-ablations", action="store_true",
                     help="skip the ablations (k-means + bf16, QPS at recall@10 >= 0.9 for AFT "
                          "heights h, constrained-field counts and 10 attribute fields)")
@@ -936,8 +936,9 @@ def run_caps(args):
     gt, g64, cnt, truth_check = exact_truth(caps, torch, w, samp)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     kinds = {"fp32": (caps.FP32, caps.KMEANS), "bf16": (caps.BF16, caps.KMEANS),
-             "fp8": (caps.FP8, caps.KMEANS), "mlp_fp32": (caps.FP32, caps.MLP),
-             "mlp_bf16": (caps.BF16, caps.MLP), "mlp_fp8": (caps.FP8, caps.MLP)}
+             "fp8": (caps.FP8, caps.KMEANS), "fp32_split": (caps.FP32_SPLIT, caps.KMEANS),
+             "mlp_fp32": (caps.FP32, caps.MLP), "mlp_bf16": (caps.BF16, caps.MLP),
+             "mlp_fp8": (caps.FP8, caps.MLP), "mlp_fp32_split": (caps.FP32_SPLIT, caps.MLP)}
     paths = [p for p in args.paths.split(",") if p]
     res = {}
     for pth in paths:

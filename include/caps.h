@@ -52,7 +52,12 @@ typedef struct caps_index caps_index;
 
 typedef enum { CAPS_L2 = 0, CAPS_IP = 1 } caps_metric;
 typedef enum { CAPS_PART_KMEANS = 0, CAPS_PART_MLP = 1 } caps_partitioner;
-typedef enum { CAPS_FP32 = 0, CAPS_BF16 = 1, CAPS_FP8E4M3 = 2 } caps_precision;
+typedef enum {
+  CAPS_FP32 = 0,
+  CAPS_BF16 = 1,
+  CAPS_FP8E4M3 = 2,
+  CAPS_FP32_SPLIT = 3
+} caps_precision;
 
 /*
  * Attribute vectors (Def. 1, "attribute model") -- exactly one of the two
@@ -119,6 +124,18 @@ typedef struct {
  *                dot product is multiplied back by both scales.  The filter
  *                is tested per (probe, row) (no penalty chunk).  Needs
  *                d % 16 == 0 and 64 <= d <= 128.
+ *                CAPS_FP32_SPLIT: fp32 distances on the tensor cores.  Each
+ *                fp32 coordinate v of a row or query is held as two bf16
+ *                terms, hi = bf16(v) and lo = bf16(v - hi); a tile's score
+ *                is hi.hi + hi.lo + lo.hi with fp32 accumulation (the
+ *                dropped lo.lo term is below 2^-16 of sum |q_j x_j|), the
+ *                filter folded into the MMA as in the bf16 penalty form;
+ *                the best rerank_factor * k candidates of each query are
+ *                then re-scored exactly in fp32 (the fixed-order chain of
+ *                CAPS_FP32) before keeping k.  Needs d % 8 == 0,
+ *                64 <= d <= 128 and the penalty form (the packed attribute
+ *                bits fit its code chunk); other indexes and k > 32 use the
+ *                fp32 scan.
  *   rerank_factor candidates re-scored per result in the bf16 and e4m3
  *                forms (0 = 4, at most 16): min(256, rerank_factor * k)
  *                candidates per query; each probed partition keeps its best

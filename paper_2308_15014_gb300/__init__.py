@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcaps_gb300.so")
 
 CAPS_OK, CAPS_EINVAL, CAPS_ENOMEM, CAPS_ECUDA, CAPS_ETIMEOUT = 0, 1, 2, 3, 4
 L2, IP = 0, 1
-FP32, BF16, FP8 = 0, 1, 2
+FP32, BF16, FP8, FP32_SPLIT = 0, 1, 2, 3
 KMEANS, MLP = 0, 1
 (ARR_CENTROIDS, ARR_BIN, ARR_TAGS, ARR_KEY, ARR_PERM, ARR_OFFSETS, ARR_MLP, ARR_LABELS,
  ARR_LABEL_BINS) = range(9)

@@ -514,6 +514,10 @@ static int build_mlp(const caps_build_params* p, const float* dX, const int32_t*
 // permutation and the tensor map over the rows.  Nothing for CAPS_FP32.
 static int prepare_precision(caps_index* ix, cudaStream_t s) {
   if (ix->prec == CAPS_FP32) return CAPS_OK;
+  // the split form rides on the penalty form; without it the index searches
+  // with the fp32 scan alone
+  const bool split = ix->prec == CAPS_FP32_SPLIT;
+  if (split && !ix->pen) return CAPS_OK;
   const int64_t N = ix->N;
   const int d = ix->d;
   const bool f8 = ix->prec == CAPS_FP8E4M3;
@@ -526,7 +530,7 @@ static int prepare_precision(caps_index* ix, cudaStream_t s) {
     ix->Xb = xb;
     if (int rc = ix->alloc(&ix->xs, (size_t)N + 4)) return rc;
   } else {
-    const int cols = ix->pen ? ((d + 63) / 64 + 1) * 64 : d;
+    const int cols = ix->pen ? ((d + 63) / 64 * (split ? 2 : 1) + 1) * 64 : d;
     uint16_t* xb = nullptr;
     if (int rc = ix->alloc(&xb, (size_t)N * cols)) return rc;
     ix->Xb = xb;
@@ -547,6 +551,7 @@ static int prepare_precision(caps_index* ix, cudaStream_t s) {
   tp.pen_bits = ix->pen_bits;
   for (int w = 0; w < 4; w++) tp.pen_mask[w] = ix->pen_mask[w];
   tp.f8 = f8 ? 1 : 0;
+  tp.split = split ? 1 : 0;
   tp.metric = ix->metric;
   tp.xs = ix->xs;
   tp.Xb = ix->Xb;
@@ -583,9 +588,11 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
         (p->mlp_judge_queries > 0 && (p->mlp_judge_m < 1 || p->mlp_judge_m > p->B)))
       return fail(CAPS_EINVAL, "mlp_judge_queries >= 0, and mlp_judge_m in [1, B] when judging");
   }
-  if (p->prec != CAPS_FP32 && p->prec != CAPS_BF16 && p->prec != CAPS_FP8E4M3)
-    return fail(CAPS_EINVAL, "precision must be CAPS_FP32, CAPS_BF16 or CAPS_FP8E4M3");
-  if (p->prec == CAPS_BF16 && (d % 8 != 0 || d < 64 || d > 128))
+  if (p->prec != CAPS_FP32 && p->prec != CAPS_BF16 && p->prec != CAPS_FP8E4M3 &&
+      p->prec != CAPS_FP32_SPLIT)
+    return fail(CAPS_EINVAL,
+                "precision must be CAPS_FP32, CAPS_BF16, CAPS_FP8E4M3 or CAPS_FP32_SPLIT");
+  if ((p->prec == CAPS_BF16 || p->prec == CAPS_FP32_SPLIT) && (d % 8 != 0 || d < 64 || d > 128))
     return fail(CAPS_EINVAL, "the bf16 form needs d a multiple of 8 in [64, 128]");
   if (p->prec == CAPS_FP8E4M3 && (d % 16 != 0 || d < 64 || d > 128))
     return fail(CAPS_EINVAL, "the e4m3 form needs d a multiple of 16 in [64, 128]");
@@ -765,7 +772,7 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
       }
     }
   }
-  if (p->prec == CAPS_BF16) {
+  if (p->prec == CAPS_BF16 || p->prec == CAPS_FP32_SPLIT) {
     // penalty form when the one-hot code of the packed attribute bits (two
     // columns per bit) and, for L2, the three parts of -|x|^2/2 fit one
     // 64-column chunk
@@ -1203,6 +1210,8 @@ bool tc_explicit_ok(const caps_index* ix, int k) {
          tc_scan_supported(ix->d, k, kp_of(ix, k), ix->meta.words_pad, f8 ? 1 : 0);
 }
 bool uses_pen(const caps_index* ix, int k) {
+  if (ix->prec == CAPS_FP32_SPLIT)
+    return k <= 32 && ix->pen && tc_split_supported(ix->d, kp_of(ix, k), ix->meta.words_pad);
   return ix->prec == CAPS_BF16 && k <= 32 && ix->pen &&
          tc_pen_supported(ix->d, kp_of(ix, k), ix->meta.words_pad);
 }
@@ -1270,8 +1279,9 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
   float* qn = nullptr;
   float* qs = nullptr;
   const int f8 = ix->prec == CAPS_FP8E4M3 ? 1 : 0;
+  const int split = ix->prec == CAPS_FP32_SPLIT ? 1 : 0;
   if (tc) {
-    if (int rc = scr.get(&Qh, (size_t)qc * ix->d)) return rc;
+    if (int rc = scr.get(&Qh, (size_t)qc * tc_vec_cols(ix->d, split))) return rc;
     if (int rc = scr.get(&qn, (size_t)qc)) return rc;
     if (f8)
       if (int rc = scr.get(&qs, (size_t)qc)) return rc;
@@ -1356,7 +1366,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
     a.out_dist = od.dev + c0 * k;
     if (tc) {
       BinWork w;
-      if (int rc = tc_query_prep(Qc, n, ix->d, Qh, qn, f8, qs, s)) return rc;
+      if (int rc = tc_query_prep(Qc, n, ix->d, Qh, qn, f8, qs, s, split)) return rc;
       const int rerank = tc_rerank_depth(k, ix->rerank_factor);
       if (int rc = tc_group(bt.probe, bt.sel, ix->h, n * m, ix->B, item_cap, &w, cscr, s))
         return rc;
@@ -1395,6 +1405,7 @@ int search_impl(const caps_index* ix, const float* Q, int64_t nq, const caps_att
       t.part = part;
       t.err = ix->err;
       t.n_rows = ix->N;
+      t.split = split;
       if (int rc = tc_scan(t, w, s)) return rc;
       if (int rc = tm.record(s)) return rc;
       if (int rc = tc_merge_rerank(t, bt.qp.dead, n, k, Qc, ix->Xp, ix->iperm, a.out_ids,

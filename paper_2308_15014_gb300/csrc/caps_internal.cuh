@@ -421,6 +421,7 @@ struct TcScanArgs {
   uint64_t* part;       // [nq*m*kp]
   int32_t* err;
   int64_t n_rows = 0;   // rows of the index (ids are below it)
+  int split = 0;        // 1: rows and queries as two bf16 terms [hi | lo | code] (fp32 form)
 };
 constexpr int kMaxRerank = 256;  // candidates re-scored exactly per query (form 1)
 // keys each partition keeps per probe: 10, 16 or 32, at least k and at least
@@ -452,6 +453,7 @@ struct TcIndexPrep {
   uint32_t pen_mask[4];
   int metric;              // CAPS_L2: the code chunk also carries -|x|^2/2
   int f8;                  // 1: e4m3 rows of ceil(d/128)*128 bytes + per-row scales
+  int split = 0;           // 1: bf16 rows [hi | lo | code] of (2*ceil(d/64)+1)*64 columns
   float* xs;               // out (f8): [N] per-row scales
   void* Xb;                // out: [N*cols] bf16 rows, cols = d, or (ceil(d/64)+1)*64 with pen
   float* xn;               // out: [N] squared norms
@@ -461,7 +463,11 @@ struct TcIndexPrep {
 };
 int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s);
 int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, int f8, float* qs,
-                  cudaStream_t s);
+                  cudaStream_t s, int split = 0);
+// bf16 columns of a query or row's vector part (split: [hi | lo], each part
+// padded to a multiple of 64)
+inline int tc_vec_cols(int d, int split) { return split ? 2 * ((d + 63) / 64) * 64 : d; }
+bool tc_split_supported(int d, int kp, int words_pad);
 // item_cap: most probes per work item (1..128; 0: 128)
 int tc_group(const int32_t* probe, const uint64_t* sel, int h, int64_t ne, int B, int item_cap,
              BinWork* w, Scratch& scr, cudaStream_t s);

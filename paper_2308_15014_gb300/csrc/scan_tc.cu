@@ -69,7 +69,9 @@ __global__ void k_rows_fp8(const float* __restrict__ Xp, int64_t N, int d, int c
 }
 
 // ---- bf16 query copy and fp32 squared norms -------------------------------
-__global__ void k_query_bf16(const float* __restrict__ Q, int64_t nq, int d,
+// split: rows of 2*hcols bf16, hi = bf16(q) in [0, d), lo = bf16(q - hi) in
+// [hcols, hcols + d), zeros elsewhere
+__global__ void k_query_bf16(const float* __restrict__ Q, int64_t nq, int d, int split,
                              __nv_bfloat16* __restrict__ Qh, float* __restrict__ qn) {
   // one warp per query: coalesced bf16 conversion, then lane 0 forms the
   // squared norm over the coordinates in order (one fma each)
@@ -77,7 +79,18 @@ __global__ void k_query_bf16(const float* __restrict__ Q, int64_t nq, int d,
   const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (q >= nq) return;
   const float* x = Q + q * d;
-  for (int j = lane; j < d; j += 32) Qh[q * d + j] = __float2bfloat16_rn(x[j]);
+  if (split) {
+    const int hcols = (d + 63) / 64 * 64;
+    __nv_bfloat16* o = Qh + q * 2 * hcols;
+    for (int j = lane; j < hcols; j += 32) {
+      const float v = j < d ? x[j] : 0.f;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      o[j] = hi;
+      o[hcols + j] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+  } else {
+    for (int j = lane; j < d; j += 32) Qh[q * d + j] = __float2bfloat16_rn(x[j]);
+  }
   if (lane == 0) {
     float acc = 0.f;
     for (int j = 0; j < d; j++) acc = fmaf(x[j], x[j], acc);
@@ -442,20 +455,25 @@ __global__ void k_tc_items_fill(const int32_t* __restrict__ bin_off,
 // attribute bits, two columns per bit, then for L2 the row's -|x|^2/2 as
 // three bf16 parts that sum to it exactly), its fp32 squared norm
 // (coordinates in order, one fma each) and the largest squared norm
+// split: the row as two bf16 terms, hi = bf16(x) in columns [0, d) and
+// lo = bf16(x - hi) in [hcols, hcols + d), hcols = ceil(d/64)*64
 __global__ void k_rows_bf16(const float* __restrict__ Xp, int64_t N, int d, int cols, int kcd,
                             const uint32_t* __restrict__ Ap, int WP, int pen, int pen_bits,
-                            uint4 pen_mask, int pen_norm, __nv_bfloat16* __restrict__ Xb,
+                            uint4 pen_mask, int pen_norm, int split, __nv_bfloat16* __restrict__ Xb,
                             float* __restrict__ xn, unsigned int* __restrict__ xn_max_bits) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   __nv_bfloat16* row = Xb + r * cols;
+  for (int j = 0; j < cols; j++) row[j] = __float2bfloat16_rn(0.f);
+  const int hcols = (d + 63) / 64 * 64;
   float acc = 0.f;
   for (int j = 0; j < d; j++) {
     const float x = Xp[r * d + j];
     acc = fmaf(x, x, acc);
-    row[j] = __float2bfloat16_rn(x);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    row[j] = hi;
+    if (split) row[hcols + j] = __float2bfloat16_rn(x - __bfloat162float(hi));
   }
-  for (int j = d; j < cols; j++) row[j] = __float2bfloat16_rn(0.f);
   xn[r] = acc;
   if (!(acc != acc)) atomicMax(xn_max_bits, __float_as_uint(acc));  // acc >= 0: bits order as floats
   if (!pen) return;
@@ -541,6 +559,12 @@ bool tc_pen_supported(int d, int kp, int words_pad) {
   return tc_fits((d + 63) / 64 + 1, words_pad, 128, true);
 }
 
+// the split form: penalty form with 64-row tiles over [hi | lo | code] rows
+bool tc_split_supported(int d, int kp, int words_pad) {
+  if (d % 8 != 0 || d < 64 || d > 128 || (kp != 10 && kp != 16)) return false;
+  return tc_fits(2 * ((d + 63) / 64) + 1, words_pad, 64, true);
+}
+
 int tc_pen_columns(int pen_bits, int metric) { return 2 * pen_bits + (metric == CAPS_L2 ? 3 : 0); }
 
 namespace {
@@ -590,8 +614,9 @@ int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
     CAPS_CUDA(cudaStreamSynchronize(s));
     return CAPS_OK;
   }
-  const int kcd = (p.d + 63) / 64;
+  const int kcd = (p.d + 63) / 64 * (p.split ? 2 : 1);  // chunks before the code chunk
   const int cols = p.pen ? (kcd + 1) * 64 : p.d;
+  if (p.split && !p.pen) return fail(CAPS_EINVAL, "the split form needs the penalty form");
   unsigned int* xmax = nullptr;
   {
     void* q = nullptr;
@@ -605,7 +630,8 @@ int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
   const uint4 pm = make_uint4(p.pen_mask[0], p.pen_mask[1], p.pen_mask[2], p.pen_mask[3]);
   k_rows_bf16<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
       p.Xp, N, p.d, cols, kcd, p.Ap, p.words_pad, p.pen, p.pen_bits, pm,
-      p.pen && p.metric == CAPS_L2 ? 1 : 0, static_cast<__nv_bfloat16*>(p.Xb), p.xn, xmax);
+      p.pen && p.metric == CAPS_L2 ? 1 : 0, p.split, static_cast<__nv_bfloat16*>(p.Xb), p.xn,
+      xmax);
   cudaError_t le = cudaGetLastError();
   unsigned int xmax_h = 0;
   if (le == cudaSuccess) le = cudaMemcpyAsync(&xmax_h, xmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
@@ -630,7 +656,8 @@ int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)N};
   cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)TC_BOX};
+  // (the split form scans 64-row tiles: a 64-row box)
+  cuuint32_t box[2] = {64, (cuuint32_t)(p.split ? tc_box_rows(64) : TC_BOX)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(static_cast<CUtensorMap*>(p.tmap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p.Xb,
                       gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -641,14 +668,14 @@ int tc_prepare_index(const TcIndexPrep& p, cudaStream_t s) {
 }
 
 int tc_query_prep(const float* Q, int64_t nq, int d, void* Qh, float* qn, int f8, float* qs,
-                  cudaStream_t s) {
+                  cudaStream_t s, int split) {
   if (nq == 0) return CAPS_OK;
   if (f8) {
     k_query_fp8<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, d, static_cast<uint8_t*>(Qh), qs, qn);
     CAPS_LAUNCH("k_query_fp8");
     return CAPS_OK;
   }
-  k_query_bf16<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, d,
+  k_query_bf16<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(Q, nq, d, split,
                                                         static_cast<__nv_bfloat16*>(Qh), qn);
   CAPS_LAUNCH("k_query_bf16");
   return CAPS_OK;
@@ -732,8 +759,10 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   a.offsets = t.offsets;
   a.m = t.m;
   a.h = t.h;
-  a.d = t.d;
-  a.kcd = t.f8 ? (t.d + 127) / 128 : (t.d + 63) / 64;
+  a.split = t.split;
+  // (split: the A operand's rows are the queries' [hi | lo] bf16 columns)
+  a.d = t.split ? tc_vec_cols(t.d, 1) : t.d;
+  a.kcd = t.f8 ? (t.d + 127) / 128 : (t.d + 63) / 64 * (t.split ? 2 : 1);
   a.kc = a.kcd + (t.pen ? 1 : 0);
   a.kp = t.kp;
   a.pen_bits = t.pen_bits;
@@ -758,6 +787,12 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   // persistent: one CTA per SM (the shared memory admits no second), never
   // more CTAs than work items
   const int64_t g = std::max<int64_t>(1, std::min<int64_t>(w.max_items, sm_count()));
+  if (t.split) {
+    if (!t.pen || !tc_split_supported(t.d, t.kp, t.words_pad))
+      return fail(CAPS_EINVAL, "the split form does not fit this index or k");
+    return tc_launch_pen(map, a, t.metric, t.words_pad, t.kp, g,
+                         tc_smem_bytes(a.kc, t.words_pad, 64, true), s, 64);
+  }
   if (t.pen) {
     if (!tc_pen_supported(t.d, t.kp, t.words_pad))
       return fail(CAPS_EINVAL, "the penalty form does not fit this index or k");

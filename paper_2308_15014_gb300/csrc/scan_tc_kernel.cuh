@@ -88,6 +88,8 @@ struct TcArgs {
   int pen_norm;          // penalty form, L2: the chunk carries -|x|^2/2 after the bit columns
   uint64_t wait_ns;      // limit of every bounded wait (ns)
   int withhold;          // test hook: the producer issues no copy or MMA for this item (-1: none)
+  int split;             // fp32 rows as two bf16 terms: chunks [hi | lo | code] on both sides,
+                         // products hi.hi + hi.lo + lo.hi (64-row tiles)
 };
 
 namespace {
@@ -266,6 +268,11 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&v)[8]) {
 }
 
 __host__ __device__ constexpr int tc_stages(int N, bool pen) { return pen ? 2 : TC_COLS / N; }
+// accumulator stages in tensor memory (64-row tiles: four, to leave shared
+// memory for the wider rows of the split form)
+__host__ __device__ constexpr int tc_acc_stages(int N) { return N == 64 ? 4 : TC_COLS / N; }
+// rows per 2-D copy: the tensor map's box (64-row tiles use a 64-row box)
+__host__ __device__ constexpr int tc_box_rows(int N) { return N < TC_BOX ? N : TC_BOX; }
 __host__ __device__ constexpr size_t tc_a_bytes(int kc) { return (size_t)kc * TC_M * 128; }
 __host__ __device__ constexpr size_t tc_b_bytes(int kc, int N) { return (size_t)kc * N * 128; }
 // per stage: attribute words, ids, norms and (e4m3 rows) scales of N + 8
@@ -289,7 +296,7 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int kc, int WP, int N, bool p
   // (one per accumulator stage; the final merge of the quarter lists reuses
   // the queues)
   return 1024 + tc_a_bytes(kc) + (size_t)tc_stages(N, pen) * tc_b_bytes(kc, N) +
-         (size_t)TC_Q * TC_C * 8 + (size_t)(TC_COLS / N) * tc_aux_bytes(WP, N, f8);
+         (size_t)TC_Q * TC_C * 8 + (size_t)tc_acc_stages(N) * tc_aux_bytes(WP, N, f8);
 }
 
 template <int KP>
@@ -367,7 +374,8 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   // SB shared-memory stages hold B tiles (free once the tile's MMAs are
   // done); ST accumulator stages in tensor memory, each with the tile's ids,
   // norms, attribute words and block ids (free once the epilogue read them)
-  constexpr int SB = tc_stages(N, PEN), ST = TC_COLS / N;
+  constexpr int SB = tc_stages(N, PEN), ST = tc_acc_stages(N);
+  constexpr int BOXR = tc_box_rows(N);
   constexpr int RA = N + 8;
   constexpr int CPT = N / TC_PARTS;  // accumulator columns per epilogue thread and tile
   extern __shared__ unsigned char smem_raw[];
@@ -702,9 +710,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
           expect_tx(&full_bar[sb], (uint32_t)(kc * N * 128));
           for (int c = 0; c < kc; c++)
 #pragma unroll
-            for (int hb = 0; hb < N / TC_BOX; hb++)
-              tma_2d(sB + (size_t)c * N * 128 + (size_t)hb * TC_BOX * 128, &tmX, 64 * c,
-                     lo + hb * TC_BOX, &full_bar[sb]);
+            for (int hb = 0; hb < N / BOXR; hb++)
+              tma_2d(sB + (size_t)c * N * 128 + (size_t)hb * BOXR * 128, &tmX, 64 * c,
+                     lo + hb * BOXR, &full_bar[sb]);
           // ids (and, per-pair form, attribute words and norms; e4m3 scales):
           // the penalty form needs only the ids
           expect_tx(&aux_bar[st], ab + (PEN ? 1 : (F8 ? 3 : 2)) * pb);
@@ -720,8 +728,11 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       // bounded wait for its first tile expires with nothing left in flight
       const int n_issue = s_item[par] == a.withhold ? 0 : n_tiles;
       // MMA steps per tile: four per vector chunk, and the used part of the
-      // penalty chunk
-      const int ksteps = PEN ? (kc - 1) * 4 + a.pen_ks : kc * 4;
+      // penalty chunk; the split form multiplies three chunk pairs for each
+      // chunk of the vector: hi.hi, hi.lo, lo.hi
+      const int hcd = a.kcd >> 1;  // split form: chunks of the hi part
+      const int ksteps = a.split ? 12 * hcd + (PEN ? a.pen_ks : 0)
+                                 : (PEN ? (kc - 1) * 4 + a.pen_ks : kc * 4);
       while (ok && tl < n_issue && tl < SB - 1) ok = load(tl++);
       for (int t = 0; ok && t < n_issue; t++) {
         if (tl < n_issue) ok = load(tl++);
@@ -736,8 +747,14 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
             const uint32_t a0 = su32(sA), b0 = su32(sB0 + sb * bstride);
             for (int ks = 0; ks < ksteps; ks++) {
               const int c = ks >> 2, kin = ks & 3;
-              const uint64_t ad = sdesc(a0 + (uint32_t)(c * TC_M * 128 + kin * 32));
-              const uint64_t bd = sdesc(b0 + (uint32_t)(c * N * 128 + kin * 32));
+              int ca = c, cb = c;  // the chunks of A and B this step multiplies
+              if (a.split) {
+                if (c >= 3 * hcd) ca = cb = a.kcd;                  // code chunk
+                else if (c >= 2 * hcd) ca = c - hcd, cb = c - 2 * hcd;  // lo . hi
+                else if (c >= hcd) ca = c - hcd;                   // hi . lo
+              }
+              const uint64_t ad = sdesc(a0 + (uint32_t)(ca * TC_M * 128 + kin * 32));
+              const uint64_t bd = sdesc(b0 + (uint32_t)(cb * N * 128 + kin * 32));
               if (F8) mma_f8(tbase + (uint32_t)(st * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
               else mma_bf16(tbase + (uint32_t)(st * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
             }
@@ -881,13 +898,13 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
         const uint32_t tacc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * N + cbeg);
         const int ncol = warp_live ? min(CPT, n - cbeg) : 0;  // warp-uniform
         if constexpr (PEN) {
-          // the thread's 32 accumulators in two loads of 16; the largest of
+          // the thread's CPT accumulators in loads of 16; the largest of
           // each 8 against the floor; only lanes with a value at or above it
           // turn pairs into keys
-          static_assert(CPT == 32, "the penalty form uses 128-row tiles");
+          static_assert(CPT % 16 == 0, "the penalty form reads 16 columns at a time");
           float fl;
 #pragma unroll 1
-          for (int h16 = 0; h16 < 2 && 16 * h16 < ncol; h16++) {  // warp-uniform bounds
+          for (int h16 = 0; h16 < CPT / 16 && 16 * h16 < ncol; h16++) {  // warp-uniform bounds
             // the probe's shared bound, fresh for every 16 columns
             {
               const uint64_t st = pthr[probe];
@@ -1098,9 +1115,10 @@ int launch_tc(const CUtensorMap& map, const TcArgs& a, int64_t grid, size_t smem
 // rows per tile; kp 10, 16 or 32.
 int tc_launch_f8(const CUtensorMap& map, const TcArgs& a, int metric, int words_pad, int kp, int N,
                  int64_t grid, size_t smem, cudaStream_t s);
-// Launch of the penalty form (scan_tc_pen.cu): N = 128 rows per tile, two
-// B-tile stages and four accumulator stages; kp 10 or 16.
+// Launch of the penalty form (scan_tc_pen.cu): N = 128 rows per tile (64
+// for the split form), two B-tile stages and four accumulator stages; kp 10
+// or 16.
 int tc_launch_pen(const CUtensorMap& map, const TcArgs& a, int metric, int words_pad, int kp,
-                  int64_t grid, size_t smem, cudaStream_t s);
+                  int64_t grid, size_t smem, cudaStream_t s, int N = 128);
 
 }  // namespace caps

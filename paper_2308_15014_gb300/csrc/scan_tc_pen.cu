@@ -7,9 +7,12 @@
 namespace caps {
 
 int tc_launch_pen(const CUtensorMap& map, const TcArgs& a, int metric, int words_pad, int kp,
-                  int64_t grid, size_t smem, cudaStream_t s) {
-#define CAPS_PEN(WPV, KPV)                                                                   \
-  return metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 128, true>(map, a, grid, smem, s) \
+                  int64_t grid, size_t smem, cudaStream_t s, int N) {
+#define CAPS_PEN(WPV, KPV)                                                                     \
+  if (N == 64)                                                                                 \
+    return metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 64, true>(map, a, grid, smem, s)   \
+                             : launch_tc<CAPS_IP, WPV, KPV, 64, true>(map, a, grid, smem, s);  \
+  return metric == CAPS_L2 ? launch_tc<CAPS_L2, WPV, KPV, 128, true>(map, a, grid, smem, s)   \
                            : launch_tc<CAPS_IP, WPV, KPV, 128, true>(map, a, grid, smem, s)
   if (kp == 10) {
     switch (words_pad) {
