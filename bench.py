@@ -161,7 +161,7 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def scan_traffic_bytes(w, perm, offsets, probe, sel, words_pad, bf16=False):
+def scan_traffic_bytes(w, perm, offsets, probe, sel, words_pad, bf16=False, split=False):
     """Algorithmic bytes of the scan for one batch.
 
     fp32 scan -- union: attribute words of every row some query selects, plus
@@ -169,7 +169,8 @@ def scan_traffic_bytes(w, perm, offsets, probe, sel, words_pad, bf16=False):
     once: the HBM floor of the whole batch); per_query: the same sums taken
     query by query (the paper's query-time term sum |p| (L + d*match)).
     bf16 tensor-core scan -- every selected row is scored, so the union is
-    each selected row's bf16 vector, attribute words, id and norm once."""
+    each selected row's bf16 vector, attribute words, id and norm once; the
+    split fp32 form reads two bf16 terms per coordinate."""
     N, d, h = w.N, w.d, w.h
     nb = h + 1
     Ar = w.A[perm]
@@ -197,8 +198,8 @@ def scan_traffic_bytes(w, perm, offsets, probe, sel, words_pad, bf16=False):
         pq_scan += (r1 - r0) * len(grp_q)
         pq_pass += int(ok.sum())
     attr_b = 4 * words_pad
-    if bf16:
-        row_b = 2 * d + attr_b + 8
+    if bf16 or split:
+        row_b = (4 if split else 2) * d + attr_b + 8
         return int(touched.sum()) * row_b, pq_scan * row_b, pq_scan, pq_pass
     union = int(touched.sum()) * attr_b + int(passed.sum()) * d * 4
     per_query = pq_scan * attr_b + pq_pass * d * 4
@@ -235,10 +236,11 @@ def dense_item_stats(w, offsets, probe, sel, group=128):
     return int(items), int(rows), int(pairs)
 
 
-def traffic_from_profile(kernel=SCAN_KERNEL, src_name=SCAN_SRC, m=None):
+def traffic_from_profile(kernel=SCAN_KERNEL, src_name=SCAN_SRC, m=None, variant=None):
     """dram bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current source of that kernel and, where the entry names
-    one, at the same probe count m (else None)."""
+    was taken on the current source of that kernel, of the same form
+    (variant) and, where the entry names one, at the same probe count m
+    (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2308_15014_gb300", "csrc", src_name)
     if not os.path.exists(p):
@@ -249,7 +251,7 @@ def traffic_from_profile(kernel=SCAN_KERNEL, src_name=SCAN_SRC, m=None):
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
     for e in entries:
         if e.get("kernel") == kernel and e.get("src_sha") == sha and \
-                (m is None or e.get("m") in (None, m)):
+                e.get("variant") == variant and (m is None or e.get("m") in (None, m)):
             return e.get("dram_bytes_per_launch")
     return None
 
@@ -953,11 +955,13 @@ def run_caps(args):
     offsets = ix.export(caps.ARR_OFFSETS)
     probe = ix.probe(w.Q, m)
     sel = ix.select(probe, w.Qb)
+    split_head = paths[0].endswith("split")
     union, per_query, rows_scanned, rows_passed = scan_traffic_bytes(
-        w, perm, offsets, probe, sel, ix.info.attr_words, bf16=paths[0].endswith("bf16"))
+        w, perm, offsets, probe, sel, ix.info.attr_words, bf16=paths[0].endswith("bf16"),
+        split=split_head)
     hbm, hbm_src = peaks()
     scan_s = stage["scan_ms"] / 1e3
-    tc_head = paths[0].endswith("bf16")
+    tc_head = paths[0].endswith("bf16") or split_head
     d_items, d_rows, d_pairs = dense_item_stats(w, offsets, probe, sel, 128 if tc_head else 32)
     achieved_gbs = union / scan_s / 1e9
     if tc_head:
@@ -969,7 +973,8 @@ def run_caps(args):
         roof = {"kernel": TC_KERNEL, "bound": "hbm", "achieved": round(achieved_gbs, 1),
                 "peak": hbm, "peak_source": hbm_src, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm, 4),
-                "traffic": traffic_from_profile(TC_KERNEL, TC_SRC, m),
+                "traffic": traffic_from_profile(TC_KERNEL, TC_SRC, m,
+                                                "split" if split_head else "bf16"),
                 "algorithmic_bytes": union, "algorithmic_bytes_per_query_sum": per_query,
                 "rows_attr_tested": rows_scanned, "rows_distance": rows_passed,
                 "work_items": d_items, "item_union_rows": d_rows, "item_dense_pairs": d_pairs}
@@ -991,7 +996,7 @@ def run_caps(args):
                 "peak": round(FP32_PEAK_TFLOPS, 1),
                 "peak_source": "derived: 152 SMs x 128 fp32 lanes x 2 flop x 2.07 GHz",
                 "unit": "TFLOP/s", "frac": round(tflops / FP32_PEAK_TFLOPS, 4),
-                "traffic": traffic_from_profile(SCAN_KERNEL, SCAN_SRC), "algorithmic_flops": flops,
+                "traffic": traffic_from_profile(SCAN_KERNEL, SCAN_SRC, m), "algorithmic_flops": flops,
                 "rows_attr_tested": rows_scanned, "rows_distance": rows_passed}
         roof_other = {"kernel": roof["kernel"], "bound": "hbm", "achieved": round(achieved_gbs, 1),
                       "peak": hbm, "peak_source": hbm_src, "unit": "GB/s",

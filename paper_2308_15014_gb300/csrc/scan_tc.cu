@@ -787,7 +787,7 @@ int tc_scan(const TcScanArgs& t, const BinWork& w, cudaStream_t s) {
   // persistent: one CTA per SM (the shared memory admits no second), never
   // more CTAs than work items
   const int64_t g = std::max<int64_t>(1, std::min<int64_t>(w.max_items, sm_count()));
-  if (t.split) {
+  if (t.split) {  // (the kernel multiplies the split chunk pairs with 64-row tiles only)
     if (!t.pen || !tc_split_supported(t.d, t.kp, t.words_pad))
       return fail(CAPS_EINVAL, "the split form does not fit this index or k");
     return tc_launch_pen(map, a, t.metric, t.words_pad, t.kp, g,

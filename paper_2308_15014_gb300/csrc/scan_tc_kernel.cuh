@@ -731,8 +731,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       // penalty chunk; the split form multiplies three chunk pairs for each
       // chunk of the vector: hi.hi, hi.lo, lo.hi
       const int hcd = a.kcd >> 1;  // split form: chunks of the hi part
-      const int ksteps = a.split ? 12 * hcd + (PEN ? a.pen_ks : 0)
-                                 : (PEN ? (kc - 1) * 4 + a.pen_ks : kc * 4);
+      const bool split = N == 64 && a.split;  // (64-row tiles only)
+      const int ksteps = split ? 12 * hcd + (PEN ? a.pen_ks : 0)
+                               : (PEN ? (kc - 1) * 4 + a.pen_ks : kc * 4);
       while (ok && tl < n_issue && tl < SB - 1) ok = load(tl++);
       for (int t = 0; ok && t < n_issue; t++) {
         if (tl < n_issue) ok = load(tl++);
@@ -748,7 +749,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
             for (int ks = 0; ks < ksteps; ks++) {
               const int c = ks >> 2, kin = ks & 3;
               int ca = c, cb = c;  // the chunks of A and B this step multiplies
-              if (a.split) {
+              if (split) {
                 if (c >= 3 * hcd) ca = cb = a.kcd;                  // code chunk
                 else if (c >= 2 * hcd) ca = c - hcd, cb = c - 2 * hcd;  // lo . hi
                 else if (c >= hcd) ca = c - hcd;                   // hi . lo
