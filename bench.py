@@ -709,7 +709,9 @@ def oracle_baseline(caps, ix, w, m, budget_s=15.0):
                       f"{part}; {build_s:.1f} s, untimed)"}
 
 
-REFERENCE_M = 40
+# the probe count at which the headline (learned + bf16) reaches recall@10
+# >= 0.9 on this workload: the reference arm's m unless one is given
+REFERENCE_M = 16
 
 
 def max_over_ranks(x, world, device):
@@ -807,10 +809,13 @@ def run_reference(args):
 # carry about 1 % error, so the right neighbours rank lower than with bf16)
 FP8_RERANK_FACTOR = 16
 
-# learned partitioner: 128 -> 512 -> 1024 (ReLU), 131,072 training points,
-# 10-NN filtered labels, Adam lr 2e-3, batches of 4096, 20 epochs
-MLP_ARGS = dict(mlp_hidden=512, mlp_epochs=20, mlp_samples=131072, mlp_batch=4096, mlp_lr=2e-3,
-                mlp_label_k=10, seed=17)
+# learned partitioner: 128 -> 512 -> 1024 (ReLU), 524,288 training points,
+# 10-NN filtered labels, Adam lr 1e-3, batches of 4096, 40 epochs, bf16
+# weights and activations with fp32 masters (recall@10 on the bench's sample
+# at m = 12 / 16 / 24: 0.894 / 0.911 / 0.930; with 131,072 points, 20 epochs,
+# lr 2e-3 and fp32 training it was 0.887 at m = 24 and 0.906 at m = 40)
+MLP_ARGS = dict(mlp_hidden=512, mlp_epochs=40, mlp_samples=524288, mlp_batch=4096, mlp_lr=1e-3,
+                mlp_label_k=10, seed=17, mlp_bf16=1)
 
 
 def measure_path(args, w, caps, prec, samp, gt, g64, cnt, flush, world, local, part=0):
