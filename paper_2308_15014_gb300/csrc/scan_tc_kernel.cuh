@@ -98,6 +98,15 @@ constexpr int TC_M = 128;     // probes per work item (MMA M, TMEM lanes)
 constexpr int TC_C = 512;     // epilogue threads: four per probe (one per quarter tile)
 constexpr int TC_T = TC_C + 64;  // + a producer warp (copies and MMAs) and a prep warp
 constexpr int TC_PARTS = TC_C / TC_M;
+// The entry (0..ne-1 of the item's probes) held by accumulator lane t: with
+// c = ceil(ne / 4), lane quarter q holds entries q c .. q c + c - 1, so that an
+// item's probes spread evenly over the four 32-lane quarters and their
+// epilogue warps while neighbouring entries (similar block selections) stay
+// in one warp.  A lane without an entry gets a value >= ne.
+__device__ __forceinline__ int slot_entry(int t, int ne) {
+  const int c = (ne + 3) >> 2, l = t & 31;
+  return l < c ? (t >> 5) * c + l : TC_M;
+}
 constexpr int TC_Q = 12;      // per-thread candidate queue (merged when > 4 wait)
 constexpr int TC_BOX = 128;   // rows per 2-D copy (the tensor map's box)
 constexpr int TC_COLS = 512;  // tensor-memory columns: TC_COLS / N accumulator stages
@@ -491,8 +500,9 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       uint32_t qm[WP], qv[WP];
 #pragma unroll
       for (int w = 0; w < WP; w++) qm[w] = qv[w] = 0u;
-      if (t < pit.ne) {
-        e = a.ent[pit.e0 + t];
+      const int jt = slot_entry(t, pit.ne);
+      if (jt < pit.ne) {
+        e = a.ent[pit.e0 + jt];
         const int q = e / a.m;
         sel = a.sel[e];
         qn = a.qn[q];
@@ -521,7 +531,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       // penalty form: P = 2^ex >= 4 (max |x|^2 + |q|^2); a pair passes the
       // filter iff its accumulator is >= -P/2 (the cut; +inf: no probe)
       float cut = INFINITY;
-      if (PEN && t < pit.ne) {
+      if (PEN && jt < pit.ne) {
         const float bound = 4.f * (a.xn_max + qn);
         int ex = (int)((__float_as_uint(bound) >> 23) & 0xffu) - 126;  // 2^ex >= bound
         ex = max(0, min(126, ex));
@@ -569,7 +579,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
   auto build_a = [&](int par) {
     const int t = tid & (TC_M - 1), qq = tid / TC_M;
     const int ne_n = s_ne[par];
-    const int q = t < ne_n ? p_e[par][t] / a.m : -1;
+    const int q = slot_entry(t, ne_n) < ne_n ? p_e[par][t] / a.m : -1;
     // 16-byte units: 8 bf16 or 16 e4m3 coordinates
     const int rowb = a.d * (F8 ? 1 : 2);
     const int units = a.kcd * 8, dunits = rowb / 16;
@@ -745,19 +755,29 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
           if (ok && t == 0) ok = mbar_wait(&afull_bar, (uint32_t)(n_done & 1), &s_fail, a.wait_ns);
           if (ok) {
             tc_fence_after();
-            const uint32_t a0 = su32(sA), b0 = su32(sB0 + sb * bstride);
-            for (int ks = 0; ks < ksteps; ks++) {
-              const int c = ks >> 2, kin = ks & 3;
-              int ca = c, cb = c;  // the chunks of A and B this step multiplies
+            // descriptors of the stage bases once; a step's operand is the
+            // base plus its byte offset / 16 (the address field of the
+            // descriptor; shared addresses stay below 256 KB, so no carry)
+            const uint64_t adb = sdesc(su32(sA)), bdb = sdesc(su32(sB0 + sb * bstride));
+            const uint32_t dt = tbase + (uint32_t)(st * N);
+            const int nch = (ksteps + 3) >> 2;  // 64-column chunks (the code chunk may be partial)
+            for (int c = 0; c < nch; c++) {
+              int ca = c, cb = c;  // the chunks of A and B this chunk step multiplies
               if (split) {
                 if (c >= 3 * hcd) ca = cb = a.kcd;                  // code chunk
                 else if (c >= 2 * hcd) ca = c - hcd, cb = c - 2 * hcd;  // lo . hi
                 else if (c >= hcd) ca = c - hcd;                   // hi . lo
               }
-              const uint64_t ad = sdesc(a0 + (uint32_t)(ca * TC_M * 128 + kin * 32));
-              const uint64_t bd = sdesc(b0 + (uint32_t)(cb * N * 128 + kin * 32));
-              if (F8) mma_f8(tbase + (uint32_t)(st * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
-              else mma_bf16(tbase + (uint32_t)(st * N), ad, bd, idesc, ks > 0 ? 1u : 0u);
+              const uint64_t ad = adb + (uint64_t)(ca * TC_M * 8), bd = bdb + (uint64_t)(cb * N * 8);
+              const int nk = min(4, ksteps - 4 * c);
+#pragma unroll
+              for (int kin = 0; kin < 4; kin++) {
+                if (kin < nk) {
+                  const uint32_t acc = (c > 0 || kin > 0) ? 1u : 0u;
+                  if (F8) mma_f8(dt, ad + (uint64_t)(2 * kin), bd + (uint64_t)(2 * kin), idesc, acc);
+                  else mma_bf16(dt, ad + (uint64_t)(2 * kin), bd + (uint64_t)(2 * kin), idesc, acc);
+                }
+              }
             }
             mma_commit(&mma_bar[st]);
             mma_commit(&bfree_bar[sb]);
@@ -773,7 +793,7 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
       // operand is built as soon as this item's MMAs are done, while the
       // producer already streams the next item's tiles)
       const int probe = tid & (TC_M - 1), part = tid / TC_M;
-      const bool active = probe < ne;
+      const bool active = slot_entry(probe, ne) < ne;
       const uint64_t my_sel = p_sel[probe];
       uint32_t my_qm[WP], my_qv[WP];
 #pragma unroll
