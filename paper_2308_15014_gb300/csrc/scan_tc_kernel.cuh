@@ -760,7 +760,31 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
             // descriptor; shared addresses stay below 256 KB, so no carry)
             const uint64_t adb = sdesc(su32(sA)), bdb = sdesc(su32(sB0 + sb * bstride));
             const uint32_t dt = tbase + (uint32_t)(st * N);
-            const int nch = (ksteps + 3) >> 2;  // 64-column chunks (the code chunk may be partial)
+            if (split) {
+              // two accumulators, so that consecutive MMAs do not wait on
+              // one another: D0 (columns st N) takes hi.hi and hi.lo, D1
+              // (columns 256 + st N) takes lo.hi and the code chunk; the
+              // epilogue adds them.  The MMAs alternate between the two.
+              const uint32_t dt1 = dt + 256u;
+              const int n1 = hcd + (PEN ? 1 : 0);
+              for (int i = 0; i < 2 * hcd; i++) {
+                const int c0a = i < hcd ? i : i - hcd, c0b = i;  // D0's chunk pair
+                const bool has1 = i < n1;
+                const int c1a = i < hcd ? hcd + i : a.kcd, c1b = i < hcd ? i : a.kcd;
+                const int nk1 = i < hcd ? 4 : a.pen_ks;
+                const uint64_t ad0 = adb + (uint64_t)(c0a * TC_M * 8), bd0 = bdb + (uint64_t)(c0b * N * 8);
+                const uint64_t ad1 = adb + (uint64_t)(c1a * TC_M * 8), bd1 = bdb + (uint64_t)(c1b * N * 8);
+#pragma unroll
+                for (int kin = 0; kin < 4; kin++) {
+                  mma_bf16(dt, ad0 + (uint64_t)(2 * kin), bd0 + (uint64_t)(2 * kin), idesc,
+                           (i > 0 || kin > 0) ? 1u : 0u);
+                  if (has1 && kin < nk1)
+                    mma_bf16(dt1, ad1 + (uint64_t)(2 * kin), bd1 + (uint64_t)(2 * kin), idesc,
+                             (i > 0 || kin > 0) ? 1u : 0u);
+                }
+              }
+            }
+            const int nch = split ? 0 : (ksteps + 3) >> 2;  // 64-column chunks (the code chunk may be partial)
             for (int c = 0; c < nch; c++) {
               int ca = c, cb = c;  // the chunks of A and B this chunk step multiplies
               if (split) {
@@ -934,7 +958,18 @@ k_scan_tc(const __grid_constant__ CUtensorMap tmX, TcArgs a) {
             fl = floor_of(thr);
             uint32_t v[16];
             tmem_ld16_issue(tacc + (uint32_t)(16 * h16), v);
-            tmem_wait16(v);
+            if constexpr (N == 64) {
+              // the split form's second accumulator (columns + 256)
+              uint32_t v2[16];
+              tmem_ld16_issue(tacc + 256u + (uint32_t)(16 * h16), v2);
+              tmem_wait16(v);
+              tmem_wait16(v2);
+#pragma unroll
+              for (int j = 0; j < 16; j++)
+                v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(v2[j]));
+            } else {
+              tmem_wait16(v);
+            }
             const int c0 = cbeg + 16 * h16, lim = ncol - 16 * h16;
             if (lim < 16) {  // rows past the end of the tile's run
 #pragma unroll
