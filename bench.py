@@ -588,7 +588,7 @@ def learned4m_line(args, caps, torch, flush):
     the balanced assignment over 8 logits), all bf16 indexes; per
     index its build time, the largest partition, the recall@10 / QPS sweep
     over m and the QPS at recall@10 >= 0.9 (the comparison at equal recall),
-    plus the build's own judge (k-means fallback).  Recall against the
+    plus the build's own arbiter (k-means fallback).  Recall against the
     oracle's brute force on a 200-query sample."""
     from workloads import config_learned4m
     t0 = time.perf_counter()
@@ -606,8 +606,8 @@ def learned4m_line(args, caps, torch, flush):
     ids = torch.empty((w.nq, w.k), dtype=torch.int64, device="cuda")
     dist = torch.empty((w.nq, w.k), dtype=torch.float32, device="cuda")
     mlp = dict(part=caps.MLP, mlp_hidden=512, mlp_epochs=20, mlp_samples=131072,
-               mlp_batch=4096, mlp_lr=2e-3, mlp_label_k=10, seed=17, mlp_judge_queries=1000,
-               mlp_judge_m=8, mlp_bf16=1)
+               mlp_batch=4096, mlp_lr=2e-3, mlp_label_k=10, seed=17, mlp_arbiter_queries=1000,
+               mlp_arbiter_m=8, mlp_bf16=1)
     variants = (("kmeans", {}), ("learned", mlp), ("learned_fp32_training", dict(mlp, mlp_bf16=0)),
                 ("learned_balanced", dict(mlp, mlp_rounds=2, mlp_balance_r=8)))
     out = {"workload": w.name, "N": w.N, "d": w.d, "B": w.B, "metric": "ip",
@@ -626,9 +626,9 @@ def learned4m_line(args, caps, torch, flush):
                "mean_partition": w.N // w.B}
         if extra:
             i = ix.info
-            res["judge"] = {"queries": 1000, "m": 8,
-                            "recall_kmeans": round(float(i.judge_recall_kmeans), 4),
-                            "recall_learned": round(float(i.judge_recall_mlp), 4),
+            res["arbiter"] = {"queries": 1000, "m": 8,
+                            "recall_kmeans": round(float(i.arbiter_recall_kmeans), 4),
+                            "recall_learned": round(float(i.arbiter_recall_mlp), 4),
                             "kept": "learned" if i.part == caps.MLP else "kmeans"}
         sweep, chosen = [], None
         for m in LEARNED4M_M_SWEEP:

@@ -173,12 +173,12 @@ typedef struct {
  *   mlp_bf16     1: train with bf16 weights and activations on the tensor
  *                cores, fp32 master weights (caps_mlp_train_bf16); 0: the
  *                fp32 step.  Assignment and probing use the fp32 weights.
- *   mlp_judge_queries, mlp_judge_m  k-means as the fallback, exact recall
- *                as the judge (0 queries = always keep the learned
+ *   mlp_arbiter_queries, mlp_arbiter_m  k-means as the fallback, exact recall
+ *                as the arbiter (0 queries = always keep the learned
  *                partitioner): that many data points (SplitMix64(seed + 5),
  *                each filtered on its own attributes, each field kept with
  *                probability 1/2, at least one) are searched with k = 10
- *                and m = mlp_judge_m on the k-means index and on the learned
+ *                and m = mlp_arbiter_m on the k-means index and on the learned
  *                one (fp32 scan); the point itself is left out of its
  *                results and of its exact filtered neighbours.  The learned
  *                partitioner is kept unless k-means reaches a higher
@@ -204,7 +204,7 @@ typedef struct {
   const int32_t* mlp_sample_cons;
   const float* mlp_init;
   int32_t mlp_rounds, mlp_balance_r;
-  int32_t mlp_judge_queries, mlp_judge_m;
+  int32_t mlp_arbiter_queries, mlp_arbiter_m;
   int32_t mlp_bf16;
 } caps_build_params;
 
@@ -309,8 +309,8 @@ typedef struct {
   int64_t n_label_bins;  /* N when the learned partitioner was built (the
                             length of CAPS_ARR_LABEL_BINS) */
   int32_t mlp_balance_r; /* R of the balanced assignment, 0 = argmax */
-  float judge_recall_kmeans, judge_recall_mlp; /* recall@10 of the build's
-                            judge (mlp_judge_queries), -1 when not judged */
+  float arbiter_recall_kmeans, arbiter_recall_mlp; /* recall@10 of the build's
+                            arbiter (mlp_arbiter_queries), -1 when not decided */
 } caps_index_info;
 
 int caps_get_info(const caps_index* index, caps_index_info* out);

@@ -60,7 +60,7 @@ class caps_build_params(ct.Structure):
                 ("mlp_label_k", ct.c_int32), ("mlp_sample_idx", ct.c_void_p),
                 ("mlp_sample_cons", ct.c_void_p), ("mlp_init", ct.c_void_p),
                 ("mlp_rounds", ct.c_int32), ("mlp_balance_r", ct.c_int32),
-                ("mlp_judge_queries", ct.c_int32), ("mlp_judge_m", ct.c_int32),
+                ("mlp_arbiter_queries", ct.c_int32), ("mlp_arbiter_m", ct.c_int32),
                 ("mlp_bf16", ct.c_int32)]
 
 
@@ -76,7 +76,7 @@ class caps_index_info(ct.Structure):
                 ("attr_words", ct.c_int32), ("device_bytes", ct.c_int64), ("part", ct.c_int32),
                 ("mlp_hidden", ct.c_int32), ("n_labels", ct.c_int64),
                 ("n_label_bins", ct.c_int64), ("mlp_balance_r", ct.c_int32),
-                ("judge_recall_kmeans", ct.c_float), ("judge_recall_mlp", ct.c_float)]
+                ("arbiter_recall_kmeans", ct.c_float), ("arbiter_recall_mlp", ct.c_float)]
 
 
 class caps_plan_info(ct.Structure):
@@ -321,7 +321,7 @@ class Index:
               seed=0, prec=FP32, rerank_factor=0, part=KMEANS, mlp_hidden=0, mlp_epochs=0,
               mlp_samples=0, mlp_batch=0, mlp_lr=0.0, mlp_label_k=0, mlp_sample_idx=None,
               mlp_sample_cons=None, mlp_init=None, mlp_rounds=0, mlp_balance_r=0,
-              mlp_judge_queries=0, mlp_judge_m=0, mlp_bf16=0, labels=None,
+              mlp_arbiter_queries=0, mlp_arbiter_m=0, mlp_bf16=0, labels=None,
               stream=None) -> "Index":
         """labels = (sp_off, sp_lab, sp_vocab): label-set attributes instead of
         the dense A / vocab."""
@@ -338,7 +338,7 @@ class Index:
                                                                   mlp_samples, mlp_batch)
         p.mlp_lr, p.mlp_label_k = mlp_lr, mlp_label_k
         p.mlp_rounds, p.mlp_balance_r = mlp_rounds, mlp_balance_r
-        p.mlp_judge_queries, p.mlp_judge_m = mlp_judge_queries, mlp_judge_m
+        p.mlp_arbiter_queries, p.mlp_arbiter_m = mlp_arbiter_queries, mlp_arbiter_m
         p.mlp_bf16 = mlp_bf16
         if mlp_sample_idx is not None:
             mlp_sample_idx = _np_or_keep(mlp_sample_idx, np.int64)

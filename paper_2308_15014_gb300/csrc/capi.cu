@@ -307,24 +307,24 @@ static int draw_cons(const int32_t* dA, int L, const int64_t* dS, int64_t S, uin
   return CAPS_OK;
 }
 
-// The build's judge between k-means and the learned partitioner: held-out
+// The build's arbiter between k-means and the learned partitioner: held-out
 // data points as queries, filtered on their own attributes, recall@10 of the
 // m-probe search against their exact filtered neighbours (themselves left
 // out).
 namespace {
-constexpr int kJudgeK = 10;
-struct Judge {
+constexpr int kArbiterK = 10;
+struct Arbiter {
   int64_t J = 0;
   std::vector<int64_t> qid;    // query point ids
   const float* Q = nullptr;    // [J*d]
   const int32_t* cons = nullptr;
-  std::vector<int64_t> exact;  // [J*(kJudgeK+1)]
+  std::vector<int64_t> exact;  // [J*(kArbiterK+1)]
 };
 }  // namespace
 
-static int judge_prepare(const caps_build_params* p, const float* dX, const int32_t* dA, int64_t N,
-                         int d, int L, Scratch& scr, cudaStream_t s, Judge* jg) {
-  jg->J = std::min<int64_t>(p->mlp_judge_queries, N);
+static int arbiter_prepare(const caps_build_params* p, const float* dX, const int32_t* dA, int64_t N,
+                         int d, int L, Scratch& scr, cudaStream_t s, Arbiter* jg) {
+  jg->J = std::min<int64_t>(p->mlp_arbiter_queries, N);
   jg->qid = floyd_sample(N, jg->J, p->seed + 5);
   int64_t* dq = nullptr;
   if (int rc = scr.get(&dq, (size_t)jg->J)) return rc;
@@ -339,10 +339,10 @@ static int judge_prepare(const caps_build_params* p, const float* dX, const int3
   return CAPS_OK;
 }
 
-// ids of the judge queries' k+1 best at m probes (fp32 scan)
-static int judge_search(caps_index* ix, const Judge& jg, int m, cudaStream_t s,
+// ids of the arbiter queries' k+1 best at m probes (fp32 scan)
+static int arbiter_search(caps_index* ix, const Arbiter& jg, int m, cudaStream_t s,
                         std::vector<int64_t>* out) {
-  const int kq = kJudgeK + 1;
+  const int kq = kArbiterK + 1;
   Scratch scr(s);
   int64_t* ids = nullptr;
   float* dist = nullptr;
@@ -368,14 +368,14 @@ static int judge_search(caps_index* ix, const Judge& jg, int m, cudaStream_t s,
 
 // mean over the queries with a neighbour of |found ∩ exact| / |exact|, both
 // the first 10 valid ids other than the query point itself
-static float judge_recall(const Judge& jg, const std::vector<int64_t>& got) {
-  const int kq = kJudgeK + 1;
+static float arbiter_recall(const Arbiter& jg, const std::vector<int64_t>& got) {
+  const int kq = kArbiterK + 1;
   double sum = 0.0;
   int64_t cnt = 0;
   for (int64_t j = 0; j < jg.J; j++) {
     auto first = [&](const std::vector<int64_t>& v, std::vector<int64_t>* o) {
       o->clear();
-      for (int t = 0; t < kq && (int)o->size() < kJudgeK; t++) {
+      for (int t = 0; t < kq && (int)o->size() < kArbiterK; t++) {
         const int64_t i = v[j * kq + t];
         if (i >= 0 && i != jg.qid[j]) o->push_back(i);
       }
@@ -584,9 +584,9 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
     if (p->mlp_balance_r < 0 || p->mlp_balance_r > 64 || p->mlp_balance_r > p->B ||
         (p->mlp_balance_r > 0 && p->B > 25600))
       return fail(CAPS_EINVAL, "mlp_balance_r must be in [0, min(64, B)] (B <= 25600 to balance)");
-    if (p->mlp_judge_queries < 0 ||
-        (p->mlp_judge_queries > 0 && (p->mlp_judge_m < 1 || p->mlp_judge_m > p->B)))
-      return fail(CAPS_EINVAL, "mlp_judge_queries >= 0, and mlp_judge_m in [1, B] when judging");
+    if (p->mlp_arbiter_queries < 0 ||
+        (p->mlp_arbiter_queries > 0 && (p->mlp_arbiter_m < 1 || p->mlp_arbiter_m > p->B)))
+      return fail(CAPS_EINVAL, "mlp_arbiter_queries >= 0, and mlp_arbiter_m in [1, B] when arbitrating");
   }
   if (p->prec != CAPS_FP32 && p->prec != CAPS_BF16 && p->prec != CAPS_FP8E4M3 &&
       p->prec != CAPS_FP32_SPLIT)
@@ -747,25 +747,25 @@ static int build_impl(const caps_build_params* p, const float* X, int64_t N, int
   };
   if (int rc = finish()) return rc;
   if (p->part == CAPS_PART_MLP) {
-    // k-means as the fallback, exact recall as the judge
-    Judge jg;
+    // k-means as the fallback, exact recall as the arbiter
+    Arbiter jg;
     std::vector<int64_t> got;
     int32_t* kbins = nullptr;
-    const bool judge = p->mlp_judge_queries > 0;
-    if (judge) {
-      if (int rc = judge_prepare(p, dX, dA, N, d, L, scr, s, &jg)) return rc;
-      if (int rc = judge_search(ix, jg, B, s, &jg.exact)) return rc;
-      if (int rc = judge_search(ix, jg, p->mlp_judge_m, s, &got)) return rc;
-      ix->judge_recall[0] = judge_recall(jg, got);
+    const bool arbiter = p->mlp_arbiter_queries > 0;
+    if (arbiter) {
+      if (int rc = arbiter_prepare(p, dX, dA, N, d, L, scr, s, &jg)) return rc;
+      if (int rc = arbiter_search(ix, jg, B, s, &jg.exact)) return rc;
+      if (int rc = arbiter_search(ix, jg, p->mlp_arbiter_m, s, &got)) return rc;
+      ix->arbiter_recall[0] = arbiter_recall(jg, got);
       if (int rc = scr.get(&kbins, (size_t)N)) return rc;
       CAPS_CUDA(cudaMemcpyAsync(kbins, ix->bin, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
     }
     if (int rc = build_mlp(p, dX, dA, N, d, meta, s, ix)) return rc;
     if (int rc = finish()) return rc;
-    if (judge) {
-      if (int rc = judge_search(ix, jg, p->mlp_judge_m, s, &got)) return rc;
-      ix->judge_recall[1] = judge_recall(jg, got);
-      if (ix->judge_recall[0] > ix->judge_recall[1]) {
+    if (arbiter) {
+      if (int rc = arbiter_search(ix, jg, p->mlp_arbiter_m, s, &got)) return rc;
+      ix->arbiter_recall[1] = arbiter_recall(jg, got);
+      if (ix->arbiter_recall[0] > ix->arbiter_recall[1]) {
         CAPS_CUDA(cudaMemcpyAsync(ix->bin, kbins, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
         ix->part = CAPS_PART_KMEANS;
         if (int rc = finish()) return rc;
@@ -847,8 +847,8 @@ extern "C" int caps_get_info(const caps_index* ix, caps_index_info* out) {
   out->n_labels = ix->n_labels;
   out->n_label_bins = ix->n_label_bins;
   out->mlp_balance_r = ix->balance_r;
-  out->judge_recall_kmeans = ix->judge_recall[0];
-  out->judge_recall_mlp = ix->judge_recall[1];
+  out->arbiter_recall_kmeans = ix->arbiter_recall[0];
+  out->arbiter_recall_mlp = ix->arbiter_recall[1];
   return CAPS_OK;
 }
 

@@ -507,7 +507,7 @@ struct caps_index {
   int32_t* label_bins = nullptr;  // [n_label_bins] the partitions the last labels were made from
   int64_t n_label_bins = 0;       // N at build time
   int balance_r = 0;              // > 0: BLISS's balanced assignment over R logits
-  float judge_recall[2] = {-1.f, -1.f};  // build judge: k-means, learned
+  float arbiter_recall[2] = {-1.f, -1.f};  // build arbiter: k-means, learned
   void* Xb = nullptr;
   float* xn = nullptr;
   float* xs = nullptr;  // e4m3 form: per-row scales [N+4]

@@ -251,8 +251,8 @@ def test_insert_into_balanced_index_continues_the_loads():
     gi.close()
 
 
-def test_judge_keeps_the_trained_network_and_falls_back_to_kmeans():
-    # k-means as the fallback, exact recall as the judge
+def test_arbiter_keeps_the_trained_network_and_falls_back_to_kmeans():
+    # k-means as the fallback, exact recall as the arbiter
     w = _wl(21, N=20_000, d=32, B=24, nq=100, metric=1, normalize=True, integer=False)
     X = torch.from_numpy(w.X).cuda()
     A = torch.from_numpy(w.A).cuda()
@@ -261,17 +261,17 @@ def test_judge_keeps_the_trained_network_and_falls_back_to_kmeans():
     # a trained network beats k-means at m = 1 (the gain test above): kept
     ml = caps.Index.build(X, A, w.vocab, w.B, part=caps.MLP, mlp_hidden=64, mlp_epochs=20,
                           mlp_samples=4000, mlp_batch=500, mlp_lr=3e-3, seed=7,
-                          mlp_judge_queries=500, mlp_judge_m=1, **base)
+                          mlp_arbiter_queries=500, mlp_arbiter_m=1, **base)
     i = ml.info
-    print(f"\njudge recall@10 at m=1: k-means {i.judge_recall_kmeans:.3f}, "
-          f"learned {i.judge_recall_mlp:.3f}")
+    print(f"\narbiter recall@10 at m=1: k-means {i.arbiter_recall_kmeans:.3f}, "
+          f"learned {i.arbiter_recall_mlp:.3f}")
     assert i.part == caps.MLP
-    assert i.judge_recall_mlp >= i.judge_recall_kmeans >= 0.0
+    assert i.arbiter_recall_mlp >= i.arbiter_recall_kmeans >= 0.0
     # every partition probed: both exact, a tie keeps the learned one
     ex = caps.Index.build(X, A, w.vocab, w.B, part=caps.MLP, mlp_hidden=64, mlp_epochs=2,
-                          mlp_samples=2000, mlp_batch=500, seed=7, mlp_judge_queries=200,
-                          mlp_judge_m=w.B, **base)
-    assert ex.info.judge_recall_kmeans == 1.0 and ex.info.judge_recall_mlp == 1.0
+                          mlp_samples=2000, mlp_batch=500, seed=7, mlp_arbiter_queries=200,
+                          mlp_arbiter_m=w.B, **base)
+    assert ex.info.arbiter_recall_kmeans == 1.0 and ex.info.arbiter_recall_mlp == 1.0
     assert ex.info.part == caps.MLP
     # an untrained random network (on the workload's own queries the oracle
     # gives it recall@10 0.77 at m = 2 against k-means' 0.85): k-means wins
@@ -281,10 +281,10 @@ def test_judge_keeps_the_trained_network_and_falls_back_to_kmeans():
     bad = rand_net(rng, w.d, H, w.B, scale=1.0)
     W = caps.mlp_flat(bad.W1, bad.b1, bad.W2, bad.b2)
     fb = caps.Index.build(X, A, w.vocab, w.B, part=caps.MLP, mlp_hidden=H, mlp_epochs=0,
-                          mlp_init=W, mlp_samples=500, mlp_judge_queries=300, mlp_judge_m=2,
+                          mlp_init=W, mlp_samples=500, mlp_arbiter_queries=300, mlp_arbiter_m=2,
                           **base)
     assert fb.info.part == caps.KMEANS
-    assert fb.info.judge_recall_kmeans > fb.info.judge_recall_mlp
+    assert fb.info.arbiter_recall_kmeans > fb.info.arbiter_recall_mlp
     for which in (caps.ARR_BIN, caps.ARR_TAGS, caps.ARR_KEY, caps.ARR_PERM, caps.ARR_OFFSETS,
                   caps.ARR_CENTROIDS):
         np.testing.assert_array_equal(fb.export(which), km.export(which))
