@@ -707,11 +707,22 @@ def oracle_baseline(caps, ix, w, m, budget_s=15.0):
         spent += time.perf_counter() - t0
         done += len(sub)
         n *= 2
+    # one core as well (the paper times its CPU program single-threaded)
+    one = order[:500]
+    O.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle_query(w, at, oi, net, one, m)
+        one_s = time.perf_counter() - t0
+    finally:
+        O.set_threads(cores)
     part = "learned partitioner's logits" if net is not None else "k-means centroids"
     return {"value": done / spent, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{done} of {w.nq} queries at m={m}, k={w.k}; the oracle's index laid out "
                       f"by the oracle from the measured GPU index's partitions (probe: the "
-                      f"{part}; {build_s:.1f} s, untimed)"}
+                      f"{part}; {build_s:.1f} s, untimed)",
+            "single_core": {"value": len(one) / one_s, "unit": UNIT, "cores": 1,
+                            "sample": f"{len(one)} of the same queries"}}
 
 
 # the probe count at which the headline (learned + bf16) reaches recall@10
