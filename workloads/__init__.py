@@ -13,6 +13,7 @@ from .synth import (  # noqa: F401
     config_small,
     config_sift1m_like,
     config_sift1m_fields,
+    config_sift1m_wide,
     config_learned4m,
     with_constraints,
     config_sparse2m,

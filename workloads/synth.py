@@ -309,6 +309,65 @@ def config_sift1m_fields(L: int, seed: int = 1002, **over) -> Workload:
     return make_dense_workload(**kw)
 
 
+def config_sift1m_wide(L: int = 100, nq: int = 1000, p_field: float = 0.03,
+                       seed: int = 1002, base: Optional[Workload] = None) -> Workload:
+    """The 1M x 128 vectors and first nq queries of config_sift1m_like with L
+    attribute fields (vocab 20/50/100 repeating, Zipf s=1.0) held as label
+    sets: field f with value v is label f * 100 + v (every point carries L
+    labels).  Each query keeps each field of a random data point with
+    probability p_field (at least one), as in the paper's appendix (0.03 for
+    L = 100), rejection-sampled into selectivity [0.1%, 30%]; a field
+    constraint is then the requirement of that label.  base: the
+    config_sift1m_like workload of the same seed, whose vectors are reused
+    (they are the same draws); attributes and constraints come from seeds
+    seed + 3000 and seed + 4000 either way."""
+    N, d, ncomp = 1_000_000, 128, 1000
+    if base is not None:
+        assert base.N == N and base.d == d and base.nq >= nq
+        X, Q = base.X, base.Q[:nq]
+    else:
+        rng = np.random.default_rng(seed)
+        centers = rng.uniform(0.0, 128.0, size=(ncomp, d))
+        X = np.rint(np.clip(_mixture(rng, N, centers, 16.0), 0.0, 255.0))
+        rq = np.random.default_rng(seed + 1000)  # (the 10,000 queries of the base workload)
+        Q = np.rint(np.clip(_mixture(rq, 10_000, centers, 16.0), 0.0, 255.0))[:nq]
+    vocab = [(20, 50, 100)[f % 3] for f in range(L)]
+    A = _dense_attrs(np.random.default_rng(seed + 3000), N, vocab, 1.0)
+    lab = (np.arange(L, dtype=np.int64)[None, :] * 100 + A).astype(np.int32)
+    sp_off = np.arange(N + 1, dtype=np.int64) * L
+    AT = np.ascontiguousarray(A.T.astype(np.uint8))  # field-major, for the selectivity counts
+    rq = np.random.default_rng(seed + 4000)
+    # counts per (field, value) pair, and the points of each, for selectivity
+    rows, sel = [], np.empty(nq)
+    for qi in range(nq):
+        for _attempt in range(10000):
+            src = int(rq.integers(0, N))
+            keep = np.nonzero(rq.random(L) < p_field)[0]
+            if len(keep) == 0:
+                keep = np.array([int(rq.integers(0, L))])
+            ok = np.ones(N, dtype=bool)
+            for f in keep:
+                ok &= AT[f] == AT[f, src]
+            s = float(ok.sum()) / N
+            if 0.001 <= s <= 0.30:
+                break
+        rows.append(np.sort(lab[src, keep]).astype(np.int32))
+        sel[qi] = s
+    q_off = np.zeros(nq + 1, dtype=np.int64)
+    q_off[1:] = np.cumsum([len(r) for r in rows])
+    ri = np.random.default_rng(seed + 2000)
+    init_idx = ri.permutation(N)[:1024].astype(np.int64)
+    return Workload(
+        name=f"sift1m_like_1M_d128_L{L}_labels", X=np.ascontiguousarray(X, dtype=np.float32),
+        Q=np.ascontiguousarray(Q, dtype=np.float32), metric=0, B=1024, h=15, iters=20, m=32, k=10,
+        init_idx=init_idx, sp_off=sp_off, sp_lab=np.ascontiguousarray(lab.ravel()),
+        sp_vocab=100 * L, q_off=q_off, q_lab=np.concatenate(rows).astype(np.int32),
+        selectivity=sel,
+        recipe=f"sift1m_like vectors; {L} fields vocab 20/50/100 Zipf(1.0) as labels f*100+v; "
+               f"queries keep each field of a random point with p={p_field}, selectivity "
+               "[0.1%,30%]")
+
+
 def config_learned4m(seed: int = 1004, **over) -> Workload:
     """4,000,000 x 96 unit-norm vectors (4000 components, centers N(0, I),
     sigma 0.3 before normalisation), inner product, 5 fields vocab
